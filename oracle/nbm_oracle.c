@@ -1,0 +1,946 @@
+/*
+ * nbm_oracle.c -- plain FP64 CPU oracle of the NBM collocation-residual step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see nbm_oracle.h).  Written for readability
+ * against the paper (arXiv 2210.14907, Sec. 2-3, Fig. 2), not for speed:
+ * every network evaluation at every stencil vertex is a separate plain
+ * forward pass, and the gradient is plain reverse mode through each one.
+ * OpenMP parallelises over collocation points only.
+ */
+#include "nbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NBO_PI 3.14159265358979323846
+
+/* ======================================================================
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC 2011): ten rounds of two 32x32->64 multiplies with
+ * a Weyl-sequence key schedule.
+ * ==================================================================== */
+void nbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * c0;
+    uint64_t p1 = (uint64_t)M1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* ======================================================================
+ * Geometry (Sec. 3: "a separate coarse mesh encapsulates a level-set
+ * function"; here the level set is analytic).
+ * ==================================================================== */
+double nbo_phi(const nbo_problem* pr, const double x[3]) {
+  double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  switch (pr->geometry) {
+    case NBO_GEOM_SPHERE:
+      return r - pr->r0;
+    case NBO_GEOM_FLOWER: {
+      if (r == 0.0) return -pr->r0;
+      /* theta: polar angle from +z; psi: azimuth in the xy-plane. */
+      double ct = x[2] / r;
+      if (ct > 1.0) ct = 1.0;
+      if (ct < -1.0) ct = -1.0;
+      double theta = acos(ct);
+      double psi = atan2(x[1], x[0]);
+      return r - pr->r0 - pr->amp * sin(pr->lobes_theta * theta) * cos(pr->lobes_psi * psi);
+    }
+    case NBO_GEOM_ALL_PLUS:
+      return 1.0;
+    case NBO_GEOM_ALL_MINUS:
+      return -1.0;
+  }
+  return 1.0;
+}
+
+void nbo_grad_phi(const nbo_problem* pr, const double x[3], double g[3]) {
+  double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  g[0] = g[1] = g[2] = 0.0;
+  if (pr->geometry == NBO_GEOM_ALL_PLUS || pr->geometry == NBO_GEOM_ALL_MINUS) return;
+  if (r == 0.0) return;
+  for (int i = 0; i < 3; ++i) g[i] = x[i] / r; /* grad r */
+  if (pr->geometry != NBO_GEOM_FLOWER) return;
+  double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+  if (rho == 0.0) return; /* the flower has a conical point on the z axis */
+  double ct = x[2] / r;
+  if (ct > 1.0) ct = 1.0;
+  if (ct < -1.0) ct = -1.0;
+  double theta = acos(ct), psi = atan2(x[1], x[0]);
+  double lt = pr->lobes_theta, lp = pr->lobes_psi, a = pr->amp;
+  /* d(theta)/dx = z x / (r^2 rho), d/dy = z y / (r^2 rho), d/dz = -rho / r^2 */
+  double dth[3] = {x[2] * x[0] / (r * r * rho), x[2] * x[1] / (r * r * rho), -rho / (r * r)};
+  /* d(psi)/dx = -y / rho^2, d/dy = x / rho^2 */
+  double dps[3] = {-x[1] / (rho * rho), x[0] / (rho * rho), 0.0};
+  double dphi_dth = -a * lt * cos(lt * theta) * cos(lp * psi);
+  double dphi_dps = a * lp * sin(lt * theta) * sin(lp * psi);
+  for (int i = 0; i < 3; ++i) g[i] += dphi_dth * dth[i] + dphi_dps * dps[i];
+}
+
+int nbo_phase(const nbo_problem* pr, const double x[3]) {
+  /* reading: phi = 0 belongs to Omega- (interior) */
+  return nbo_phi(pr, x) <= 0.0 ? 0 : 1;
+}
+
+/* Manufactured pair of the benchmark configurations:
+ *   u- = exp(x) cos(y) sin(z)   (so Laplacian u- = -u-)
+ *   u+ = x^2 + y^2 + z^2        (Laplacian u+ = 6)                      */
+double nbo_exact_u(const nbo_problem* pr, int s, const double x[3]) {
+  (void)pr;
+  if (s == 0) return exp(x[0]) * cos(x[1]) * sin(x[2]);
+  return x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+}
+
+void nbo_exact_grad_u(const nbo_problem* pr, int s, const double x[3], double g[3]) {
+  (void)pr;
+  if (s == 0) {
+    double e = exp(x[0]);
+    g[0] = e * cos(x[1]) * sin(x[2]);
+    g[1] = -e * sin(x[1]) * sin(x[2]);
+    g[2] = e * cos(x[1]) * cos(x[2]);
+  } else {
+    g[0] = 2.0 * x[0];
+    g[1] = 2.0 * x[1];
+    g[2] = 2.0 * x[2];
+  }
+}
+
+/* f^s = k^s u^s - mu^s Laplacian(u^s)  (Sec. 2, constant mu^s and k^s). */
+double nbo_rhs_f(const nbo_problem* pr, int s, const double x[3]) {
+  double u = nbo_exact_u(pr, s, x);
+  if (s == 0) return pr->k_minus * u - pr->mu_minus * (-u);
+  return pr->k_plus * u - pr->mu_plus * 6.0;
+}
+
+/* [u] = u+ - u- (reading: jumps are plus side minus minus side). */
+double nbo_alpha(const nbo_problem* pr, const double x[3]) {
+  return nbo_exact_u(pr, 1, x) - nbo_exact_u(pr, 0, x);
+}
+
+/* [mu d_n u] = mu+ grad u+ . n - mu- grad u- . n, n = grad phi / |grad phi|
+ * pointing from Omega- into Omega+. */
+double nbo_beta(const nbo_problem* pr, const double x[3]) {
+  double gp[3], gm[3], gphi[3];
+  nbo_exact_grad_u(pr, 1, x, gp);
+  nbo_exact_grad_u(pr, 0, x, gm);
+  nbo_grad_phi(pr, x, gphi);
+  double nn = sqrt(gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2]);
+  if (nn == 0.0) return 0.0;
+  double b = 0.0;
+  for (int i = 0; i < 3; ++i) b += (pr->mu_plus * gp[i] - pr->mu_minus * gm[i]) * gphi[i] / nn;
+  return b;
+}
+
+/* Dirichlet data on the cube boundary: the outer solution (Sec. 2). */
+double nbo_dirichlet_g(const nbo_problem* pr, const double x[3]) {
+  int s = (pr->geometry == NBO_GEOM_ALL_MINUS) ? 0 : 1;
+  return nbo_exact_u(pr, s, x);
+}
+
+/* ======================================================================
+ * Implicit compute cell C_p = p + [-h/2, h/2]^3 (Fig. 2: "placing implicit
+ * cells ... calculating interface-cell crossings").  Reading: phi is taken
+ * linear on each tetrahedron of the Freudenthal-Kuhn six-tetrahedron split
+ * of the cube, so every fraction has a closed form.
+ * ==================================================================== */
+
+/* Fraction of a triangle where the linear interpolant of (f0,f1,f2) is <= 0. */
+double nbo_tri_fraction(double f0, double f1, double f2) {
+  double f[3] = {f0, f1, f2};
+  int neg[3], nn = 0;
+  for (int i = 0; i < 3; ++i) {
+    neg[i] = f[i] <= 0.0;
+    nn += neg[i];
+  }
+  if (nn == 0) return 0.0;
+  if (nn == 3) return 1.0;
+  if (nn == 1) {
+    int a = neg[0] ? 0 : (neg[1] ? 1 : 2);
+    int b = (a + 1) % 3, c = (a + 2) % 3;
+    /* corner triangle cut at t_b = fa/(fa-fb), t_c = fa/(fa-fc) */
+    return (f[a] / (f[a] - f[b])) * (f[a] / (f[a] - f[c]));
+  }
+  int c = !neg[0] ? 0 : (!neg[1] ? 1 : 2);
+  int a = (c + 1) % 3, b = (c + 2) % 3;
+  return 1.0 - (f[c] / (f[c] - f[a])) * (f[c] / (f[c] - f[b]));
+}
+
+/* Fraction of a tetrahedron where the linear interpolant is <= 0. */
+double nbo_tet_fraction(double f0, double f1, double f2, double f3) {
+  double f[4] = {f0, f1, f2, f3};
+  int neg[4], nn = 0;
+  for (int i = 0; i < 4; ++i) {
+    neg[i] = f[i] <= 0.0;
+    nn += neg[i];
+  }
+  if (nn == 0) return 0.0;
+  if (nn == 4) return 1.0;
+  if (nn == 1 || nn == 3) {
+    int lone = -1;
+    for (int i = 0; i < 4; ++i)
+      if (neg[i] == (nn == 1)) lone = i;
+    double prod = 1.0;
+    for (int i = 0; i < 4; ++i)
+      if (i != lone) prod *= f[lone] / (f[lone] - f[i]);
+    return nn == 1 ? prod : 1.0 - prod;
+  }
+  /* two below, two above: closed form of the divided difference of
+   * (-s)_+^3 over the four values, written without cancellation.        */
+  double A = 0, B = 0, C = 0, Dd = 0;
+  int gotn = 0, gotp = 0;
+  for (int i = 0; i < 4; ++i) {
+    if (neg[i]) {
+      if (gotn++ == 0) A = -f[i]; else B = -f[i];
+    } else {
+      if (gotp++ == 0) C = f[i]; else Dd = f[i];
+    }
+  }
+  double num = C * Dd * (A * A + A * B + B * B) + (C + Dd) * A * B * (A + B) + A * A * B * B;
+  double den = (C + A) * (Dd + A) * (C + B) * (Dd + B);
+  return num / den;
+}
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double a[3]) { return sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+/* crossing point of the zero level on edge u(neg) -> v(pos) */
+static void edge_cross(const double xu[3], double fu, const double xv[3], double fv, double out[3]) {
+  double t = fu / (fu - fv);
+  for (int i = 0; i < 3; ++i) out[i] = xu[i] + t * (xv[i] - xu[i]);
+}
+
+static void tri_area_centroid(const double a[3], const double b[3], const double c[3],
+                              double* area, double cen[3]) {
+  double e1[3], e2[3], cr[3];
+  for (int i = 0; i < 3; ++i) {
+    e1[i] = b[i] - a[i];
+    e2[i] = c[i] - a[i];
+  }
+  cross3(e1, e2, cr);
+  *area = 0.5 * norm3(cr);
+  for (int i = 0; i < 3; ++i) cen[i] = (a[i] + b[i] + c[i]) / 3.0;
+}
+
+/* interface polygon of one tetrahedron: area and area-weighted centroid sum */
+static void tet_interface(const double X[4][3], const double f[4], double* area, double wc[3]) {
+  int neg[4], nn = 0;
+  for (int i = 0; i < 4; ++i) {
+    neg[i] = f[i] <= 0.0;
+    nn += neg[i];
+  }
+  *area = 0.0;
+  wc[0] = wc[1] = wc[2] = 0.0;
+  if (nn == 0 || nn == 4) return;
+  if (nn == 1 || nn == 3) {
+    int lone = -1;
+    for (int i = 0; i < 4; ++i)
+      if (neg[i] == (nn == 1)) lone = i;
+    double P[3][3];
+    int k = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (i == lone) continue;
+      if (neg[lone]) edge_cross(X[lone], f[lone], X[i], f[i], P[k]);
+      else edge_cross(X[i], f[i], X[lone], f[lone], P[k]);
+      ++k;
+    }
+    double cen[3];
+    tri_area_centroid(P[0], P[1], P[2], area, cen);
+    for (int i = 0; i < 3; ++i) wc[i] = *area * cen[i];
+    return;
+  }
+  int a = -1, b = -1, c = -1, d = -1;
+  for (int i = 0; i < 4; ++i) {
+    if (neg[i]) { if (a < 0) a = i; else b = i; }
+    else { if (c < 0) c = i; else d = i; }
+  }
+  /* cyclic order of the quadrilateral: ac, ad, bd, bc */
+  double Q[4][3];
+  edge_cross(X[a], f[a], X[c], f[c], Q[0]);
+  edge_cross(X[a], f[a], X[d], f[d], Q[1]);
+  edge_cross(X[b], f[b], X[d], f[d], Q[2]);
+  edge_cross(X[b], f[b], X[c], f[c], Q[3]);
+  double a1, a2, c1[3], c2[3];
+  tri_area_centroid(Q[0], Q[1], Q[2], &a1, c1);
+  tri_area_centroid(Q[0], Q[2], Q[3], &a2, c2);
+  *area = a1 + a2;
+  for (int i = 0; i < 3; ++i) wc[i] = a1 * c1[i] + a2 * c2[i];
+}
+
+void nbo_cell_geometry(const nbo_problem* pr, const double p[3], double h, nbo_cell* out) {
+  memset(out, 0, sizeof(*out));
+  /* corner c has offsets ((c&1), (c>>1)&1, (c>>2)&1) - 1/2, times h */
+  double X[8][3], F[8];
+  int nneg = 0;
+  for (int c = 0; c < 8; ++c) {
+    for (int i = 0; i < 3; ++i) X[c][i] = p[i] + h * ((double)((c >> i) & 1) - 0.5);
+    F[c] = nbo_phi(pr, X[c]);
+    nneg += F[c] <= 0.0;
+  }
+  if (nneg == 0 || nneg == 8) {
+    int s = nneg == 0 ? 1 : 0;
+    out->cut = 0;
+    out->phase = s;
+    out->V[s] = 1.0;
+    for (int f = 0; f < 6; ++f) out->A[s][f] = 1.0;
+    out->S = 0.0;
+    for (int i = 0; i < 3; ++i) out->centroid[i] = out->xg[i] = p[i];
+    return;
+  }
+  out->cut = 1;
+  out->phase = nbo_phase(pr, p);
+  /* six tetrahedra 0 -> e_a -> e_a+e_b -> 7 for every permutation (a,b,c) */
+  static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  double vneg = 0.0, area = 0.0, wc[3] = {0, 0, 0};
+  for (int t = 0; t < 6; ++t) {
+    int v1 = 1 << perms[t][0];
+    int v2 = v1 | (1 << perms[t][1]);
+    int idx[4] = {0, v1, v2, 7};
+    double Xt[4][3], ft[4];
+    for (int k = 0; k < 4; ++k) {
+      for (int i = 0; i < 3; ++i) Xt[k][i] = X[idx[k]][i];
+      ft[k] = F[idx[k]];
+    }
+    vneg += nbo_tet_fraction(ft[0], ft[1], ft[2], ft[3]) / 6.0;
+    double ta, tw[3];
+    tet_interface(Xt, ft, &ta, tw);
+    area += ta;
+    for (int i = 0; i < 3; ++i) wc[i] += tw[i];
+  }
+  out->V[0] = vneg;
+  out->V[1] = 1.0 - vneg;
+  /* faces: axis i, side sd; split along the diagonal from the face's
+   * lowest to its highest corner (the split the tetrahedra induce). */
+  for (int i = 0; i < 3; ++i) {
+    int j = (i + 1) % 3, k = (i + 2) % 3;
+    for (int sd = 0; sd < 2; ++sd) {
+      int base = sd << i;
+      int c00 = base, c10 = base | (1 << j), c01 = base | (1 << k), c11 = base | (1 << j) | (1 << k);
+      double fr = 0.5 * (nbo_tri_fraction(F[c00], F[c10], F[c11]) +
+                         nbo_tri_fraction(F[c00], F[c01], F[c11]));
+      out->A[0][2 * i + sd] = fr;
+      out->A[1][2 * i + sd] = 1.0 - fr;
+    }
+  }
+  out->S = area / (h * h);
+  if (area > 0.0) {
+    double x[3];
+    for (int i = 0; i < 3; ++i) x[i] = out->centroid[i] = wc[i] / area;
+    /* project onto phi = 0: at most three Newton steps along grad phi */
+    for (int it = 0; it < 3; ++it) {
+      double g[3];
+      double ph = nbo_phi(pr, x);
+      nbo_grad_phi(pr, x, g);
+      double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+      if (gg <= 1e-300) break;
+      for (int i = 0; i < 3; ++i) x[i] -= ph * g[i] / gg;
+    }
+    for (int i = 0; i < 3; ++i) out->xg[i] = x[i];
+  } else {
+    for (int i = 0; i < 3; ++i) out->centroid[i] = out->xg[i] = p[i];
+  }
+}
+
+/* ======================================================================
+ * Networks (Sec. 3: "two neural networks are used to represent the
+ * solution on each side"): a_0 = x, z_l = W_l a_{l-1} + b_l,
+ * a_l = tanh(z_l) for the hidden layers, u = w . a_L + b.
+ * Layout per net: W1[H][3], b1[H], then (W_l[H][H], b_l[H]) for
+ * l = 2..n_hidden, then w[H], b.  Net minus first, then net plus.
+ * ==================================================================== */
+int64_t nbo_params_per_net(const nbo_problem* pr) {
+  int64_t H = pr->width;
+  return 4 * H + (int64_t)(pr->n_hidden - 1) * (H * H + H) + H + 1;
+}
+
+/* forward; acts (if given) receives the n_hidden hidden activations */
+static double mlp_forward(const nbo_problem* pr, const double* th, const double x[3], double* acts) {
+  int H = pr->width, L = pr->n_hidden;
+  double* a = acts;
+  double buf[2][512];
+  double* cur = buf[0];
+  const double* W = th;
+  const double* b = th + 3 * H;
+  for (int n = 0; n < H; ++n) {
+    double z = b[n];
+    for (int j = 0; j < 3; ++j) z += W[3 * n + j] * x[j];
+    cur[n] = tanh(z);
+  }
+  if (a) memcpy(a, cur, sizeof(double) * H);
+  const double* q = th + 4 * H;
+  for (int l = 1; l < L; ++l) {
+    double* nxt = buf[l & 1];
+    const double* Wl = q;
+    const double* bl = q + (int64_t)H * H;
+    for (int n = 0; n < H; ++n) {
+      double z = bl[n];
+      for (int k = 0; k < H; ++k) z += Wl[(int64_t)n * H + k] * cur[k];
+      nxt[n] = tanh(z);
+    }
+    cur = nxt;
+    if (a) memcpy(a + (int64_t)l * H, cur, sizeof(double) * H);
+    q += (int64_t)H * H + H;
+  }
+  double u = q[H];
+  for (int n = 0; n < H; ++n) u += q[n] * cur[n];
+  return u;
+}
+
+double nbo_mlp_eval(const nbo_problem* pr, const double* theta_net, const double x[3]) {
+  return mlp_forward(pr, theta_net, x, NULL);
+}
+
+/* reverse mode of one evaluation: grad += c * du/dtheta */
+static void mlp_backward(const nbo_problem* pr, const double* th, const double x[3], double c,
+                         const double* acts, double* grad) {
+  int H = pr->width, L = pr->n_hidden;
+  double g[512], gz[512];
+  /* offsets of each layer */
+  int64_t off_out = 4 * H + (int64_t)(L - 1) * (H * H + H);
+  const double* w = th + off_out;
+  const double* aL = acts + (int64_t)(L - 1) * H;
+  for (int n = 0; n < H; ++n) {
+    grad[off_out + n] += c * aL[n];
+    g[n] = c * w[n];
+  }
+  grad[off_out + H] += c;
+  for (int l = L - 1; l >= 1; --l) {
+    /* layer l+1 in 1-based numbering: input acts[l-1], output acts[l] */
+    int64_t off = 4 * H + (int64_t)(l - 1) * (H * H + H);
+    const double* Wl = th + off;
+    const double* aout = acts + (int64_t)l * H;
+    const double* ain = acts + (int64_t)(l - 1) * H;
+    for (int n = 0; n < H; ++n) gz[n] = g[n] * (1.0 - aout[n] * aout[n]);
+    for (int n = 0; n < H; ++n) {
+      for (int k = 0; k < H; ++k) grad[off + (int64_t)n * H + k] += gz[n] * ain[k];
+      grad[off + (int64_t)H * H + n] += gz[n];
+    }
+    for (int k = 0; k < H; ++k) {
+      double s = 0.0;
+      for (int n = 0; n < H; ++n) s += Wl[(int64_t)n * H + k] * gz[n];
+      g[k] = s;
+    }
+  }
+  const double* a1 = acts;
+  for (int n = 0; n < H; ++n) {
+    double gz1 = g[n] * (1.0 - a1[n] * a1[n]);
+    for (int j = 0; j < 3; ++j) grad[3 * n + j] += gz1 * x[j];
+    grad[3 * H + n] += gz1;
+  }
+}
+
+/* ======================================================================
+ * Collocation points ("randomly sampled points", Sec. 3).  Uniform points
+ * lie on the lattice -1 + k 2^-22, k in [1, 2^23-1], so p +- h is exact for
+ * power-of-two h.  Band points (|phi| < 4h) are placed along rays from the
+ * origin at a uniform offset t in (-4h, 4h) from the interface radius.
+ * Counter of point i at step t: {i, t_lo, t_hi, 0x4E424D31}; key = seed.
+ * ==================================================================== */
+static double quantize_coord(double v) {
+  double k = floor((v + 1.0) * 4194304.0 + 0.5);
+  if (k < 1.0) k = 1.0;
+  if (k > 8388607.0) k = 8388607.0;
+  return -1.0 + k / 4194304.0;
+}
+
+void nbo_sample_points(const nbo_problem* pr, uint64_t seed, int64_t step, int64_t n,
+                       int64_t n_band, double* pts) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int has_iface = pr->geometry == NBO_GEOM_SPHERE || pr->geometry == NBO_GEOM_FLOWER;
+  int64_t n_uniform = n - n_band;
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0x4E424D31u};
+    uint32_t r[4];
+    nbo_philox4x32_10(ctr, key, r);
+    double* x = pts + 3 * i;
+    if (i < n_uniform || !has_iface) {
+      for (int j = 0; j < 3; ++j) {
+        uint64_t k = 1 + (((uint64_t)r[j] * 8388607ull) >> 32);
+        x[j] = -1.0 + (double)k / 4194304.0;
+      }
+    } else {
+      double u[3];
+      for (int j = 0; j < 3; ++j) u[j] = ((double)(r[j] >> 8) + 0.5) / 16777216.0;
+      double cth = 1.0 - 2.0 * u[0];
+      double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+      double psi = 2.0 * NBO_PI * u[1];
+      double t = (2.0 * u[2] - 1.0) * 4.0 * pr->h;
+      double R = pr->r0;
+      if (pr->geometry == NBO_GEOM_FLOWER)
+        R += pr->amp * sin(pr->lobes_theta * acos(cth)) * cos(pr->lobes_psi * psi);
+      double dir[3] = {sth * cos(psi), sth * sin(psi), cth};
+      for (int j = 0; j < 3; ++j) x[j] = quantize_coord((R + t) * dir[j]);
+    }
+  }
+}
+
+/* ======================================================================
+ * Point residual (Sec. 3 and Fig. 2; the equation itself is missing from
+ * the text, so this is the reading).  Integrating the PDE over both parts
+ * of the cell and using the flux-jump condition on the interface gives,
+ * after division by h,
+ *   B = h^2 sum_s V^s (k^s U^s(p) - f^s(p))
+ *       - sum_faces sum_s A^s_f mu^s (U^s(p + sigma h e_i) - U^s(p))
+ *       + h S beta(x_G)
+ * with U^s(q) = g(q) whenever q leaves the cube (Dirichlet data).
+ * Jacobi preconditioner M = diag(A):  D = sum_f sum_s A^s_f mu^s + h^2 sum_s V^s k^s.
+ * Value jump (cut cells with S > 0):  J = U+(x_G) - U-(x_G) - alpha(x_G).
+ * r_p^2 = (B/D)^2 + lambda J^2.
+ * ==================================================================== */
+static double mu_of(const nbo_problem* pr, int s) { return s == 0 ? pr->mu_minus : pr->mu_plus; }
+static double k_of(const nbo_problem* pr, int s) { return s == 0 ? pr->k_minus : pr->k_plus; }
+
+static int outside_box(const double q[3]) {
+  return fabs(q[0]) >= 1.0 || fabs(q[1]) >= 1.0 || fabs(q[2]) >= 1.0;
+}
+
+/* One point: all evaluations, the rows, and (if grad != NULL) the gradient
+ * of (scale * r^2) accumulated into grad.  mode 1 substitutes exact u^s. */
+static void point_core(const nbo_problem* pr, const double* theta, const double p[3], int mode,
+                       double scale, double* grad, nbo_point_terms* out) {
+  const double h = pr->h;
+  int64_t Pn = nbo_params_per_net(pr);
+  nbo_cell cell;
+  nbo_cell_geometry(pr, p, h, &cell);
+  int L = pr->n_hidden, H = pr->width;
+  /* U[s][0] at p, U[s][1+f] at the neighbour across face f, U[s][7] at x_G */
+  double U[2][8];
+  int inside[6];
+  double Q[8][3];
+  for (int i = 0; i < 3; ++i) Q[0][i] = p[i];
+  for (int f = 0; f < 6; ++f) {
+    int ax = f / 2;
+    double sg = (f & 1) ? 1.0 : -1.0;
+    for (int i = 0; i < 3; ++i) Q[1 + f][i] = p[i] + (i == ax ? sg * h : 0.0);
+    inside[f] = !outside_box(Q[1 + f]);
+  }
+  for (int i = 0; i < 3; ++i) Q[7][i] = cell.xg[i];
+  int has_jump = cell.cut && cell.S > 0.0;
+  int used[2];
+  double* acts = NULL;
+  if (grad) acts = (double*)malloc(sizeof(double) * 2 * 8 * L * H);
+  for (int s = 0; s < 2; ++s) {
+    double any = cell.V[s];
+    for (int f = 0; f < 6; ++f) any += cell.A[s][f];
+    used[s] = any > 0.0 || has_jump;
+    for (int e = 0; e < 8; ++e) {
+      U[s][e] = 0.0;
+      if (!used[s]) continue;
+      if (e == 7 && !has_jump) continue;
+      if (e >= 1 && e <= 6 && !inside[e - 1]) {
+        U[s][e] = nbo_dirichlet_g(pr, Q[e]);
+        continue;
+      }
+      if (mode == 1) {
+        U[s][e] = nbo_exact_u(pr, s, Q[e]);
+      } else {
+        const double* th = theta + s * Pn;
+        U[s][e] = mlp_forward(pr, th, Q[e], acts ? acts + ((int64_t)s * 8 + e) * L * H : NULL);
+      }
+    }
+  }
+  double B = 0.0, D = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    double mu = mu_of(pr, s), k = k_of(pr, s);
+    B += h * h * cell.V[s] * (k * U[s][0] - nbo_rhs_f(pr, s, p));
+    D += h * h * cell.V[s] * k;
+    for (int f = 0; f < 6; ++f) {
+      B -= cell.A[s][f] * mu * (U[s][1 + f] - U[s][0]);
+      D += cell.A[s][f] * mu;
+    }
+  }
+  if (has_jump) B += h * cell.S * nbo_beta(pr, cell.xg);
+  double J = 0.0;
+  if (has_jump) J = U[1][7] - U[0][7] - nbo_alpha(pr, cell.xg);
+  double rB = B / D;
+  double r2 = rB * rB + pr->lambda_jump * J * J;
+  if (out) {
+    out->B = B;
+    out->D = D;
+    out->J = J;
+    out->r2 = r2;
+    out->has_jump = has_jump;
+    out->cut = cell.cut;
+  }
+  if (grad && mode == 0) {
+    /* d(scale r^2)/dU for each evaluation, then reverse mode through it */
+    double cB = scale * 2.0 * rB / D;
+    double cJ = scale * 2.0 * pr->lambda_jump * J;
+    for (int s = 0; s < 2; ++s) {
+      if (!used[s]) continue;
+      double mu = mu_of(pr, s), k = k_of(pr, s);
+      double c[8] = {0};
+      c[0] = h * h * cell.V[s] * k;
+      for (int f = 0; f < 6; ++f) {
+        c[0] += cell.A[s][f] * mu;
+        c[1 + f] = -cell.A[s][f] * mu;
+      }
+      for (int e = 0; e < 7; ++e) c[e] *= cB;
+      c[7] = has_jump ? (s == 1 ? cJ : -cJ) : 0.0;
+      for (int e = 0; e < 8; ++e) {
+        if (c[e] == 0.0) continue;
+        if (e >= 1 && e <= 6 && !inside[e - 1]) continue;
+        if (e == 7 && !has_jump) continue;
+        mlp_backward(pr, theta + s * Pn, Q[e], c[e], acts + ((int64_t)s * 8 + e) * L * H,
+                     grad + s * Pn);
+      }
+    }
+  }
+  free(acts);
+}
+
+void nbo_point_terms_eval(const nbo_problem* pr, const double* theta, const double p[3], int mode,
+                          nbo_point_terms* out) {
+  point_core(pr, theta, p, mode, 0.0, NULL, out);
+}
+
+static int pick_threads(int n_threads) {
+#ifdef _OPENMP
+  return n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+  (void)n_threads;
+  return 1;
+#endif
+}
+
+double nbo_loss(const nbo_problem* pr, const double* theta, const double* pts, int64_t n,
+                double* r2_out, int n_threads) {
+  if (n <= 0) return 0.0;
+  int nt = pick_threads(n_threads);
+  double* part = (double*)calloc(nt, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double acc = 0.0;
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      nbo_point_terms t;
+      point_core(pr, theta, pts + 3 * i, 0, 0.0, NULL, &t);
+      if (r2_out) r2_out[i] = t.r2;
+      acc += t.r2;
+    }
+    part[tid] = acc;
+  }
+  double s = 0.0;
+  for (int t = 0; t < nt; ++t) s += part[t];
+  free(part);
+  return s / (double)n;
+}
+
+double nbo_loss_grad(const nbo_problem* pr, const double* theta, const double* pts, int64_t n,
+                     double* grad, int n_threads) {
+  int64_t P = 2 * nbo_params_per_net(pr);
+  memset(grad, 0, sizeof(double) * P);
+  if (n <= 0) return 0.0;
+  int nt = pick_threads(n_threads);
+  double* part = (double*)calloc(nt, sizeof(double));
+  double* gpart = (double*)calloc((size_t)nt * P, sizeof(double));
+  double scale = 1.0 / (double)n;
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double acc = 0.0;
+    double* g = gpart + (size_t)tid * P;
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      nbo_point_terms t;
+      point_core(pr, theta, pts + 3 * i, 0, scale, g, &t);
+      acc += t.r2;
+    }
+    part[tid] = acc;
+  }
+  double s = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    s += part[t];
+    for (int64_t j = 0; j < P; ++j) grad[j] += gpart[(size_t)t * P + j];
+  }
+  free(part);
+  free(gpart);
+  return s / (double)n;
+}
+
+/* Adam (Kingma & Ba 2015), bias-corrected, step t >= 1, no weight decay. */
+void nbo_adam_step(double* theta, double* m, double* v, const double* grad, int64_t n, int64_t t,
+                   double lr, double beta1, double beta2, double eps) {
+  double c1 = 1.0 - pow(beta1, (double)t);
+  double c2 = 1.0 - pow(beta2, (double)t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+    double mh = m[i] / c1, vh = v[i] / c2;
+    theta[i] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+void nbo_train(const nbo_problem* pr, double* theta, double* m, double* v, int64_t step0,
+               int n_steps, int64_t batch, int64_t n_band, double lr, double beta1, double beta2,
+               double eps, uint64_t seed, double* loss_hist, int n_threads) {
+  int64_t P = 2 * nbo_params_per_net(pr);
+  double* pts = (double*)malloc(sizeof(double) * 3 * batch);
+  double* g = (double*)malloc(sizeof(double) * P);
+  for (int k = 0; k < n_steps; ++k) {
+    int64_t t = step0 + k + 1;
+    nbo_sample_points(pr, seed, t, batch, n_band, pts);
+    double L = nbo_loss_grad(pr, theta, pts, batch, g, n_threads);
+    if (loss_hist) loss_hist[k] = L;
+    nbo_adam_step(theta, m, v, g, P, t, lr, beta1, beta2, eps);
+  }
+  free(pts);
+  free(g);
+}
+
+/* ======================================================================
+ * Grid evaluation and the grid scheme (the plain mesh-based method that
+ * NBM lifts off the grid, Sec. 1 and Sec. 3).  Nodes -1 + i h_g,
+ * i = 0..n, h_g = 2/n; node (i,j,k) at index i + (n+1)(j + (n+1)k).
+ * ==================================================================== */
+static int64_t node_id(int n, int i, int j, int k) {
+  return (int64_t)i + (int64_t)(n + 1) * ((int64_t)j + (int64_t)(n + 1) * k);
+}
+
+void nbo_eval_grid(const nbo_problem* pr, const double* theta, int n, double* u_out, int n_threads) {
+  int64_t Pn = nbo_params_per_net(pr);
+  double hg = 2.0 / n;
+  int nt = pick_threads(n_threads);
+  int64_t total = (int64_t)(n + 1) * (n + 1) * (n + 1);
+#pragma omp parallel for schedule(static) num_threads(nt)
+  for (int64_t id = 0; id < total; ++id) {
+    int i = (int)(id % (n + 1)), j = (int)((id / (n + 1)) % (n + 1)), k = (int)(id / ((int64_t)(n + 1) * (n + 1)));
+    double x[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};
+    int s = nbo_phase(pr, x);
+    u_out[id] = mlp_forward(pr, theta + s * Pn, x, NULL);
+  }
+}
+
+/* Grid rows: the same balance row B_p at every interior node, with one
+ * unknown u_q per node.  A net-s value at a node of the other phase is
+ * u_q +- J(q) (reading: J(q) = u+(q) - u-(q) of the manufactured pair,
+ * the "exact jump" extension), which moves every jump term to the RHS and
+ * leaves A symmetric: A_pp = D_p, A_pq = -w_f, w_f = sum_s A^s_f mu^s. */
+typedef struct {
+  double diag;
+  double w[6];
+  double rhs;
+} grid_row;
+
+static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, grid_row* row) {
+  double hg = pg->h;
+  int idx[3] = {i, j, k};
+  double p[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};
+  nbo_cell cell;
+  nbo_cell_geometry(pg, p, hg, &cell);
+  int sp = nbo_phase(pg, p);
+  /* c^s(q): correction so that U^s(q) = u_q + c^s(q) */
+  double cp[2] = {0, 0};
+  {
+    double jmp = nbo_alpha(pg, p);
+    if (sp == 1) cp[0] = -jmp; else cp[1] = jmp;
+  }
+  row->diag = 0.0;
+  row->rhs = 0.0;
+  double known = 0.0; /* terms of B that do not involve the unknowns */
+  for (int s = 0; s < 2; ++s) {
+    double k_s = k_of(pg, s);
+    row->diag += hg * hg * cell.V[s] * k_s;
+    known += hg * hg * cell.V[s] * (k_s * cp[s] - nbo_rhs_f(pg, s, p));
+  }
+  for (int f = 0; f < 6; ++f) {
+    int ax = f / 2, sg = (f & 1) ? 1 : -1;
+    int nb[3] = {idx[0], idx[1], idx[2]};
+    nb[ax] += sg;
+    double q[3] = {-1.0 + nb[0] * hg, -1.0 + nb[1] * hg, -1.0 + nb[2] * hg};
+    int bnd = nb[ax] == 0 || nb[ax] == n;
+    int sq = nbo_phase(pg, q);
+    double cq[2] = {0, 0};
+    if (!bnd) {
+      /* boundary neighbours carry g(q) for both networks, as in B_p */
+      double jq = nbo_alpha(pg, q);
+      if (sq == 1) cq[0] = -jq; else cq[1] = jq;
+    }
+    double wf = 0.0;
+    for (int s = 0; s < 2; ++s) {
+      double a = cell.A[s][f] * mu_of(pg, s);
+      wf += a;
+      known -= a * (cq[s] - cp[s]);
+    }
+    row->diag += wf;
+    if (bnd) {
+      /* Dirichlet node: its value g(q) is known */
+      known -= wf * nbo_dirichlet_g(pg, q);
+      row->w[f] = 0.0;
+    } else {
+      row->w[f] = wf;
+    }
+  }
+  if (cell.cut && cell.S > 0.0) known += hg * cell.S * nbo_beta(pg, cell.xg);
+  /* B = diag u_p - sum w_f u_q + known = 0  ->  A u = -known */
+  row->rhs = -known;
+}
+
+int nbo_grid_assemble_dense(const nbo_problem* pr, int n, double* A, double* b) {
+  nbo_problem pg = *pr;
+  pg.h = 2.0 / n;
+  int m1 = n - 1;
+  int64_t m = (int64_t)m1 * m1 * m1;
+  memset(A, 0, sizeof(double) * m * m);
+  for (int k = 1; k < n; ++k)
+    for (int j = 1; j < n; ++j)
+      for (int i = 1; i < n; ++i) {
+        grid_row row;
+        grid_row_build(&pg, n, i, j, k, &row);
+        int64_t r = (i - 1) + (int64_t)m1 * ((j - 1) + (int64_t)m1 * (k - 1));
+        A[r * m + r] = row.diag;
+        b[r] = row.rhs;
+        for (int f = 0; f < 6; ++f) {
+          if (row.w[f] == 0.0) continue;
+          int ax = f / 2, sg = (f & 1) ? 1 : -1;
+          int nb[3] = {i, j, k};
+          nb[ax] += sg;
+          int64_t c = (nb[0] - 1) + (int64_t)m1 * ((nb[1] - 1) + (int64_t)m1 * (nb[2] - 1));
+          A[r * m + c] -= row.w[f];
+        }
+      }
+  return 0;
+}
+
+/* Jacobi-preconditioned conjugate gradients on the interior nodes;
+ * stops at ||r|| <= rtol ||b||.  Returns 0 on convergence, 1 otherwise. */
+int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter, double* u_out,
+                      int* iters_out, double* relres_out, int n_threads) {
+  nbo_problem pg = *pr;
+  pg.h = 2.0 / n;
+  int nt = pick_threads(n_threads);
+  int m1 = n - 1;
+  int64_t m = (int64_t)m1 * m1 * m1;
+  grid_row* rows = (grid_row*)malloc(sizeof(grid_row) * m);
+#pragma omp parallel for schedule(static) num_threads(nt)
+  for (int64_t r = 0; r < m; ++r) {
+    int i = 1 + (int)(r % m1), j = 1 + (int)((r / m1) % m1), k = 1 + (int)(r / ((int64_t)m1 * m1));
+    grid_row_build(&pg, n, i, j, k, &rows[r]);
+  }
+  double* x = (double*)calloc(m, sizeof(double));
+  double* rr = (double*)malloc(sizeof(double) * m);
+  double* z = (double*)malloc(sizeof(double) * m);
+  double* pp = (double*)malloc(sizeof(double) * m);
+  double* Ap = (double*)malloc(sizeof(double) * m);
+  int64_t strides[3] = {1, m1, (int64_t)m1 * m1};
+  double bnorm2 = 0.0;
+  for (int64_t r = 0; r < m; ++r) {
+    rr[r] = rows[r].rhs;
+    bnorm2 += rr[r] * rr[r];
+  }
+  double bnorm = sqrt(bnorm2);
+  double rz = 0.0;
+  for (int64_t r = 0; r < m; ++r) {
+    z[r] = rr[r] / rows[r].diag;
+    pp[r] = z[r];
+    rz += rr[r] * z[r];
+  }
+  int it = 0;
+  double rnorm = bnorm;
+  int status = 1;
+  if (bnorm == 0.0) status = 0;
+  while (status != 0 && it < max_iter) {
+    double pAp = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : pAp) num_threads(nt)
+    for (int64_t r = 0; r < m; ++r) {
+      double s = rows[r].diag * pp[r];
+      for (int f = 0; f < 6; ++f)
+        if (rows[r].w[f] != 0.0) s -= rows[r].w[f] * pp[r + ((f & 1) ? 1 : -1) * strides[f / 2]];
+      Ap[r] = s;
+      pAp += pp[r] * s;
+    }
+    double alpha = rz / pAp;
+    double rz_new = 0.0, rn2 = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : rz_new, rn2) num_threads(nt)
+    for (int64_t r = 0; r < m; ++r) {
+      x[r] += alpha * pp[r];
+      rr[r] -= alpha * Ap[r];
+      z[r] = rr[r] / rows[r].diag;
+      rz_new += rr[r] * z[r];
+      rn2 += rr[r] * rr[r];
+    }
+    ++it;
+    rnorm = sqrt(rn2);
+    if (rnorm <= rtol * bnorm) {
+      status = 0;
+      break;
+    }
+    double beta = rz_new / rz;
+    rz = rz_new;
+    for (int64_t r = 0; r < m; ++r) pp[r] = z[r] + beta * pp[r];
+  }
+  /* write the full node array: Dirichlet data on the boundary */
+  double hg = pg.h;
+  for (int k = 0; k <= n; ++k)
+    for (int j = 0; j <= n; ++j)
+      for (int i = 0; i <= n; ++i) {
+        int64_t id = node_id(n, i, j, k);
+        if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) {
+          double q[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};
+          u_out[id] = nbo_dirichlet_g(&pg, q);
+        } else {
+          u_out[id] = x[(i - 1) + (int64_t)m1 * ((j - 1) + (int64_t)m1 * (k - 1))];
+        }
+      }
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = bnorm > 0 ? rnorm / bnorm : 0.0;
+  free(rows);
+  free(x);
+  free(rr);
+  free(z);
+  free(pp);
+  free(Ap);
+  return status;
+}
+
+/* L-infinity and RMS error against the exact solution of the node's phase
+ * over the interior nodes (the paper's metrics, Table 1). */
+void nbo_grid_error(const nbo_problem* pr, int n, const double* u, double* linf, double* rmse) {
+  double hg = 2.0 / n, mx = 0.0, s2 = 0.0;
+  int64_t cnt = 0;
+  for (int k = 1; k < n; ++k)
+    for (int j = 1; j < n; ++j)
+      for (int i = 1; i < n; ++i) {
+        double q[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};
+        int s = nbo_phase(pr, q);
+        double e = fabs(u[node_id(n, i, j, k)] - nbo_exact_u(pr, s, q));
+        if (e > mx) mx = e;
+        s2 += e * e;
+        ++cnt;
+      }
+  *linf = mx;
+  *rmse = cnt ? sqrt(s2 / cnt) : 0.0;
+}
