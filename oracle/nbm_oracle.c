@@ -61,11 +61,9 @@ double nbo_phi(const nbo_problem* pr, const double x[3]) {
       return r - pr->r0;
     case NBO_GEOM_FLOWER: {
       if (r == 0.0) return -pr->r0;
-      /* theta: polar angle from +z; psi: azimuth in the xy-plane. */
-      double ct = x[2] / r;
-      if (ct > 1.0) ct = 1.0;
-      if (ct < -1.0) ct = -1.0;
-      double theta = acos(ct);
+      /* theta: polar angle from +z, written atan2(rho, z) (well conditioned
+       * at the poles, same angle as acos(z/r)); psi: azimuth. */
+      double theta = atan2(sqrt(x[0] * x[0] + x[1] * x[1]), x[2]);
       double psi = atan2(x[1], x[0]);
       return r - pr->r0 - pr->amp * sin(pr->lobes_theta * theta) * cos(pr->lobes_psi * psi);
     }
@@ -86,10 +84,7 @@ void nbo_grad_phi(const nbo_problem* pr, const double x[3], double g[3]) {
   if (pr->geometry != NBO_GEOM_FLOWER) return;
   double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
   if (rho == 0.0) return; /* the flower has a conical point on the z axis */
-  double ct = x[2] / r;
-  if (ct > 1.0) ct = 1.0;
-  if (ct < -1.0) ct = -1.0;
-  double theta = acos(ct), psi = atan2(x[1], x[0]);
+  double theta = atan2(rho, x[2]), psi = atan2(x[1], x[0]);
   double lt = pr->lobes_theta, lp = pr->lobes_psi, a = pr->amp;
   /* d(theta)/dx = z x / (r^2 rho), d/dy = z y / (r^2 rho), d/dz = -rho / r^2 */
   double dth[3] = {x[2] * x[0] / (r * r * rho), x[2] * x[1] / (r * r * rho), -rho / (r * r)};
