@@ -1,0 +1,164 @@
+/*
+ * nbm.h -- C ABI of libnbm, a GB300 (sm_103a) implementation of the fused
+ * collocation-residual training step of the Neural Bootstrapping Method
+ * (NBM; Mistani, Pakravan, Ilango, Choudhry, Gibou, "Neuro-Symbolic Partial
+ * Differential Equation Solver", arXiv 2210.14907).
+ *
+ * The method (Sec. 3 and Fig. 2 of the paper): two networks u^- and u^+,
+ * one per side of a level-set interface Gamma, are evaluated at the vertices
+ * of an implicit finite-volume cell placed at each random collocation point;
+ * the cell's discretization of  k u - div(mu grad u) = f  with the jump
+ * conditions [u] = alpha, [mu d_n u] = beta (Sec. 2) gives a locally
+ * preconditioned residual r_p = ||M^-1 A u - M^-1 b||; the squared residuals
+ * are averaged into the loss, differentiated through the kernels and fed to
+ * Adam.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an nbm_status; on failure nbm_last_error() returns a
+ *    thread-local, human-readable message.  No call aborts the process.
+ *  - Array arguments are caller-owned DEVICE pointers unless marked "host".
+ *    The library never frees them and never keeps them past the call.
+ *    Float arrays must be 4-byte aligned; nothing else is assumed.
+ *  - The library owns only the nbm_problem object and the device workspace
+ *    it allocates (grown on demand to the largest batch seen); nbm_destroy
+ *    frees both.
+ *  - Work is enqueued on `stream` in order.  Calls that return a value
+ *    through a HOST pointer synchronize `stream` before returning; the others
+ *    are asynchronous.
+ *  - Parameter vector: FP32, network minus then network plus.  Each network
+ *    is W1[H][3], b1[H], then (W_l[H][H], b_l[H]) for l = 2..n_hidden, then
+ *    w_out[H], b_out; P = 2 * (4H + (n_hidden-1)(H^2+H) + H + 1).
+ *  - Collocation points: FP32, array-of-structs [n][3], inside the open cube
+ *    (-1,1)^3.  Passing pts == NULL draws them on the device from the
+ *    counter-based Philox4x32-10 stream (seed, step): uniform points on the
+ *    lattice -1 + k 2^-22, plus round(band_fraction*n) points within 4h of
+ *    Gamma.
+ *  - One nbm_problem may be used by one host thread at a time.
+ */
+#ifndef NBM_H
+#define NBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* nbm_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  NBM_OK = 0,
+  NBM_ERR_INVALID_ARG = 1,   /* bad descriptor, size, pointer or unsupported shape     */
+  NBM_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed            */
+  NBM_ERR_NOT_CONVERGED = 3, /* grid CG hit max_iter before reaching rtol              */
+  NBM_ERR_NONFINITE = 4,     /* the loss or the gradient of a step was NaN/Inf         */
+  NBM_ERR_OOM = 5,           /* device workspace could not be allocated                */
+  NBM_ERR_DEVICE_TIMEOUT = 6 /* a bounded device-side wait gave up (kernel returned)  */
+} nbm_status;
+
+typedef enum {
+  NBM_GEOM_SPHERE = 1,    /* phi = |x| - r0                                           */
+  NBM_GEOM_FLOWER = 2,    /* phi = r - r0 - amp sin(lobes_theta*theta) cos(lobes_psi*psi),
+                             theta = polar angle from +z, psi = azimuth                */
+  NBM_GEOM_ALL_PLUS = 3,  /* no interface; the whole cube is Omega+                   */
+  NBM_GEOM_ALL_MINUS = 4  /* no interface; the whole cube is Omega-                   */
+} nbm_geometry;
+
+typedef enum {
+  NBM_PREC_FP32 = 0,      /* hidden-layer GEMMs in FP32 FFMA (the plain path)         */
+  NBM_PREC_BF16 = 1,      /* hidden-layer GEMMs on tcgen05, BF16 in / FP32 accumulate  */
+  NBM_PREC_FP16 = 2       /* hidden-layer GEMMs on tcgen05, FP16 in / FP32 accumulate
+                             (grid evaluation only)                                   */
+} nbm_precision;
+
+/* Problem descriptor (Sec. 2 problem + Sec. 3 NBM settings).  Manufactured
+ * solution of the benchmark: u- = exp(x)cos(y)sin(z), u+ = x^2+y^2+z^2;
+ * f, alpha, beta and the Dirichlet data g = u+ follow analytically. */
+typedef struct {
+  int32_t geometry;       /* nbm_geometry                                             */
+  int32_t n_hidden;       /* number of tanh layers (>= 2)                             */
+  int32_t width;          /* H: 64 or 128 (FP32 path), 128 (tcgen05 path)             */
+  int32_t precision;      /* nbm_precision of the training/residual path              */
+  double r0, amp, lobes_theta, lobes_psi;
+  double mu_minus, mu_plus; /* constant diffusion coefficients, > 0                    */
+  double k_minus, k_plus;   /* constant reaction coefficients, >= 0                    */
+  double h;               /* stencil spacing of the implicit cell, 0 < h <= 0.25      */
+  double lambda_jump;     /* weight of the value-jump row in r_p^2 (1 in the paper's reading) */
+  double band_fraction;   /* share of sampled points drawn within 4h of Gamma         */
+  int32_t fp64_stencil;   /* -1: automatic (on for h <= 2/512), 0: off, 1: on          */
+  int32_t reserved;
+} nbm_problem_desc;
+
+typedef struct nbm_problem nbm_problem;
+
+/* Thread-local message describing the last failure of this thread. */
+const char* nbm_last_error(void);
+
+/* Validates `d` and creates a problem object on the current CUDA device.
+ * Returns NBM_ERR_INVALID_ARG for an unsupported descriptor (e.g. a width
+ * the chosen precision path does not implement).  *out is NULL on failure. */
+int nbm_init_problem(const nbm_problem_desc* d, nbm_problem** out);
+
+/* Frees the problem and its workspace.  Safe on NULL.  The caller must make
+ * sure no work of this problem is still running on any stream. */
+int nbm_destroy(nbm_problem* p);
+
+/* Number of FP32 parameters P of the network pair. */
+int64_t nbm_param_count(const nbm_problem* p);
+
+/* Draws n collocation points (Sec. 3, "randomly sampled points") from the
+ * Philox4x32-10 stream keyed by `seed` at counter `step`; pts_out is [n][3]. */
+int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, float* pts_out,
+                      nbm_stream_t stream);
+
+/* Forward pass of the NBM residual (Sec. 3, Fig. 2): for every point, the two
+ * networks at the 2d+1 cell vertices (and at the interface point of cut
+ * cells), the balance and jump rows, r_p^2 = (B/D)^2 + lambda J^2.
+ *   params  [P]            network pair
+ *   pts     [n][3] or NULL (NULL: sample with seed/step)
+ *   r2_out  [n] or NULL    per-point squared residual
+ *   loss_out (host) or NULL: mean of r_p^2 in FP64; synchronizes the stream. */
+int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,
+                 int64_t step, float* r2_out, double* loss_out, nbm_stream_t stream);
+
+/* Loss and its gradient with respect to all P parameters (Sec. 3, "the
+ * automatic differentiation loop passes across the NBM kernels"), by the
+ * hand-written backward kernels.  grad_out [P] is overwritten.
+ * loss_out (host) or NULL; a non-NULL loss_out synchronizes the stream. */
+int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,
+                  int64_t step, float* grad_out, double* loss_out, nbm_stream_t stream);
+
+/* n_steps fused training steps (sample -> cell geometry -> two-network stencil
+ * forward -> residual -> backward -> Adam, Sec. 3).  Step t (1-based, t =
+ * *step_io + 1, ...) samples `batch` points at Philox counter t and applies a
+ * bias-corrected Adam update (Kingma & Ba) with constant lr.
+ *   params, adam_m, adam_v  [P] updated in place (m, v zero for a fresh run)
+ *   step_io (host)          in: steps already taken; out: += n_steps
+ *   loss_hist [n_steps] or NULL: loss of each step before its update.
+ * Asynchronous: step_io is updated on the host immediately. */
+int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v, int64_t* step_io,
+                    int n_steps, int64_t batch, float lr, float beta1, float beta2, float eps,
+                    uint64_t seed, float* loss_hist, nbm_stream_t stream);
+
+/* Evaluates the trained surrogate on the (n+1)^3 nodes -1 + i*2/n of the
+ * cube, each node with the network of its side of Gamma (phi <= 0: minus).
+ * Node (i,j,k) is u_out[i + (n+1)(j + (n+1)k)].  `precision` selects the
+ * hidden-GEMM type (nbm_precision). */
+int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision, float* u_out,
+                  nbm_stream_t stream);
+
+/* The plain mesh-based method the NBM is bootstrapped from: the same
+ * finite-volume rows assembled on the grid of spacing 2/n, one unknown per
+ * interior node, solved in FP64 by Jacobi-preconditioned conjugate gradients
+ * until ||r|| <= rtol ||b|| or max_iter.  The other side's value at a node
+ * across Gamma is the node value plus the exact jump u+ - u- of the
+ * manufactured pair.  u_out [(n+1)^3] FP64 (boundary nodes = Dirichlet data).
+ * iters_out, relres_out (host) or NULL.  Synchronizes the stream.
+ * Returns NBM_ERR_NOT_CONVERGED (with u_out filled) if max_iter is reached. */
+int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
+                      int* iters_out, double* relres_out, nbm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBM_H */

@@ -1,0 +1,364 @@
+// nbm_api.cu -- the C ABI of libnbm (include/nbm.h): argument checking, the
+// device workspace, and the order of the stage launches of one NBM step
+// (arXiv 2210.14907, Sec. 3): sample -> classify/partition -> cut geometry ->
+// cut-cell forward (both networks) -> cut rows -> fused stencil step ->
+// loss / gradient reduction -> Adam.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "nbm_device.cuh"
+
+namespace nbm {
+
+static thread_local char g_err[512] = "no error";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define NBM_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? NBM_ERR_OOM : NBM_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
+  memset(&P, 0, sizeof(P));
+  P.geometry = d.geometry;
+  P.H = d.width;
+  P.L = d.n_hidden;
+  P.fp64 = d.fp64_stencil < 0 ? (d.h <= 2.0 / 512 + 1e-15) : (d.fp64_stencil != 0);
+  P.r0 = d.r0;
+  P.amp = d.amp;
+  P.lt = d.lobes_theta;
+  P.lp = d.lobes_psi;
+  P.mu[0] = d.mu_minus;
+  P.mu[1] = d.mu_plus;
+  P.k[0] = d.k_minus;
+  P.k[1] = d.k_plus;
+  P.h = d.h;
+  P.lambda = d.lambda_jump;
+  P.hf = (float)d.h;
+  P.inv_hf = (float)(1.0 / d.h);
+  P.h2f = (float)(d.h * d.h);
+  P.inv_h2f = (float)(1.0 / (d.h * d.h));
+  P.r0f = (float)d.r0;
+  P.ampf = (float)d.amp;
+  P.ltf = (float)d.lobes_theta;
+  P.lpf = (float)d.lobes_psi;
+  P.muf[0] = (float)d.mu_minus;
+  P.muf[1] = (float)d.mu_plus;
+  P.kf[0] = (float)d.k_minus;
+  P.kf[1] = (float)d.k_plus;
+  const int64_t H = d.width;
+  P.p_net = 4 * H + (int64_t)(d.n_hidden - 1) * (H * H + H) + H + 1;
+}
+
+static void ws_free(Workspace& w) {
+  void* ptrs[] = {w.x, w.y, w.z, w.cls, w.blockcnt, w.list_minus, w.list_plus, w.cut_pt,
+                  w.counters, w.cut, w.cut_out, w.cut_seed, w.loss_part, w.cut_loss_part, w.loss,
+                  w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.corr, w.status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  w = Workspace();
+}
+
+template <typename T>
+static cudaError_t dalloc(T*& p, size_t count) {
+  return cudaMalloc((void**)&p, count * sizeof(T) + 16);
+}
+
+static int ws_reserve(Problem& pb, int64_t n) {
+  Workspace& w = pb.ws;
+  if (w.cap_n >= n && w.grid > 0) return NBM_OK;
+  ws_free(w);
+  const int64_t cap = n < 1024 ? 1024 : n;
+  const int nb = (int)((cap + 255) / 256);
+  const int ncb = (int)((cap + 127) / 128);
+  const int grid = pb.num_sms;
+  const int64_t H = pb.desc.width, L = pb.desc.n_hidden;
+  NBM_CUDA(dalloc(w.x, cap));
+  NBM_CUDA(dalloc(w.y, cap));
+  NBM_CUDA(dalloc(w.z, cap));
+  NBM_CUDA(dalloc(w.cls, cap));
+  NBM_CUDA(dalloc(w.blockcnt, 3 * (size_t)nb));
+  NBM_CUDA(dalloc(w.list_minus, cap));
+  NBM_CUDA(dalloc(w.list_plus, cap));
+  NBM_CUDA(dalloc(w.cut_pt, cap));
+  NBM_CUDA(dalloc(w.counters, 4));
+  NBM_CUDA(dalloc(w.cut, cap));
+  NBM_CUDA(dalloc(w.cut_out, 16 * (size_t)cap));
+  NBM_CUDA(dalloc(w.cut_seed, 16 * (size_t)cap));
+  NBM_CUDA(dalloc(w.loss_part, grid));
+  NBM_CUDA(dalloc(w.cut_loss_part, ncb));
+  NBM_CUDA(dalloc(w.loss, 1));
+  NBM_CUDA(dalloc(w.gpart, (size_t)grid * 2 * pb.p_net));
+  NBM_CUDA(dalloc(w.gpart_flag, 2 * (size_t)grid));
+  NBM_CUDA(dalloc(w.wt, 2 * (size_t)(L - 1) * H * H));
+  NBM_CUDA(dalloc((uint16_t*&)w.wtc, 2 * (size_t)(L - 1) * H * H));
+  NBM_CUDA(dalloc(w.grad, 2 * (size_t)pb.p_net));
+  NBM_CUDA(dalloc(w.step, 1));
+  NBM_CUDA(dalloc(w.corr, 2));
+  NBM_CUDA(dalloc(w.status, 1));
+  NBM_CUDA(cudaMemset(w.status, 0, sizeof(int)));
+  NBM_CUDA(cudaMemset(w.step, 0, sizeof(int64_t)));
+  w.cap_n = cap;
+  w.grid = grid;
+  return NBM_OK;
+}
+
+static int check_desc(const nbm_problem_desc* d) {
+  if (!d) return fail(NBM_ERR_INVALID_ARG, "descriptor is NULL");
+  if (d->geometry < NBM_GEOM_SPHERE || d->geometry > NBM_GEOM_ALL_MINUS)
+    return fail(NBM_ERR_INVALID_ARG, "unknown geometry %d", d->geometry);
+  if (d->n_hidden < 2 || d->n_hidden > 4)
+    return fail(NBM_ERR_INVALID_ARG, "n_hidden must be 2..4 (got %d)", d->n_hidden);
+  if (d->width != 64 && d->width != 128)
+    return fail(NBM_ERR_INVALID_ARG, "width must be 64 or 128 (got %d)", d->width);
+  if (d->precision != NBM_PREC_FP32 && d->precision != NBM_PREC_BF16)
+    return fail(NBM_ERR_INVALID_ARG, "training precision must be FP32 or BF16 (got %d)",
+                d->precision);
+  if (d->precision != NBM_PREC_FP32 && !tc_supported(d->width, d->n_hidden))
+    return fail(NBM_ERR_INVALID_ARG, "the tensor-core path needs width 128 and 2..4 layers");
+  if (!(d->h > 0.0 && d->h <= 0.25)) return fail(NBM_ERR_INVALID_ARG, "h must be in (0, 0.25]");
+  if (!(d->mu_minus > 0.0 && d->mu_plus > 0.0)) return fail(NBM_ERR_INVALID_ARG, "mu must be > 0");
+  if (!(d->k_minus >= 0.0 && d->k_plus >= 0.0)) return fail(NBM_ERR_INVALID_ARG, "k must be >= 0");
+  if (!(d->band_fraction >= 0.0 && d->band_fraction <= 1.0))
+    return fail(NBM_ERR_INVALID_ARG, "band_fraction must be in [0, 1]");
+  if (!(d->lambda_jump >= 0.0)) return fail(NBM_ERR_INVALID_ARG, "lambda_jump must be >= 0");
+  if (d->geometry == NBM_GEOM_SPHERE || d->geometry == NBM_GEOM_FLOWER) {
+    if (!(d->r0 > 0.0 && d->r0 + fabs(d->amp) < 0.9))
+      return fail(NBM_ERR_INVALID_ARG, "interface must lie inside the cube (r0 + |amp| < 0.9)");
+  }
+  return NBM_OK;
+}
+
+static int check_n(int64_t n) {
+  if (n <= 0) return fail(NBM_ERR_INVALID_ARG, "batch must be positive (got %lld)", (long long)n);
+  if (n > (int64_t)1 << 30) return fail(NBM_ERR_INVALID_ARG, "batch too large (> 2^30)");
+  return NBM_OK;
+}
+
+static int64_t band_count(const nbm_problem_desc& d, int64_t n) {
+  if (d.geometry != NBM_GEOM_SPHERE && d.geometry != NBM_GEOM_FLOWER) return 0;
+  return (int64_t)floor(d.band_fraction * (double)n + 0.5);
+}
+
+static StepArgs base_args(Problem& pb, const float* params, int mode, float scale) {
+  Workspace& w = pb.ws;
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = w.x;
+  a.y = w.y;
+  a.z = w.z;
+  a.list[0] = w.list_minus;
+  a.list[1] = w.list_plus;
+  a.counters = w.counters;
+  a.cut = w.cut;
+  a.params = params;
+  a.wt = w.wt;
+  a.wtc = w.wtc;
+  a.cut_out = w.cut_out;
+  a.cut_seed = w.cut_seed;
+  a.loss_part = w.loss_part;
+  a.gpart = w.gpart;
+  a.gpart_flag = w.gpart_flag;
+  a.status = w.status;
+  a.mode = mode;
+  a.scale = scale;
+  return a;
+}
+
+static cudaError_t launch_step(Problem& pb, const ProbDev& P, const StepArgs& a, cudaStream_t st) {
+  if (pb.desc.precision == NBM_PREC_FP32) return launch_step_fp32(P, a, pb.ws.grid, st);
+  return launch_step_tc(P, a, pb.ws.grid, pb.desc.precision, st);
+}
+
+// sample/classify .. cut rows; leaves seeds of cut cells in the workspace
+static int front_stages(Problem& pb, const ProbDev& P, const float* params, const float* pts,
+                        int64_t n, uint64_t seed, const int64_t* step_dev, int64_t step_host,
+                        bool want_seeds, float* r2_out, cudaStream_t st) {
+  Workspace& w = pb.ws;
+  NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, n), w,
+                                  st));
+  NBM_CUDA(launch_cut_geometry(P, n, w, st));
+  StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)n);
+  NBM_CUDA(launch_step(pb, P, a, st));
+  NBM_CUDA(launch_cut_residual(P, n, (float)(1.0 / (double)n), want_seeds, r2_out, w, st));
+  return NBM_OK;
+}
+
+static int read_loss(Problem& pb, double* loss_out, cudaStream_t st) {
+  NBM_CUDA(cudaMemcpyAsync(loss_out, pb.ws.loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  int status = 0;
+  NBM_CUDA(cudaMemcpyAsync(&status, pb.ws.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NBM_CUDA(cudaStreamSynchronize(st));
+  if (status & 2) {
+    cudaMemsetAsync(pb.ws.status, 0, sizeof(int), st);
+    return fail(NBM_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up");
+  }
+  if (!std::isfinite(*loss_out)) {
+    cudaMemsetAsync(pb.ws.status, 0, sizeof(int), st);
+    return fail(NBM_ERR_NONFINITE, "loss is not finite");
+  }
+  return NBM_OK;
+}
+
+}  // namespace nbm
+
+using namespace nbm;
+
+struct nbm_problem {
+  Problem pb;
+};
+
+extern "C" {
+
+const char* nbm_last_error(void) { return g_err; }
+
+int nbm_init_problem(const nbm_problem_desc* d, nbm_problem** out) {
+  if (!out) return fail(NBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = check_desc(d);
+  if (rc) return rc;
+  nbm_problem* p = new (std::nothrow) nbm_problem();
+  if (!p) return fail(NBM_ERR_OOM, "host allocation failed");
+  p->pb.desc = *d;
+  cudaError_t e = cudaGetDevice(&p->pb.device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&p->pb.num_sms, cudaDevAttrMultiProcessorCount, p->pb.device);
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(NBM_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  ProbDev P;
+  make_prob_dev(*d, P);
+  p->pb.p_net = P.p_net;
+  *out = p;
+  return NBM_OK;
+}
+
+int nbm_destroy(nbm_problem* p) {
+  if (!p) return NBM_OK;
+  ws_free(p->pb.ws);
+  delete p;
+  return NBM_OK;
+}
+
+int64_t nbm_param_count(const nbm_problem* p) { return p ? 2 * p->pb.p_net : -1; }
+
+int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, float* pts_out,
+                      nbm_stream_t stream) {
+  if (!p || !pts_out) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  int rc = check_n(n);
+  if (rc) return rc;
+  Problem& pb = p->pb;
+  rc = ws_reserve(pb, n);
+  if (rc) return rc;
+  ProbDev P;
+  make_prob_dev(pb.desc, P);
+  cudaStream_t st = (cudaStream_t)stream;
+  NBM_CUDA(launch_sample_classify(P, nullptr, seed, nullptr, step, n, band_count(pb.desc, n),
+                                  pb.ws, st));
+  // interleave SoA -> [n][3] via three strided 2D copies
+  NBM_CUDA(cudaMemcpy2DAsync(pts_out, 3 * sizeof(float), pb.ws.x, sizeof(float), sizeof(float), n,
+                             cudaMemcpyDeviceToDevice, st));
+  NBM_CUDA(cudaMemcpy2DAsync(pts_out + 1, 3 * sizeof(float), pb.ws.y, sizeof(float),
+                             sizeof(float), n, cudaMemcpyDeviceToDevice, st));
+  NBM_CUDA(cudaMemcpy2DAsync(pts_out + 2, 3 * sizeof(float), pb.ws.z, sizeof(float),
+                             sizeof(float), n, cudaMemcpyDeviceToDevice, st));
+  return NBM_OK;
+}
+
+int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,
+                 int64_t step, float* r2_out, double* loss_out, nbm_stream_t stream) {
+  if (!p || !params) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  int rc = check_n(n);
+  if (rc) return rc;
+  Problem& pb = p->pb;
+  rc = ws_reserve(pb, n);
+  if (rc) return rc;
+  ProbDev P;
+  make_prob_dev(pb.desc, P);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = pb.desc.precision;
+  NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
+  rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, false, r2_out, st);
+  if (rc) return rc;
+  StepArgs a = base_args(pb, params, MODE_RESIDUAL, 1.0f / (float)n);
+  a.r2_out = r2_out;
+  NBM_CUDA(launch_step(pb, P, a, st));
+  NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, false, nullptr, nullptr, nullptr, nullptr, 0.f,
+                         0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st));
+  if (loss_out) return read_loss(pb, loss_out, st);
+  return NBM_OK;
+}
+
+int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,
+                  int64_t step, float* grad_out, double* loss_out, nbm_stream_t stream) {
+  if (!p || !params || !grad_out) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  int rc = check_n(n);
+  if (rc) return rc;
+  Problem& pb = p->pb;
+  rc = ws_reserve(pb, n);
+  if (rc) return rc;
+  ProbDev P;
+  make_prob_dev(pb.desc, P);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = pb.desc.precision;
+  NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
+  rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st);
+  if (rc) return rc;
+  StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)n);
+  NBM_CUDA(launch_step(pb, P, a, st));
+  NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, true, nullptr, nullptr, nullptr, grad_out, 0.f,
+                         0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st));
+  if (loss_out) return read_loss(pb, loss_out, st);
+  return NBM_OK;
+}
+
+int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v, int64_t* step_io,
+                    int n_steps, int64_t batch, float lr, float beta1, float beta2, float eps,
+                    uint64_t seed, float* loss_hist, nbm_stream_t stream) {
+  if (!p || !params || !adam_m || !adam_v || !step_io)
+    return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  if (n_steps < 0) return fail(NBM_ERR_INVALID_ARG, "n_steps < 0");
+  if (*step_io < 0) return fail(NBM_ERR_INVALID_ARG, "*step_io < 0");
+  if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps > 0.f))
+    return fail(NBM_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  int rc = check_n(batch);
+  if (rc) return rc;
+  if (n_steps == 0) return NBM_OK;
+  Problem& pb = p->pb;
+  rc = ws_reserve(pb, batch);
+  if (rc) return rc;
+  ProbDev P;
+  make_prob_dev(pb.desc, P);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = pb.desc.precision;
+  const int64_t base = *step_io;
+  NBM_CUDA(cudaMemcpyAsync(pb.ws.step, step_io, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
+  for (int k = 0; k < n_steps; ++k) {
+    rc = front_stages(pb, P, params, nullptr, batch, seed, pb.ws.step, 0, true, nullptr, st);
+    if (rc) return rc;
+    StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)batch);
+    NBM_CUDA(launch_step(pb, P, a, st));
+    NBM_CUDA(launch_finish(P, batch, pb.ws.grid, true, false, params, adam_m, adam_v, nullptr, lr,
+                           beta1, beta2, eps, loss_hist, base, prec, pb.ws, st));
+  }
+  *step_io = base + n_steps;
+  return NBM_OK;
+}
+
+}  // extern "C"

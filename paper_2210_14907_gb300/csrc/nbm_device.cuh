@@ -1,0 +1,287 @@
+// nbm_device.cuh -- device-side building blocks of the NBM training step
+// (arXiv 2210.14907, Sec. 2-3): problem constants, Philox4x32-10, level sets,
+// manufactured data, the difference-form tanh layer and its adjoint, and the
+// per-point balance/jump rows.  Shared by every kernel translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbm_host.h"
+
+namespace nbm {
+
+// ---------------------------------------------------------------------------
+// Problem constants, passed by value to every kernel.
+// ---------------------------------------------------------------------------
+struct ProbDev {
+  int geometry;  // nbm_geometry
+  int H, L;      // width, number of tanh layers
+  int fp64;      // residual combination in FP64
+  double r0, amp, lt, lp;
+  double mu[2], k[2];
+  double h, lambda;
+  float hf, inv_hf, h2f, inv_h2f;  // h, 1/h, h^2, 1/h^2 in FP32
+  float r0f, ampf, ltf, lpf;
+  float muf[2], kf[2];
+  int64_t p_net;  // parameters per network
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += W0;
+      k1 += W1;
+    }
+#ifdef __CUDA_ARCH__
+    uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+#else
+    uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+constexpr uint32_t kPointStream = 0x4E424D31u;  // 4th counter word of point draws
+
+// ---------------------------------------------------------------------------
+// Level sets (Sec. 3: the level set gives the cell/interface crossings).
+// theta = atan2(rho, z) is the polar angle, psi = atan2(y, x) the azimuth.
+// ---------------------------------------------------------------------------
+__device__ inline float phi_f(const ProbDev& P, float x, float y, float z) {
+  if (P.geometry == NBM_GEOM_ALL_PLUS) return 1.f;
+  if (P.geometry == NBM_GEOM_ALL_MINUS) return -1.f;
+  float rho2 = x * x + y * y;
+  float r = sqrtf(rho2 + z * z);
+  if (P.geometry == NBM_GEOM_SPHERE) return r - P.r0f;
+  if (r == 0.f) return -P.r0f;
+  float th = atan2f(sqrtf(rho2), z), ps = atan2f(y, x);
+  return r - P.r0f - P.ampf * sinf(P.ltf * th) * cosf(P.lpf * ps);
+}
+
+__device__ inline double phi_d(const ProbDev& P, double x, double y, double z) {
+  if (P.geometry == NBM_GEOM_ALL_PLUS) return 1.0;
+  if (P.geometry == NBM_GEOM_ALL_MINUS) return -1.0;
+  double rho2 = x * x + y * y;
+  double r = sqrt(rho2 + z * z);
+  if (P.geometry == NBM_GEOM_SPHERE) return r - P.r0;
+  if (r == 0.0) return -P.r0;
+  double th = atan2(sqrt(rho2), z), ps = atan2(y, x);
+  return r - P.r0 - P.amp * sin(P.lt * th) * cos(P.lp * ps);
+}
+
+__device__ inline void grad_phi_d(const ProbDev& P, const double x[3], double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  if (P.geometry == NBM_GEOM_ALL_PLUS || P.geometry == NBM_GEOM_ALL_MINUS) return;
+  double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+  double r = sqrt(rho * rho + x[2] * x[2]);
+  if (r == 0.0) return;
+  for (int i = 0; i < 3; ++i) g[i] = x[i] / r;
+  if (P.geometry != NBM_GEOM_FLOWER || rho == 0.0) return;
+  double th = atan2(rho, x[2]), ps = atan2(x[1], x[0]);
+  double r2 = r * r;
+  double dth[3] = {x[2] * x[0] / (r2 * rho), x[2] * x[1] / (r2 * rho), -rho / r2};
+  double dps[3] = {-x[1] / (rho * rho), x[0] / (rho * rho), 0.0};
+  double a = -P.amp * P.lt * cos(P.lt * th) * cos(P.lp * ps);
+  double b = P.amp * P.lp * sin(P.lt * th) * sin(P.lp * ps);
+  for (int i = 0; i < 3; ++i) g[i] += a * dth[i] + b * dps[i];
+}
+
+// ---------------------------------------------------------------------------
+// Manufactured pair: u- = e^x cos y sin z (Lap u- = -u-), u+ = |x|^2 (Lap = 6).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline T exact_u(int s, T x, T y, T z) {
+  if (s == 0) return exp(x) * cos(y) * sin(z);
+  return x * x + y * y + z * z;
+}
+template <>
+__device__ inline float exact_u<float>(int s, float x, float y, float z) {
+  if (s == 0) return expf(x) * cosf(y) * sinf(z);
+  return x * x + y * y + z * z;
+}
+
+template <typename T>
+__device__ inline T rhs_f(const ProbDev& P, int s, T x, T y, T z) {
+  T u = exact_u<T>(s, x, y, z);
+  T mu = (T)P.mu[s], k = (T)P.k[s];
+  return s == 0 ? k * u + mu * u : k * u - (T)6 * mu;
+}
+
+template <typename T>
+__device__ inline T dirichlet_g(const ProbDev& P, T x, T y, T z) {
+  return exact_u<T>(P.geometry == NBM_GEOM_ALL_MINUS ? 0 : 1, x, y, z);
+}
+
+__device__ inline void exact_grad_u_d(int s, const double x[3], double g[3]) {
+  if (s == 0) {
+    double e = exp(x[0]);
+    g[0] = e * cos(x[1]) * sin(x[2]);
+    g[1] = -e * sin(x[1]) * sin(x[2]);
+    g[2] = e * cos(x[1]) * cos(x[2]);
+  } else {
+    g[0] = 2 * x[0];
+    g[1] = 2 * x[1];
+    g[2] = 2 * x[2];
+  }
+}
+
+__device__ inline double alpha_d(const double x[3]) {
+  return exact_u<double>(1, x[0], x[1], x[2]) - exact_u<double>(0, x[0], x[1], x[2]);
+}
+
+__device__ inline double beta_d(const ProbDev& P, const double x[3]) {
+  double gp[3], gm[3], gf[3];
+  exact_grad_u_d(1, x, gp);
+  exact_grad_u_d(0, x, gm);
+  grad_phi_d(P, x, gf);
+  double nn = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
+  if (nn == 0.0) return 0.0;
+  double b = 0.0;
+  for (int i = 0; i < 3; ++i) b += (P.mu[1] * gp[i] - P.mu[0] * gm[i]) * gf[i] / nn;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// tanh.  Accurate path: CUDA's tanhf.  Fast path: the SFU approximation
+// (tanh.approx.f32), used only where the mixed-precision tolerance allows.
+// ---------------------------------------------------------------------------
+template <bool FAST>
+__device__ __forceinline__ float act_tanh(float x) {
+  if constexpr (FAST) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  } else {
+    return tanhf(x);
+  }
+}
+template <bool FAST>
+__device__ __forceinline__ float rcp(float x) {
+  if constexpr (FAST) return __frcp_rn(x);
+  else return 1.0f / x;
+}
+
+// ---------------------------------------------------------------------------
+// Difference-form tanh layer.  For one unit of one point the stencil values
+// z(p), z(p +- h e_i) are carried as
+//   z            centre pre-activation,
+//   mu_i  = (z(p+h e_i) + z(p-h e_i))/2 - z(p)     (symmetric, O(h^2)),
+//   del_i = (z(p+h e_i) - z(p-h e_i))/2            (antisymmetric, O(h)),
+// scaled as mt = mu/h^2 and dt = del/h.  With t = tanh z the layer outputs
+// the same three kinds of quantity for a = tanh(.), computed from tanh
+// addition identities so that no O(1) values are subtracted:
+//   tanh(z+mu) - tanh z          = Tm (1-t^2)/(1+t Tm),     Tm = tanh mu
+//   [tanh(w+d) + tanh(w-d)]/2 - tanh w = -tw (1-tw^2) Td^2/(1-tw^2 Td^2)
+//   [tanh(w+d) - tanh(w-d)]/2    = (1-tw^2) Td/(1-tw^2 Td^2),  Td = tanh d,
+// with w = z + mu and tw = tanh w = (t+Tm)/(1+t Tm).
+// Evaluating the network this way is exactly the same function as seven
+// independent evaluations; it only changes the rounding.
+// ---------------------------------------------------------------------------
+template <bool FAST>
+__device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, float h, float h2,
+                                                 float inv_h, float inv_h2, float& mo, float& dout) {
+  float mu = mt * h2, de = dt * h;
+  float Tm = act_tanh<FAST>(mu), Td = act_tanh<FAST>(de);
+  float q = rcp<FAST>(fmaf(t, Tm, 1.0f));
+  float tw = (t + Tm) * q;
+  float sw = fmaf(-tw, tw, 1.0f);
+  float dm = Tm * fmaf(-t, t, 1.0f) * q;
+  float Td2 = Td * Td;
+  float r2 = rcp<FAST>(fmaf(-tw * tw, Td2, 1.0f));
+  float m = fmaf(-tw * sw * Td2, r2, dm);
+  float d = sw * Td * r2;
+  mo = m * inv_h2;
+  dout = d * inv_h;
+}
+
+// Adjoint of one stencil axis.  Inputs: forward outputs t (centre), mo, dout
+// (scaled), upstream gradients with respect to the scaled outputs (Gm, Gd).
+// Writes the gradients with respect to the scaled inputs (gmu, gdel) and
+// returns the contribution to d/dz.  With s0 = 1-t^2, m = mo h^2, d = dout h:
+//   P = -(2 t m + m^2 + d^2)  = (s+ + s- - 2 s0)/2,
+//   Q = -2 d (t + m)          = (s+ - s-)/2,      s+- = 1 - tanh^2(z+mu+-del),
+//   dm/dz = P, dm/dmu = s0+P, dm/ddel = Q, dd/dz = dd/dmu = Q, dd/ddel = s0+P.
+__device__ __forceinline__ float tanh_stencil_bwd(float t, float s0, float mo, float dout,
+                                                  float Gm_s, float Gd_s, float h, float h2,
+                                                  float inv_h, float inv_h2, float& gmu_s,
+                                                  float& gdel_s) {
+  float m = mo * h2, d = dout * h;
+  float Gm = Gm_s * inv_h2, Gd = Gd_s * inv_h;
+  float P = -fmaf(2.f * t, m, fmaf(m, m, d * d));
+  float Q = -2.f * d * (t + m);
+  float S = s0 + P;
+  gmu_s = fmaf(S, Gm, Q * Gd) * h2;
+  gdel_s = fmaf(Q, Gm, S * Gd) * h;
+  return fmaf(P, Gm, Q * Gd);
+}
+
+// ---------------------------------------------------------------------------
+// Balance row of an uncut cell of phase s (Sec. 3 reading):
+//   B/h^2 = k U(p) - f(p) - mu sum_{i,sigma} dU_{sigma i}/h^2,
+//   dU_{+-i}/h^2 = Mt_i +- Dt_i/h   (interior neighbour)
+//               = (g(q) - U(p))/h^2  (neighbour outside the cube: Dirichlet),
+//   D = 6 mu + h^2 k,  r = B/D.
+// out[8] = network outputs (U, Mt1..3, Dt1..3, unused); seeds[8] receives
+// d(scale * r^2)/d(out).  Returns r^2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline T uncut_residual(const ProbDev& P, int s, float px, float py, float pz,
+                                   const float out[8], T scale, float seeds[8]) {
+  const T h = (T)P.h, h2 = h * h, mu = (T)P.mu[s], k = (T)P.k[s];
+  const T U = (T)out[0];
+  const T x[3] = {(T)px, (T)py, (T)pz};
+  T Bt = k * U - rhs_f<T>(P, s, x[0], x[1], x[2]);
+  T dU = k;
+  T dM[3], dD[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dM[i] = 0;
+    dD[i] = 0;
+#pragma unroll
+    for (int sg = -1; sg <= 1; sg += 2) {
+      T q[3] = {x[0], x[1], x[2]};
+      q[i] += sg * h;
+      bool bnd = fabs(q[i]) >= (T)1;
+      if (bnd) {
+        T g = dirichlet_g<T>(P, q[0], q[1], q[2]);
+        Bt -= mu * (g - U) / h2;
+        dU += mu / h2;
+      } else {
+        Bt -= mu * ((T)out[1 + i] + (T)sg * (T)out[4 + i] / h);
+        dM[i] -= mu;
+        dD[i] -= mu * (T)sg / h;
+      }
+    }
+  }
+  T D = (T)6 * mu + h2 * k;
+  T r = h2 * Bt / D;
+  T c = scale * (T)2 * r * h2 / D;
+  seeds[0] = (float)(c * dU);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    seeds[1 + i] = (float)(c * dM[i]);
+    seeds[4 + i] = (float)(c * dD[i]);
+  }
+  seeds[7] = 0.f;
+  return r * r;
+}
+
+}  // namespace nbm

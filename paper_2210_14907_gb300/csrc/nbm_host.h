@@ -1,0 +1,113 @@
+// nbm_host.h -- internal declarations shared by the libnbm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbm.h"
+
+namespace nbm {
+
+struct ProbDev;
+
+// Kernel modes of the fused step kernels.
+enum StepMode : int {
+  MODE_CUT_FWD = 0,   // forward of cut-cell points through both networks
+  MODE_RESIDUAL = 1,  // forward + residual of uncut points
+  MODE_TRAIN = 2      // forward + residual + backward + weight gradient
+};
+
+// Geometry of one cut cell (computed in FP64 by the classifier pipeline).
+struct CutRec {
+  double Vm;       // volume fraction of Omega- (Omega+ has 1 - Vm)
+  double Am[6];    // face fractions of Omega-, face f = 2*axis + (side > 0)
+  double S;        // interface area / h^2
+  double xg[3];    // interface point (projected centroid)
+  double beta;     // [mu d_n u] at xg
+  double alpha;    // [u] at xg
+  double f[2];     // f^-(p), f^+(p)
+  int point;       // collocation point index
+  int has_jump;    // S > 0
+};
+
+// Everything the fused step kernels read or write.
+struct StepArgs {
+  const float* x;
+  const float* y;
+  const float* z;
+  const int* list[2];     // phase lists; entry >= 0 point index, < 0 cut id -(e+1)
+  const int* counters;    // [0] n-, [1] n+, [2] n_cut
+  const CutRec* cut;
+  const float* params;    // FP32 parameter pair
+  const float* wt;        // FP32 transposed hidden weights [net][layer][k][u]
+  const void* wtc;        // 16-bit hidden weights in the tensor-core layout [net][layer]
+  float* cut_out;         // [n_cut][2][8] network outputs of cut points
+  const float* cut_seed;  // [n_cut][2][8] seeds of cut points
+  float* r2_out;          // [n] or nullptr
+  double* loss_part;      // [grid] partial sums of r^2 over uncut points
+  float* gpart;           // [grid][2][p_net] partial gradients
+  int* gpart_flag;        // [grid][2]
+  int* status;            // device status word (bounded waits)
+  int mode;
+  float scale;            // 1/N
+};
+
+// Device workspace of a problem (grown on demand).
+struct Workspace {
+  int64_t cap_n = 0;       // points
+  int grid = 0;            // CTAs of the fused kernels
+  float *x = nullptr, *y = nullptr, *z = nullptr;
+  uint8_t* cls = nullptr;
+  int* blockcnt = nullptr;  // [3][nb]
+  int* list_minus = nullptr;
+  int* list_plus = nullptr;
+  int* cut_pt = nullptr;
+  int* counters = nullptr;  // [4]
+  CutRec* cut = nullptr;
+  float* cut_out = nullptr;
+  float* cut_seed = nullptr;
+  double* loss_part = nullptr;      // [grid]
+  double* cut_loss_part = nullptr;  // [nb_cut]
+  double* loss = nullptr;           // [1]
+  float* gpart = nullptr;
+  int* gpart_flag = nullptr;
+  float* wt = nullptr;              // FP32 transposed hidden weights
+  void* wtc = nullptr;              // 16-bit hidden weights
+  float* grad = nullptr;            // [P]
+  int64_t* step = nullptr;          // [1] device step counter
+  float* corr = nullptr;            // [2] Adam bias corrections of the current step
+  int* status = nullptr;            // [1]
+};
+
+struct Problem {
+  nbm_problem_desc desc;
+  int device = 0;
+  int num_sms = 0;
+  int64_t p_net = 0;
+  Workspace ws;
+};
+
+void make_prob_dev(const nbm_problem_desc& d, ProbDev& P);
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
+                                   const int64_t* step_dev, int64_t step_host, int64_t n,
+                                   int64_t n_band, Workspace& ws, cudaStream_t st);
+cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
+cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
+                                float* r2_out, Workspace& ws, cudaStream_t st);
+cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,
+                                cudaStream_t st);
+cudaError_t launch_step_fp32(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int prec, cudaStream_t st);
+cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
+                          float* params, float* m, float* v, float* grad_out, float lr, float b1,
+                          float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
+                          Workspace& ws, cudaStream_t st);
+cudaError_t launch_eval_grid(const ProbDev& P, const float* params, int n, int prec, float* u,
+                             Workspace& ws, int grid, cudaStream_t st);
+size_t tc_smem_bytes(int L);
+size_t fp32_smem_bytes(int H, int L);
+int tc_supported(int H, int L);
+
+}  // namespace nbm

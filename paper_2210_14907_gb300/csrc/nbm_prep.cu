@@ -1,0 +1,614 @@
+// nbm_prep.cu -- the light stages of the NBM step (arXiv 2210.14907, Sec. 3):
+//   sample + classify  : Philox collocation points, cut/uncut decision of the
+//                        implicit cell from the level set at its 8 corners
+//   scan + scatter     : stable phase partition (two networks -> two lists;
+//                        cut cells go into both and into the cut list)
+//   cut geometry       : FP64 Kuhn-split volume / face / interface fractions
+//                        and the interface point of every cut cell
+//   cut residual       : balance + jump rows of cut cells (both networks)
+//   weight staging     : FP32 transposed and 16-bit tensor-core copies
+//   finish             : deterministic loss / gradient reduction and Adam
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "nbm_device.cuh"
+
+namespace nbm {
+
+constexpr int kBlk = 256;
+
+// ------------------------------------------------------------------------
+// Collocation points.  Uniform: lattice -1 + k 2^-22, k = 1 + floor(r (2^23-1)
+// / 2^32) per axis (integer arithmetic, identical everywhere).  Band: a ray
+// direction uniform on the sphere and an offset t in (-4h, 4h) from the
+// interface radius along it, in FP64, quantised to the same lattice.
+// ------------------------------------------------------------------------
+__device__ inline double quantize_coord(double v) {
+  double k = floor((v + 1.0) * 4194304.0 + 0.5);
+  k = fmin(fmax(k, 1.0), 8388607.0);
+  return -1.0 + k / 4194304.0;
+}
+
+__device__ inline void draw_point(const ProbDev& P, uint64_t seed, int64_t step, int64_t i,
+                                  bool band, float p[3]) {
+  uint32_t r[4];
+  philox4x32_10((uint32_t)i, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), kPointStream,
+                (uint32_t)seed, (uint32_t)(seed >> 32), r);
+  if (!band) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      uint32_t k = 1u + (uint32_t)(((uint64_t)r[j] * 8388607ull) >> 32);
+      p[j] = -1.0f + (float)k * (1.0f / 4194304.0f);
+    }
+    return;
+  }
+  double u0 = ((double)(r[0] >> 8) + 0.5) / 16777216.0;
+  double u1 = ((double)(r[1] >> 8) + 0.5) / 16777216.0;
+  double u2 = ((double)(r[2] >> 8) + 0.5) / 16777216.0;
+  double cth = 1.0 - 2.0 * u0;
+  double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+  double psi = 2.0 * 3.14159265358979323846 * u1;
+  double t = (2.0 * u2 - 1.0) * 4.0 * P.h;
+  double R = P.r0;
+  if (P.geometry == NBM_GEOM_FLOWER) R += P.amp * sin(P.lt * acos(cth)) * cos(P.lp * psi);
+  p[0] = (float)quantize_coord((R + t) * sth * cos(psi));
+  p[1] = (float)quantize_coord((R + t) * sth * sin(psi));
+  p[2] = (float)quantize_coord((R + t) * cth);
+}
+
+// Number of corners of the cell p + [-h/2, h/2]^3 with phi <= 0.  FP32 first;
+// corners whose FP32 value is within the FP32 error band of 0 are redone in
+// FP64 so that the decision is the FP64 one.
+__device__ inline int count_neg_corners(const ProbDev& P, const float p[3]) {
+  const float hh = 0.5f * P.hf;
+  float f[8];
+  float mn = 1e30f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float cx = p[0] + ((c & 1) ? hh : -hh), cy = p[1] + ((c & 2) ? hh : -hh),
+          cz = p[2] + ((c & 4) ? hh : -hh);
+    f[c] = phi_f(P, cx, cy, cz);
+    mn = fminf(mn, fabsf(f[c]));
+  }
+  int nneg = 0;
+  if (mn < 2e-5f) {
+    const double hd = 0.5 * P.h;
+    for (int c = 0; c < 8; ++c) {
+      double cx = (double)p[0] + ((c & 1) ? hd : -hd), cy = (double)p[1] + ((c & 2) ? hd : -hd),
+             cz = (double)p[2] + ((c & 4) ? hd : -hd);
+      nneg += phi_d(P, cx, cy, cz) <= 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) nneg += f[c] <= 0.f;
+  }
+  return nneg;
+}
+
+__global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float* __restrict__ pts_in,
+                                                          uint64_t seed, const int64_t* step_dev,
+                                                          int64_t step_host, int64_t n,
+                                                          int64_t n_band, float* X, float* Y,
+                                                          float* Z, uint8_t* cls, int* blockcnt,
+                                                          int nb) {
+  int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
+  int c = -1;
+  if (i < n) {
+    float p[3];
+    if (pts_in) {
+      p[0] = pts_in[3 * i];
+      p[1] = pts_in[3 * i + 1];
+      p[2] = pts_in[3 * i + 2];
+    } else {
+      int64_t step = step_dev ? (*step_dev + 1) : step_host;
+      bool iface = P.geometry == NBM_GEOM_SPHERE || P.geometry == NBM_GEOM_FLOWER;
+      draw_point(P, seed, step, i, iface && i >= n - n_band, p);
+    }
+    X[i] = p[0];
+    Y[i] = p[1];
+    Z[i] = p[2];
+    int nneg = count_neg_corners(P, p);
+    c = nneg == 8 ? 0 : (nneg == 0 ? 1 : 2);
+    cls[i] = (uint8_t)c;
+  }
+  int cm = __syncthreads_count(c == 0 || c == 2);
+  int cp = __syncthreads_count(c == 1 || c == 2);
+  int cc = __syncthreads_count(c == 2);
+  if (threadIdx.x == 0) {
+    blockcnt[blockIdx.x] = cm;
+    blockcnt[nb + blockIdx.x] = cp;
+    blockcnt[2 * nb + blockIdx.x] = cc;
+  }
+}
+
+// Exclusive scan of the three per-block count arrays (one CTA).  counters[0..2]
+// receive the totals (n-, n+, n_cut).
+__global__ void __launch_bounds__(1024) k_scan_counts(int* blockcnt, int nb, int* counters) {
+  __shared__ int warp_tot[32];
+  for (int m = 0; m < 3; ++m) {
+    int* a = blockcnt + (int64_t)m * nb;
+    int per = (nb + 1023) / 1024;
+    int lo = threadIdx.x * per, hi = min(lo + per, nb);
+    int s = 0;
+    for (int j = lo; j < hi; ++j) s += a[j];
+    // block exclusive scan of s
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int v = warp_tot[lane], iv = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, iv, o);
+        if (lane >= o) iv += t;
+      }
+      warp_tot[lane] = iv - v;
+      if (lane == 31) counters[m] = iv;
+    }
+    __syncthreads();
+    int run = warp_tot[w] + incl - s;
+    for (int j = lo; j < hi; ++j) {
+      int v = a[j];
+      a[j] = run;
+      run += v;
+    }
+    __syncthreads();
+  }
+}
+
+// Stable scatter: list order = point order.  Entry >= 0: uncut point index;
+// entry < 0: cut cell -(cut_id + 1).
+__global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* __restrict__ cls, int64_t n,
+                                                  const int* __restrict__ blockoff, int nb,
+                                                  int* list_m, int* list_p, int* cut_pt) {
+  __shared__ int wsum[3][kBlk / 32];
+  int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
+  int c = i < n ? (int)cls[i] : -1;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned lt = (1u << lane) - 1u;
+  bool f[3] = {c == 0 || c == 2, c == 1 || c == 2, c == 2};
+  int rank[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    unsigned b = __ballot_sync(0xffffffffu, f[m]);
+    rank[m] = __popc(b & lt);
+    if (lane == 0) wsum[m][w] = __popc(b);
+  }
+  __syncthreads();
+  int pos[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    int off = blockoff[(int64_t)m * nb + blockIdx.x];
+    for (int k = 0; k < w; ++k) off += wsum[m][k];
+    pos[m] = off + rank[m];
+  }
+  if (c < 0) return;
+  int cut_id = pos[2];
+  if (c == 2) cut_pt[cut_id] = (int)i;
+  int e = c == 2 ? -(cut_id + 1) : (int)i;
+  if (f[0]) list_m[pos[0]] = e;
+  if (f[1]) list_p[pos[1]] = e;
+}
+
+// ------------------------------------------------------------------------
+// Cut-cell geometry in FP64.  phi is linear on each tetrahedron of the
+// Freudenthal-Kuhn split (six tetrahedra 0 -> e_a -> e_a+e_b -> 7); faces are
+// split along the diagonal from their lowest to their highest corner.
+// ------------------------------------------------------------------------
+__device__ inline double frac_tri(double a, double b, double c) {
+  int na = a <= 0.0, nb = b <= 0.0, nc = c <= 0.0;
+  int k = na + nb + nc;
+  if (k == 0) return 0.0;
+  if (k == 3) return 1.0;
+  if (k == 1) {
+    double l = na ? a : (nb ? b : c);
+    double o1 = na ? b : a, o2 = nc ? b : c;  // the two positive values
+    return (l / (l - o1)) * (l / (l - o2));
+  }
+  double l = !na ? a : (!nb ? b : c);
+  double o1 = !na ? b : a, o2 = !nc ? b : c;  // the two non-positive values
+  return 1.0 - (l / (l - o1)) * (l / (l - o2));
+}
+
+__device__ inline double frac_tet(const double f[4]) {
+  int neg = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
+  if (neg == 0) return 0.0;
+  if (neg == 4) return 1.0;
+  if (neg == 1 || neg == 3) {
+    bool want_neg = neg == 1;
+    int lone = 0;
+    for (int i = 0; i < 4; ++i)
+      if ((f[i] <= 0.0) == want_neg) lone = i;
+    double prod = 1.0;
+    for (int i = 0; i < 4; ++i)
+      if (i != lone) prod *= f[lone] / (f[lone] - f[i]);
+    return neg == 1 ? prod : 1.0 - prod;
+  }
+  // two on each side: A, B = -values below, C, D = values above
+  double A = -1.0, B = -1.0, C = -1.0, D = -1.0;
+  for (int i = 0; i < 4; ++i) {
+    if (f[i] <= 0.0) {
+      if (A < 0.0) A = -f[i]; else B = -f[i];
+    } else {
+      if (C < 0.0) C = f[i]; else D = f[i];
+    }
+  }
+  double num = C * D * (A * A + A * B + B * B) + (C + D) * A * B * (A + B) + A * A * B * B;
+  return num / ((C + A) * (D + A) * (C + B) * (D + B));
+}
+
+__device__ inline void lerp_zero(const double* xu, double fu, const double* xv, double fv,
+                                 double* o) {
+  double t = fu / (fu - fv);
+  for (int i = 0; i < 3; ++i) o[i] = xu[i] + t * (xv[i] - xu[i]);
+}
+
+__device__ inline double tri_area_acc(const double* a, const double* b, const double* c,
+                                      double* wc) {
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+         cz = e1[0] * e2[1] - e1[1] * e2[0];
+  double ar = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  for (int i = 0; i < 3; ++i) wc[i] += ar * (a[i] + b[i] + c[i]) / 3.0;
+  return ar;
+}
+
+// interface polygon of one tetrahedron: returns its area, adds area*centroid
+__device__ inline double tet_iface(const double X[4][3], const double f[4], double* wc) {
+  int neg = 0;
+  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
+  if (neg == 0 || neg == 4) return 0.0;
+  if (neg == 1 || neg == 3) {
+    bool want_neg = neg == 1;
+    int lone = 0;
+    for (int i = 0; i < 4; ++i)
+      if ((f[i] <= 0.0) == want_neg) lone = i;
+    double Pp[3][3];
+    int k = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (i == lone) continue;
+      if (want_neg) lerp_zero(X[lone], f[lone], X[i], f[i], Pp[k]);
+      else lerp_zero(X[i], f[i], X[lone], f[lone], Pp[k]);
+      ++k;
+    }
+    return tri_area_acc(Pp[0], Pp[1], Pp[2], wc);
+  }
+  int a = -1, b = -1, c = -1, d = -1;
+  for (int i = 0; i < 4; ++i) {
+    if (f[i] <= 0.0) { if (a < 0) a = i; else b = i; }
+    else { if (c < 0) c = i; else d = i; }
+  }
+  double Q[4][3];
+  lerp_zero(X[a], f[a], X[c], f[c], Q[0]);
+  lerp_zero(X[a], f[a], X[d], f[d], Q[1]);
+  lerp_zero(X[b], f[b], X[d], f[d], Q[2]);
+  lerp_zero(X[b], f[b], X[c], f[c], Q[3]);
+  return tri_area_acc(Q[0], Q[1], Q[2], wc) + tri_area_acc(Q[0], Q[2], Q[3], wc);
+}
+
+__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __restrict__ X,
+                                                      const float* __restrict__ Y,
+                                                      const float* __restrict__ Z,
+                                                      const int* __restrict__ cut_pt,
+                                                      const int* __restrict__ counters,
+                                                      CutRec* cut) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= counters[2]) return;
+  int i = cut_pt[id];
+  const double h = P.h;
+  double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
+  double C[8][3], F[8];
+  for (int c = 0; c < 8; ++c) {
+    for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
+    F[c] = phi_d(P, C[c][0], C[c][1], C[c][2]);
+  }
+  double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0};
+  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int t = 0; t < 6; ++t) {
+    int v1 = 1 << perm[t][0];
+    int v2 = v1 | (1 << perm[t][1]);
+    int idx[4] = {0, v1, v2, 7};
+    double Xt[4][3], ft[4];
+    for (int k = 0; k < 4; ++k) {
+      for (int a = 0; a < 3; ++a) Xt[k][a] = C[idx[k]][a];
+      ft[k] = F[idx[k]];
+    }
+    vneg += frac_tet(ft) / 6.0;
+    area += tet_iface(Xt, ft, wc);
+  }
+  CutRec r;
+  r.Vm = vneg;
+  for (int a = 0; a < 3; ++a) {
+    int j = (a + 1) % 3, k = (a + 2) % 3;
+    for (int sd = 0; sd < 2; ++sd) {
+      int b0 = sd << a;
+      int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << k), c11 = c10 | (1 << k);
+      r.Am[2 * a + sd] = 0.5 * (frac_tri(F[c00], F[c10], F[c11]) + frac_tri(F[c00], F[c01], F[c11]));
+    }
+  }
+  r.S = area / (h * h);
+  r.has_jump = area > 0.0;
+  double xg[3] = {p[0], p[1], p[2]};
+  if (area > 0.0) {
+    for (int a = 0; a < 3; ++a) xg[a] = wc[a] / area;
+    for (int it = 0; it < 3; ++it) {  // Newton projection onto phi = 0
+      double g[3];
+      double ph = phi_d(P, xg[0], xg[1], xg[2]);
+      grad_phi_d(P, xg, g);
+      double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+      if (gg <= 1e-300) break;
+      for (int a = 0; a < 3; ++a) xg[a] -= ph * g[a] / gg;
+    }
+  }
+  for (int a = 0; a < 3; ++a) r.xg[a] = xg[a];
+  r.beta = r.has_jump ? beta_d(P, xg) : 0.0;
+  r.alpha = r.has_jump ? alpha_d(xg) : 0.0;
+  r.f[0] = rhs_f<double>(P, 0, p[0], p[1], p[2]);
+  r.f[1] = rhs_f<double>(P, 1, p[0], p[1], p[2]);
+  r.point = i;
+  cut[id] = r;
+}
+
+// ------------------------------------------------------------------------
+// Rows of a cut cell from the outputs of both networks (FP64):
+//   B = h^2 sum_s V^s (k^s U^s - f^s) - sum_s sum_f A^s_f mu^s dU^s_f + h S beta,
+//   dU^s_{sigma i} = h^2 Mt_i + sigma h Dt_i  or  g(q) - U^s  at the cube boundary,
+//   D = sum_s sum_f A^s_f mu^s + h^2 sum_s V^s k^s,   J = U+(xg) - U-(xg) - alpha,
+//   r^2 = (B/D)^2 + lambda J^2;   seeds = d(scale r^2)/d(outputs).
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __restrict__ X,
+                                                      const float* __restrict__ Y,
+                                                      const float* __restrict__ Z,
+                                                      const int* __restrict__ counters,
+                                                      const CutRec* __restrict__ cut,
+                                                      const float* __restrict__ out,
+                                                      float* seeds, float scale, float* r2_out,
+                                                      double* loss_part) {
+  __shared__ double red[128];
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (id < counters[2]) {
+    CutRec c = cut[id];
+    const int i = c.point;
+    const double h = P.h, h2 = h * h;
+    const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
+    const float* o = out + (int64_t)id * 16;
+    double B = 0.0, D = 0.0;
+    double dU[2], dM[2][3], dD[2][3];
+    bool bnd[6];
+    double g[6];
+    for (int f = 0; f < 6; ++f) {
+      int a = f >> 1;
+      double q[3] = {p[0], p[1], p[2]};
+      q[a] += (f & 1) ? h : -h;
+      bnd[f] = fabs(q[a]) >= 1.0;
+      g[f] = bnd[f] ? dirichlet_g<double>(P, q[0], q[1], q[2]) : 0.0;
+    }
+    for (int s = 0; s < 2; ++s) {
+      const double V = s ? 1.0 - c.Vm : c.Vm;
+      const double mu = P.mu[s], k = P.k[s];
+      const double U = (double)o[8 * s];
+      B += h2 * V * (k * U - c.f[s]);
+      D += h2 * V * k;
+      dU[s] = h2 * V * k;
+      for (int a = 0; a < 3; ++a) dM[s][a] = dD[s][a] = 0.0;
+      for (int f = 0; f < 6; ++f) {
+        const int a = f >> 1;
+        const double sg = (f & 1) ? 1.0 : -1.0;
+        const double A = s ? 1.0 - c.Am[f] : c.Am[f];
+        const double w = A * mu;
+        D += w;
+        if (bnd[f]) {
+          // U^s(p) enters the row directly only through Dirichlet faces: the
+          // interior faces carry it inside the increments Mt, Dt
+          B -= w * (g[f] - U);
+          dU[s] += w;
+        } else {
+          B -= w * (h2 * (double)o[8 * s + 1 + a] + sg * h * (double)o[8 * s + 4 + a]);
+          dM[s][a] -= w * h2;
+          dD[s][a] -= w * sg * h;
+        }
+      }
+    }
+    if (c.has_jump) B += h * c.S * c.beta;
+    const double J = c.has_jump ? (double)o[15] - (double)o[7] - c.alpha : 0.0;
+    const double rB = B / D;
+    r2 = rB * rB + P.lambda * J * J;
+    if (seeds) {
+      const double cB = (double)scale * 2.0 * rB / D;
+      const double cJ = (double)scale * 2.0 * P.lambda * J;
+      float* sd = seeds + (int64_t)id * 16;
+      for (int s = 0; s < 2; ++s) {
+        sd[8 * s] = (float)(cB * dU[s]);
+        for (int a = 0; a < 3; ++a) {
+          sd[8 * s + 1 + a] = (float)(cB * dM[s][a]);
+          sd[8 * s + 4 + a] = (float)(cB * dD[s][a]);
+        }
+        sd[8 * s + 7] = c.has_jump ? (float)(s ? cJ : -cJ) : 0.f;
+      }
+    }
+    if (r2_out) r2_out[i] = (float)r2;
+  }
+  red[threadIdx.x] = r2;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// ------------------------------------------------------------------------
+// Weight staging.  Hidden layer l of net s (W[u][k], u = output unit):
+//   wt  : FP32 transpose, wt[((s*(L-1) + l-1)*H + k)*H + u] = W[u][k]
+//   wtc : 16-bit copy in the tensor-core shared-memory image (H = 128):
+//         8-row x 128-byte atoms with the 128-byte XOR swizzle,
+//         atom (cb, ug) at (cb*16 + ug)*1024 for column block cb = k/64 and
+//         row group ug = u/8.
+// ------------------------------------------------------------------------
+__host__ __device__ inline uint32_t tc_tile_offset(int u, int c) {
+  int cb = c >> 6, cc = c & 63, ug = u >> 3, r = u & 7;
+  return (uint32_t)((cb * 16 + ug) * 1024 + r * 128 + ((((cc >> 3) ^ r) & 7) << 4) + (cc & 7) * 2);
+}
+
+__global__ void k_prep_weights(ProbDev P, const float* __restrict__ params, float* wt, void* wtc,
+                               int prec) {
+  const int H = P.H, L = P.L;
+  const int64_t per = (int64_t)H * H;
+  const int64_t total = 2 * (int64_t)(L - 1) * per;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t blk = e / per;
+    int s = (int)(blk / (L - 1)), l = (int)(blk % (L - 1)) + 1;
+    int rem = (int)(e % per);
+    int u = rem / H, k = rem % H;
+    const float w = params[(int64_t)s * P.p_net + 4 * H + (int64_t)(l - 1) * (per + H) + rem];
+    if (wt) wt[blk * per + (int64_t)k * H + u] = w;
+    if (wtc && H == 128) {
+      char* base = (char*)wtc + blk * per * 2;
+      if (prec == NBM_PREC_FP16)
+        *(__half*)(base + tc_tile_offset(u, k)) = __float2half_rn(w);
+      else
+        *(__nv_bfloat16*)(base + tc_tile_offset(u, k)) = __float2bfloat16_rn(w);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Finish: loss (fixed-order sums), then gradient reduction over CTA partials
+// (fixed order) and, when training, Adam (Kingma & Ba, bias-corrected).
+// ------------------------------------------------------------------------
+__global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __restrict__ clp,
+                       int nclp, double scale, double* loss, int64_t* step, float* loss_hist,
+                       int64_t hist_base, int* status, float b1, float b2, float* corr) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < nlp; j += 256) s += lp[j];
+  for (int j = threadIdx.x; j < nclp; j += 256) s += clp[j];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double L = red[0] * scale;
+    *loss = L;
+    if (!isfinite(L)) atomicOr(status, 1);
+    if (step) {
+      int64_t t = *step + 1;
+      *step = t;
+      if (loss_hist) loss_hist[t - hist_base - 1] = (float)L;
+      corr[0] = (float)(1.0 - pow((double)b1, (double)t));
+      corr[1] = (float)(1.0 - pow((double)b2, (double)t));
+    }
+  }
+}
+
+__global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpart,
+                              const int* __restrict__ flag, float* grad_out, float* params,
+                              float* m, float* v, float lr, float b1, float b2, float eps,
+                              const float* corr, const double* loss, float* wt, void* wtc,
+                              int prec) {
+  const int64_t pn = P.p_net;
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 2 * pn) return;
+  const int s = (int)(j / pn);
+  const int64_t jj = j - s * pn;
+  float g = 0.f;
+  for (int c = 0; c < grid; ++c)
+    if (flag[2 * c + s]) g += gpart[((int64_t)c * 2 + s) * pn + jj];
+  if (grad_out) grad_out[j] = g;
+  if (!params) return;
+  if (!isfinite(*loss)) return;  // non-finite step: skip the update
+  float mj = b1 * m[j] + (1.f - b1) * g;
+  float vj = b2 * v[j] + (1.f - b2) * g * g;
+  m[j] = mj;
+  v[j] = vj;
+  float mh = mj / corr[0], vh = vj / corr[1];
+  float w = params[j] - lr * mh / (sqrtf(vh) + eps);
+  params[j] = w;
+  // restage hidden weights for the next step
+  const int H = P.H;
+  const int64_t per = (int64_t)H * H;
+  if (jj >= 4 * H && jj < 4 * H + (int64_t)(P.L - 1) * (per + H)) {
+    int64_t q = jj - 4 * H;
+    int l = (int)(q / (per + H)) + 1;
+    int64_t rem = q % (per + H);
+    if (rem < per) {
+      int u = (int)(rem / H), k = (int)(rem % H);
+      int64_t blk = (int64_t)s * (P.L - 1) + (l - 1);
+      if (wt) wt[blk * per + (int64_t)k * H + u] = w;
+      if (wtc && H == 128) {
+        char* base = (char*)wtc + blk * per * 2;
+        if (prec == NBM_PREC_FP16) *(__half*)(base + tc_tile_offset(u, k)) = __float2half_rn(w);
+        else *(__nv_bfloat16*)(base + tc_tile_offset(u, k)) = __float2bfloat16_rn(w);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------
+cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
+                                   const int64_t* step_dev, int64_t step_host, int64_t n,
+                                   int64_t n_band, Workspace& ws, cudaStream_t st) {
+  int nb = (int)((n + kBlk - 1) / kBlk);
+  k_sample_classify<<<nb, kBlk, 0, st>>>(P, pts_in, seed, step_dev, step_host, n, n_band, ws.x,
+                                         ws.y, ws.z, ws.cls, ws.blockcnt, nb);
+  k_scan_counts<<<1, 1024, 0, st>>>(ws.blockcnt, nb, ws.counters);
+  k_scatter<<<nb, kBlk, 0, st>>>(ws.cls, n, ws.blockcnt, nb, ws.list_minus, ws.list_plus,
+                                 ws.cut_pt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
+  int nb = (int)((n + 127) / 128);
+  k_cut_geometry<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
+                                float* r2_out, Workspace& ws, cudaStream_t st) {
+  int nb = (int)((n + 127) / 128);
+  k_cut_residual<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.counters, ws.cut, ws.cut_out,
+                                     want_seeds ? ws.cut_seed : nullptr, scale, r2_out,
+                                     ws.cut_loss_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,
+                                cudaStream_t st) {
+  k_prep_weights<<<2 * (P.L - 1) * 16, 256, 0, st>>>(P, params, ws.wt,
+                                                     (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
+                          float* params, float* m, float* v, float* grad_out, float lr, float b1,
+                          float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
+                          Workspace& ws, cudaStream_t st) {
+  int ncb = (int)((n + 127) / 128);
+  k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb, 1.0 / (double)n, ws.loss,
+                            adam ? ws.step : nullptr, loss_hist, hist_base, ws.status, b1, b2,
+                            ws.corr);
+  if (adam || want_grad) {
+    int64_t tot = 2 * P.p_net;
+    k_reduce_adam<<<(int)((tot + 255) / 256), 256, 0, st>>>(
+        P, grid, ws.gpart, ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps,
+        ws.corr, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nbm
