@@ -61,6 +61,7 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
   P.kf[1] = (float)d.k_plus;
   const int64_t H = d.width;
   P.p_net = 4 * H + (int64_t)(d.n_hidden - 1) * (H * H + H) + H + 1;
+  P.gstride = (P.p_net + 3) & ~(int64_t)3;  // 16-byte aligned slices
 }
 
 static void ws_free(Workspace& w) {
@@ -101,7 +102,7 @@ static int ws_reserve(Problem& pb, int64_t n) {
   NBM_CUDA(dalloc(w.loss_part, grid));
   NBM_CUDA(dalloc(w.cut_loss_part, ncb));
   NBM_CUDA(dalloc(w.loss, 1));
-  NBM_CUDA(dalloc(w.gpart, (size_t)grid * 2 * pb.p_net));
+  NBM_CUDA(dalloc(w.gpart, (size_t)grid * 2 * ((pb.p_net + 3) & ~(int64_t)3)));
   NBM_CUDA(dalloc(w.gpart_flag, 2 * (size_t)grid));
   NBM_CUDA(dalloc(w.wt, 2 * (size_t)(L - 1) * H * H));
   NBM_CUDA(dalloc((uint16_t*&)w.wtc, 2 * (size_t)(L - 1) * H * H));

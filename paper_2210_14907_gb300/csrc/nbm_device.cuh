@@ -25,6 +25,7 @@ struct ProbDev {
   float r0f, ampf, ltf, lpf;
   float muf[2], kf[2];
   int64_t p_net;  // parameters per network
+  int64_t gstride;  // per-CTA partial-gradient slice stride (p_net rounded up to 4)
 };
 
 // ---------------------------------------------------------------------------

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256, 1) k_step_fp32(ProbDev P, StepArgs a) {
     }
     if (lane == 0) stage[(size_t)w * nsmall + nsmall - 1] = gbo;
     __syncthreads();
-    float* gp = a.gpart + ((int64_t)blockIdx.x * 2 + net) * P.p_net;
+    float* gp = a.gpart + ((int64_t)blockIdx.x * 2 + net) * P.gstride;
     for (int idx = tid; idx < nsmall; idx += blockDim.x) {
       float s = 0.f;
       for (int ww = 0; ww < 8; ++ww) s += stage[(size_t)ww * nsmall + idx];
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256, 1) k_step_fp32(ProbDev P, StepArgs a) {
               }
           }
         }
-        float* gp = a.gpart + ((int64_t)blockIdx.x * 2 + net) * P.p_net + 4 * H +
+        float* gp = a.gpart + ((int64_t)blockIdx.x * 2 + net) * P.gstride + 4 * H +
                     (int64_t)(g - 1) * (H * H + H);
 #pragma unroll
         for (int i = 0; i < UB; ++i)

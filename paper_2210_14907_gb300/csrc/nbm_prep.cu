@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 
 #include "nbm_device.cuh"
+#include "nbm_tc_ptx.cuh"
 
 namespace nbm {
 
@@ -455,10 +456,7 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
 //         atom (cb, ug) at (cb*16 + ug)*1024 for column block cb = k/64 and
 //         row group ug = u/8.
 // ------------------------------------------------------------------------
-__host__ __device__ inline uint32_t tc_tile_offset(int u, int c) {
-  int cb = c >> 6, cc = c & 63, ug = u >> 3, r = u & 7;
-  return (uint32_t)((cb * 16 + ug) * 1024 + r * 128 + ((((cc >> 3) ^ r) & 7) << 4) + (cc & 7) * 2);
-}
+__host__ __device__ inline uint32_t tc_tile_offset(int u, int c) { return tc::img_off(u, c); }
 
 __global__ void k_prep_weights(ProbDev P, const float* __restrict__ params, float* wt, void* wtc,
                                int prec) {
@@ -526,7 +524,7 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
   const int64_t jj = j - s * pn;
   float g = 0.f;
   for (int c = 0; c < grid; ++c)
-    if (flag[2 * c + s]) g += gpart[((int64_t)c * 2 + s) * pn + jj];
+    if (flag[2 * c + s]) g += gpart[((int64_t)c * 2 + s) * P.gstride + jj];
   if (grad_out) grad_out[j] = g;
   if (!params) return;
   if (!isfinite(*loss)) return;  // non-finite step: skip the update

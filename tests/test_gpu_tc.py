@@ -1,0 +1,110 @@
+"""Parity of the BF16 tcgen05 path with the FP64 oracle (through the C ABI).
+
+Tolerances (mixed path): residual and loss relative error <= 2e-3, gradient
+relative error (2-norm) <= 5e-3.  Residual error is measured on r_p, norm-wise.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pyoracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+RES_TOL, LOSS_TOL, GRAD_TOL = 2e-3, 2e-3, 5e-3
+
+
+def _nbm():
+    import paper_2210_14907_gb300 as nbm
+    return nbm
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _pair(geom, L, h, mu_p, prec, fp64=-1, band=0.0):
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=geom, n_hidden=L, width=128, precision=prec, mu_minus=1.0,
+                        mu_plus=mu_p, h=h, band_fraction=band, fp64_stencil=fp64)
+    o = O.make_problem(geometry=geom, n_hidden=L, width=128, mu_minus=1.0, mu_plus=mu_p, h=h)
+    return nbm.Problem(d), o
+
+
+CASES = [
+    # geometry, L, h, mu+, n_uniform, n_shell, fp64 rows
+    (O.GEOM_SPHERE, 3, 2 / 128, 10.0, 1500, 500, 0),   # C2 architecture
+    (O.GEOM_FLOWER, 4, 2 / 256, 100.0, 700, 700, 0),   # C3 architecture, many cut cells
+    (O.GEOM_SPHERE, 4, 2 / 1024, 10.0, 600, 200, 1),   # C4 resolution, FP64 rows
+    (O.GEOM_SPHERE, 2, 2 / 64, 10.0, 800, 200, 0),     # one hidden GEMM
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"g{c[0]}L{c[1]}n{round(2 / c[2])}")
+def test_bf16_residual_loss_gradient_match_oracle(case):
+    nbm = _nbm()
+    geom, L, h, mu_p, nu, ns, fp64 = case
+    prob, o = _pair(geom, L, h, mu_p, nbm.PREC_BF16, fp64)
+    pts = inputs.mixed_points(nu, ns, seed=L + 100)
+    th = inputs.glorot_params(128, L, seed=8, bias_scale=0.1)
+    L_ref, r2_ref = O.loss(o, th.astype(np.float64), pts, want_r2=True)
+    _, g_ref = O.loss_grad(o, th.astype(np.float64), pts)
+    tp = torch.from_numpy(th).cuda()
+    tx = torch.from_numpy(pts.astype(np.float32)).cuda()
+    loss, r2 = prob.residual(tp, tx)
+    loss2, g = prob.loss_grad(tp, tx)
+    er = _rel(np.sqrt(r2.cpu().numpy()), np.sqrt(r2_ref))
+    el = abs(loss - L_ref) / L_ref
+    eg = _rel(g.cpu().numpy(), g_ref)
+    print(f"bf16 case {case[:3]}: residual {er:.2e} loss {el:.2e} grad {eg:.2e}")
+    assert er <= RES_TOL and el <= LOSS_TOL and abs(loss2 - L_ref) / L_ref <= LOSS_TOL
+    assert eg <= GRAD_TOL
+
+
+def test_bf16_ragged_and_tiny_batches():
+    nbm = _nbm()
+    prob, o = _pair(O.GEOM_SPHERE, 3, 2 / 32, 10.0, nbm.PREC_BF16)
+    th = inputs.glorot_params(128, 3, seed=5, bias_scale=0.1)
+    for n in (1, 15, 17, 33):
+        pts = inputs.mixed_points(max(n - 6, 0), 0, seed=n)[-n:]
+        L_ref, g_ref = O.loss_grad(o, th.astype(np.float64), pts)
+        loss, g = prob.loss_grad(torch.from_numpy(th).cuda(), torch.from_numpy(pts.astype(np.float32)).cuda())
+        assert abs(loss - L_ref) / L_ref <= LOSS_TOL, n
+        assert _rel(g.cpu().numpy(), g_ref) <= GRAD_TOL, n
+
+
+def test_bf16_training_tracks_fp32_training():
+    """C2 shape, 30 steps at a reduced batch: the mixed path's loss curve follows the FP32 path."""
+    nbm = _nbm()
+    res = {}
+    for prec in (nbm.PREC_FP32, nbm.PREC_BF16):
+        d = nbm.config("C2", precision=prec)
+        prob = nbm.Problem(d)
+        tp = torch.from_numpy(inputs.glorot_params(128, 3, seed=0)).cuda()
+        m = torch.zeros_like(tp)
+        v = torch.zeros_like(tp)
+        hist = torch.zeros(30, device="cuda")
+        prob.train_steps(tp, m, v, 0, 30, 16384, lr=1e-3, seed=1, loss_hist=hist)
+        res[prec] = hist.cpu().numpy()
+    h32, h16 = res[nbm.PREC_FP32], res[nbm.PREC_BF16]
+    assert np.all(np.isfinite(h16)) and h16[-1] < h16[0]
+    assert np.max(np.abs(h16 - h32) / h32) < 2e-2
+
+
+def test_bf16_deterministic_and_resumable():
+    nbm = _nbm()
+    d = nbm.config("C3")
+    prob = nbm.Problem(d)
+    th = inputs.glorot_params(128, 4, seed=1)
+    outs = []
+    for split in ((6,), (3, 3)):
+        tp = torch.from_numpy(th).cuda()
+        m = torch.zeros_like(tp)
+        v = torch.zeros_like(tp)
+        s = 0
+        for k in split:
+            s = prob.train_steps(tp, m, v, s, k, 20000, seed=3)
+        outs.append((tp, m, v))
+    for x, y in zip(outs[0], outs[1]):
+        assert torch.equal(x, y)
