@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the fused NBM training step (arXiv 2210.14907, Sec. 3).
+
+One step = sample 262,144 collocation points -> cut-cell geometry -> two-network
+7-point stencil forward (BF16 tcgen05 hidden GEMMs) -> FV balance / jump rows
+-> squared loss -> backward -> Adam, on the sphere-interface workload with
+h = 2/128 and two 3->128->128->128->1 tanh networks (the mixed-precision
+configuration).  Prints one JSON line (rank 0).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Timing: every timed step is bracketed by CUDA events on the launching stream;
+L2 is flushed (256 MiB write) between timed steps, outside the events.  The
+fused kernel is additionally timed live (libnbm's event profiler) for the
+roofline line.  Under torchrun each rank trains its own replica on its own GPU
+(weak scaling, no collective on the data path); the reported time is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("collocation pts/sec per train step (mixed vs FP32, same L∞ err); "
+          "% tensor peak")
+UNIT = "collocation points/s"
+WORKLOAD = ("sphere interface (r0=0.5, mu-=1, mu+=10), h=2/128, 262144 uniform collocation "
+            "points per step, two 3->128->128->128->1 tanh MLPs, BF16 tcgen05 hidden GEMMs "
+            "with FP32 accumulate, Adam lr 1e-3")
+BATCH = 262_144
+# DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture
+# summarised in profiles/fused_step_tc_C2.md; None when the kernel changed since.
+FUSED_TRAFFIC_BYTES = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["bf16_tflops"], d["bf16_tflops_sustained"], d["hbm_gbs"], "measured"
+    except Exception:
+        return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = str(gpu_index)
+        self.rows = []
+        self.proc = None
+        self.mark = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[0] == self.idx:
+                self.rows.append((time.time(), parts))
+
+    def begin(self):
+        self.mark = time.time()
+
+    def end(self):
+        self.mark_end = time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [p for (t, p) in self.rows if self.mark and self.mark <= t <= self.mark_end + 0.05]
+        if not rows:
+            rows = [p for (_, p) in self.rows[-5:]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows), "reasons": reasons}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(config_name="C2", target_s=10.0):
+    """The FP64 oracle (OpenMP over points, all host cores) on a bounded sample of
+    the workload: loss + gradient + Adam on a sub-batch of sampled points."""
+    import numpy as np
+
+    from oracle import pyoracle as O
+    O.build()
+    geom = O.GEOM_SPHERE
+    pr = O.make_problem(geometry=geom, n_hidden=3, width=128, mu_minus=1.0, mu_plus=10.0,
+                        h=2.0 / 128)
+    P = 2 * O.params_per_net(pr)
+    rng = np.random.default_rng(0)
+    th = rng.uniform(-0.1, 0.1, P)
+    m = np.zeros(P)
+    v = np.zeros(P)
+
+    def run(n):
+        pts = O.sample_points(pr, 1, 1, n, 0)
+        t0 = time.perf_counter()
+        _, g = O.loss_grad(pr, th, pts)
+        O.adam_step(th, m, v, g, 1)
+        return time.perf_counter() - t0
+
+    t1 = run(1024)
+    n = int(min(BATCH, max(1024, 1024 * target_s / max(t1, 1e-3))))
+    t = run(n)
+    cores = os.cpu_count()
+    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} sampled points of the {BATCH}-point step (loss, gradient, Adam), "
+                      f"FP64 oracle, OpenMP {cores} threads, {t:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cb = cpu_baseline(target_s=min(20.0, 4.0 * max(1, args.steps // 10)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * BATCH / cb["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH,
+                       "reference": "FP64 CPU oracle (the paper publishes no code)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp32-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2210_14907_gb300 as nbm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    burst, sustained, hbm, peak_src = _peaks()
+
+    def timed_run(prec, steps, warmup, profile):
+        d = nbm.config("C2", precision=prec)
+        prob = nbm.Problem(d)
+        params = nbm.xavier_init(d, seed=0, device=dev)
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        seed = 1 + rank
+        st = prob.train_steps(params, m, v, 0, warmup, BATCH, seed=seed)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        torch.cuda.synchronize()
+        _barrier(ws)
+        torch.cuda.synchronize()
+        if profile:
+            prob.profile(True)
+        t_wall = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            st = prob.train_steps(params, m, v, st, 1, BATCH, seed=seed)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        _barrier(ws)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        fused = prob.profile(False) if profile else (None, None)
+        assert torch.isfinite(params).all()
+        return ms, fused, t_wall, prob, params, m, v, st
+
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.3)
+    clk.begin()
+    ms, (fused_ms, fused_n), wall, prob, params, m, v, st = timed_run(
+        nbm.PREC_BF16, args.steps, args.warmup, True)
+    clk.end()
+    ms_max = _max_over_ranks(ws, ms)
+    value = ws * args.steps * BATCH / (ms_max / 1e3)
+
+    # plain FP32 path on the same workload (the comparison the metric asks for)
+    k32 = args.fp32_steps if args.fp32_steps is not None else max(5, args.steps // 40)
+    ms32, _, _, _, _, _, _, _ = timed_run(nbm.PREC_FP32, k32, 3, False)
+    ms32 = _max_over_ranks(ws, ms32)
+    value32 = ws * k32 * BATCH / (ms32 / 1e3)
+    clk.stop()
+
+    # end to end through the public API: per step, the step's collocation points
+    # are copied from pinned host memory and the step's loss is read back
+    k_e2e = max(10, args.steps // 20)
+    rng = np.random.default_rng(rank)
+    host = torch.from_numpy(
+        (-1.0 + rng.integers(1, 2**23, size=(k_e2e, BATCH, 3)) * 2.0**-22).astype(np.float32)
+    ).pin_memory()
+    dpts = torch.empty(BATCH, 3, device=dev)
+    hist = torch.zeros(1, device=dev)
+    hloss = torch.zeros(1).pin_memory()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for k in range(k_e2e):
+        dpts.copy_(host[k], non_blocking=True)
+        st = prob.train_steps(params, m, v, st, 1, BATCH, seed=1 + rank, pts=dpts, loss_hist=hist)
+        hloss.copy_(hist, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        assert np.isfinite(hloss.item())
+    e2e_s = _max_over_ranks(ws, time.perf_counter() - t0)
+    e2e = {"value": ws * k_e2e * BATCH / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": BATCH * 3 * 4, "d2h_bytes_per_step": 4, "steps": k_e2e}
+
+    # roofline of the fused tcgen05 kernel: algorithmic FLOPs = 7 stencil
+    # evaluations x (forward + input-gradient + weight-gradient) x 2 H^2 per
+    # hidden GEMM layer, per collocation point
+    H, NG = 128, 2
+    flops_pt = 21 * NG * 2 * H * H
+    per_launch = flops_pt * BATCH
+    t_launch = fused_ms / max(fused_n, 1) / 1e3
+    achieved = per_launch / t_launch / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": sustained,
+            "peak_kind": f"bf16 dense, {peak_src} sustained", "unit": "TFLOP/s",
+            "frac": achieved / sustained, "kernel": "k_step_tc (fused forward+residual+backward)",
+            "launch_ms": t_launch * 1e3, "flops_per_launch": per_launch,
+            "traffic": FUSED_TRAFFIC_BYTES}
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH, "h": "2/128",
+                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},
+            "fp32_path": {"value": value32, "unit": UNIT, "steps": k32,
+                          "ms_per_step": ms32 / k32, "mixed_speedup": value / value32},
+            "roofline": roof, "e2e": e2e, "gpu_launches": 9 * args.steps,
+            "clocks": clk.summary(), "wall_s": wall}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -134,11 +134,14 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
  * bias-corrected Adam update (Kingma & Ba) with constant lr.
  *   params, adam_m, adam_v  [P] updated in place (m, v zero for a fresh run)
  *   step_io (host)          in: steps already taken; out: += n_steps
+ *   pts [n_steps][batch][3] or NULL: caller-supplied collocation points of
+ *                           each step (e.g. points staged from the host);
+ *                           NULL draws them on the device as described above
  *   loss_hist [n_steps] or NULL: loss of each step before its update.
  * Asynchronous: step_io is updated on the host immediately. */
 int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v, int64_t* step_io,
                     int n_steps, int64_t batch, float lr, float beta1, float beta2, float eps,
-                    uint64_t seed, float* loss_hist, nbm_stream_t stream);
+                    uint64_t seed, const float* pts, float* loss_hist, nbm_stream_t stream);
 
 /* Evaluates the trained surrogate on the (n+1)^3 nodes -1 + i*2/n of the
  * cube, each node with the network of its side of Gamma (phi <= 0: minus).
@@ -157,6 +160,14 @@ int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision, flo
  * Returns NBM_ERR_NOT_CONVERGED (with u_out filled) if max_iter is reached. */
 int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
                       int* iters_out, double* relres_out, nbm_stream_t stream);
+
+/* Optional timing of the fused stencil-step kernel (the dominant kernel of a
+ * training step).  enable = 1 clears the counters and brackets every later
+ * launch of that kernel with CUDA events on its own stream; enable = 0 stops
+ * recording, synchronizes, and returns the summed device time (ms) and the
+ * number of timed launches through the host pointers (either may be NULL).
+ * Up to 65536 launches are recorded; later ones are not timed. */
+int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused_launches_out);
 
 #ifdef __cplusplus
 }

@@ -138,7 +138,9 @@ def load_library(build_if_missing: bool = True):
     L.nbm_loss_grad.argtypes = [P, P, P, C.c_int64, C.c_uint64, C.c_int64, P,
                                 C.POINTER(C.c_double), P]
     L.nbm_train_steps.argtypes = [P, P, P, P, C.POINTER(C.c_int64), C.c_int, C.c_int64,
-                                  C.c_float, C.c_float, C.c_float, C.c_float, C.c_uint64, P, P]
+                                  C.c_float, C.c_float, C.c_float, C.c_float, C.c_uint64, P, P, P]
+    L.nbm_profile.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.nbm_profile.restype = C.c_int
     L.nbm_eval_grid.argtypes = [P, P, C.c_int, C.c_int, P, P]
     L.nbm_grid_cg_solve.argtypes = [P, C.c_int, C.c_double, C.c_int, P, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double), P]
@@ -223,14 +225,22 @@ class Problem:
         return (loss.value if sync else None), grad
 
     def train_steps(self, params, m, v, step, n_steps, batch, lr=1e-3, beta1=0.9, beta2=0.999,
-                    eps=1e-8, seed=1, loss_hist=None, stream=None):
+                    eps=1e-8, seed=1, loss_hist=None, pts=None, stream=None):
         for t in (params, m, v):
             _dev(t)
+        _dev(pts)
         st = C.c_int64(step)
         _check(self.lib.nbm_train_steps(self.handle, _ptr(params), _ptr(m), _ptr(v),
                                         C.byref(st), n_steps, batch, lr, beta1, beta2, eps, seed,
-                                        _ptr(loss_hist), _stream(stream)))
+                                        _ptr(pts), _ptr(loss_hist), _stream(stream)))
         return st.value
+
+    def profile(self, enable):
+        """enable=True starts timing the fused kernel; enable=False returns (ms, launches)."""
+        ms = C.c_double(0.0)
+        n = C.c_int64(0)
+        _check(self.lib.nbm_profile(self.handle, 1 if enable else 0, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def eval_grid(self, params, n, precision=PREC_FP16, out=None, stream=None):
         _dev(params)

@@ -184,6 +184,25 @@ static cudaError_t launch_step(Problem& pb, const ProbDev& P, const StepArgs& a,
   return launch_step_tc(P, a, pb.ws.grid, pb.desc.precision, st);
 }
 
+// the fused MODE_TRAIN launch, bracketed by events while profiling is on
+static cudaError_t launch_timed(Problem& pb, const ProbDev& P, const StepArgs& a, cudaStream_t st) {
+  Profiler& pr = pb.prof;
+  const bool rec = pr.on && pr.n < Profiler::kMax;
+  if (rec) {
+    if (!pr.ev[2 * pr.n]) {
+      cudaEventCreate(&pr.ev[2 * pr.n]);
+      cudaEventCreate(&pr.ev[2 * pr.n + 1]);
+    }
+    cudaEventRecord(pr.ev[2 * pr.n], st);
+  }
+  cudaError_t e = launch_step(pb, P, a, st);
+  if (rec) {
+    cudaEventRecord(pr.ev[2 * pr.n + 1], st);
+    ++pr.n;
+  }
+  return e;
+}
+
 // sample/classify .. cut rows; leaves seeds of cut cells in the workspace
 static int front_stages(Problem& pb, const ProbDev& P, const float* params, const float* pts,
                         int64_t n, uint64_t seed, const int64_t* step_dev, int64_t step_host,
@@ -251,11 +270,34 @@ int nbm_init_problem(const nbm_problem_desc* d, nbm_problem** out) {
 int nbm_destroy(nbm_problem* p) {
   if (!p) return NBM_OK;
   ws_free(p->pb.ws);
+  for (cudaEvent_t& e : p->pb.prof.ev)
+    if (e) cudaEventDestroy(e);
   delete p;
   return NBM_OK;
 }
 
 int64_t nbm_param_count(const nbm_problem* p) { return p ? 2 * p->pb.p_net : -1; }
+
+int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused_launches_out) {
+  if (!p) return fail(NBM_ERR_INVALID_ARG, "NULL problem");
+  Profiler& pr = p->pb.prof;
+  if (enable) {
+    pr.on = true;
+    pr.n = 0;
+    return NBM_OK;
+  }
+  pr.on = false;
+  double ms = 0.0;
+  for (int i = 0; i < pr.n; ++i) {
+    NBM_CUDA(cudaEventSynchronize(pr.ev[2 * i + 1]));
+    float t = 0.f;
+    NBM_CUDA(cudaEventElapsedTime(&t, pr.ev[2 * i], pr.ev[2 * i + 1]));
+    ms += t;
+  }
+  if (fused_ms_out) *fused_ms_out = ms;
+  if (fused_launches_out) *fused_launches_out = pr.n;
+  return NBM_OK;
+}
 
 int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, float* pts_out,
                       nbm_stream_t stream) {
@@ -320,7 +362,7 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
   rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st);
   if (rc) return rc;
   StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)n);
-  NBM_CUDA(launch_step(pb, P, a, st));
+  NBM_CUDA(launch_timed(pb, P, a, st));
   NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, true, nullptr, nullptr, nullptr, grad_out, 0.f,
                          0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st));
   if (loss_out) return read_loss(pb, loss_out, st);
@@ -329,7 +371,7 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
 
 int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v, int64_t* step_io,
                     int n_steps, int64_t batch, float lr, float beta1, float beta2, float eps,
-                    uint64_t seed, float* loss_hist, nbm_stream_t stream) {
+                    uint64_t seed, const float* pts, float* loss_hist, nbm_stream_t stream) {
   if (!p || !params || !adam_m || !adam_v || !step_io)
     return fail(NBM_ERR_INVALID_ARG, "NULL argument");
   if (n_steps < 0) return fail(NBM_ERR_INVALID_ARG, "n_steps < 0");
@@ -351,10 +393,11 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
   NBM_CUDA(cudaMemcpyAsync(pb.ws.step, step_io, sizeof(int64_t), cudaMemcpyHostToDevice, st));
   NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
   for (int k = 0; k < n_steps; ++k) {
-    rc = front_stages(pb, P, params, nullptr, batch, seed, pb.ws.step, 0, true, nullptr, st);
+    const float* pk = pts ? pts + (int64_t)k * batch * 3 : nullptr;
+    rc = front_stages(pb, P, params, pk, batch, seed, pb.ws.step, 0, true, nullptr, st);
     if (rc) return rc;
     StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)batch);
-    NBM_CUDA(launch_step(pb, P, a, st));
+    NBM_CUDA(launch_timed(pb, P, a, st));
     NBM_CUDA(launch_finish(P, batch, pb.ws.grid, true, false, params, adam_m, adam_v, nullptr, lr,
                            beta1, beta2, eps, loss_hist, base, prec, pb.ws, st));
   }

@@ -176,8 +176,13 @@ __device__ __forceinline__ float act_tanh(float x) {
 }
 template <bool FAST>
 __device__ __forceinline__ float rcp(float x) {
-  if constexpr (FAST) return __frcp_rn(x);
-  else return 1.0f / x;
+  if constexpr (FAST) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  } else {
+    return 1.0f / x;
+  }
 }
 
 // ---------------------------------------------------------------------------

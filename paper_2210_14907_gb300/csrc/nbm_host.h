@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nbm.h"
 
 namespace nbm {
@@ -79,7 +81,15 @@ struct Workspace {
   int* status = nullptr;            // [1]
 };
 
+struct Profiler {
+  static constexpr int kMax = 65536;
+  bool on = false;
+  int n = 0;
+  std::vector<cudaEvent_t> ev = std::vector<cudaEvent_t>(2 * kMax, nullptr);
+};
+
 struct Problem {
+  Profiler prof;
   nbm_problem_desc desc;
   int device = 0;
   int num_sms = 0;

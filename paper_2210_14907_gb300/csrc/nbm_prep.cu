@@ -296,7 +296,7 @@ __device__ inline double tet_iface(const double X[4][3], const double f[4], doub
   return tri_area_acc(Q[0], Q[1], Q[2], wc) + tri_area_acc(Q[0], Q[2], Q[3], wc);
 }
 
-__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __restrict__ X,
+__global__ void __launch_bounds__(32) k_cut_geometry(ProbDev P, const float* __restrict__ X,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ Z,
                                                       const int* __restrict__ cut_pt,
@@ -571,8 +571,9 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
 }
 
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
-  int nb = (int)((n + 127) / 128);
-  k_cut_geometry<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
+  // one warp per block: the few cut cells spread over every SM (FP64, latency bound)
+  int nb = (int)((n + 31) / 32);
+  k_cut_geometry<<<nb, 32, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
   return cudaGetLastError();
 }
 

@@ -560,6 +560,16 @@ static cudaError_t launch_tc_t(const ProbDev& P, const StepArgs& a, int grid, cu
 
 cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int prec, cudaStream_t st) {
   if (P.H != 128) return cudaErrorInvalidValue;
+  // The tanh/reciprocal of the epilogue run on the SFU (tanh.approx, rcp.approx,
+  // relative error ~2^-11): every value they produce is rounded to BF16
+  // (2^-9) before the next GEMM, so they do not add an error class.  The
+  // fine-h mode (FP64 rows) keeps the accurate functions: there the BF16
+  // rounding alone already uses most of the gradient tolerance.
+  if (prec == NBM_PREC_BF16 && !P.fp64) {
+    if (P.L == 2) return launch_tc_t<2, true, true>(P, a, grid, st);
+    if (P.L == 3) return launch_tc_t<3, true, true>(P, a, grid, st);
+    if (P.L == 4) return launch_tc_t<4, true, true>(P, a, grid, st);
+  }
   if (prec == NBM_PREC_BF16) {
     if (P.L == 2) return launch_tc_t<2, true, false>(P, a, grid, st);
     if (P.L == 3) return launch_tc_t<3, true, false>(P, a, grid, st);
