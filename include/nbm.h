@@ -169,6 +169,29 @@ int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* 
  * Up to 65536 launches are recorded; later ones are not timed. */
 int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused_launches_out);
 
+/* nbm_loss_grad without any device allocation, for callers that cannot call
+ * cudaMalloc while they run: code that executes inside a CUDA-graph capture
+ * or under a caller-owned memory pool, a real-time or embedded host that
+ * forbids allocation after start-up, or a plugin whose host framework owns
+ * all device memory.  (The paper has no counterpart: this is a deployment
+ * variant of the loss-and-gradient call.)
+ *   Arguments, results and precision path are those of nbm_loss_grad; the
+ *   caller still owns params, pts, grad_out.
+ *   Scratch: one static device array of about 12 MB inside libnbm, held on
+ *   every GPU that loads the library until the process exits.  Limits:
+ *   n <= 16384 points, width <= 128, n_hidden <= 4; the fused kernels run on
+ *   at most 16 CTAs.  Larger requests return NBM_ERR_INVALID_ARG.
+ *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
+ *   on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   once per device); make that first call before any stream capture.
+ *   Every call shares the array and leaves its contents behind (the status
+ *   word is cleared at the start of each call); calls whose work overlaps on
+ *   the GPU (different streams, host threads or problems) race on it and
+ *   must be serialized by the caller. */
+int nbm_loss_grad_static(nbm_problem* p, const float* params, const float* pts, int64_t n,
+                         uint64_t seed, int64_t step, float* grad_out, double* loss_out,
+                         nbm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

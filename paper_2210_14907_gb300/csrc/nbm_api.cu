@@ -241,6 +241,12 @@ struct nbm_problem {
   Problem pb;
 };
 
+namespace nbm {
+void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+const nbm_problem_desc& problem_desc(const nbm_problem* p) { return p->pb.desc; }
+int problem_num_sms(const nbm_problem* p) { return p->pb.num_sms; }
+}  // namespace nbm
+
 extern "C" {
 
 const char* nbm_last_error(void) { return g_err; }

@@ -98,6 +98,10 @@ struct Problem {
 };
 
 void make_prob_dev(const nbm_problem_desc& d, ProbDev& P);
+// accessors for translation units that do not see the problem object
+void set_error_message(const char* msg);
+const nbm_problem_desc& problem_desc(const nbm_problem* p);
+int problem_num_sms(const nbm_problem* p);
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
