@@ -65,7 +65,8 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
 }
 
 static void ws_free(Workspace& w) {
-  void* ptrs[] = {w.x, w.y, w.z, w.cls, w.blockcnt, w.list_minus, w.list_plus, w.cut_pt,
+  void* ptrs[] = {w.x, w.y, w.z, w.cls, w.blockcnt, w.list_minus, w.list_plus, w.cut_pt, w.rec,
+                  w.rec_cut,
                   w.counters, w.cut, w.cut_out, w.cut_seed, w.loss_part, w.cut_loss_part, w.loss,
                   w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.corr, w.status};
   for (void* p : ptrs)
@@ -97,6 +98,8 @@ static int ws_reserve(Problem& pb, int64_t n) {
   NBM_CUDA(dalloc(w.cut_pt, cap));
   NBM_CUDA(dalloc(w.counters, 4));
   NBM_CUDA(dalloc(w.cut, cap));
+  NBM_CUDA(dalloc(w.rec, 2 * (size_t)cap + 64));
+  NBM_CUDA(dalloc(w.rec_cut, (size_t)cap + 32));
   NBM_CUDA(dalloc(w.cut_out, 16 * (size_t)cap));
   NBM_CUDA(dalloc(w.cut_seed, 16 * (size_t)cap));
   NBM_CUDA(dalloc(w.loss_part, grid));
@@ -165,6 +168,8 @@ static StepArgs base_args(Problem& pb, const float* params, int mode, float scal
   a.list[1] = w.list_plus;
   a.counters = w.counters;
   a.cut = w.cut;
+  a.rec = w.rec;
+  a.rec_cut = w.rec_cut;
   a.params = params;
   a.wt = w.wt;
   a.wtc = w.wtc;
@@ -211,6 +216,7 @@ static int front_stages(Problem& pb, const ProbDev& P, const float* params, cons
   NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, n), w,
                                   st));
   NBM_CUDA(launch_cut_geometry(P, n, w, st));
+  if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(n, w, st));
   StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)n);
   NBM_CUDA(launch_step(pb, P, a, st));
   NBM_CUDA(launch_cut_residual(P, n, (float)(1.0 / (double)n), want_seeds, r2_out, w, st));

@@ -119,10 +119,26 @@ __device__ inline float exact_u<float>(int s, float x, float y, float z) {
   return x * x + y * y + z * z;
 }
 
+// Problem constants in the working precision: the FP32 paths read the FP32
+// copies (an FP64 operation is slow on this part and would sit on the
+// critical path of the residual rows).
+template <typename T>
+__device__ __forceinline__ T pc_h(const ProbDev& P) {
+  if constexpr (sizeof(T) == 4) return P.hf; else return P.h;
+}
+template <typename T>
+__device__ __forceinline__ T pc_mu(const ProbDev& P, int s) {
+  if constexpr (sizeof(T) == 4) return P.muf[s]; else return P.mu[s];
+}
+template <typename T>
+__device__ __forceinline__ T pc_k(const ProbDev& P, int s) {
+  if constexpr (sizeof(T) == 4) return P.kf[s]; else return P.k[s];
+}
+
 template <typename T>
 __device__ inline T rhs_f(const ProbDev& P, int s, T x, T y, T z) {
   T u = exact_u<T>(s, x, y, z);
-  T mu = (T)P.mu[s], k = (T)P.k[s];
+  T mu = pc_mu<T>(P, s), k = pc_k<T>(P, s);
   return s == 0 ? k * u + mu * u : k * u - (T)6 * mu;
 }
 
@@ -251,7 +267,7 @@ __device__ __forceinline__ float tanh_stencil_bwd(float t, float s0, float mo, f
 template <typename T>
 __device__ inline T uncut_residual(const ProbDev& P, int s, float px, float py, float pz,
                                    const float out[8], T scale, float seeds[8]) {
-  const T h = (T)P.h, h2 = h * h, mu = (T)P.mu[s], k = (T)P.k[s];
+  const T h = pc_h<T>(P), h2 = h * h, mu = pc_mu<T>(P, s), k = pc_k<T>(P, s);
   const T U = (T)out[0];
   const T x[3] = {(T)px, (T)py, (T)pz};
   T Bt = k * U - rhs_f<T>(P, s, x[0], x[1], x[2]);
@@ -287,6 +303,58 @@ __device__ inline T uncut_residual(const ProbDev& P, int s, float px, float py, 
     seeds[4 + i] = (float)(c * dD[i]);
   }
   seeds[7] = 0.f;
+  return r * r;
+}
+
+// The same rows evaluated by the 8 lanes of one point (lanes 8j .. 8j+7 of a
+// warp; lane k holds output column k): lane 0 the reaction/source term, lanes
+// 1..6 one cell face each (face f = 2 axis + side), summed with shuffles.
+// Every lane returns r^2 and receives the seed of its own column.  All 32
+// lanes of the warp must call it.
+template <typename T>
+__device__ inline T uncut_residual8(const ProbDev& P, int s, float px, float py, float pz,
+                                    float out_k, int k, int lane, T scale, float& seed_k) {
+  const unsigned full = 0xffffffffu;
+  const int base = lane & ~7;
+  const T h = pc_h<T>(P), h2 = h * h, mu = pc_mu<T>(P, s), kk = pc_k<T>(P, s);
+  const T U = (T)__shfl_sync(full, out_k, base);
+  const bool face = k >= 1 && k <= 6;
+  const int f = face ? k - 1 : 0;
+  const int ax = f >> 1;
+  const T sg = (f & 1) ? (T)1 : (T)-1;
+  const T Mt = (T)__shfl_sync(full, out_k, base + 1 + ax);
+  const T Dt = (T)__shfl_sync(full, out_k, base + 4 + ax);
+  T term = 0;
+  int bnd = 0;
+  if (k == 0) {
+    term = kk * U - rhs_f<T>(P, s, (T)px, (T)py, (T)pz);
+  } else if (face) {
+    const T qx = (T)px + (ax == 0 ? sg * h : (T)0);
+    const T qy = (T)py + (ax == 1 ? sg * h : (T)0);
+    const T qz = (T)pz + (ax == 2 ? sg * h : (T)0);
+    const T qa = ax == 0 ? qx : (ax == 1 ? qy : qz);
+    bnd = fabs(qa) >= (T)1;
+    term = bnd ? -mu * (dirichlet_g<T>(P, qx, qy, qz) - U) / h2 : -mu * (Mt + sg * Dt / h);
+  }
+  T Bt = term;
+  int nb = bnd;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    Bt += __shfl_xor_sync(full, Bt, o);
+    nb += __shfl_xor_sync(full, nb, o);
+  }
+  const T D = (T)6 * mu + h2 * kk;
+  const T r = h2 * Bt / D;
+  const T c = scale * (T)2 * r * h2 / D;
+  // Dirichlet flags of the two faces of this column's axis
+  const int ia = (k >= 4 && k <= 6) ? k - 4 : ((k >= 1 && k <= 3) ? k - 1 : 0);
+  const int bm = __shfl_sync(full, bnd, base + 1 + 2 * ia);
+  const int bp = __shfl_sync(full, bnd, base + 2 + 2 * ia);
+  T sd = 0;
+  if (k == 0) sd = c * (kk + (T)nb * mu / h2);
+  else if (k <= 3) sd = c * (-mu * (T)((bm ? 0 : 1) + (bp ? 0 : 1)));
+  else if (k <= 6) sd = c * (-mu * (T)((bp ? 0 : 1) - (bm ? 0 : 1)) / h);
+  seed_k = (float)sd;
   return r * r;
 }
 

@@ -32,6 +32,15 @@ struct CutRec {
   int has_jump;    // S > 0
 };
 
+// One collocation point of a tensor-core tile, gathered in list order so that a
+// tile's 16 records are one contiguous 512-byte block.
+struct PRec {
+  float x, y, z;     // point
+  float gx, gy, gz;  // interface point of a cut cell (0 otherwise)
+  int pt;            // point index, -1 for padding
+  int cutj;          // -1: uncut; else 2*cut_id + has_jump
+};
+
 // Everything the fused step kernels read or write.
 struct StepArgs {
   const float* x;
@@ -40,6 +49,8 @@ struct StepArgs {
   const int* list[2];     // phase lists; entry >= 0 point index, < 0 cut id -(e+1)
   const int* counters;    // [0] n-, [1] n+, [2] n_cut
   const CutRec* cut;
+  const PRec* rec;        // tile records of the two phase lists (tensor-core path)
+  const PRec* rec_cut;    // tile records of the cut list (tensor-core path)
   const float* params;    // FP32 parameter pair
   const float* wt;        // FP32 transposed hidden weights [net][layer][k][u]
   const void* wtc;        // 16-bit hidden weights in the tensor-core layout [net][layer]
@@ -66,6 +77,8 @@ struct Workspace {
   int* cut_pt = nullptr;
   int* counters = nullptr;  // [4]
   CutRec* cut = nullptr;
+  PRec* rec = nullptr;      // [2 cap + 64]
+  PRec* rec_cut = nullptr;  // [cap + 32]
   float* cut_out = nullptr;
   float* cut_seed = nullptr;
   double* loss_part = nullptr;      // [grid]
@@ -108,6 +121,7 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
+cudaError_t launch_gather_tiles(int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
                                 float* r2_out, Workspace& ws, cudaStream_t st);
 cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,

@@ -32,6 +32,8 @@ constexpr size_t kScratchBytes =
     + 3 * align256(kStaticMaxPoints * 4)                   // two phase lists, cut list
     + align256(4 * 4)                                      // counters
     + align256(kStaticMaxPoints * sizeof(CutRec))          // cut cells
+    + align256((2 * kStaticMaxPoints + 64) * sizeof(PRec))  // tile records, phase lists
+    + align256((kStaticMaxPoints + 32) * sizeof(PRec))      // tile records, cut list
     + 2 * align256(kStaticMaxPoints * 16 * 4)              // cut outputs and seeds
     + align256(kStaticMaxGrid * 8)                         // loss partials
     + align256(((kStaticMaxPoints + 127) / 128) * 8)       // cut loss partials
@@ -123,6 +125,8 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   w.cut_pt = carve<int>(cur, kStaticMaxPoints * 4);
   w.counters = carve<int>(cur, 16);
   w.cut = carve<CutRec>(cur, kStaticMaxPoints * sizeof(CutRec));
+  w.rec = carve<PRec>(cur, (2 * kStaticMaxPoints + 64) * sizeof(PRec));
+  w.rec_cut = carve<PRec>(cur, (kStaticMaxPoints + 32) * sizeof(PRec));
   w.cut_out = carve<float>(cur, kStaticMaxPoints * 16 * 4);
   w.cut_seed = carve<float>(cur, kStaticMaxPoints * 16 * 4);
   w.loss_part = carve<double>(cur, kStaticMaxGrid * 8);
@@ -150,6 +154,7 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
           : 0;
   if (e == cudaSuccess) e = launch_sample_classify(P, pts, seed, nullptr, step, n, n_band, w, st);
   if (e == cudaSuccess) e = launch_cut_geometry(P, n, w, st);
+  if (e == cudaSuccess && prec != NBM_PREC_FP32) e = launch_gather_tiles(n, w, st);
   StepArgs a;
   memset(&a, 0, sizeof(a));
   a.x = w.x;
@@ -159,6 +164,8 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   a.list[1] = w.list_plus;
   a.counters = w.counters;
   a.cut = w.cut;
+  a.rec = w.rec;
+  a.rec_cut = w.rec_cut;
   a.params = params;
   a.wt = w.wt;
   a.wtc = w.wtc;

@@ -449,6 +449,66 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
 }
 
 // ------------------------------------------------------------------------
+// Tile records of the tensor-core kernel: tile t of 16 points, t < T0 from the
+// minus list, then the plus list (each padded to a multiple of 16), and the
+// cut list on its own.  One thread per record; the grid covers the worst case.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather_tiles(const int* __restrict__ counters,
+                                                      const int* __restrict__ list_m,
+                                                      const int* __restrict__ list_p,
+                                                      const int* __restrict__ cut_pt,
+                                                      const float* __restrict__ X,
+                                                      const float* __restrict__ Y,
+                                                      const float* __restrict__ Z,
+                                                      const CutRec* __restrict__ cut, PRec* rec,
+                                                      PRec* rec_cut, int64_t cap) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nm = counters[0], np = counters[1], nc = counters[2];
+  const int64_t T0 = (nm + 15) / 16, T1 = (np + 15) / 16, Tc = (nc + 15) / 16;
+  auto fill = [&](int e, PRec& o) {
+    int pt, cid = -1;
+    if (e >= 0) {
+      pt = e;
+    } else {
+      cid = -e - 1;
+      pt = cut_pt[cid];
+    }
+    o.x = X[pt];
+    o.y = Y[pt];
+    o.z = Z[pt];
+    o.pt = pt;
+    if (cid >= 0) {
+      const CutRec& c = cut[cid];
+      o.gx = (float)c.xg[0];
+      o.gy = (float)c.xg[1];
+      o.gz = (float)c.xg[2];
+      o.cutj = 2 * cid + (c.has_jump ? 1 : 0);
+    } else {
+      o.gx = o.gy = o.gz = 0.f;
+      o.cutj = -1;
+    }
+  };
+  PRec o;
+  o.x = o.y = o.z = o.gx = o.gy = o.gz = 0.f;
+  o.pt = -1;
+  o.cutj = -1;
+  if (r < 16 * (T0 + T1)) {
+    const int64_t t = r / 16, k = r % 16;
+    const int64_t slot = (t < T0 ? t : t - T0) * 16 + k;
+    if (t < T0 ? slot < nm : slot < np) fill((t < T0 ? list_m : list_p)[slot], o);
+    rec[r] = o;
+  }
+  if (r < 16 * Tc) {
+    PRec c;
+    c.x = c.y = c.z = c.gx = c.gy = c.gz = 0.f;
+    c.pt = -1;
+    c.cutj = -1;
+    if (r < nc) fill(-(int)r - 1, c);
+    rec_cut[r] = c;
+  }
+}
+
+// ------------------------------------------------------------------------
 // Weight staging.  Hidden layer l of net s (W[u][k], u = output unit):
 //   wt  : FP32 transpose, wt[((s*(L-1) + l-1)*H + k)*H + u] = W[u][k]
 //   wtc : 16-bit copy in the tensor-core shared-memory image (H = 128):
@@ -583,6 +643,14 @@ cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool w
   k_cut_residual<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.counters, ws.cut, ws.cut_out,
                                      want_seeds ? ws.cut_seed : nullptr, scale, r2_out,
                                      ws.cut_loss_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_tiles(int64_t n, Workspace& ws, cudaStream_t st) {
+  const int64_t worst = 2 * n + 32;  // both lists padded
+  k_gather_tiles<<<(int)((worst + 255) / 256), 256, 0, st>>>(
+      ws.counters, ws.list_minus, ws.list_plus, ws.cut_pt, ws.x, ws.y, ws.z, ws.cut, ws.rec,
+      ws.rec_cut, n);
   return cudaGetLastError();
 }
 

@@ -1,13 +1,13 @@
 // nbm_tc.cu -- the mixed-precision fused NBM step on the 5th-generation tensor
 // cores (tcgen05, TMEM accumulators), arXiv 2210.14907 Sec. 3 / Fig. 2.
 //
-// One persistent CTA per SM, 8 warps.  A tile is 16 collocation points x 8
+// One persistent CTA per SM, 16 warps.  A tile is 16 collocation points x 8
 // columns (centre value, symmetric and antisymmetric stencil increments of the
 // three axes in difference form, and the interface-point value of cut cells),
 // i.e. 128 GEMM columns.  Every hidden layer is one 128 x 128 x 128 product
 // D[unit][col] = W[unit][k] A[k][col] on tcgen05 with 16-bit operands and FP32
 // accumulation in TMEM; warp w reads TMEM lanes 32(w%4).. (one unit per
-// thread) for columns 64(w/4).. (8 points).  The epilogue applies the tanh
+// thread) for columns 32(w/4).. (4 points).  The epilogue applies the tanh
 // stencil layer in FP32 and writes the next 16-bit operand image to shared
 // memory.  The first layer (K = 3), the output layer (H -> 1, a warp
 // transpose-reduction), the residual rows and the seeds stay FP32 (FP64 rows
@@ -33,12 +33,7 @@ namespace {
 
 constexpr int kTPts = 16;  // points per tile
 constexpr int kImg = 32768;
-constexpr int kMisc = 1536;
-
-struct PInfo {
-  int pt, cut_id, valid, jump;
-  float x, y, z, gx, gy, gz;
-};
+constexpr int kMisc = 2048;
 
 template <bool BF>
 struct F16T;
@@ -66,6 +61,23 @@ struct F16T<false> {
 };
 
 template <bool BF>
+__device__ __forceinline__ void store8o(unsigned char* img, uint32_t off, const float* o) {
+  uint4 pk;
+  pk.x = F16T<BF>::pack(o[0], o[1]);
+  pk.y = F16T<BF>::pack(o[2], o[3]);
+  pk.z = F16T<BF>::pack(o[4], o[5]);
+  pk.w = F16T<BF>::pack(o[6], o[7]);
+  *reinterpret_cast<uint4*>(img + off) = pk;
+}
+template <bool BF>
+__device__ __forceinline__ void load8o(const unsigned char* img, uint32_t off, float* o) {
+  const uint4 pk = *reinterpret_cast<const uint4*>(img + off);
+  float2 a = F16T<BF>::unpack(pk.x), b = F16T<BF>::unpack(pk.y), c = F16T<BF>::unpack(pk.z),
+         d = F16T<BF>::unpack(pk.w);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
+}
+template <bool BF>
 __device__ __forceinline__ void store8(unsigned char* img, int row, int col0, const float* o) {
   uint4 pk;
   pk.x = F16T<BF>::pack(o[0], o[1]);
@@ -83,44 +95,38 @@ __device__ __forceinline__ void load8(const unsigned char* img, int row, int col
   o[4] = c.x; o[5] = c.y; o[6] = d.x; o[7] = d.y;
 }
 
-// Sum of v[0..63] over the 32 lanes of the warp; on return lane l holds the
-// sums of columns base, base+1.
-__device__ __forceinline__ void warp_transpose_reduce64(float (&v)[64], int lane, float& s0,
-                                                        float& s1, int& base) {
+// Sum of v[0..31] over the 32 lanes of the warp: on return lane l holds the
+// sum of column l (recursive halving, one exchange per value).
+__device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane, float& s) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < 16; ++i) {
     const bool hi = lane & 16;
-    const float keep = hi ? v[32 + i] : v[i], send = hi ? v[i] : v[32 + i];
+    const float keep = hi ? v[16 + i] : v[i], send = hi ? v[i] : v[16 + i];
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < 8; ++i) {
     const bool hi = lane & 8;
-    const float keep = hi ? v[16 + i] : v[i], send = hi ? v[i] : v[16 + i];
+    const float keep = hi ? v[8 + i] : v[i], send = hi ? v[i] : v[8 + i];
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 4; ++i) {
     const bool hi = lane & 4;
-    const float keep = hi ? v[8 + i] : v[i], send = hi ? v[i] : v[8 + i];
+    const float keep = hi ? v[4 + i] : v[i], send = hi ? v[i] : v[4 + i];
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     const bool hi = lane & 2;
-    const float keep = hi ? v[4 + i] : v[i], send = hi ? v[i] : v[4 + i];
+    const float keep = hi ? v[2 + i] : v[i], send = hi ? v[i] : v[2 + i];
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
+  {
     const bool hi = lane & 1;
-    const float keep = hi ? v[2 + i] : v[i], send = hi ? v[i] : v[2 + i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    const float keep = hi ? v[1] : v[0], send = hi ? v[0] : v[1];
+    s = keep + __shfl_xor_sync(0xffffffffu, send, 1);
   }
-  base = ((lane & 16) ? 32 : 0) + ((lane & 8) ? 16 : 0) + ((lane & 4) ? 8 : 0) +
-         ((lane & 2) ? 4 : 0) + ((lane & 1) ? 2 : 0);
-  s0 = v[0];
-  s1 = v[1];
 }
 
 }  // namespace
@@ -128,10 +134,16 @@ __device__ __forceinline__ void warp_transpose_reduce64(float (&v)[64], int lane
 size_t tc_smem_bytes(int L) { return (size_t)(2 * L - 1) * kImg + 1024 + kMisc; }
 int tc_supported(int H, int L) { return H == 128 && L >= 2 && L <= 4; }
 
-template <int L, bool BF, bool FAST>
-__global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
+// Column convention.  SCALED: the difference columns hold mt = mu/h^2 and
+// dt = del/h (keeps FP16 operands out of the subnormal range).  Unscaled (BF16,
+// whose exponent range is that of FP32): they hold mu and del themselves,
+// which saves the rescaling in every epilogue; the output stage converts to
+// the scaled convention of the residual rows.
+template <int L, bool BF, bool FAST, bool SCALED>
+__global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
   constexpr int H = 128;
   constexpr int NG = L - 1;  // hidden GEMM layers
+  constexpr int kPPT = 4;    // points per thread (16 warps = 4 lane quadrants x 4 column groups)
   constexpr uint32_t NCOLS = (NG + 1) * 128 <= 256 ? 256 : 512;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -140,18 +152,25 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
   unsigned char* misc = sm + (2 * L - 1) * kImg;
   uint64_t* bar_w = (uint64_t*)misc;
   uint64_t* bar_mma = (uint64_t*)(misc + 8);
-  uint32_t* tslot = (uint32_t*)(misc + 16);
-  PInfo* pinfo = (PInfo*)(misc + 64);                 // 16 x 40 B
-  float* seeds = (float*)(misc + 64 + 16 * 40 + 64);  // 128 floats
-  double* loss_red = (double*)(misc + 64 + 16 * 40 + 64 + 512);  // 8 doubles
-  float* red = (float*)(Aimg + (L - 1) * kImg);       // [4][128] scratch (forward end only)
-  float* outv = red + 4 * 128;                        // [128]
+  uint64_t* bar_p = (uint64_t*)(misc + 16);
+  uint32_t* tslot = (uint32_t*)(misc + 24);
+  PRec* pbuf = (PRec*)(misc + 64);                 // [2][16] tile records (double buffer)
+  float* seeds = (float*)(misc + 64 + 1024);       // 128 floats
+  double* loss_red = (double*)(misc + 64 + 1024 + 512);  // 16 doubles
+  float* red = (float*)(Aimg + (L - 1) * kImg);    // [4][128] scratch (forward end only)
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int q = w & 3, ch = w >> 2;
-  const int u = 32 * q + lane;
+  const int q = w & 3, cg = w >> 2;
+  const int u = 32 * q + lane;   // unit (TMEM lane) of this thread
+  const int col0 = 32 * cg;      // first of this thread's 32 columns (points 4cg .. 4cg+3)
+  // image byte offset of (unit u, point 4cg + j): the row part is fixed per
+  // thread, the 16-byte chunk is ((4cg + j) mod 8) xor (u mod 8)
+  const uint32_t row_off = (uint32_t)(((cg >> 1) * 16 + (u >> 3)) * 1024 + (u & 7) * 128);
+  const uint32_t pbase = (uint32_t)((cg & 1) << 2), uxor = (uint32_t)(u & 7);
+  auto poff = [&](int j) -> uint32_t { return row_off + ((((pbase + j) ^ uxor) & 7u) << 4); };
   const bool train = a.mode == MODE_TRAIN;
-  const float hf = P.hf, h2f = P.h2f, ihf = P.inv_hf, ih2f = P.inv_h2f;
+  const float hs = SCALED ? P.hf : 1.f, h2s = SCALED ? P.h2f : 1.f;
+  const float ihs = SCALED ? P.inv_hf : 1.f, ih2s = SCALED ? P.inv_h2f : 1.f;
   const uint32_t id_fwd = idesc_f16(BF, false, true);
   const uint32_t id_dgr = idesc_f16(BF, true, true);
   const uint32_t id_wgr = idesc_f16(BF, false, false);
@@ -159,6 +178,7 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
   if (tid == 0) {
     mbar_init(smem_u32(bar_w), 1);
     mbar_init(smem_u32(bar_mma), 1);
+    mbar_init(smem_u32(bar_p), 1);
     fence_mbar_init();
   }
   if (w == 0) tmem_alloc(smem_u32(tslot), NCOLS);
@@ -168,7 +188,7 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
   const uint32_t tmem = *tslot;
   const uint32_t d_tm = tmem;                      // D: columns [0, 128)
   const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-  uint32_t ph_w = 0, ph_mma = 0;
+  uint32_t ph_w = 0, ph_mma = 0, ph_p = 0;
   bool aborted = false;
 
   const int nm = a.counters[0], np = a.counters[1], nc = a.counters[2];
@@ -183,6 +203,16 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
   const int64_t tb = (int64_t)blockIdx.x * T / gridDim.x;
   const int64_t te = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
 
+  // tile records: one 512-byte bulk copy per tile, fetched a tile ahead
+  const PRec* recs = a.mode == MODE_CUT_FWD ? a.rec_cut : a.rec;
+  auto prefetch = [&](int64_t tau) {
+    const int64_t r = a.mode == MODE_CUT_FWD ? (tau < T0 ? tau : tau - T0) : tau;
+    fence_proxy_async();
+    mbar_expect_tx(smem_u32(bar_p), 16 * sizeof(PRec));
+    bulk_g2s(smem_u32(pbuf + 16 * (tau & 1)), recs + 16 * r, 16 * sizeof(PRec), smem_u32(bar_p));
+  };
+  if (tid == 0 && tb < te) prefetch(tb);
+
   // per-net constants of this thread's unit
   float w1[3] = {0.f, 0.f, 0.f}, b1 = 0.f, bh[NG], wo = 0.f, bo = 0.f;
 #pragma unroll
@@ -191,7 +221,8 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
   float gW1[3] = {0.f, 0.f, 0.f}, gb1 = 0.f, gbh[NG], gwo = 0.f, gbo = 0.f;
 #pragma unroll
   for (int g = 0; g < NG; ++g) gbh[g] = 0.f;
-  double loss_acc = 0.0;
+  float loss_acc = 0.f;     // per-thread FP32 sum of r^2 (FP32 rows)
+  double loss_acc_d = 0.0;  // per-thread FP64 sum of r^2 (FP64 rows)
   int cur_net = -1;
   bool first_tile = true;
   int wrote0 = 0, wrote1 = 0;
@@ -212,38 +243,40 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
     float* gp = a.gpart + ((int64_t)blockIdx.x * 2 + net) * P.gstride;
 #pragma unroll 1
     for (int g = 1; g <= NG; ++g) {
-      float* dst = gp + 4 * H + (int64_t)(g - 1) * (H * H + H) + (int64_t)u * H + 64 * ch;
-#pragma unroll 1
-      for (int b = 0; b < 2; ++b) {
-        float v[32];
-        tmem_ld32(tmem + 128u * g + lane_base + 64 * ch + 32 * b, v);
+      float* dst = gp + 4 * H + (int64_t)(g - 1) * (H * H + H) + (int64_t)u * H + col0;
+      float v[32];
+      tmem_ld32(tmem + 128u * g + lane_base + col0, v);
 #pragma unroll
-        for (int i = 0; i < 32; i += 4)
-          *reinterpret_cast<float4*>(dst + 32 * b + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-      }
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
     }
-    // small parameters: the two column halves of a unit are combined in smem
-    float* stage = (float*)Aimg;  // [128 units][8]
+    // small parameters: the four column groups of a unit are combined in smem
+    float* stage = (float*)Aimg;  // [4 groups][128 units][8]
     fence_before_sync();
     __syncthreads();
-    if (ch == 1) {
-      float* s = stage + 8 * u;
+    {
+      float* s = stage + (cg * 128 + u) * 8;
       s[0] = gW1[0]; s[1] = gW1[1]; s[2] = gW1[2]; s[3] = gb1; s[4] = gwo;
 #pragma unroll
       for (int g = 0; g < NG; ++g) s[5 + g] = gbh[g];
     }
     __syncthreads();
-    if (ch == 0) {
-      const float* s = stage + 8 * u;
-      gp[3 * u] = gW1[0] + s[0];
-      gp[3 * u + 1] = gW1[1] + s[1];
-      gp[3 * u + 2] = gW1[2] + s[2];
-      gp[3 * H + u] = gb1 + s[3];
+    if (cg == 0) {
+      float t[8];
 #pragma unroll
-      for (int g = 0; g < NG; ++g)
-        gp[4 * H + (int64_t)g * (H * H + H) + (int64_t)H * H + u] = gbh[g] + s[5 + g];
+      for (int k = 0; k < 8; ++k) t[k] = stage[u * 8 + k];
+#pragma unroll
+      for (int c2 = 1; c2 < 4; ++c2)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[k] += stage[(c2 * 128 + u) * 8 + k];
+      gp[3 * u] = t[0];
+      gp[3 * u + 1] = t[1];
+      gp[3 * u + 2] = t[2];
+      gp[3 * H + u] = t[3];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) gp[4 * H + (int64_t)g * (H * H + H) + (int64_t)H * H + u] = t[5 + g];
       const int64_t oo = 4 * H + (int64_t)NG * (H * H + H);
-      gp[oo + u] = gwo + s[4];
+      gp[oo + u] = t[4];
       if (tid == 0) gp[oo + H] = gbo;
     }
     gW1[0] = gW1[1] = gW1[2] = gb1 = gwo = gbo = 0.f;
@@ -285,64 +318,53 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
         break;
       }
     }
-    // ---- tile points
-    if (tid < kTPts) {
-      const int64_t slot = local * kTPts + tid;
-      PInfo pi;
-      pi.valid = 0;
-      pi.cut_id = -1;
-      pi.pt = 0;
-      pi.jump = 0;
-      pi.x = pi.y = pi.z = pi.gx = pi.gy = pi.gz = 0.f;
-      if (a.mode == MODE_CUT_FWD) {
-        if (slot < nc) {
-          pi.valid = 1;
-          pi.cut_id = (int)slot;
-        }
-      } else if (slot < (net ? np : nm)) {
-        pi.valid = 1;
-        const int e = a.list[net][slot];
-        if (e < 0) pi.cut_id = -e - 1;
-        else pi.pt = e;
+    // ---- tile records (prefetched during the previous tile)
+    {
+      bool ok = mbar_wait_bounded(smem_u32(bar_p), ph_p);
+      ph_p ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(a.status, 2);
+        aborted = true;
+        break;
       }
-      if (pi.valid && pi.cut_id >= 0) {
-        const CutRec& cr = a.cut[pi.cut_id];
-        pi.pt = cr.point;
-        pi.jump = cr.has_jump;
-        pi.gx = (float)cr.xg[0];
-        pi.gy = (float)cr.xg[1];
-        pi.gz = (float)cr.xg[2];
-      }
-      if (pi.valid) {
-        pi.x = a.x[pi.pt];
-        pi.y = a.y[pi.pt];
-        pi.z = a.z[pi.pt];
-      }
-      pinfo[tid] = pi;
+      if (tid == 0 && tau + 1 < te) prefetch(tau + 1);
     }
-    __syncthreads();
+    const PRec* pr = pbuf + 16 * (tau & 1);
+    // seed of a cut point (from the cut-row kernel): load it now, use it after
+    // the forward, so that the global-memory latency is hidden
+    float cut_sd = 0.f;
+    if (train && tid < 128) {
+      const PRec& pc = pr[tid >> 3];
+      if (pc.pt >= 0 && pc.cutj >= 0)
+        cut_sd = __ldg(a.cut_seed + (int64_t)(pc.cutj >> 1) * 16 + net * 8 + (tid & 7));
+    }
 
-    // ---- layer 1 (3 -> H) in FP32; exact increments mt = 0, dt_i = W1[u][i]
-#pragma unroll 2
-    for (int pp = 0; pp < 8; ++pp) {
-      const int p = 8 * ch + pp;
-      const PInfo pi = pinfo[p];
-      const float z = fmaf(w1[0], pi.x, fmaf(w1[1], pi.y, fmaf(w1[2], pi.z, b1)));
-      const float t = act_tanh<FAST>(z);
-      float o[8];
-      o[0] = t;
+    // ---- layer 1 (3 -> H) in FP32; exact increments mu = 0, del_i = h W1[u][i]
+    {
+      const float dl1[3] = {SCALED ? w1[0] : w1[0] * P.hf, SCALED ? w1[1] : w1[1] * P.hf,
+                            SCALED ? w1[2] : w1[2] * P.hf};
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-        tanh_stencil_fwd<FAST>(t, 0.f, w1[i], hf, h2f, ihf, ih2f, o[1 + i], o[4 + i]);
-      o[7] = pi.jump ? act_tanh<FAST>(fmaf(w1[0], pi.gx, fmaf(w1[1], pi.gy, fmaf(w1[2], pi.gz, b1))))
-                     : 0.f;
-      store8<BF>(Aimg, u, 8 * p, o);
+      for (int pp = 0; pp < kPPT; ++pp) {
+        const int p = 4 * cg + pp;
+        const PRec pi = pr[p];
+        const float z = fmaf(w1[0], pi.x, fmaf(w1[1], pi.y, fmaf(w1[2], pi.z, b1)));
+        const float t = act_tanh<FAST>(z);
+        float o[8];
+        o[0] = t;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          tanh_stencil_fwd<FAST>(t, 0.f, dl1[i], hs, h2s, ihs, ih2s, o[1 + i], o[4 + i]);
+        const bool jump = pi.cutj >= 0 && (pi.cutj & 1);
+        o[7] = jump ? act_tanh<FAST>(fmaf(w1[0], pi.gx, fmaf(w1[1], pi.gy, fmaf(w1[2], pi.gz, b1))))
+                    : 0.f;
+        store8o<BF>(Aimg, poff(pp), o);
+      }
     }
     fence_proxy_async();
     __syncthreads();
 
     // ---- hidden layers on the tensor cores
-    float last[64];
+    float last[32];
 #pragma unroll 1
     for (int g = 1; g <= NG; ++g) {
       if (tid == 0) {
@@ -359,26 +381,23 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
       float bb = bh[0];
 #pragma unroll
       for (int i = 1; i < NG; ++i) bb = (g - 1 == i) ? bh[i] : bb;
+      float acc[32];
+      tmem_ld32(d_tm + lane_base + col0, acc);
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        float acc[32];
-        tmem_ld32(d_tm + lane_base + 64 * ch + 32 * b, acc);
+      for (int j = 0; j < kPPT; ++j) {
+        const float* c = acc + 8 * j;
+        float o[8];
+        const float t = act_tanh<FAST>(c[0] + bb);
+        o[0] = t;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float* c = acc + 8 * j;
-          float o[8];
-          const float t = act_tanh<FAST>(c[0] + bb);
-          o[0] = t;
+        for (int i = 0; i < 3; ++i)
+          tanh_stencil_fwd<FAST>(t, c[1 + i], c[4 + i], hs, h2s, ihs, ih2s, o[1 + i], o[4 + i]);
+        o[7] = act_tanh<FAST>(c[7] + bb);
+        if (g < NG) {
+          store8o<BF>(Aimg + g * kImg, poff(j), o);
+        } else {
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
-            tanh_stencil_fwd<FAST>(t, c[1 + i], c[4 + i], hf, h2f, ihf, ih2f, o[1 + i], o[4 + i]);
-          o[7] = act_tanh<FAST>(c[7] + bb);
-          if (g < NG) {
-            store8<BF>(Aimg + g * kImg, u, 8 * (8 * ch + 4 * b + j), o);
-          } else {
-#pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) last[32 * b + 8 * j + c2] = o[c2];
-          }
+          for (int c2 = 0; c2 < 8; ++c2) last[8 * j + c2] = o[c2];
         }
       }
       fence_before_sync();
@@ -387,58 +406,62 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
     }
     if (aborted) break;
 
-    // ---- output layer (H -> 1) in FP32
+    // ---- output layer (H -> 1) in FP32: sum over the 32 units of the warp,
+    // then over the four lane quadrants
     {
-      float v[64];
+      float v[32];
 #pragma unroll
-      for (int i = 0; i < 64; ++i) v[i] = wo * last[i];
-      float s0, s1;
-      int base;
-      warp_transpose_reduce64(v, lane, s0, s1, base);
-      red[q * 128 + 64 * ch + base] = s0;
-      red[q * 128 + 64 * ch + base + 1] = s1;
+      for (int i = 0; i < 32; ++i) v[i] = wo * last[i];
+      float s;
+      warp_transpose_reduce32(v, lane, s);  // lane l: column col0 + l
+      red[q * 128 + col0 + lane] = s;
     }
     __syncthreads();
+    // ---- output columns and residual rows: thread (p, k) owns column 8p + k
+    // of point p; the centre term (k = 0) and the six cell faces (k = 1..6)
+    // are combined across the 8 lanes of the point
     if (tid < 128) {
-      const int c = tid;
-      float s = red[c] + red[128 + c] + red[256 + c] + red[384 + c];
-      if ((c & 7) == 0 || (c & 7) == 7) s += bo;
-      outv[c] = s;
-    }
-    __syncthreads();
-
-    // ---- residual rows and seeds (one thread per point)
-    if (tid < kTPts) {
-      const PInfo pi = pinfo[tid];
-      float sd[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float out[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) out[c] = outv[8 * tid + c];
+      const int c = tid, p = c >> 3, k = c & 7;
+      float o = red[c] + red[128 + c] + red[256 + c] + red[384 + c];
+      if (k == 0 || k == 7) o += bo;
+      // scaled convention of the rows: U, Mt_i = M_i/h^2, Dt_i = D_i/h, U(x_G)
+      if (!SCALED) o *= (k >= 1 && k <= 3) ? P.inv_h2f : ((k >= 4 && k <= 6) ? P.inv_hf : 1.f);
+      const PRec pi = pr[p];
+      const bool valid = pi.pt >= 0, is_cut = pi.cutj >= 0;
+      float sd = 0.f;
       if (a.mode == MODE_CUT_FWD) {
-        if (pi.valid) {
-#pragma unroll
-          for (int c = 0; c < 8; ++c) a.cut_out[(int64_t)pi.cut_id * 16 + net * 8 + c] = out[c];
+        if (valid) a.cut_out[(int64_t)(pi.cutj >> 1) * 16 + net * 8 + k] = o;
+      } else {
+        float sr, r2;
+        double r2d = 0.0;
+        if (P.fp64) {
+          r2d = uncut_residual8<double>(P, net, pi.x, pi.y, pi.z, o, k, lane, (double)a.scale, sr);
+          r2 = (float)r2d;
+        } else {
+          r2 = uncut_residual8<float>(P, net, pi.x, pi.y, pi.z, o, k, lane, a.scale, sr);
         }
-      } else if (pi.valid && pi.cut_id < 0) {
-        double r2;
-        if (P.fp64) r2 = uncut_residual<double>(P, net, pi.x, pi.y, pi.z, out, (double)a.scale, sd);
-        else r2 = (double)uncut_residual<float>(P, net, pi.x, pi.y, pi.z, out, a.scale, sd);
-        loss_acc += r2;
-        if (a.r2_out) a.r2_out[pi.pt] = (float)r2;
-      } else if (pi.valid && train) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) sd[c] = a.cut_seed[(int64_t)pi.cut_id * 16 + net * 8 + c];
+        if (valid && !is_cut) {
+          sd = sr;
+          if (k == 0) {
+            if (P.fp64) loss_acc_d += r2d;
+            else loss_acc += r2;
+            if (a.r2_out) a.r2_out[pi.pt] = r2;
+          }
+        } else if (valid && train) {
+          sd = cut_sd;
+        }
       }
-#pragma unroll
-      for (int c = 0; c < 8; ++c) seeds[8 * tid + c] = sd[c];
+      // seeds in this kernel's column convention
+      if (!SCALED) sd *= (k >= 1 && k <= 3) ? P.inv_h2f : ((k >= 4 && k <= 6) ? P.inv_hf : 1.f);
+      seeds[c] = sd;
     }
     __syncthreads();
     if (!train) continue;
 
     // ---- backward: adjoint of the last tanh layer (FP32 state in registers)
 #pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-      const int p = 8 * ch + pp;
+    for (int pp = 0; pp < kPPT; ++pp) {
+      const int p = 4 * cg + pp;
       float sd[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) sd[c] = seeds[8 * p + c];
@@ -452,12 +475,12 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
       float gzc = s0 * (wo * sd[0]);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        gzc += tanh_stencil_bwd(t, s0, st[1 + i], st[4 + i], wo * sd[1 + i], wo * sd[4 + i], hf,
-                                h2f, ihf, ih2f, gz[1 + i], gz[4 + i]);
+        gzc += tanh_stencil_bwd(t, s0, st[1 + i], st[4 + i], wo * sd[1 + i], wo * sd[4 + i], hs,
+                                h2s, ihs, ih2s, gz[1 + i], gz[4 + i]);
       gz[0] = gzc;
       gz[7] = fmaf(-st[7], st[7], 1.f) * (wo * sd[7]);
       gbh[NG - 1] += gz[0] + gz[7];
-      store8<BF>(Aimg + (L - 1) * kImg, u, 8 * p, gz);
+      store8o<BF>(Aimg + (L - 1) * kImg, poff(pp), gz);
     }
     if (tid == 0) {
       float s = 0.f;
@@ -489,37 +512,36 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
         break;
       }
       unsigned char* img = Aimg + (g - 1) * kImg;  // state of act[g-1]
+      float G[32];
+      tmem_ld32(d_tm + lane_base + col0, G);
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        float G[32];
-        tmem_ld32(d_tm + lane_base + 64 * ch + 32 * b, G);
+      for (int j = 0; j < kPPT; ++j) {
+        const int p = 4 * cg + j;
+        float st[8];
+        load8o<BF>(img, poff(j), st);
+        const float* Gp = G + 8 * j;
+        const float t = st[0], s0 = fmaf(-t, t, 1.f);
+        float gz[8];
+        float gzc = s0 * Gp[0];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int p = 8 * ch + 4 * b + j;
-          float st[8];
-          load8<BF>(img, u, 8 * p, st);
-          const float* Gp = G + 8 * j;
-          const float t = st[0], s0 = fmaf(-t, t, 1.f);
-          float gz[8];
-          float gzc = s0 * Gp[0];
+        for (int i = 0; i < 3; ++i)
+          gzc += tanh_stencil_bwd(t, s0, st[1 + i], st[4 + i], Gp[1 + i], Gp[4 + i], hs, h2s,
+                                  ihs, ih2s, gz[1 + i], gz[4 + i]);
+        gz[0] = gzc;
+        gz[7] = fmaf(-st[7], st[7], 1.f) * Gp[7];
+        if (g > 1) {
+          const float gsum = gz[0] + gz[7];
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
-            gzc += tanh_stencil_bwd(t, s0, st[1 + i], st[4 + i], Gp[1 + i], Gp[4 + i], hf, h2f,
-                                    ihf, ih2f, gz[1 + i], gz[4 + i]);
-          gz[0] = gzc;
-          gz[7] = fmaf(-st[7], st[7], 1.f) * Gp[7];
-          if (g > 1) {
-            const float gsum = gz[0] + gz[7];
-#pragma unroll
-            for (int i = 0; i < NG; ++i) gbh[i] += (g - 2 == i) ? gsum : 0.f;
-            store8<BF>(img, u, 8 * p, gz);
-          } else {
-            const PInfo pi = pinfo[p];
-            gW1[0] += fmaf(gz[0], pi.x, fmaf(gz[7], pi.gx, gz[4]));
-            gW1[1] += fmaf(gz[0], pi.y, fmaf(gz[7], pi.gy, gz[5]));
-            gW1[2] += fmaf(gz[0], pi.z, fmaf(gz[7], pi.gz, gz[6]));
-            gb1 += gz[0] + gz[7];
-          }
+          for (int i = 0; i < NG; ++i) gbh[i] += (g - 2 == i) ? gsum : 0.f;
+          store8o<BF>(img, poff(j), gz);
+        } else {
+          // d del_i / d W1[u][i] = h (unscaled columns) or 1 (scaled)
+          const PRec pi = pr[p];
+          const float dd = SCALED ? 1.f : P.hf;
+          gW1[0] += fmaf(gz[0], pi.x, fmaf(gz[7], pi.gx, gz[4] * dd));
+          gW1[1] += fmaf(gz[0], pi.y, fmaf(gz[7], pi.gy, gz[5] * dd));
+          gW1[2] += fmaf(gz[0], pi.z, fmaf(gz[7], pi.gz, gz[6] * dd));
+          gb1 += gz[0] + gz[7];
         }
       }
       fence_before_sync();
@@ -530,14 +552,15 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
   }
 
   if (!aborted && train && cur_net >= 0) flush(cur_net);
+  double lsum = (double)loss_acc + loss_acc_d;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
-  if (lane == 0) loss_red[w] = loss_acc;
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if (lane == 0) loss_red[w] = lsum;
   fence_before_sync();
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
-    for (int ww = 0; ww < 8; ++ww) s += loss_red[ww];
+    for (int ww = 0; ww < 16; ++ww) s += loss_red[ww];
     if (a.mode != MODE_CUT_FWD) a.loss_part[blockIdx.x] = s;
     if (train) {
       a.gpart_flag[2 * blockIdx.x] = aborted ? 0 : wrote0;
@@ -550,11 +573,12 @@ __global__ void __launch_bounds__(256, 1) k_step_tc(ProbDev P, StepArgs a) {
 
 template <int L, bool BF, bool FAST>
 static cudaError_t launch_tc_t(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st) {
+  constexpr bool SCALED = !BF;  // FP16 operands need the 1/h^2, 1/h column scaling
   const size_t smem = tc_smem_bytes(L);
-  cudaError_t e = cudaFuncSetAttribute(k_step_tc<L, BF, FAST>,
+  cudaError_t e = cudaFuncSetAttribute(k_step_tc<L, BF, FAST, SCALED>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_step_tc<L, BF, FAST><<<grid, 256, smem, st>>>(P, a);
+  k_step_tc<L, BF, FAST, SCALED><<<grid, 512, smem, st>>>(P, a);
   return cudaGetLastError();
 }
 
