@@ -1,0 +1,176 @@
+// nbm_geom.cuh -- FP64 geometry of the implicit compute cell (arXiv
+// 2210.14907, Fig. 2: "interface-cell crossings"): the level set is taken
+// linear on each tetrahedron of the Freudenthal-Kuhn six-tetrahedron split of
+// the cube, which gives closed forms for the volume fractions, the face
+// fractions (each face split along the diagonal from its lowest to its
+// highest corner, the split the tetrahedra induce) and the interface polygon.
+#pragma once
+
+#include "nbm_device.cuh"
+
+namespace nbm {
+
+__device__ inline double frac_tri(double a, double b, double c) {
+  int na = a <= 0.0, nb = b <= 0.0, nc = c <= 0.0;
+  int k = na + nb + nc;
+  if (k == 0) return 0.0;
+  if (k == 3) return 1.0;
+  if (k == 1) {
+    double l = na ? a : (nb ? b : c);
+    double o1 = na ? b : a, o2 = nc ? b : c;  // the two positive values
+    return (l / (l - o1)) * (l / (l - o2));
+  }
+  double l = !na ? a : (!nb ? b : c);
+  double o1 = !na ? b : a, o2 = !nc ? b : c;  // the two non-positive values
+  return 1.0 - (l / (l - o1)) * (l / (l - o2));
+}
+
+__device__ inline double frac_tet(const double f[4]) {
+  int neg = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
+  if (neg == 0) return 0.0;
+  if (neg == 4) return 1.0;
+  if (neg == 1 || neg == 3) {
+    bool want_neg = neg == 1;
+    int lone = 0;
+    for (int i = 0; i < 4; ++i)
+      if ((f[i] <= 0.0) == want_neg) lone = i;
+    double prod = 1.0;
+    for (int i = 0; i < 4; ++i)
+      if (i != lone) prod *= f[lone] / (f[lone] - f[i]);
+    return neg == 1 ? prod : 1.0 - prod;
+  }
+  // two on each side: A, B = -values below, C, D = values above
+  double A = -1.0, B = -1.0, C = -1.0, D = -1.0;
+  for (int i = 0; i < 4; ++i) {
+    if (f[i] <= 0.0) {
+      if (A < 0.0) A = -f[i]; else B = -f[i];
+    } else {
+      if (C < 0.0) C = f[i]; else D = f[i];
+    }
+  }
+  double num = C * D * (A * A + A * B + B * B) + (C + D) * A * B * (A + B) + A * A * B * B;
+  return num / ((C + A) * (D + A) * (C + B) * (D + B));
+}
+
+__device__ inline void lerp_zero(const double* xu, double fu, const double* xv, double fv,
+                                 double* o) {
+  double t = fu / (fu - fv);
+  for (int i = 0; i < 3; ++i) o[i] = xu[i] + t * (xv[i] - xu[i]);
+}
+
+__device__ inline double tri_area_acc(const double* a, const double* b, const double* c,
+                                      double* wc) {
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+         cz = e1[0] * e2[1] - e1[1] * e2[0];
+  double ar = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  for (int i = 0; i < 3; ++i) wc[i] += ar * (a[i] + b[i] + c[i]) / 3.0;
+  return ar;
+}
+
+// interface polygon of one tetrahedron: returns its area, adds area*centroid
+__device__ inline double tet_iface(const double X[4][3], const double f[4], double* wc) {
+  int neg = 0;
+  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
+  if (neg == 0 || neg == 4) return 0.0;
+  if (neg == 1 || neg == 3) {
+    bool want_neg = neg == 1;
+    int lone = 0;
+    for (int i = 0; i < 4; ++i)
+      if ((f[i] <= 0.0) == want_neg) lone = i;
+    double Pp[3][3];
+    int k = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (i == lone) continue;
+      if (want_neg) lerp_zero(X[lone], f[lone], X[i], f[i], Pp[k]);
+      else lerp_zero(X[i], f[i], X[lone], f[lone], Pp[k]);
+      ++k;
+    }
+    return tri_area_acc(Pp[0], Pp[1], Pp[2], wc);
+  }
+  int a = -1, b = -1, c = -1, d = -1;
+  for (int i = 0; i < 4; ++i) {
+    if (f[i] <= 0.0) { if (a < 0) a = i; else b = i; }
+    else { if (c < 0) c = i; else d = i; }
+  }
+  double Q[4][3];
+  lerp_zero(X[a], f[a], X[c], f[c], Q[0]);
+  lerp_zero(X[a], f[a], X[d], f[d], Q[1]);
+  lerp_zero(X[b], f[b], X[d], f[d], Q[2]);
+  lerp_zero(X[b], f[b], X[c], f[c], Q[3]);
+  return tri_area_acc(Q[0], Q[1], Q[2], wc) + tri_area_acc(Q[0], Q[2], Q[3], wc);
+}
+
+struct CellGeo {
+  double Vm;      // volume fraction of Omega-
+  double Am[6];   // face fractions of Omega-, face f = 2 axis + (side > 0)
+  double S;       // interface area / h^2
+  double xg[3];   // area-weighted interface centroid projected onto phi = 0
+  int has_jump;   // S > 0
+  int cut;        // corners on both sides
+};
+
+// Geometry of the cell p + [-h/2, h/2]^3.  Uncut cells (all corners on one
+// side, phi = 0 counted as minus) get fractions exactly 0 or 1.
+__device__ inline void cell_geometry_d(const ProbDev& P, const double p[3], double h, CellGeo& g) {
+  double C[8][3], F[8];
+  int nneg = 0;
+  for (int c = 0; c < 8; ++c) {
+    for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
+    F[c] = phi_d(P, C[c][0], C[c][1], C[c][2]);
+    nneg += F[c] <= 0.0;
+  }
+  g.S = 0.0;
+  g.has_jump = 0;
+  for (int a = 0; a < 3; ++a) g.xg[a] = p[a];
+  if (nneg == 0 || nneg == 8) {
+    const double v = nneg == 8 ? 1.0 : 0.0;
+    g.Vm = v;
+    for (int f = 0; f < 6; ++f) g.Am[f] = v;
+    g.cut = 0;
+    return;
+  }
+  g.cut = 1;
+  double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0};
+  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int t = 0; t < 6; ++t) {
+    int v1 = 1 << perm[t][0];
+    int v2 = v1 | (1 << perm[t][1]);
+    int idx[4] = {0, v1, v2, 7};
+    double Xt[4][3], ft[4];
+    for (int k = 0; k < 4; ++k) {
+      for (int a = 0; a < 3; ++a) Xt[k][a] = C[idx[k]][a];
+      ft[k] = F[idx[k]];
+    }
+    vneg += frac_tet(ft) / 6.0;
+    area += tet_iface(Xt, ft, wc);
+  }
+  g.Vm = vneg;
+  for (int a = 0; a < 3; ++a) {
+    int j = (a + 1) % 3, k = (a + 2) % 3;
+    for (int sd = 0; sd < 2; ++sd) {
+      int b0 = sd << a;
+      int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << k), c11 = c10 | (1 << k);
+      g.Am[2 * a + sd] =
+          0.5 * (frac_tri(F[c00], F[c10], F[c11]) + frac_tri(F[c00], F[c01], F[c11]));
+    }
+  }
+  g.S = area / (h * h);
+  g.has_jump = area > 0.0;
+  if (area > 0.0) {
+    for (int a = 0; a < 3; ++a) g.xg[a] = wc[a] / area;
+    for (int it = 0; it < 3; ++it) {  // Newton projection onto phi = 0
+      double gr[3];
+      double ph = phi_d(P, g.xg[0], g.xg[1], g.xg[2]);
+      grad_phi_d(P, g.xg, gr);
+      double gg = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+      if (gg <= 1e-300) break;
+      for (int a = 0; a < 3; ++a) g.xg[a] -= ph * gr[a] / gg;
+    }
+  }
+}
+
+}  // namespace nbm

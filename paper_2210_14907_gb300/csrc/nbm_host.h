@@ -132,8 +132,6 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
                           Workspace& ws, cudaStream_t st);
-cudaError_t launch_eval_grid(const ProbDev& P, const float* params, int n, int prec, float* u,
-                             Workspace& ws, int grid, cudaStream_t st);
 size_t tc_smem_bytes(int L);
 size_t fp32_smem_bytes(int H, int L);
 int tc_supported(int H, int L);

@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 
 #include "nbm_device.cuh"
+#include "nbm_geom.cuh"
 #include "nbm_tc_ptx.cuh"
 
 namespace nbm {
@@ -197,105 +198,6 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* __restrict__ cl
   if (f[1]) list_p[pos[1]] = e;
 }
 
-// ------------------------------------------------------------------------
-// Cut-cell geometry in FP64.  phi is linear on each tetrahedron of the
-// Freudenthal-Kuhn split (six tetrahedra 0 -> e_a -> e_a+e_b -> 7); faces are
-// split along the diagonal from their lowest to their highest corner.
-// ------------------------------------------------------------------------
-__device__ inline double frac_tri(double a, double b, double c) {
-  int na = a <= 0.0, nb = b <= 0.0, nc = c <= 0.0;
-  int k = na + nb + nc;
-  if (k == 0) return 0.0;
-  if (k == 3) return 1.0;
-  if (k == 1) {
-    double l = na ? a : (nb ? b : c);
-    double o1 = na ? b : a, o2 = nc ? b : c;  // the two positive values
-    return (l / (l - o1)) * (l / (l - o2));
-  }
-  double l = !na ? a : (!nb ? b : c);
-  double o1 = !na ? b : a, o2 = !nc ? b : c;  // the two non-positive values
-  return 1.0 - (l / (l - o1)) * (l / (l - o2));
-}
-
-__device__ inline double frac_tet(const double f[4]) {
-  int neg = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
-  if (neg == 0) return 0.0;
-  if (neg == 4) return 1.0;
-  if (neg == 1 || neg == 3) {
-    bool want_neg = neg == 1;
-    int lone = 0;
-    for (int i = 0; i < 4; ++i)
-      if ((f[i] <= 0.0) == want_neg) lone = i;
-    double prod = 1.0;
-    for (int i = 0; i < 4; ++i)
-      if (i != lone) prod *= f[lone] / (f[lone] - f[i]);
-    return neg == 1 ? prod : 1.0 - prod;
-  }
-  // two on each side: A, B = -values below, C, D = values above
-  double A = -1.0, B = -1.0, C = -1.0, D = -1.0;
-  for (int i = 0; i < 4; ++i) {
-    if (f[i] <= 0.0) {
-      if (A < 0.0) A = -f[i]; else B = -f[i];
-    } else {
-      if (C < 0.0) C = f[i]; else D = f[i];
-    }
-  }
-  double num = C * D * (A * A + A * B + B * B) + (C + D) * A * B * (A + B) + A * A * B * B;
-  return num / ((C + A) * (D + A) * (C + B) * (D + B));
-}
-
-__device__ inline void lerp_zero(const double* xu, double fu, const double* xv, double fv,
-                                 double* o) {
-  double t = fu / (fu - fv);
-  for (int i = 0; i < 3; ++i) o[i] = xu[i] + t * (xv[i] - xu[i]);
-}
-
-__device__ inline double tri_area_acc(const double* a, const double* b, const double* c,
-                                      double* wc) {
-  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-  double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
-         cz = e1[0] * e2[1] - e1[1] * e2[0];
-  double ar = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
-  for (int i = 0; i < 3; ++i) wc[i] += ar * (a[i] + b[i] + c[i]) / 3.0;
-  return ar;
-}
-
-// interface polygon of one tetrahedron: returns its area, adds area*centroid
-__device__ inline double tet_iface(const double X[4][3], const double f[4], double* wc) {
-  int neg = 0;
-  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
-  if (neg == 0 || neg == 4) return 0.0;
-  if (neg == 1 || neg == 3) {
-    bool want_neg = neg == 1;
-    int lone = 0;
-    for (int i = 0; i < 4; ++i)
-      if ((f[i] <= 0.0) == want_neg) lone = i;
-    double Pp[3][3];
-    int k = 0;
-    for (int i = 0; i < 4; ++i) {
-      if (i == lone) continue;
-      if (want_neg) lerp_zero(X[lone], f[lone], X[i], f[i], Pp[k]);
-      else lerp_zero(X[i], f[i], X[lone], f[lone], Pp[k]);
-      ++k;
-    }
-    return tri_area_acc(Pp[0], Pp[1], Pp[2], wc);
-  }
-  int a = -1, b = -1, c = -1, d = -1;
-  for (int i = 0; i < 4; ++i) {
-    if (f[i] <= 0.0) { if (a < 0) a = i; else b = i; }
-    else { if (c < 0) c = i; else d = i; }
-  }
-  double Q[4][3];
-  lerp_zero(X[a], f[a], X[c], f[c], Q[0]);
-  lerp_zero(X[a], f[a], X[d], f[d], Q[1]);
-  lerp_zero(X[b], f[b], X[d], f[d], Q[2]);
-  lerp_zero(X[b], f[b], X[c], f[c], Q[3]);
-  return tri_area_acc(Q[0], Q[1], Q[2], wc) + tri_area_acc(Q[0], Q[2], Q[3], wc);
-}
-
 __global__ void __launch_bounds__(32) k_cut_geometry(ProbDev P, const float* __restrict__ X,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ Z,
@@ -305,54 +207,17 @@ __global__ void __launch_bounds__(32) k_cut_geometry(ProbDev P, const float* __r
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= counters[2]) return;
   int i = cut_pt[id];
-  const double h = P.h;
-  double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
-  double C[8][3], F[8];
-  for (int c = 0; c < 8; ++c) {
-    for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
-    F[c] = phi_d(P, C[c][0], C[c][1], C[c][2]);
-  }
-  double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0};
-  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  for (int t = 0; t < 6; ++t) {
-    int v1 = 1 << perm[t][0];
-    int v2 = v1 | (1 << perm[t][1]);
-    int idx[4] = {0, v1, v2, 7};
-    double Xt[4][3], ft[4];
-    for (int k = 0; k < 4; ++k) {
-      for (int a = 0; a < 3; ++a) Xt[k][a] = C[idx[k]][a];
-      ft[k] = F[idx[k]];
-    }
-    vneg += frac_tet(ft) / 6.0;
-    area += tet_iface(Xt, ft, wc);
-  }
+  const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
+  CellGeo g;
+  cell_geometry_d(P, p, P.h, g);
   CutRec r;
-  r.Vm = vneg;
-  for (int a = 0; a < 3; ++a) {
-    int j = (a + 1) % 3, k = (a + 2) % 3;
-    for (int sd = 0; sd < 2; ++sd) {
-      int b0 = sd << a;
-      int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << k), c11 = c10 | (1 << k);
-      r.Am[2 * a + sd] = 0.5 * (frac_tri(F[c00], F[c10], F[c11]) + frac_tri(F[c00], F[c01], F[c11]));
-    }
-  }
-  r.S = area / (h * h);
-  r.has_jump = area > 0.0;
-  double xg[3] = {p[0], p[1], p[2]};
-  if (area > 0.0) {
-    for (int a = 0; a < 3; ++a) xg[a] = wc[a] / area;
-    for (int it = 0; it < 3; ++it) {  // Newton projection onto phi = 0
-      double g[3];
-      double ph = phi_d(P, xg[0], xg[1], xg[2]);
-      grad_phi_d(P, xg, g);
-      double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-      if (gg <= 1e-300) break;
-      for (int a = 0; a < 3; ++a) xg[a] -= ph * g[a] / gg;
-    }
-  }
-  for (int a = 0; a < 3; ++a) r.xg[a] = xg[a];
-  r.beta = r.has_jump ? beta_d(P, xg) : 0.0;
-  r.alpha = r.has_jump ? alpha_d(xg) : 0.0;
+  r.Vm = g.Vm;
+  for (int f = 0; f < 6; ++f) r.Am[f] = g.Am[f];
+  r.S = g.S;
+  r.has_jump = g.has_jump;
+  for (int a = 0; a < 3; ++a) r.xg[a] = g.xg[a];
+  r.beta = r.has_jump ? beta_d(P, g.xg) : 0.0;
+  r.alpha = r.has_jump ? alpha_d(g.xg) : 0.0;
   r.f[0] = rhs_f<double>(P, 0, p[0], p[1], p[2]);
   r.f[1] = rhs_f<double>(P, 1, p[0], p[1], p[2]);
   r.point = i;

@@ -602,9 +602,5 @@ cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int pr
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_eval_grid(const ProbDev&, const float*, int, int, float*, Workspace&, int,
-                             cudaStream_t) {
-  return cudaErrorNotSupported;
-}
 
 }  // namespace nbm

@@ -1,0 +1,108 @@
+"""Grid evaluation of the surrogate and the grid CG solve, against the FP64 oracle.
+
+Evaluation tolerances (norm-wise relative over the nodes): FP32 1e-5; FP16
+hidden GEMMs 2e-3 (11-bit operands and SFU tanh, the mixed-path residual
+bar); BF16 1e-2 (8-bit operands).  CG: both sides solve to a relative residual
+of 1e-12, the solutions agree to 1e-8 of max|u|.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pyoracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _nbm():
+    import paper_2210_14907_gb300 as nbm
+    return nbm
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _clear_of_interface(o, n):
+    """Grids with a node on phi = 0 leave the side of that node to the last ulp of
+    the platform's FP64 cos/atan2 (the oracle's and CUDA's differ there); the
+    parity grids below keep every node at least 1e-9 away from the interface."""
+    x = -1.0 + np.arange(n + 1) * 2.0 / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    ph = [abs(O.phi(o, p)) for p in np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)]
+    return min(ph) > 1e-9
+
+
+@pytest.mark.parametrize("geom,H,L,n", [(O.GEOM_SPHERE, 64, 2, 16), (O.GEOM_FLOWER, 128, 4, 18),
+                                        (O.GEOM_SPHERE, 128, 3, 1), (O.GEOM_FLOWER, 128, 3, 5)])
+def test_eval_grid_fp32_matches_oracle(geom, H, L, n):
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=geom, n_hidden=L, width=H)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=geom, n_hidden=L, width=H)
+    if geom == O.GEOM_FLOWER:
+        assert _clear_of_interface(o, n)
+    th = inputs.glorot_params(H, L, seed=21, bias_scale=0.2)
+    ref = O.eval_grid(o, th.astype(np.float64), n)
+    got = prob.eval_grid(torch.from_numpy(th).cuda(), n, precision=nbm.PREC_FP32).cpu().numpy()
+    assert got.shape == ref.shape
+    assert _rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 2e-3), (1, 1e-2)], ids=["fp16", "bf16"])
+@pytest.mark.parametrize("L,n", [(3, 22), (4, 17), (4, 1)])
+def test_eval_grid_tensor_cores_match_oracle(prec, tol, L, n):
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_FLOWER, n_hidden=L, width=128, precision=nbm.PREC_BF16)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_FLOWER, n_hidden=L, width=128)
+    assert _clear_of_interface(o, n)
+    th = inputs.glorot_params(128, L, seed=22, bias_scale=0.2)
+    ref = O.eval_grid(o, th.astype(np.float64), n)
+    got = prob.eval_grid(torch.from_numpy(th).cuda(), n, precision=prec).cpu().numpy()
+    err = _rel(got, ref)
+    print(f"eval prec {prec} L {L} n {n}: rel {err:.2e}")
+    assert err <= tol
+
+
+@pytest.mark.parametrize("geom,mu_p,n", [(O.GEOM_SPHERE, 10.0, 16), (O.GEOM_FLOWER, 100.0, 14),
+                                         (O.GEOM_ALL_MINUS, 10.0, 9)])
+def test_grid_cg_matches_oracle(geom, mu_p, n):
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=geom, mu_minus=1.0, mu_plus=mu_p, k_minus=0.5)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=geom, mu_minus=1.0, mu_plus=mu_p, k_minus=0.5)
+    if geom == O.GEOM_FLOWER:
+        assert _clear_of_interface(o, n)
+    st, ref, it_ref, rr_ref = O.grid_cg_solve(o, n, rtol=1e-12, max_iter=20000)
+    assert st == 0
+    u, it, rr, ok = prob.grid_cg_solve(n, rtol=1e-12, max_iter=20000)
+    assert ok and rr <= 1e-12
+    u = u.cpu().numpy()
+    assert np.max(np.abs(u - ref)) <= 1e-8 * np.max(np.abs(ref))
+    assert abs(it - it_ref) <= 12  # the device checks convergence every 10 iterations
+
+
+def test_grid_cg_second_order_without_interface():
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_ALL_MINUS, mu_minus=2.0, k_minus=1.0)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_ALL_MINUS, mu_minus=2.0, k_minus=1.0)
+    errs = []
+    for n in (16, 32, 64):
+        u, it, rr, ok = prob.grid_cg_solve(n, rtol=1e-12, max_iter=50000)
+        assert ok
+        errs.append(O.grid_error(o, n, u.cpu().numpy())[0])
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+def test_grid_cg_reports_non_convergence():
+    nbm = _nbm()
+    prob = nbm.Problem(nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE))
+    u, it, rr, ok = prob.grid_cg_solve(32, rtol=1e-12, max_iter=3)
+    assert not ok and it == 3 and rr > 1e-12
+    assert torch.isfinite(u).all()
+    with pytest.raises(nbm.NBMError) as e:
+        prob.grid_cg_solve(1, rtol=1e-10)
+    assert e.value.code == 1
