@@ -175,6 +175,59 @@ def cpu_baseline(config_name="C2", target_s=10.0):
                       f"FP64 oracle, OpenMP {cores} threads, {t:.1f} s"}
 
 
+def secondary(dev, hbm_peak, peak_src):
+    """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
+    flower-interface 3->128x4->1 architecture) and the FP64 grid CG solve of the
+    same discretization at 128^3 and 256^3 (the plain method the NBM lifts off
+    its grid)."""
+    import torch
+
+    import paper_2210_14907_gb300 as nbm
+    from oracle import pyoracle as O
+    out = {}
+    d = nbm.config("C5")
+    prob = nbm.Problem(d)
+    params = nbm.xavier_init(d, seed=0, device=dev)
+    n = 512
+    nodes = (n + 1) ** 3
+    u = torch.empty(nodes, device=dev)
+    prob.eval_grid(params, n, precision=nbm.PREC_FP16, out=u)
+    times = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        prob.eval_grid(params, n, precision=nbm.PREC_FP16, out=u)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = min(times)
+    flops = nodes * 3 * 2 * 128 * 128  # hidden GEMMs of the node's own network
+    out["eval_grid"] = {"metric": "grid points/s (trained-surrogate inference)", "value": nodes / ms * 1e3,
+                        "unit": "grid points/s", "grid": "513^3 nodes", "precision": "fp16",
+                        "ms": ms, "tensor_tflops": flops / ms / 1e9}
+    del u
+    torch.cuda.empty_cache()
+    for n in (128, 256):
+        dcg = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+        pcg = nbm.Problem(dcg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ucg, it, rr, ok = pcg.grid_cg_solve(n, rtol=1e-10, max_iter=100000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        m = (n - 1) ** 3
+        gbs = it * 136 * m / wall / 1e9  # algorithmic bytes: SpMV 48 + update 56 + direction 32 per unknown
+        o = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+        linf, rmse = O.grid_error(o, n, ucg.cpu().numpy())
+        out[f"grid_cg_{n}"] = {"unknowns": m, "iterations": it, "relres": rr, "converged": ok,
+                               "wall_s": wall, "achieved_gbs": gbs,
+                               "hbm_frac": gbs / hbm_peak, "hbm_peak": f"{hbm_peak} GB/s {peak_src} copy",
+                               "linf_exact": linf, "rmse_exact": rmse}
+        del ucg
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -200,6 +253,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp32-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -312,6 +366,8 @@ def main():
                           "ms_per_step": ms32 / k32, "mixed_speedup": value / value32},
             "roofline": roof, "e2e": e2e, "gpu_launches": 9 * args.steps,
             "clocks": clk.summary(), "wall_s": wall}
+    if ws == 1 and not args.no_secondary:
+        line["secondary"] = secondary(dev, hbm, peak_src)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -51,7 +51,8 @@ __device__ inline void jump_corr(const ProbDev& P, const double x[3], int sx, do
 }
 
 __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* diag, double* wx,
-                                                  double* wy, double* wz, double* rhs) {
+                                                  double* wy, double* wz, double* rhs,
+                                                  double* inv_diag) {
   const int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (r >= G.m) return;
   int idx[3];
@@ -91,13 +92,16 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* dia
   }
   if (cg.cut && cg.has_jump) known += h * cg.S * beta_d(P, cg.xg);
   diag[r] = dg;
+  inv_diag[r] = 1.0 / dg;  // the Jacobi preconditioner, applied by multiplication
   wx[r] = wplus[0];
   wy[r] = wplus[1];
   wz[r] = wplus[2];
   rhs[r] = -known;
 }
 
-// y = A v on the interior nodes; block partial of v . y
+// y = A v on the interior nodes; block partial of v . y.  Launched on a 3-D
+// grid (x: runs of 256 nodes of one row, y: row j, z: plane k), so node
+// indices need no integer division.
 __global__ void __launch_bounds__(kB) k_spmv_dot(Grid G, const double* __restrict__ diag,
                                                  const double* __restrict__ wx,
                                                  const double* __restrict__ wy,
@@ -105,11 +109,11 @@ __global__ void __launch_bounds__(kB) k_spmv_dot(Grid G, const double* __restric
                                                  const double* __restrict__ v, double* y,
                                                  double* part) {
   __shared__ double red[kB / 32];
-  const int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x;
+  const int i = blockIdx.x * kB + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
   double d = 0.0;
-  if (r < G.m) {
-    const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
-    const int i = (int)(r % G.m1), j = (int)((r / G.m1) % G.m1), k = (int)(r / s2);
+  if (i < G.m1) {
+    const int64_t r = i + s1 * j + s2 * k;
     const double vr = v[r];
     double acc = diag[r] * vr;
     if (i + 1 < G.m1) acc -= wx[r] * v[r + 1];
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(kB) k_spmv_dot(Grid G, const double* __restric
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kB / 32; ++w) s += red[w];
-    part[blockIdx.x] = s;
+    part[blockIdx.x + gridDim.x * ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = s;
   }
 }
 
@@ -166,7 +170,7 @@ __global__ void k_beta(double* sc) {
 
 // x += alpha p; r -= alpha Ap; partials of r.z and r.r (z = r / diag)
 __global__ void __launch_bounds__(kB) k_update(Grid G, const double* __restrict__ sc,
-                                               const double* __restrict__ diag,
+                                               const double* __restrict__ inv_diag,
                                                const double* __restrict__ p,
                                                const double* __restrict__ Ap, double* x, double* r,
                                                double* part, int nparts) {
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(kB) k_update(Grid G, const double* __restrict_
     x[i] += a * p[i];
     const double ri = r[i] - a * Ap[i];
     r[i] = ri;
-    rz = ri * ri / diag[i];
+    rz = ri * ri * inv_diag[i];
     rr = ri * ri;
   }
 #pragma unroll
@@ -204,11 +208,11 @@ __global__ void __launch_bounds__(kB) k_update(Grid G, const double* __restrict_
 
 // p = r / diag + beta p   (beta = 0: p = z for the first direction)
 __global__ void __launch_bounds__(kB) k_pupdate(Grid G, const double* __restrict__ sc, int first,
-                                                const double* __restrict__ diag,
+                                                const double* __restrict__ inv_diag,
                                                 const double* __restrict__ r, double* p) {
   const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (i >= G.m) return;
-  const double z = r[i] / diag[i];
+  const double z = r[i] * inv_diag[i];
   p[i] = first ? z : z + sc[5] * p[i];
 }
 
@@ -255,12 +259,15 @@ extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_ite
   const int nb = (int)((G.m + kB - 1) / kB);
   const int64_t nodes = (int64_t)(n + 1) * (n + 1) * (n + 1);
   double *diag = nullptr, *wx = nullptr, *wy = nullptr, *wz = nullptr, *r = nullptr, *x = nullptr,
-         *pv = nullptr, *Ap = nullptr, *part = nullptr, *sc = nullptr;
-  double** bufs[] = {&diag, &wx, &wy, &wz, &r, &x, &pv, &Ap};
+         *pv = nullptr, *Ap = nullptr, *idg = nullptr, *part = nullptr, *sc = nullptr;
+  double** bufs[] = {&diag, &wx, &wy, &wz, &r, &x, &pv, &Ap, &idg};
+  const dim3 sgrid((unsigned)((G.m1 + kB - 1) / kB), (unsigned)G.m1, (unsigned)G.m1);
+  const int nsp = (int)(sgrid.x * sgrid.y * sgrid.z);  // SpMV partials
   cudaError_t e = cudaSuccess;
   for (double** b : bufs)
     if (e == cudaSuccess) e = cudaMalloc((void**)b, sizeof(double) * (size_t)(G.m > 0 ? G.m : 1));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&part, sizeof(double) * 2 * (size_t)nb);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&part, sizeof(double) * 2 * (size_t)(nb > nsp ? nb : nsp));
   if (e == cudaSuccess) e = cudaMalloc((void**)&sc, sizeof(double) * 8);
   auto cleanup = [&]() {
     for (double** b : bufs)
@@ -276,16 +283,16 @@ extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_ite
   };
   if (e != cudaSuccess) return cuda_fail(e);
 
-  k_grid_rows<<<nb, kB, 0, st>>>(P, G, diag, wx, wy, wz, r);
+  k_grid_rows<<<nb, kB, 0, st>>>(P, G, diag, wx, wy, wz, r, idg);
   cudaMemsetAsync(x, 0, sizeof(double) * G.m, st);
   cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
   cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
   cudaMemsetAsync(sc, 0, sizeof(double) * 8, st);
   // r = b: rz = r.(r/diag), rr = r.r (an update with alpha = 0)
-  k_update<<<nb, kB, 0, st>>>(G, sc, diag, pv, Ap, x, r, part, nb);
+  k_update<<<nb, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part, nb);
   k_reduce_parts<<<1, 256, 0, st>>>(part, nb, 2, sc + 3);
   k_beta<<<1, 1, 0, st>>>(sc);
-  k_pupdate<<<nb, kB, 0, st>>>(G, sc, 1, diag, r, pv);
+  k_pupdate<<<nb, kB, 0, st>>>(G, sc, 1, idg, r, pv);
   double host_sc[8];
   e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -295,13 +302,13 @@ extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_ite
   double rnorm = bnorm;
   bool converged = bnorm == 0.0;
   while (!converged && it < max_iter) {
-    k_spmv_dot<<<nb, kB, 0, st>>>(G, diag, wx, wy, wz, pv, Ap, part);
-    k_reduce_parts<<<1, 256, 0, st>>>(part, nb, 1, sc + 1);
+    k_spmv_dot<<<sgrid, kB, 0, st>>>(G, diag, wx, wy, wz, pv, Ap, part);
+    k_reduce_parts<<<1, 256, 0, st>>>(part, nsp, 1, sc + 1);
     k_alpha<<<1, 1, 0, st>>>(sc);
-    k_update<<<nb, kB, 0, st>>>(G, sc, diag, pv, Ap, x, r, part, nb);
+    k_update<<<nb, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part, nb);
     k_reduce_parts<<<1, 256, 0, st>>>(part, nb, 2, sc + 3);
     k_beta<<<1, 1, 0, st>>>(sc);
-    k_pupdate<<<nb, kB, 0, st>>>(G, sc, 0, diag, r, pv);
+    k_pupdate<<<nb, kB, 0, st>>>(G, sc, 0, idg, r, pv);
     ++it;
     if (it % 10 == 0 || it == max_iter) {
       e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
