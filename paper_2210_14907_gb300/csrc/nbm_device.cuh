@@ -164,6 +164,42 @@ __device__ inline double alpha_d(const double x[3]) {
   return exact_u<double>(1, x[0], x[1], x[2]) - exact_u<double>(0, x[0], x[1], x[2]);
 }
 
+// FP32 versions of the level-set gradient, [u] and [mu d_n u] (the FP32 rows)
+__device__ inline void grad_phi_f(const ProbDev& P, const float x[3], float g[3]) {
+  g[0] = g[1] = g[2] = 0.f;
+  if (P.geometry == NBM_GEOM_ALL_PLUS || P.geometry == NBM_GEOM_ALL_MINUS) return;
+  const float rho = sqrtf(x[0] * x[0] + x[1] * x[1]);
+  const float r = sqrtf(rho * rho + x[2] * x[2]);
+  if (r == 0.f) return;
+  for (int i = 0; i < 3; ++i) g[i] = x[i] / r;
+  if (P.geometry != NBM_GEOM_FLOWER || rho == 0.f) return;
+  const float th = atan2f(rho, x[2]), ps = atan2f(x[1], x[0]);
+  const float r2 = r * r;
+  const float dth[3] = {x[2] * x[0] / (r2 * rho), x[2] * x[1] / (r2 * rho), -rho / r2};
+  const float dps[3] = {-x[1] / (rho * rho), x[0] / (rho * rho), 0.f};
+  const float a = -P.ampf * P.ltf * cosf(P.ltf * th) * cosf(P.lpf * ps);
+  const float b = P.ampf * P.lpf * sinf(P.ltf * th) * sinf(P.lpf * ps);
+  for (int i = 0; i < 3; ++i) g[i] += a * dth[i] + b * dps[i];
+}
+
+__device__ inline float alpha_f(const float x[3]) {
+  return exact_u<float>(1, x[0], x[1], x[2]) - exact_u<float>(0, x[0], x[1], x[2]);
+}
+
+__device__ inline float beta_f(const ProbDev& P, const float x[3]) {
+  const float e = expf(x[0]);
+  const float gm[3] = {e * cosf(x[1]) * sinf(x[2]), -e * sinf(x[1]) * sinf(x[2]),
+                       e * cosf(x[1]) * cosf(x[2])};
+  const float gp[3] = {2.f * x[0], 2.f * x[1], 2.f * x[2]};
+  float gf[3];
+  grad_phi_f(P, x, gf);
+  const float nn = sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
+  if (nn == 0.f) return 0.f;
+  float b = 0.f;
+  for (int i = 0; i < 3; ++i) b += (P.muf[1] * gp[i] - P.muf[0] * gm[i]) * gf[i] / nn;
+  return b;
+}
+
 __device__ inline double beta_d(const ProbDev& P, const double x[3]) {
   double gp[3], gm[3], gf[3];
   exact_grad_u_d(1, x, gp);

@@ -198,30 +198,122 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* __restrict__ cl
   if (f[1]) list_p[pos[1]] = e;
 }
 
-__global__ void __launch_bounds__(32) k_cut_geometry(ProbDev P, const float* __restrict__ X,
+// One cut cell per 8 lanes: corner values, tetrahedra and faces are spread
+// over the lanes and combined with shuffles; beta, alpha, f- and f+ (FP64
+// transcendentals) are evaluated by four different lanes.  FP64 is narrow on
+// this part, so the per-cell dependency chain, not the operation count, sets
+// the time.
+__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __restrict__ X,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ Z,
                                                       const int* __restrict__ cut_pt,
                                                       const int* __restrict__ counters,
                                                       CutRec* cut) {
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= counters[2]) return;
-  int i = cut_pt[id];
+  const unsigned full = 0xffffffffu;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int id = gid >> 3, k = threadIdx.x & 7, base = (threadIdx.x & 31) & ~7;
+  const int nc = counters[2];
+  if ((gid >> 5) * 4 >= nc) return;  // the whole warp (4 cells) is past the cut list
+  const bool live = id < nc;
+  const int i = live ? cut_pt[id] : 0;
+  const double h = P.h;
   const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
-  CellGeo g;
-  cell_geometry_d(P, p, P.h, g);
-  CutRec r;
-  r.Vm = g.Vm;
-  for (int f = 0; f < 6; ++f) r.Am[f] = g.Am[f];
-  r.S = g.S;
-  r.has_jump = g.has_jump;
-  for (int a = 0; a < 3; ++a) r.xg[a] = g.xg[a];
-  r.beta = r.has_jump ? beta_d(P, g.xg) : 0.0;
-  r.alpha = r.has_jump ? alpha_d(g.xg) : 0.0;
-  r.f[0] = rhs_f<double>(P, 0, p[0], p[1], p[2]);
-  r.f[1] = rhs_f<double>(P, 1, p[0], p[1], p[2]);
-  r.point = i;
-  cut[id] = r;
+  // corner k
+  double Ck[3];
+  for (int a = 0; a < 3; ++a) Ck[a] = p[a] + h * ((double)((k >> a) & 1) - 0.5);
+  const double Fk = phi_d(P, Ck[0], Ck[1], Ck[2]);
+  double F[8], C[8][3];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    F[c] = __shfl_sync(full, Fk, base + c);
+    for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
+  }
+  // tetrahedron k (k < 6): volume fraction, interface area and centroid
+  double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0};
+  if (k < 6) {
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int v1 = 1 << perm[k][0];
+    const int v2 = v1 | (1 << perm[k][1]);
+    const int idx[4] = {0, v1, v2, 7};
+    double Xt[4][3], ft[4];
+    for (int t = 0; t < 4; ++t) {
+      for (int a = 0; a < 3; ++a) Xt[t][a] = C[idx[t]][a];
+      ft[t] = F[idx[t]];
+    }
+    vneg = frac_tet(ft) / 6.0;
+    area = tet_iface(Xt, ft, wc);
+  }
+  // face k (k < 6): fraction of Omega-
+  double Afk = 0.0;
+  if (k < 6) {
+    const int a = k >> 1, sd = k & 1, j = (a + 1) % 3, kk = (a + 2) % 3;
+    const int b0 = sd << a;
+    const int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << kk), c11 = c10 | (1 << kk);
+    Afk = 0.5 * (frac_tri(F[c00], F[c10], F[c11]) + frac_tri(F[c00], F[c01], F[c11]));
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    vneg += __shfl_xor_sync(full, vneg, o);
+    area += __shfl_xor_sync(full, area, o);
+    for (int a = 0; a < 3; ++a) wc[a] += __shfl_xor_sync(full, wc[a], o);
+  }
+  double xg[3] = {p[0], p[1], p[2]};
+  if (area > 0.0) {
+    for (int a = 0; a < 3; ++a) xg[a] = wc[a] / area;
+    if (P.fp64) {
+      for (int it = 0; it < 3; ++it) {  // Newton projection onto phi = 0
+        double g[3];
+        const double ph = phi_d(P, xg[0], xg[1], xg[2]);
+        grad_phi_d(P, xg, g);
+        const double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        if (gg <= 1e-300) break;
+        for (int a = 0; a < 3; ++a) xg[a] -= ph * g[a] / gg;
+      }
+    } else {
+      // FP32 rows: the projection in FP32 (x_G to ~1e-7; both networks and
+      // alpha are evaluated at the same x_G)
+      float xf[3] = {(float)xg[0], (float)xg[1], (float)xg[2]};
+      for (int it = 0; it < 3; ++it) {
+        float g[3];
+        const float ph = phi_f(P, xf[0], xf[1], xf[2]);
+        grad_phi_f(P, xf, g);
+        const float gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        if (gg <= 1e-30f) break;
+        for (int a = 0; a < 3; ++a) xf[a] -= ph * g[a] / gg;
+      }
+      for (int a = 0; a < 3; ++a) xg[a] = xf[a];
+    }
+  }
+  // four point functions on four lanes (FP64 for the FP64 rows, else FP32)
+  double val = 0.0;
+  if (P.fp64) {
+    if (k == 0 && area > 0.0) val = beta_d(P, xg);
+    else if (k == 1 && area > 0.0) val = alpha_d(xg);
+    else if (k == 2) val = rhs_f<double>(P, 0, p[0], p[1], p[2]);
+    else if (k == 3) val = rhs_f<double>(P, 1, p[0], p[1], p[2]);
+  } else {
+    const float xf[3] = {(float)xg[0], (float)xg[1], (float)xg[2]};
+    if (k == 0 && area > 0.0) val = beta_f(P, xf);
+    else if (k == 1 && area > 0.0) val = alpha_f(xf);
+    else if (k == 2) val = rhs_f<float>(P, 0, (float)p[0], (float)p[1], (float)p[2]);
+    else if (k == 3) val = rhs_f<float>(P, 1, (float)p[0], (float)p[1], (float)p[2]);
+  }
+  const double beta = __shfl_sync(full, val, base + 0), alpha = __shfl_sync(full, val, base + 1);
+  const double f0 = __shfl_sync(full, val, base + 2), f1 = __shfl_sync(full, val, base + 3);
+  if (!live) return;
+  CutRec* r = cut + id;
+  if (k < 6) r->Am[k] = Afk;
+  if (k == 0) {
+    r->Vm = vneg;
+    r->S = area / (h * h);
+    r->has_jump = area > 0.0;
+    for (int a = 0; a < 3; ++a) r->xg[a] = xg[a];
+    r->beta = beta;
+    r->alpha = alpha;
+    r->f[0] = f0;
+    r->f[1] = f1;
+    r->point = i;
+  }
 }
 
 // ------------------------------------------------------------------------
@@ -496,9 +588,9 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
 }
 
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
-  // one warp per block: the few cut cells spread over every SM (FP64, latency bound)
-  int nb = (int)((n + 31) / 32);
-  k_cut_geometry<<<nb, 32, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
+  // 8 lanes per cut cell, 16 cells per block (grid sized for the worst case)
+  int nb = (int)((n + 15) / 16);
+  k_cut_geometry<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
   return cudaGetLastError();
 }
 
