@@ -175,6 +175,92 @@ def cpu_baseline(config_name="C2", target_s=10.0):
                       f"FP64 oracle, OpenMP {cores} threads, {t:.1f} s"}
 
 
+def sphere_exact(x):
+    """Manufactured solution of the sphere workload (u- inside r <= 1/2, u+ outside)."""
+    import numpy as np
+    r = np.sqrt((x ** 2).sum(1))
+    um = np.exp(x[:, 0]) * np.cos(x[:, 1]) * np.sin(x[:, 2])
+    return np.where(r <= 0.5, um, (x ** 2).sum(1))
+
+
+def node_errors(u, n):
+    """L-infinity and RMS error over the interior nodes of the (n+1)^3 grid."""
+    import numpy as np
+    g = -1.0 + np.arange(n + 1) * 2.0 / n
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    x = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    e = np.abs(np.asarray(u, np.float64) - sphere_exact(x)).reshape(n + 1, n + 1, n + 1)
+    e = e[1:-1, 1:-1, 1:-1]
+    return float(e.max()), float(np.sqrt((e ** 2).mean()))
+
+
+def trilinear(u, n, x):
+    import numpy as np
+    U = np.asarray(u, np.float64).reshape(n + 1, n + 1, n + 1)
+    t = (x + 1.0) * n / 2.0
+    i0 = np.clip(np.floor(t).astype(int), 0, n - 1)
+    f = t - i0
+    out = np.zeros(len(x))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                w = ((f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1])
+                     * (f[:, 2] if dz else 1 - f[:, 2]))
+                out += w * U[i0[:, 2] + dz, i0[:, 1] + dy, i0[:, 0] + dx]
+    return out
+
+
+def accuracy(dev, steps=2000):
+    """The metric's accuracy half: the mixed (BF16) and the plain FP32 training step,
+    each run for the workload's 2000 Adam steps from the same start, then the
+    exact-solution error at the 129^3 nodes; and what the trained surrogate gains
+    over the plain method (the grid CG solve at the same h, interpolated
+    trilinearly) at random points within 2h of the interface."""
+    import numpy as np
+    import torch
+
+    import paper_2210_14907_gb300 as nbm
+    out = {"steps": steps, "batch": BATCH, "lr": 1e-3}
+    keep = None
+    for prec, name in ((nbm.PREC_BF16, "mixed_bf16"), (nbm.PREC_FP32, "fp32")):
+        d = nbm.config("C2", precision=prec)
+        prob = nbm.Problem(d)
+        params = nbm.xavier_init(d, seed=0, device=dev)
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        hist = torch.zeros(steps, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.train_steps(params, m, v, 0, steps, BATCH, lr=1e-3, seed=1, loss_hist=hist)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        u = prob.eval_grid(params, 128, precision=nbm.PREC_FP32).cpu().numpy()
+        linf, rmse = node_errors(u, 128)
+        out[name] = {"linf": linf, "rmse": rmse, "final_loss": float(hist[-50:].mean()),
+                     "train_s": wall}
+        if prec == nbm.PREC_BF16:
+            keep = (prob, params)
+    out["mixed_over_fp32_linf"] = out["mixed_bf16"]["linf"] / out["fp32"]["linf"]
+    prob, params = keep
+    n = 128
+    ucg, it, rr, ok = prob.grid_cg_solve(n, rtol=1e-10)
+    ucg = ucg.cpu().numpy()
+    rng = np.random.default_rng(0)
+    dirs = rng.normal(size=(200000, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    pts = dirs * (0.5 + rng.uniform(-4.0 / n, 4.0 / n, 200000))[:, None]
+    ex = sphere_exact(pts)
+    us = prob.eval_points(params, torch.from_numpy(pts.astype(np.float32)).to(dev)).cpu().numpy()
+    es, eg = np.abs(us - ex), np.abs(trilinear(ucg, n, pts) - ex)
+    out["gain_near_interface"] = {
+        "points": "200000 random points within 2h of Gamma, h = 2/128",
+        "surrogate_linf": float(es.max()), "surrogate_rmse": float(np.sqrt((es ** 2).mean())),
+        "grid_cg_trilinear_linf": float(eg.max()),
+        "grid_cg_trilinear_rmse": float(np.sqrt((eg ** 2).mean())),
+        "surrogate_bytes": params.numel() * 4, "grid_solution_bytes": (n + 1) ** 3 * 8}
+    return out
+
+
 def secondary(dev, hbm_peak, peak_src):
     """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
     flower-interface 3->128x4->1 architecture) and the FP64 grid CG solve of the
@@ -183,7 +269,6 @@ def secondary(dev, hbm_peak, peak_src):
     import torch
 
     import paper_2210_14907_gb300 as nbm
-    from oracle import pyoracle as O
     out = {}
     d = nbm.config("C5")
     prob = nbm.Problem(d)
@@ -217,8 +302,7 @@ def secondary(dev, hbm_peak, peak_src):
         wall = time.perf_counter() - t0
         m = (n - 1) ** 3
         gbs = it * 136 * m / wall / 1e9  # algorithmic bytes: SpMV 48 + update 56 + direction 32 per unknown
-        o = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
-        linf, rmse = O.grid_error(o, n, ucg.cpu().numpy())
+        linf, rmse = node_errors(ucg.cpu().numpy(), n)
         out[f"grid_cg_{n}"] = {"unknowns": m, "iterations": it, "relres": rr, "converged": ok,
                                "wall_s": wall, "achieved_gbs": gbs,
                                "hbm_frac": gbs / hbm_peak, "hbm_peak": f"{hbm_peak} GB/s {peak_src} copy",
@@ -254,6 +338,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -368,6 +453,8 @@ def main():
             "clocks": clk.summary(), "wall_s": wall}
     if ws == 1 and not args.no_secondary:
         line["secondary"] = secondary(dev, hbm, peak_src)
+    if ws == 1 and not args.no_accuracy:
+        line["accuracy"] = accuracy(dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -150,6 +150,13 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
 int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision, float* u_out,
                   nbm_stream_t stream);
 
+/* The trained surrogate at n arbitrary points pts [n][3] (FP32, inside the
+ * cube), each with the network of its side of the interface; u_out [n].
+ * Same precision choices and kernels as nbm_eval_grid.  Synchronizes the
+ * stream for the 16-bit paths. */
+int nbm_eval_points(nbm_problem* p, const float* params, const float* pts, int64_t n,
+                    int precision, float* u_out, nbm_stream_t stream);
+
 /* The plain mesh-based method the NBM is bootstrapped from: the same
  * finite-volume rows assembled on the grid of spacing 2/n, one unknown per
  * interior node, solved in FP64 by Jacobi-preconditioned conjugate gradients

@@ -142,6 +142,8 @@ def load_library(build_if_missing: bool = True):
     L.nbm_profile.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.nbm_profile.restype = C.c_int
     L.nbm_eval_grid.argtypes = [P, P, C.c_int, C.c_int, P, P]
+    L.nbm_eval_points.argtypes = [P, P, P, C.c_int64, C.c_int, P, P]
+    L.nbm_eval_points.restype = C.c_int
     L.nbm_grid_cg_solve.argtypes = [P, C.c_int, C.c_double, C.c_int, P, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double), P]
     for fn in ("nbm_init_problem", "nbm_destroy", "nbm_sample_points", "nbm_residual",
@@ -248,6 +250,15 @@ class Problem:
             out = torch.empty((n + 1) ** 3, device="cuda", dtype=torch.float32)
         _check(self.lib.nbm_eval_grid(self.handle, _ptr(params), n, precision, _ptr(out),
                                       _stream(stream)))
+        return out
+
+    def eval_points(self, params, pts, precision=PREC_FP32, out=None, stream=None):
+        _dev(params)
+        _dev(pts)
+        if out is None:
+            out = torch.empty(pts.shape[0], device="cuda", dtype=torch.float32)
+        _check(self.lib.nbm_eval_points(self.handle, _ptr(params), _ptr(pts), pts.shape[0],
+                                        precision, _ptr(out), _stream(stream)))
         return out
 
     def grid_cg_solve(self, n, rtol=1e-10, max_iter=20000, out=None, stream=None):

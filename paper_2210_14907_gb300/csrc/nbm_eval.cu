@@ -61,9 +61,11 @@ __device__ __forceinline__ void reduce32(float (&v)[32], int lane, float& s) {
   s = v[0];
 }
 
+// Points: the (n+1)^3 grid nodes, or (pts != nullptr) npts points pts[3i..3i+2].
 template <int L, bool BF>
 __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __restrict__ params,
                                                     const unsigned char* __restrict__ wimg, int n,
+                                                    const float* __restrict__ pts, int64_t npts,
                                                     float* __restrict__ u_out, int* status) {
   constexpr int H = 128, NG = L - 1;
   extern __shared__ unsigned char smem_raw[];
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
   fence_after_sync();
   const uint32_t tmem = *tslot;
   uint32_t ph_w = 0, ph_mma = 0;
-  const int64_t N1 = n + 1, total = N1 * N1 * N1;
+  const int64_t N1 = n + 1, total = pts ? npts : N1 * N1 * N1;
   const int64_t T = (total + 127) / 128;
   const int64_t tb = (int64_t)blockIdx.x * T / gridDim.x, te = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
   const float hg = 2.0f / (float)n;
@@ -128,10 +130,16 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
         int f = 0;
         float x = 0.f, y = 0.f, z = 0.f;
         if (id < total) {
-          const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
-          x = -1.f + hg * (float)i;
-          y = -1.f + hg * (float)j;
-          z = -1.f + hg * (float)k;
+          if (pts) {
+            x = pts[3 * id];
+            y = pts[3 * id + 1];
+            z = pts[3 * id + 2];
+          } else {
+            const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
+            x = -1.f + hg * (float)i;
+            y = -1.f + hg * (float)j;
+            z = -1.f + hg * (float)k;
+          }
           f = node_phase(P, x, y, z) == s;
         }
         xs[tid] = x;
@@ -225,19 +233,26 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
 // ([unit][thread]), weights read through the read-only cache.
 template <int H, int L>
 __global__ void __launch_bounds__(128) k_eval_fp32(ProbDev P, const float* __restrict__ params,
-                                                   int n, float* __restrict__ u_out) {
+                                                   int n, const float* __restrict__ pts,
+                                                   int64_t npts, float* __restrict__ u_out) {
   extern __shared__ float act[];  // [2][H][128]
   const int tid = threadIdx.x;
-  const int64_t N1 = n + 1, total = N1 * N1 * N1;
+  const int64_t N1 = n + 1, total = pts ? npts : N1 * N1 * N1;
   const int64_t id = (int64_t)blockIdx.x * 128 + tid;
   const float hg = 2.0f / (float)n;
   float x = 0.f, y = 0.f, z = 0.f;
   int s = 0;
   if (id < total) {
-    const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
-    x = -1.f + hg * (float)i;
-    y = -1.f + hg * (float)j;
-    z = -1.f + hg * (float)k;
+    if (pts) {
+      x = pts[3 * id];
+      y = pts[3 * id + 1];
+      z = pts[3 * id + 2];
+    } else {
+      const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
+      x = -1.f + hg * (float)i;
+      y = -1.f + hg * (float)j;
+      z = -1.f + hg * (float)k;
+    }
     s = node_phase(P, x, y, z);
   }
   float result = 0.f;
@@ -270,24 +285,25 @@ __global__ void __launch_bounds__(128) k_eval_fp32(ProbDev P, const float* __res
 
 template <int L, bool BF>
 cudaError_t launch_eval_tc_t(const ProbDev& P, const float* params, const unsigned char* wimg,
-                             int n, float* u, int grid, int* status, cudaStream_t st) {
+                             int n, const float* pts, int64_t npts, float* u, int grid, int* status,
+                             cudaStream_t st) {
   const size_t smem = (size_t)(L + 1) * kImgE + 1024 + 8192;
   cudaError_t e = cudaFuncSetAttribute(k_eval_tc<L, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_eval_tc<L, BF><<<grid, 512, smem, st>>>(P, params, wimg, n, u, status);
+  k_eval_tc<L, BF><<<grid, 512, smem, st>>>(P, params, wimg, n, pts, npts, u, status);
   return cudaGetLastError();
 }
 
 template <int H, int L>
-cudaError_t launch_eval_fp32_t(const ProbDev& P, const float* params, int n, float* u,
-                               cudaStream_t st) {
+cudaError_t launch_eval_fp32_t(const ProbDev& P, const float* params, int n, const float* pts,
+                               int64_t npts, float* u, cudaStream_t st) {
   const size_t smem = 2 * (size_t)H * 128 * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_eval_fp32<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t total = (int64_t)(n + 1) * (n + 1) * (n + 1);
-  k_eval_fp32<H, L><<<(int)((total + 127) / 128), 128, smem, st>>>(P, params, n, u);
+  const int64_t total = pts ? npts : (int64_t)(n + 1) * (n + 1) * (n + 1);
+  k_eval_fp32<H, L><<<(int)((total + 127) / 128), 128, smem, st>>>(P, params, n, pts, npts, u);
   return cudaGetLastError();
 }
 
@@ -296,15 +312,15 @@ cudaError_t launch_eval_fp32_t(const ProbDev& P, const float* params, int n, flo
 
 using namespace nbm;
 
-extern "C" int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision,
-                             float* u_out, nbm_stream_t stream) {
+static int eval_common(nbm_problem* p, const float* params, int n, const float* pts, int64_t npts,
+                       int precision, float* u_out, nbm_stream_t stream) {
   char msg[256];
   if (!p || !params || !u_out) {
     set_error_message("NULL argument");
     return NBM_ERR_INVALID_ARG;
   }
   const nbm_problem_desc& d = problem_desc(p);
-  if (n < 1 || n > 4096) {
+  if (!pts && (n < 1 || n > 4096)) {
     snprintf(msg, sizeof(msg), "grid evaluation needs 1 <= n <= 4096 (n=%d)", n);
     set_error_message(msg);
     return NBM_ERR_INVALID_ARG;
@@ -323,7 +339,7 @@ extern "C" int nbm_eval_grid(nbm_problem* p, const float* params, int n, int pre
   cudaError_t e = cudaSuccess;
   if (precision == NBM_PREC_FP32) {
 #define NBM_EVAL32(HH, LL) \
-  else if (d.width == HH && d.n_hidden == LL) e = launch_eval_fp32_t<HH, LL>(P, params, n, u_out, st);
+  else if (d.width == HH && d.n_hidden == LL) e = launch_eval_fp32_t<HH, LL>(P, params, n, pts, npts, u_out, st);
     if (false) {
     }
     NBM_EVAL32(64, 2) NBM_EVAL32(64, 3) NBM_EVAL32(64, 4) NBM_EVAL32(128, 2) NBM_EVAL32(128, 3)
@@ -344,12 +360,12 @@ extern "C" int nbm_eval_grid(nbm_problem* p, const float* params, int n, int pre
     const int grid = problem_num_sms(p);
     const bool bf = precision == NBM_PREC_BF16;
     if (e == cudaSuccess) {
-      if (d.n_hidden == 2) e = bf ? launch_eval_tc_t<2, true>(P, params, wimg, n, u_out, grid, status, st)
-                                  : launch_eval_tc_t<2, false>(P, params, wimg, n, u_out, grid, status, st);
-      else if (d.n_hidden == 3) e = bf ? launch_eval_tc_t<3, true>(P, params, wimg, n, u_out, grid, status, st)
-                                       : launch_eval_tc_t<3, false>(P, params, wimg, n, u_out, grid, status, st);
-      else e = bf ? launch_eval_tc_t<4, true>(P, params, wimg, n, u_out, grid, status, st)
-                  : launch_eval_tc_t<4, false>(P, params, wimg, n, u_out, grid, status, st);
+      if (d.n_hidden == 2) e = bf ? launch_eval_tc_t<2, true>(P, params, wimg, n, pts, npts, u_out, grid, status, st)
+                                  : launch_eval_tc_t<2, false>(P, params, wimg, n, pts, npts, u_out, grid, status, st);
+      else if (d.n_hidden == 3) e = bf ? launch_eval_tc_t<3, true>(P, params, wimg, n, pts, npts, u_out, grid, status, st)
+                                       : launch_eval_tc_t<3, false>(P, params, wimg, n, pts, npts, u_out, grid, status, st);
+      else e = bf ? launch_eval_tc_t<4, true>(P, params, wimg, n, pts, npts, u_out, grid, status, st)
+                  : launch_eval_tc_t<4, false>(P, params, wimg, n, pts, npts, u_out, grid, status, st);
     }
     int hs = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -367,4 +383,18 @@ extern "C" int nbm_eval_grid(nbm_problem* p, const float* params, int n, int pre
     return NBM_ERR_CUDA;
   }
   return NBM_OK;
+}
+
+extern "C" int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision,
+                             float* u_out, nbm_stream_t stream) {
+  return eval_common(p, params, n, nullptr, 0, precision, u_out, stream);
+}
+
+extern "C" int nbm_eval_points(nbm_problem* p, const float* params, const float* pts, int64_t n,
+                               int precision, float* u_out, nbm_stream_t stream) {
+  if (!pts || n <= 0 || n > ((int64_t)1 << 34)) {
+    set_error_message("nbm_eval_points: need pts != NULL and 0 < n <= 2^34");
+    return NBM_ERR_INVALID_ARG;
+  }
+  return eval_common(p, params, 0, pts, n, precision, u_out, stream);
 }
