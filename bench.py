@@ -40,7 +40,7 @@ WORKLOAD = ("sphere interface (r0=0.5, mu-=1, mu+=10), h=2/128, 262144 uniform c
 BATCH = 262_144
 # DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture
 # summarised in profiles/fused_step_tc_C2.md; None when the kernel changed since.
-FUSED_TRAFFIC_BYTES = 8_970_000  # 8.91 MB read + 0.06 MB write (ncu; k_step_tc as of commit ca96876)
+FUSED_TRAFFIC_BYTES = 9_100_000  # 8.98 MB read + 0.12 MB write per launch (ncu capture of the two-group k_step_tc)
 
 
 def _peaks():

@@ -59,6 +59,12 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
   P.muf[1] = (float)d.mu_plus;
   P.kf[0] = (float)d.k_minus;
   P.kf[1] = (float)d.k_plus;
+  P.inv_h = 1.0 / d.h;
+  P.inv_h2 = 1.0 / (d.h * d.h);
+  for (int s = 0; s < 2; ++s) {
+    P.inv_D[s] = 1.0 / (6.0 * P.mu[s] + d.h * d.h * P.k[s]);
+    P.inv_Df[s] = (float)P.inv_D[s];
+  }
   const int64_t H = d.width;
   P.p_net = 4 * H + (int64_t)(d.n_hidden - 1) * (H * H + H) + H + 1;
   P.gstride = (P.p_net + 3) & ~(int64_t)3;  // 16-byte aligned slices
@@ -216,7 +222,7 @@ static int front_stages(Problem& pb, const ProbDev& P, const float* params, cons
   NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, n), w,
                                   st));
   NBM_CUDA(launch_cut_geometry(P, n, w, st));
-  if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(n, w, st));
+  if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(P, n, w, st));
   StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)n);
   NBM_CUDA(launch_step(pb, P, a, st));
   NBM_CUDA(launch_cut_residual(P, n, (float)(1.0 / (double)n), want_seeds, r2_out, w, st));

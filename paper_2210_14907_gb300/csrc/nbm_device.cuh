@@ -24,6 +24,8 @@ struct ProbDev {
   float hf, inv_hf, h2f, inv_h2f;  // h, 1/h, h^2, 1/h^2 in FP32
   float r0f, ampf, ltf, lpf;
   float muf[2], kf[2];
+  double inv_h, inv_h2, inv_D[2];  // 1/h, 1/h^2, 1/(6 mu_s + h^2 k_s) of the uncut rows
+  float inv_Df[2];
   int64_t p_net;  // parameters per network
   int64_t gstride;  // per-CTA partial-gradient slice stride (p_net rounded up to 4)
 };
@@ -270,6 +272,19 @@ __device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, fl
   dout = d * inv_h;
 }
 
+// The same for mu = 0 (the first layer, whose symmetric increments vanish):
+// Tm = 0, tw = t, dm = 0.
+template <bool FAST>
+__device__ __forceinline__ void tanh_stencil_fwd0(float t, float dt, float h, float inv_h,
+                                                  float inv_h2, float& mo, float& dout) {
+  const float Td = act_tanh<FAST>(dt * h);
+  const float sw = fmaf(-t, t, 1.0f);
+  const float Td2 = Td * Td;
+  const float r2 = rcp<FAST>(fmaf(-t * t, Td2, 1.0f));
+  mo = (-t * sw * Td2 * r2) * inv_h2;
+  dout = (sw * Td * r2) * inv_h;
+}
+
 // Adjoint of one stencil axis.  Inputs: forward outputs t (centre), mo, dout
 // (scaled), upstream gradients with respect to the scaled outputs (Gm, Gd).
 // Writes the gradients with respect to the scaled inputs (gmu, gdel) and
@@ -342,55 +357,62 @@ __device__ inline T uncut_residual(const ProbDev& P, int s, float px, float py, 
   return r * r;
 }
 
-// The same rows evaluated by the 8 lanes of one point (lanes 8j .. 8j+7 of a
-// warp; lane k holds output column k): lane 0 the reaction/source term, lanes
-// 1..6 one cell face each (face f = 2 axis + side), summed with shuffles.
-// Every lane returns r^2 and receives the seed of its own column.  All 32
-// lanes of the warp must call it.
+// The same rows for one point in one thread of the tensor-core path.  fsrc =
+// f^s(p), evaluated ahead (the tile records carry it); divisions by h, h^2
+// and D are multiplications by the reciprocals in P.  out[8] = network
+// outputs in the scaled convention (U, Mt1..3, Dt1..3, unused); sd[8]
+// receives d(scale * r^2)/d(out).  Returns r^2.
 template <typename T>
-__device__ inline T uncut_residual8(const ProbDev& P, int s, float px, float py, float pz,
-                                    float out_k, int k, int lane, T scale, float& seed_k) {
-  const unsigned full = 0xffffffffu;
-  const int base = lane & ~7;
+__device__ __forceinline__ T uncut_residual_pt(const ProbDev& P, int s, float px, float py,
+                                               float pz, T fsrc, const float out[8], T scale,
+                                               float sd[8]) {
   const T h = pc_h<T>(P), h2 = h * h, mu = pc_mu<T>(P, s), kk = pc_k<T>(P, s);
-  const T U = (T)__shfl_sync(full, out_k, base);
-  const bool face = k >= 1 && k <= 6;
-  const int f = face ? k - 1 : 0;
-  const int ax = f >> 1;
-  const T sg = (f & 1) ? (T)1 : (T)-1;
-  const T Mt = (T)__shfl_sync(full, out_k, base + 1 + ax);
-  const T Dt = (T)__shfl_sync(full, out_k, base + 4 + ax);
-  T term = 0;
-  int bnd = 0;
-  if (k == 0) {
-    term = kk * U - rhs_f<T>(P, s, (T)px, (T)py, (T)pz);
-  } else if (face) {
-    const T qx = (T)px + (ax == 0 ? sg * h : (T)0);
-    const T qy = (T)py + (ax == 1 ? sg * h : (T)0);
-    const T qz = (T)pz + (ax == 2 ? sg * h : (T)0);
-    const T qa = ax == 0 ? qx : (ax == 1 ? qy : qz);
-    bnd = fabs(qa) >= (T)1;
-    term = bnd ? -mu * (dirichlet_g<T>(P, qx, qy, qz) - U) / h2 : -mu * (Mt + sg * Dt / h);
+  T ih, ih2, iD;
+  if constexpr (sizeof(T) == 4) {
+    ih = P.inv_hf;
+    ih2 = P.inv_h2f;
+    iD = P.inv_Df[s];
+  } else {
+    ih = P.inv_h;
+    ih2 = P.inv_h2;
+    iD = P.inv_D[s];
   }
-  T Bt = term;
-  int nb = bnd;
+  const T U = (T)out[0];
+  const T x[3] = {(T)px, (T)py, (T)pz};
+  T Bt = kk * U - fsrc;
+  T nb = 0;  // Dirichlet faces
+  T cM[3], cD[3];
 #pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    Bt += __shfl_xor_sync(full, Bt, o);
-    nb += __shfl_xor_sync(full, nb, o);
+  for (int i = 0; i < 3; ++i) {
+    const T Mt = (T)out[1 + i], Dt = (T)out[4 + i];
+    T qm[3] = {x[0], x[1], x[2]}, qp[3] = {x[0], x[1], x[2]};
+    qm[i] -= h;
+    qp[i] += h;
+    const bool bm = fabs(qm[i]) >= (T)1, bp = fabs(qp[i]) >= (T)1;
+    if (bm) {
+      Bt -= mu * (dirichlet_g<T>(P, qm[0], qm[1], qm[2]) - U) * ih2;
+      nb += (T)1;
+    } else {
+      Bt -= mu * (Mt - Dt * ih);
+    }
+    if (bp) {
+      Bt -= mu * (dirichlet_g<T>(P, qp[0], qp[1], qp[2]) - U) * ih2;
+      nb += (T)1;
+    } else {
+      Bt -= mu * (Mt + Dt * ih);
+    }
+    cM[i] = -mu * (T)((bm ? 0 : 1) + (bp ? 0 : 1));
+    cD[i] = -mu * (T)((bp ? 0 : 1) - (bm ? 0 : 1)) * ih;
   }
-  const T D = (T)6 * mu + h2 * kk;
-  const T r = h2 * Bt / D;
-  const T c = scale * (T)2 * r * h2 / D;
-  // Dirichlet flags of the two faces of this column's axis
-  const int ia = (k >= 4 && k <= 6) ? k - 4 : ((k >= 1 && k <= 3) ? k - 1 : 0);
-  const int bm = __shfl_sync(full, bnd, base + 1 + 2 * ia);
-  const int bp = __shfl_sync(full, bnd, base + 2 + 2 * ia);
-  T sd = 0;
-  if (k == 0) sd = c * (kk + (T)nb * mu / h2);
-  else if (k <= 3) sd = c * (-mu * (T)((bm ? 0 : 1) + (bp ? 0 : 1)));
-  else if (k <= 6) sd = c * (-mu * (T)((bp ? 0 : 1) - (bm ? 0 : 1)) / h);
-  seed_k = (float)sd;
+  const T r = h2 * Bt * iD;
+  const T c = scale * (T)2 * r * h2 * iD;
+  sd[0] = (float)(c * (kk + nb * mu * ih2));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sd[1 + i] = (float)(c * cM[i]);
+    sd[4 + i] = (float)(c * cD[i]);
+  }
+  sd[7] = 0.f;
   return r * r;
 }
 

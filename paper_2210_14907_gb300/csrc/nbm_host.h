@@ -36,7 +36,8 @@ struct CutRec {
 // tile's 16 records are one contiguous 512-byte block.
 struct PRec {
   float x, y, z;     // point
-  float gx, gy, gz;  // interface point of a cut cell (0 otherwise)
+  float gx, gy, gz;  // cut cell: interface point.  Uncut point: gx = f^s(p) in
+                     // FP32 (FP64 rows: gx + gy = f^s(p) as a two-float sum), gz = 0
   int pt;            // point index, -1 for padding
   int cutj;          // -1: uncut; else 2*cut_id + has_jump
 };
@@ -121,7 +122,7 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
-cudaError_t launch_gather_tiles(int64_t n, Workspace& ws, cudaStream_t st);
+cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
                                 float* r2_out, Workspace& ws, cudaStream_t st);
 cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,

@@ -154,7 +154,7 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
           : 0;
   if (e == cudaSuccess) e = launch_sample_classify(P, pts, seed, nullptr, step, n, n_band, w, st);
   if (e == cudaSuccess) e = launch_cut_geometry(P, n, w, st);
-  if (e == cudaSuccess && prec != NBM_PREC_FP32) e = launch_gather_tiles(n, w, st);
+  if (e == cudaSuccess && prec != NBM_PREC_FP32) e = launch_gather_tiles(P, n, w, st);
   StepArgs a;
   memset(&a, 0, sizeof(a));
   a.x = w.x;

@@ -406,11 +406,14 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
 }
 
 // ------------------------------------------------------------------------
-// Tile records of the tensor-core kernel: tile t of 16 points, t < T0 from the
-// minus list, then the plus list (each padded to a multiple of 16), and the
-// cut list on its own.  One thread per record; the grid covers the worst case.
+// Tile records of the tensor-core kernel: the minus list, then the plus list
+// (each padded to a multiple of 16 records), and the cut list on its own.  An
+// uncut point's record also carries the source term f^s(p) of its balance row
+// (Sec. 3), so that the fused kernel's residual stage does no transcendental
+// arithmetic.  One thread per record; the grid covers the worst case.
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gather_tiles(const int* __restrict__ counters,
+__global__ void __launch_bounds__(256) k_gather_tiles(const ProbDev P,
+                                                      const int* __restrict__ counters,
                                                       const int* __restrict__ list_m,
                                                       const int* __restrict__ list_p,
                                                       const int* __restrict__ cut_pt,
@@ -422,7 +425,8 @@ __global__ void __launch_bounds__(256) k_gather_tiles(const int* __restrict__ co
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nm = counters[0], np = counters[1], nc = counters[2];
   const int64_t T0 = (nm + 15) / 16, T1 = (np + 15) / 16, Tc = (nc + 15) / 16;
-  auto fill = [&](int e, PRec& o) {
+  // s: phase of the list (0 minus, 1 plus); uncut points carry f^s(p)
+  auto fill = [&](int e, int s, PRec& o) {
     int pt, cid = -1;
     if (e >= 0) {
       pt = e;
@@ -440,8 +444,15 @@ __global__ void __launch_bounds__(256) k_gather_tiles(const int* __restrict__ co
       o.gy = (float)c.xg[1];
       o.gz = (float)c.xg[2];
       o.cutj = 2 * cid + (c.has_jump ? 1 : 0);
+    } else if (P.fp64) {
+      const double f = rhs_f<double>(P, s, (double)o.x, (double)o.y, (double)o.z);
+      o.gx = (float)f;
+      o.gy = (float)(f - (double)o.gx);
+      o.gz = 0.f;
+      o.cutj = -1;
     } else {
-      o.gx = o.gy = o.gz = 0.f;
+      o.gx = rhs_f<float>(P, s, o.x, o.y, o.z);
+      o.gy = o.gz = 0.f;
       o.cutj = -1;
     }
   };
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(256) k_gather_tiles(const int* __restrict__ co
   if (r < 16 * (T0 + T1)) {
     const int64_t t = r / 16, k = r % 16;
     const int64_t slot = (t < T0 ? t : t - T0) * 16 + k;
-    if (t < T0 ? slot < nm : slot < np) fill((t < T0 ? list_m : list_p)[slot], o);
+    if (t < T0 ? slot < nm : slot < np) fill((t < T0 ? list_m : list_p)[slot], t < T0 ? 0 : 1, o);
     rec[r] = o;
   }
   if (r < 16 * Tc) {
@@ -460,7 +471,7 @@ __global__ void __launch_bounds__(256) k_gather_tiles(const int* __restrict__ co
     c.x = c.y = c.z = c.gx = c.gy = c.gz = 0.f;
     c.pt = -1;
     c.cutj = -1;
-    if (r < nc) fill(-(int)r - 1, c);
+    if (r < nc) fill(-(int)r - 1, 0, c);
     rec_cut[r] = c;
   }
 }
@@ -603,10 +614,10 @@ cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool w
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_tiles(int64_t n, Workspace& ws, cudaStream_t st) {
+cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
   const int64_t worst = 2 * n + 32;  // both lists padded
   k_gather_tiles<<<(int)((worst + 255) / 256), 256, 0, st>>>(
-      ws.counters, ws.list_minus, ws.list_plus, ws.cut_pt, ws.x, ws.y, ws.z, ws.cut, ws.rec,
+      P, ws.counters, ws.list_minus, ws.list_plus, ws.cut_pt, ws.x, ws.y, ws.z, ws.cut, ws.rec,
       ws.rec_cut, n);
   return cudaGetLastError();
 }
