@@ -241,6 +241,26 @@ def accuracy(dev, steps=2000):
         if prec == nbm.PREC_BF16:
             keep = (prob, params)
     out["mixed_over_fp32_linf"] = out["mixed_bf16"]["linf"] / out["fp32"]["linf"]
+    # implicit refinement (the paper's base 64^3 cells refined onto 128^3, 256^3,
+    # 512^3): the same network, points and steps, every point with four cells
+    d = nbm.config("C2")
+    d.h, d.refine_levels = 2.0 / 64, 3
+    prob = nbm.Problem(d)
+    params = nbm.xavier_init(d, seed=0, device=dev)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    hist = torch.zeros(steps, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prob.train_steps(params, m, v, 0, steps, BATCH, lr=1e-3, seed=1, loss_hist=hist)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    u = prob.eval_grid(params, 128, precision=nbm.PREC_FP32).cpu().numpy()
+    linf, rmse = node_errors(u, 128)
+    out["refined_mixed_bf16"] = {
+        "cells": "h = 2/64 refined onto 2/128, 2/256, 2/512 (4 cells per point)",
+        "linf": linf, "rmse": rmse, "final_loss": float(hist[-50:].mean()), "train_s": wall,
+        "points_per_s": steps * BATCH / wall}
     prob, params = keep
     n = 128
     ucg, it, rr, ok = prob.grid_cg_solve(n, rtol=1e-10)

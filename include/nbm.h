@@ -85,8 +85,13 @@ typedef struct {
   double h;               /* stencil spacing of the implicit cell, 0 < h <= 0.25      */
   double lambda_jump;     /* weight of the value-jump row in r_p^2 (1 in the paper's reading) */
   double band_fraction;   /* share of sampled points drawn within 4h of Gamma         */
-  int32_t fp64_stencil;   /* -1: automatic (on for h <= 2/512), 0: off, 1: on          */
-  int32_t reserved;
+  int32_t fp64_stencil;   /* -1: automatic (on for h <= 2/512, per level), 0: off, 1: on */
+  int32_t refine_levels;  /* implicit refinement (Sec. 3, Fig. 2: cells "at multi-resolutions";
+                             Sec. 4.2: a base resolution refined three times).  0..3: every
+                             collocation point also gets the cells of spacing h/2, ...,
+                             h/2^refine_levels; their rows are stacked into r_p, i.e.
+                             r_p^2 = sum over the levels of (B/D)^2 + lambda J^2.  Band
+                             points stay within 4h of the base spacing. */
 } nbm_problem_desc;
 
 typedef struct nbm_problem nbm_problem;
@@ -113,7 +118,9 @@ int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, fl
 
 /* Forward pass of the NBM residual (Sec. 3, Fig. 2): for every point, the two
  * networks at the 2d+1 cell vertices (and at the interface point of cut
- * cells), the balance and jump rows, r_p^2 = (B/D)^2 + lambda J^2.
+ * cells), the balance and jump rows, r_p^2 = (B/D)^2 + lambda J^2 (summed
+ * over the refinement levels when refine_levels > 0: one pass of the cells of
+ * spacing h/2^l per level l, on the same points).
  *   params  [P]            network pair
  *   pts     [n][3] or NULL (NULL: sample with seed/step)
  *   r2_out  [n] or NULL    per-point squared residual
@@ -186,8 +193,9 @@ int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused
  *   caller still owns params, pts, grad_out.
  *   Scratch: one static device array of about 12 MB inside libnbm, held on
  *   every GPU that loads the library until the process exits.  Limits:
- *   n <= 16384 points, width <= 128, n_hidden <= 4; the fused kernels run on
- *   at most 16 CTAs.  Larger requests return NBM_ERR_INVALID_ARG.
+ *   n <= 16384 points, width <= 128, n_hidden <= 4, refine_levels == 0; the
+ *   fused kernels run on at most 16 CTAs.  Other requests return
+ *   NBM_ERR_INVALID_ARG.
  *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
  *   on a device looks up the array's device address (cudaGetSymbolAddress,
  *   once per device); make that first call before any stream capture.

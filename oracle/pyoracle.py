@@ -231,6 +231,39 @@ def loss_grad(pr, theta, pts, n_threads=0):
     return L, g
 
 
+def level_problem(pr, level):
+    """Copy of `pr` whose implicit cell has spacing h / 2^level."""
+    q = Problem.from_buffer_copy(pr)
+    q.h = pr.h / 2.0 ** level
+    return q
+
+
+# Implicit refinement (Sec. 3 and Fig. 2: implicit cells "at multi-resolutions";
+# Sec. 4.2: a base resolution implicitly refined three times).  The paper does
+# not say how the levels' rows are combined; the reading taken here stacks the
+# rows of every level into the point's residual vector, so that r_p^2 (and the
+# loss) is the sum over the levels l = 0..levels of the single-level r_p^2 of the
+# cell of spacing h / 2^l around the same point.
+
+
+def loss_levels(pr, levels, theta, pts, n_threads=0, want_r2=False):
+    total, r2s = 0.0, None
+    for lv in range(levels + 1):
+        L, r2 = loss(level_problem(pr, lv), theta, pts, n_threads, want_r2=True)
+        total += L
+        r2s = r2 if r2s is None else r2s + r2
+    return (total, r2s) if want_r2 else total
+
+
+def loss_grad_levels(pr, levels, theta, pts, n_threads=0):
+    total, g = 0.0, None
+    for lv in range(levels + 1):
+        L, gl = loss_grad(level_problem(pr, lv), theta, pts, n_threads)
+        total += L
+        g = gl if g is None else g + gl
+    return total, g
+
+
 def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     lib().nbo_adam_step(_dp(theta), _dp(m), _dp(v), _dp(_vec(grad)), len(theta), t, lr, beta1,
                         beta2, eps)

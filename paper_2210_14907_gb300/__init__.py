@@ -41,7 +41,7 @@ class _Desc(C.Structure):
                 ("mu_minus", C.c_double), ("mu_plus", C.c_double), ("k_minus", C.c_double),
                 ("k_plus", C.c_double), ("h", C.c_double), ("lambda_jump", C.c_double),
                 ("band_fraction", C.c_double), ("fp64_stencil", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("refine_levels", C.c_int32)]
 
 
 @dataclasses.dataclass
@@ -63,12 +63,13 @@ class ProblemDesc:
     lambda_jump: float = 1.0
     band_fraction: float = 0.0
     fp64_stencil: int = -1
+    refine_levels: int = 0  # implicit refinement: also the cells of spacing h/2, ..., h/2^levels
 
     def to_c(self) -> _Desc:
         return _Desc(self.geometry, self.n_hidden, self.width, self.precision, self.r0,
                      self.amp, self.lobes_theta, self.lobes_psi, self.mu_minus, self.mu_plus,
                      self.k_minus, self.k_plus, self.h, self.lambda_jump, self.band_fraction,
-                     self.fp64_stencil, 0)
+                     self.fp64_stencil, self.refine_levels)
 
 
 def config(name: str, precision: int | None = None) -> ProblemDesc:

@@ -31,12 +31,15 @@ static int fail(int code, const char* fmt, ...) {
                   #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
   } while (0)
 
-void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
+void make_prob_dev(const nbm_problem_desc& d, ProbDev& P, int level) {
   memset(&P, 0, sizeof(P));
+  const double h = ldexp(d.h, -level);  // cell spacing of this refinement level
   P.geometry = d.geometry;
   P.H = d.width;
   P.L = d.n_hidden;
-  P.fp64 = d.fp64_stencil < 0 ? (d.h <= 2.0 / 512 + 1e-15) : (d.fp64_stencil != 0);
+  P.fp64 = d.fp64_stencil < 0 ? (h <= 2.0 / 512 + 1e-15) : (d.fp64_stencil != 0);
+  P.level = level;
+  P.h_band = d.h;
   P.r0 = d.r0;
   P.amp = d.amp;
   P.lt = d.lobes_theta;
@@ -45,12 +48,12 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
   P.mu[1] = d.mu_plus;
   P.k[0] = d.k_minus;
   P.k[1] = d.k_plus;
-  P.h = d.h;
+  P.h = h;
   P.lambda = d.lambda_jump;
-  P.hf = (float)d.h;
-  P.inv_hf = (float)(1.0 / d.h);
-  P.h2f = (float)(d.h * d.h);
-  P.inv_h2f = (float)(1.0 / (d.h * d.h));
+  P.hf = (float)h;
+  P.inv_hf = (float)(1.0 / h);
+  P.h2f = (float)(h * h);
+  P.inv_h2f = (float)(1.0 / (h * h));
   P.r0f = (float)d.r0;
   P.ampf = (float)d.amp;
   P.ltf = (float)d.lobes_theta;
@@ -59,10 +62,10 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P) {
   P.muf[1] = (float)d.mu_plus;
   P.kf[0] = (float)d.k_minus;
   P.kf[1] = (float)d.k_plus;
-  P.inv_h = 1.0 / d.h;
-  P.inv_h2 = 1.0 / (d.h * d.h);
+  P.inv_h = 1.0 / h;
+  P.inv_h2 = 1.0 / (h * h);
   for (int s = 0; s < 2; ++s) {
-    P.inv_D[s] = 1.0 / (6.0 * P.mu[s] + d.h * d.h * P.k[s]);
+    P.inv_D[s] = 1.0 / (6.0 * P.mu[s] + h * h * P.k[s]);
     P.inv_Df[s] = (float)P.inv_D[s];
   }
   const int64_t H = d.width;
@@ -74,7 +77,8 @@ static void ws_free(Workspace& w) {
   void* ptrs[] = {w.x, w.y, w.z, w.cls, w.blockcnt, w.list_minus, w.list_plus, w.cut_pt, w.rec,
                   w.rec_cut,
                   w.counters, w.cut, w.cut_out, w.cut_seed, w.loss_part, w.cut_loss_part, w.loss,
-                  w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.corr, w.status};
+                  w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.corr, w.status, w.loss_acc,
+                  w.gacc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -111,6 +115,8 @@ static int ws_reserve(Problem& pb, int64_t n) {
   NBM_CUDA(dalloc(w.loss_part, grid));
   NBM_CUDA(dalloc(w.cut_loss_part, ncb));
   NBM_CUDA(dalloc(w.loss, 1));
+  NBM_CUDA(dalloc(w.loss_acc, 1));
+  NBM_CUDA(dalloc(w.gacc, 2 * (size_t)pb.p_net));
   NBM_CUDA(dalloc(w.gpart, (size_t)grid * 2 * ((pb.p_net + 3) & ~(int64_t)3)));
   NBM_CUDA(dalloc(w.gpart_flag, 2 * (size_t)grid));
   NBM_CUDA(dalloc(w.wt, 2 * (size_t)(L - 1) * H * H));
@@ -145,6 +151,10 @@ static int check_desc(const nbm_problem_desc* d) {
   if (!(d->band_fraction >= 0.0 && d->band_fraction <= 1.0))
     return fail(NBM_ERR_INVALID_ARG, "band_fraction must be in [0, 1]");
   if (!(d->lambda_jump >= 0.0)) return fail(NBM_ERR_INVALID_ARG, "lambda_jump must be >= 0");
+  if (d->refine_levels < 0 || d->refine_levels > 3)
+    return fail(NBM_ERR_INVALID_ARG, "refine_levels must be 0..3 (got %d)", d->refine_levels);
+  if (!(ldexp(d->h, -d->refine_levels) >= 0x1p-12))
+    return fail(NBM_ERR_INVALID_ARG, "finest refined spacing h/2^levels must be >= 2^-12");
   if (d->geometry == NBM_GEOM_SPHERE || d->geometry == NBM_GEOM_FLOWER) {
     if (!(d->r0 > 0.0 && d->r0 + fabs(d->amp) < 0.9))
       return fail(NBM_ERR_INVALID_ARG, "interface must lie inside the cube (r0 + |amp| < 0.9)");
@@ -348,18 +358,22 @@ int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t 
   Problem& pb = p->pb;
   rc = ws_reserve(pb, n);
   if (rc) return rc;
-  ProbDev P;
-  make_prob_dev(pb.desc, P);
   cudaStream_t st = (cudaStream_t)stream;
-  const int prec = pb.desc.precision;
-  NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
-  rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, false, r2_out, st);
-  if (rc) return rc;
-  StepArgs a = base_args(pb, params, MODE_RESIDUAL, 1.0f / (float)n);
-  a.r2_out = r2_out;
-  NBM_CUDA(launch_step(pb, P, a, st));
-  NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, false, nullptr, nullptr, nullptr, nullptr, 0.f,
-                         0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st));
+  const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
+  ProbDev P0;
+  make_prob_dev(pb.desc, P0, 0);
+  NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
+  for (int lv = 0; lv < nlev; ++lv) {  // refinement levels: the same points, spacing h/2^lv
+    ProbDev P;
+    make_prob_dev(pb.desc, P, lv);
+    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, false, r2_out, st);
+    if (rc) return rc;
+    StepArgs a = base_args(pb, params, MODE_RESIDUAL, 1.0f / (float)n);
+    a.r2_out = r2_out;
+    NBM_CUDA(launch_step(pb, P, a, st));
+    NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, false, nullptr, nullptr, nullptr, nullptr, 0.f,
+                           0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st, lv, nlev));
+  }
   if (loss_out) return read_loss(pb, loss_out, st);
   return NBM_OK;
 }
@@ -372,17 +386,21 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
   Problem& pb = p->pb;
   rc = ws_reserve(pb, n);
   if (rc) return rc;
-  ProbDev P;
-  make_prob_dev(pb.desc, P);
   cudaStream_t st = (cudaStream_t)stream;
-  const int prec = pb.desc.precision;
-  NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
-  rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st);
-  if (rc) return rc;
-  StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)n);
-  NBM_CUDA(launch_timed(pb, P, a, st));
-  NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, true, nullptr, nullptr, nullptr, grad_out, 0.f,
-                         0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st));
+  const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
+  ProbDev P0;
+  make_prob_dev(pb.desc, P0, 0);
+  NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
+  for (int lv = 0; lv < nlev; ++lv) {
+    ProbDev P;
+    make_prob_dev(pb.desc, P, lv);
+    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st);
+    if (rc) return rc;
+    StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)n);
+    NBM_CUDA(launch_timed(pb, P, a, st));
+    NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, true, nullptr, nullptr, nullptr, grad_out, 0.f,
+                           0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st, lv, nlev));
+  }
   if (loss_out) return read_loss(pb, loss_out, st);
   return NBM_OK;
 }
@@ -403,21 +421,26 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
   Problem& pb = p->pb;
   rc = ws_reserve(pb, batch);
   if (rc) return rc;
-  ProbDev P;
-  make_prob_dev(pb.desc, P);
   cudaStream_t st = (cudaStream_t)stream;
-  const int prec = pb.desc.precision;
+  const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
   const int64_t base = *step_io;
+  ProbDev PL[4];
+  for (int lv = 0; lv < nlev; ++lv) make_prob_dev(pb.desc, PL[lv], lv);
   NBM_CUDA(cudaMemcpyAsync(pb.ws.step, step_io, sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  NBM_CUDA(launch_prep_weights(P, params, prec, pb.ws, st));
+  NBM_CUDA(launch_prep_weights(PL[0], params, prec, pb.ws, st));
   for (int k = 0; k < n_steps; ++k) {
     const float* pk = pts ? pts + (int64_t)k * batch * 3 : nullptr;
-    rc = front_stages(pb, P, params, pk, batch, seed, pb.ws.step, 0, true, nullptr, st);
-    if (rc) return rc;
-    StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)batch);
-    NBM_CUDA(launch_timed(pb, P, a, st));
-    NBM_CUDA(launch_finish(P, batch, pb.ws.grid, true, false, params, adam_m, adam_v, nullptr, lr,
-                           beta1, beta2, eps, loss_hist, base, prec, pb.ws, st));
+    // refinement levels: the same points (the device step counter advances
+    // after the last level), spacing h/2^lv; one Adam update per step
+    for (int lv = 0; lv < nlev; ++lv) {
+      const ProbDev& P = PL[lv];
+      rc = front_stages(pb, P, params, pk, batch, seed, pb.ws.step, 0, true, nullptr, st);
+      if (rc) return rc;
+      StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)batch);
+      NBM_CUDA(launch_timed(pb, P, a, st));
+      NBM_CUDA(launch_finish(P, batch, pb.ws.grid, true, false, params, adam_m, adam_v, nullptr,
+                             lr, beta1, beta2, eps, loss_hist, base, prec, pb.ws, st, lv, nlev));
+    }
   }
   *step_io = base + n_steps;
   return NBM_OK;

@@ -21,6 +21,8 @@ struct ProbDev {
   double r0, amp, lt, lp;
   double mu[2], k[2];
   double h, lambda;
+  double h_band;   // base spacing: band points are drawn within 4 h_band of Gamma
+  int level;       // refinement level of this pass (0: base cell; > 0 accumulates r2_out)
   float hf, inv_hf, h2f, inv_h2f;  // h, 1/h, h^2, 1/h^2 in FP32
   float r0f, ampf, ltf, lpf;
   float muf[2], kf[2];

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256, 1) k_step_fp32(ProbDev P, StepArgs a) {
       else r2 = (double)uncut_residual<float>(P, net, px, py, pz, out, a.scale, sd);
       if (lane == 0) {
         loss_acc += r2;
-        if (a.r2_out) a.r2_out[pt] = (float)r2;
+        if (a.r2_out) a.r2_out[pt] = (P.level ? a.r2_out[pt] : 0.f) + (float)r2;
       }
 #pragma unroll
       for (int c = 0; c < 8; ++c) seeds[c] = sd[c];

@@ -85,6 +85,8 @@ struct Workspace {
   double* loss_part = nullptr;      // [grid]
   double* cut_loss_part = nullptr;  // [nb_cut]
   double* loss = nullptr;           // [1]
+  double* loss_acc = nullptr;       // [1] loss of the refinement levels done so far
+  float* gacc = nullptr;            // [2 p_net] gradient of the refinement levels done so far
   float* gpart = nullptr;
   int* gpart_flag = nullptr;
   float* wt = nullptr;              // FP32 transposed hidden weights
@@ -111,7 +113,8 @@ struct Problem {
   Workspace ws;
 };
 
-void make_prob_dev(const nbm_problem_desc& d, ProbDev& P);
+// Device constants of refinement level `level` (cell spacing h / 2^level).
+void make_prob_dev(const nbm_problem_desc& d, ProbDev& P, int level = 0);
 // accessors for translation units that do not see the problem object
 void set_error_message(const char* msg);
 const nbm_problem_desc& problem_desc(const nbm_problem* p);
@@ -132,7 +135,7 @@ cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int pr
 cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
-                          Workspace& ws, cudaStream_t st);
+                          Workspace& ws, cudaStream_t st, int level = 0, int n_levels = 1);
 size_t tc_smem_bytes(int L);
 size_t fp32_smem_bytes(int H, int L);
 int tc_supported(int H, int L);

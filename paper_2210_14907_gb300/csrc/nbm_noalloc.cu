@@ -106,6 +106,9 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   make_prob_dev(d, P);
   if (d.width > 128 || d.n_hidden - 1 > kStaticMaxHidden || P.gstride > kStaticMaxPNetStride)
     return fail_static(NBM_ERR_INVALID_ARG, "network larger than the static-scratch limit");
+  if (d.refine_levels != 0)
+    return fail_static(NBM_ERR_INVALID_ARG,
+                       "refinement levels need the problem's own workspace (nbm_loss_grad)");
   unsigned char* base = nullptr;
   int rc = scratch_base(&base);
   if (rc) return rc;

@@ -50,7 +50,7 @@ __device__ inline void draw_point(const ProbDev& P, uint64_t seed, int64_t step,
   double cth = 1.0 - 2.0 * u0;
   double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
   double psi = 2.0 * 3.14159265358979323846 * u1;
-  double t = (2.0 * u2 - 1.0) * 4.0 * P.h;
+  double t = (2.0 * u2 - 1.0) * 4.0 * P.h_band;
   double R = P.r0;
   if (P.geometry == NBM_GEOM_FLOWER) R += P.amp * sin(P.lt * acos(cth)) * cos(P.lp * psi);
   p[0] = (float)quantize_coord((R + t) * sth * cos(psi));
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
         sd[8 * s + 7] = c.has_jump ? (float)(s ? cJ : -cJ) : 0.f;
       }
     }
-    if (r2_out) r2_out[i] = (float)r2;
+    if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
   }
   red[threadIdx.x] = r2;
   __syncthreads();
@@ -513,9 +513,14 @@ __global__ void k_prep_weights(ProbDev P, const float* __restrict__ params, floa
 // Finish: loss (fixed-order sums), then gradient reduction over CTA partials
 // (fixed order) and, when training, Adam (Kingma & Ba, bias-corrected).
 // ------------------------------------------------------------------------
+// Loss of the step: the sum of the partials times 1/N.  With refinement
+// levels, the levels' losses are summed in *loss_acc (acc_in: add the levels
+// done so far; last == 0: only accumulate) and the step is finished after the
+// last level.
 __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __restrict__ clp,
                        int nclp, double scale, double* loss, int64_t* step, float* loss_hist,
-                       int64_t hist_base, int* status, float b1, float b2, float* corr) {
+                       int64_t hist_base, int* status, float b1, float b2, float* corr,
+                       double* loss_acc, int acc_in, int last) {
   __shared__ double red[256];
   double s = 0.0;
   for (int j = threadIdx.x; j < nlp; j += 256) s += lp[j];
@@ -528,6 +533,11 @@ __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __r
   }
   if (threadIdx.x == 0) {
     double L = red[0] * scale;
+    if (acc_in) L += *loss_acc;
+    if (!last) {
+      *loss_acc = L;
+      return;
+    }
     *loss = L;
     if (!isfinite(L)) atomicOr(status, 1);
     if (step) {
@@ -540,11 +550,14 @@ __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __r
   }
 }
 
+// Gradient of the step (fixed CTA order), then Adam.  With refinement levels
+// the levels' gradients are summed in gacc: gacc_in (levels done so far) is
+// added, and a level that is not the last stores the sum in gacc_out and stops.
 __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpart,
                               const int* __restrict__ flag, float* grad_out, float* params,
                               float* m, float* v, float lr, float b1, float b2, float eps,
                               const float* corr, const double* loss, float* wt, void* wtc,
-                              int prec) {
+                              int prec, const float* gacc_in, float* gacc_out) {
   const int64_t pn = P.p_net;
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= 2 * pn) return;
@@ -553,6 +566,11 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
   float g = 0.f;
   for (int c = 0; c < grid; ++c)
     if (flag[2 * c + s]) g += gpart[((int64_t)c * 2 + s) * P.gstride + jj];
+  if (gacc_in) g += gacc_in[j];
+  if (gacc_out) {
+    gacc_out[j] = g;
+    return;
+  }
   if (grad_out) grad_out[j] = g;
   if (!params) return;
   if (!isfinite(*loss)) return;  // non-finite step: skip the update
@@ -632,16 +650,18 @@ cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec,
 cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
-                          Workspace& ws, cudaStream_t st) {
+                          Workspace& ws, cudaStream_t st, int level, int n_levels) {
+  const bool last = level == n_levels - 1;
   int ncb = (int)((n + 127) / 128);
   k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb, 1.0 / (double)n, ws.loss,
                             adam ? ws.step : nullptr, loss_hist, hist_base, ws.status, b1, b2,
-                            ws.corr);
+                            ws.corr, ws.loss_acc, level > 0, last);
   if (adam || want_grad) {
     int64_t tot = 2 * P.p_net;
     k_reduce_adam<<<(int)((tot + 255) / 256), 256, 0, st>>>(
         P, grid, ws.gpart, ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps,
-        ws.corr, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
+        ws.corr, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
+        level > 0 ? ws.gacc : nullptr, last ? nullptr : ws.gacc);
   }
   return cudaGetLastError();
 }

@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
             r2 = uncut_residual_pt<float>(P, net, pi.x, pi.y, pi.z, pi.gx, o, a.scale, sd);
             loss_acc += r2;
           }
-          if (a.r2_out) a.r2_out[pi.pt] = r2;
+          if (a.r2_out) a.r2_out[pi.pt] = (P.level ? a.r2_out[pi.pt] : 0.f) + r2;
           // seeds in this kernel's column convention
           if (!SCALED) {
 #pragma unroll

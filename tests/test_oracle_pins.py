@@ -314,6 +314,37 @@ def test_loss_is_mean_of_point_residuals_and_splits_over_ranks():
     assert np.allclose(gs, gf, rtol=1e-12, atol=1e-15)
 
 
+def test_refinement_levels_stack_the_rows_of_every_spacing():
+    """Implicit refinement (Sec. 3, Fig. 2; reading: the rows of the cells of
+    spacing h, h/2, h/4 around the same point are stacked into r_p): the
+    multi-level r_p^2 equals the per-point terms of each spacing summed, a point
+    can be cut at one level and uncut at another, and the multi-level gradient
+    matches central differences of the multi-level loss."""
+    pr = _small_problem(O.GEOM_FLOWER)
+    rng = np.random.default_rng(14)
+    P = 2 * O.params_per_net(pr)
+    th = rng.normal(size=P) * 0.5
+    pts = O.sample_points(pr, 5, 3, 90, 60)
+    q = O.level_problem(pr, 2)
+    assert q.h == pr.h / 4 and q.mu_plus == pr.mu_plus and q.geometry == pr.geometry
+    L, r2 = O.loss_levels(pr, 2, th, pts, want_r2=True)
+    assert abs(L - r2.mean()) < 1e-13 * max(1.0, L)
+    n_changed = 0
+    for i, p in enumerate(pts):
+        terms = [O.point_terms(O.level_problem(pr, lv), th, p) for lv in range(3)]
+        ref = sum(t["r2"] for t in terms)
+        assert abs(r2[i] - ref) <= 1e-12 * max(1.0, ref)
+        n_changed += len({t["cut"] for t in terms}) > 1
+    assert n_changed > 0
+    Lg, g = O.loss_grad_levels(pr, 2, th, pts)
+    assert abs(Lg - L) < 1e-13 * max(1.0, L)
+    for j in rng.choice(P, size=24, replace=False):
+        e = np.zeros(P)
+        e[j] = 1e-6
+        fd = (O.loss_levels(pr, 2, th + e, pts) - O.loss_levels(pr, 2, th - e, pts)) / 2e-6
+        assert abs(fd - g[j]) <= 1e-6 * np.max(np.abs(g)) + 1e-6 * abs(g[j])
+
+
 # ------------------------------------------------------------------ Adam ----
 def test_adam_closed_form_first_two_steps():
     """Kingma & Ba: with zero state, step 1 moves each weight by lr*g/(|g|+eps)."""
