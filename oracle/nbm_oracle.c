@@ -100,17 +100,35 @@ int nbo_phase(const nbo_problem* pr, const double x[3]) {
   return nbo_phi(pr, x) <= 0.0 ? 0 : 1;
 }
 
-/* Manufactured pair of the benchmark configurations:
- *   u- = exp(x) cos(y) sin(z)   (so Laplacian u- = -u-)
- *   u+ = x^2 + y^2 + z^2        (Laplacian u+ = 6)                      */
+/* Manufactured pairs.
+ * Solution 0 (the benchmark configurations), constant mu^s:
+ *   u- = exp(x) cos(y) sin(z)   (Laplacian u- = -u-)
+ *   u+ = x^2 + y^2 + z^2        (Laplacian u+ = 6)
+ * Solution 1 (Sec. 4.1):
+ *   u- = exp(z),  u+ = cos(x) sin(y),
+ *   mu- = y^2 ln(x + 2) + 4,  mu+ = exp(-z).                             */
 double nbo_exact_u(const nbo_problem* pr, int s, const double x[3]) {
-  (void)pr;
+  if (pr->solution == 1) {
+    if (s == 0) return exp(x[2]);
+    return cos(x[0]) * sin(x[1]);
+  }
   if (s == 0) return exp(x[0]) * cos(x[1]) * sin(x[2]);
   return x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
 }
 
 void nbo_exact_grad_u(const nbo_problem* pr, int s, const double x[3], double g[3]) {
-  (void)pr;
+  if (pr->solution == 1) {
+    if (s == 0) {
+      g[0] = 0.0;
+      g[1] = 0.0;
+      g[2] = exp(x[2]);
+    } else {
+      g[0] = -sin(x[0]) * sin(x[1]);
+      g[1] = cos(x[0]) * cos(x[1]);
+      g[2] = 0.0;
+    }
+    return;
+  }
   if (s == 0) {
     double e = exp(x[0]);
     g[0] = e * cos(x[1]) * sin(x[2]);
@@ -123,11 +141,43 @@ void nbo_exact_grad_u(const nbo_problem* pr, int s, const double x[3], double g[
   }
 }
 
-/* f^s = k^s u^s - mu^s Laplacian(u^s)  (Sec. 2, constant mu^s and k^s). */
+static double exact_laplacian(const nbo_problem* pr, int s, const double x[3]) {
+  if (pr->solution == 1) {
+    if (s == 0) return exp(x[2]);
+    return -2.0 * cos(x[0]) * sin(x[1]);
+  }
+  if (s == 0) return -nbo_exact_u(pr, 0, x);
+  return 6.0;
+}
+
+double nbo_mu(const nbo_problem* pr, int s, const double x[3]) {
+  if (pr->solution == 1) {
+    if (s == 0) return x[1] * x[1] * log(x[0] + 2.0) + 4.0;
+    return exp(-x[2]);
+  }
+  return s == 0 ? pr->mu_minus : pr->mu_plus;
+}
+
+static void mu_grad(const nbo_problem* pr, int s, const double x[3], double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  if (pr->solution != 1) return;
+  if (s == 0) {
+    g[0] = x[1] * x[1] / (x[0] + 2.0);
+    g[1] = 2.0 * x[1] * log(x[0] + 2.0);
+  } else {
+    g[2] = -exp(-x[2]);
+  }
+}
+
+/* f^s = k^s u^s - div(mu^s grad u^s) = k^s u^s - mu^s Lap(u^s) - grad(mu^s).grad(u^s)
+ * (Sec. 2 with k^s constant). */
 double nbo_rhs_f(const nbo_problem* pr, int s, const double x[3]) {
-  double u = nbo_exact_u(pr, s, x);
-  if (s == 0) return pr->k_minus * u - pr->mu_minus * (-u);
-  return pr->k_plus * u - pr->mu_plus * 6.0;
+  double k = s == 0 ? pr->k_minus : pr->k_plus;
+  double gu[3], gm[3];
+  nbo_exact_grad_u(pr, s, x, gu);
+  mu_grad(pr, s, x, gm);
+  return k * nbo_exact_u(pr, s, x) - nbo_mu(pr, s, x) * exact_laplacian(pr, s, x) -
+         (gm[0] * gu[0] + gm[1] * gu[1] + gm[2] * gu[2]);
 }
 
 /* [u] = u+ - u- (reading: jumps are plus side minus minus side). */
@@ -145,7 +195,8 @@ double nbo_beta(const nbo_problem* pr, const double x[3]) {
   double nn = sqrt(gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2]);
   if (nn == 0.0) return 0.0;
   double b = 0.0;
-  for (int i = 0; i < 3; ++i) b += (pr->mu_plus * gp[i] - pr->mu_minus * gm[i]) * gphi[i] / nn;
+  const double mp = nbo_mu(pr, 1, x), mm = nbo_mu(pr, 0, x);
+  for (int i = 0; i < 3; ++i) b += (mp * gp[i] - mm * gm[i]) * gphi[i] / nn;
   return b;
 }
 
@@ -365,7 +416,8 @@ void nbo_cell_geometry(const nbo_problem* pr, const double p[3], double h, nbo_c
 /* ======================================================================
  * Networks (Sec. 3: "two neural networks are used to represent the
  * solution on each side"): a_0 = x, z_l = W_l a_{l-1} + b_l,
- * a_l = tanh(z_l) for the hidden layers, u = w . a_L + b.
+ * a_l = act(z_l) for the hidden layers (tanh, or sin for the sine-activated
+ * networks of Sec. 4.1), u = w . a_L + b.
  * Layout per net: W1[H][3], b1[H], then (W_l[H][H], b_l[H]) for
  * l = 2..n_hidden, then w[H], b.  Net minus first, then net plus.
  * ==================================================================== */
@@ -374,20 +426,35 @@ int64_t nbo_params_per_net(const nbo_problem* pr) {
   return 4 * H + (int64_t)(pr->n_hidden - 1) * (H * H + H) + H + 1;
 }
 
-/* forward; acts (if given) receives the n_hidden hidden activations */
+/* activation and its derivative at z */
+static double act_fn(const nbo_problem* pr, double z, double* dz) {
+  if (pr->activation == 1) {
+    *dz = cos(z);
+    return sin(z);
+  }
+  double t = tanh(z);
+  *dz = 1.0 - t * t;
+  return t;
+}
+
+/* forward; acts (if given, 2 n_hidden H values) receives the hidden
+ * activations act(z_l) followed by their derivatives act'(z_l) */
 static double mlp_forward(const nbo_problem* pr, const double* th, const double x[3], double* acts) {
   int H = pr->width, L = pr->n_hidden;
   double* a = acts;
-  double buf[2][512];
+  double buf[2][512], dbuf[512];
   double* cur = buf[0];
   const double* W = th;
   const double* b = th + 3 * H;
   for (int n = 0; n < H; ++n) {
     double z = b[n];
     for (int j = 0; j < 3; ++j) z += W[3 * n + j] * x[j];
-    cur[n] = tanh(z);
+    cur[n] = act_fn(pr, z, &dbuf[n]);
   }
-  if (a) memcpy(a, cur, sizeof(double) * H);
+  if (a) {
+    memcpy(a, cur, sizeof(double) * H);
+    memcpy(a + (int64_t)L * H, dbuf, sizeof(double) * H);
+  }
   const double* q = th + 4 * H;
   for (int l = 1; l < L; ++l) {
     double* nxt = buf[l & 1];
@@ -396,10 +463,13 @@ static double mlp_forward(const nbo_problem* pr, const double* th, const double 
     for (int n = 0; n < H; ++n) {
       double z = bl[n];
       for (int k = 0; k < H; ++k) z += Wl[(int64_t)n * H + k] * cur[k];
-      nxt[n] = tanh(z);
+      nxt[n] = act_fn(pr, z, &dbuf[n]);
     }
     cur = nxt;
-    if (a) memcpy(a + (int64_t)l * H, cur, sizeof(double) * H);
+    if (a) {
+      memcpy(a + (int64_t)l * H, cur, sizeof(double) * H);
+      memcpy(a + (int64_t)(L + l) * H, dbuf, sizeof(double) * H);
+    }
     q += (int64_t)H * H + H;
   }
   double u = q[H];
@@ -429,9 +499,9 @@ static void mlp_backward(const nbo_problem* pr, const double* th, const double x
     /* layer l+1 in 1-based numbering: input acts[l-1], output acts[l] */
     int64_t off = 4 * H + (int64_t)(l - 1) * (H * H + H);
     const double* Wl = th + off;
-    const double* aout = acts + (int64_t)l * H;
+    const double* dout = acts + (int64_t)(L + l) * H;  /* act'(z) of layer l+1 */
     const double* ain = acts + (int64_t)(l - 1) * H;
-    for (int n = 0; n < H; ++n) gz[n] = g[n] * (1.0 - aout[n] * aout[n]);
+    for (int n = 0; n < H; ++n) gz[n] = g[n] * dout[n];
     for (int n = 0; n < H; ++n) {
       for (int k = 0; k < H; ++k) grad[off + (int64_t)n * H + k] += gz[n] * ain[k];
       grad[off + (int64_t)H * H + n] += gz[n];
@@ -442,9 +512,9 @@ static void mlp_backward(const nbo_problem* pr, const double* th, const double x
       g[k] = s;
     }
   }
-  const double* a1 = acts;
+  const double* d1 = acts + (int64_t)L * H;
   for (int n = 0; n < H; ++n) {
-    double gz1 = g[n] * (1.0 - a1[n] * a1[n]);
+    double gz1 = g[n] * d1[n];
     for (int j = 0; j < 3; ++j) grad[3 * n + j] += gz1 * x[j];
     grad[3 * H + n] += gz1;
   }
@@ -501,14 +571,15 @@ void nbo_sample_points(const nbo_problem* pr, uint64_t seed, int64_t step, int64
  * of the cell and using the flux-jump condition on the interface gives,
  * after division by h,
  *   B = h^2 sum_s V^s (k^s U^s(p) - f^s(p))
- *       - sum_faces sum_s A^s_f mu^s (U^s(p + sigma h e_i) - U^s(p))
+ *       - sum_faces sum_s A^s_f mu^s_f (U^s(p + sigma h e_i) - U^s(p))
  *       + h S beta(x_G)
- * with U^s(q) = g(q) whenever q leaves the cube (Dirichlet data).
- * Jacobi preconditioner M = diag(A):  D = sum_f sum_s A^s_f mu^s + h^2 sum_s V^s k^s.
+ * with U^s(q) = g(q) whenever q leaves the cube (Dirichlet data) and
+ * mu^s_f = mu^s at the face centre p + sigma (h/2) e_i (constant for the
+ * benchmark pair).
+ * Jacobi preconditioner M = diag(A):  D = sum_f sum_s A^s_f mu^s_f + h^2 sum_s V^s k^s.
  * Value jump (cut cells with S > 0):  J = U+(x_G) - U-(x_G) - alpha(x_G).
  * r_p^2 = (B/D)^2 + lambda J^2.
  * ==================================================================== */
-static double mu_of(const nbo_problem* pr, int s) { return s == 0 ? pr->mu_minus : pr->mu_plus; }
 static double k_of(const nbo_problem* pr, int s) { return s == 0 ? pr->k_minus : pr->k_plus; }
 
 static int outside_box(const double q[3]) {
@@ -539,7 +610,7 @@ static void point_core(const nbo_problem* pr, const double* theta, const double 
   int has_jump = cell.cut && cell.S > 0.0;
   int used[2];
   double* acts = NULL;
-  if (grad) acts = (double*)malloc(sizeof(double) * 2 * 8 * L * H);
+  if (grad) acts = (double*)malloc(sizeof(double) * 2 * 8 * 2 * L * H);
   for (int s = 0; s < 2; ++s) {
     double any = cell.V[s];
     for (int f = 0; f < 6; ++f) any += cell.A[s][f];
@@ -556,18 +627,25 @@ static void point_core(const nbo_problem* pr, const double* theta, const double 
         U[s][e] = nbo_exact_u(pr, s, Q[e]);
       } else {
         const double* th = theta + s * Pn;
-        U[s][e] = mlp_forward(pr, th, Q[e], acts ? acts + ((int64_t)s * 8 + e) * L * H : NULL);
+        U[s][e] = mlp_forward(pr, th, Q[e], acts ? acts + ((int64_t)s * 8 + e) * 2 * L * H : NULL);
       }
     }
   }
+  /* mu^s at the six face centres p + sigma (h/2) e_i */
+  double muf[2][6];
+  for (int f = 0; f < 6; ++f) {
+    double c[3] = {p[0], p[1], p[2]};
+    c[f / 2] += (f & 1) ? 0.5 * h : -0.5 * h;
+    for (int s = 0; s < 2; ++s) muf[s][f] = nbo_mu(pr, s, c);
+  }
   double B = 0.0, D = 0.0;
   for (int s = 0; s < 2; ++s) {
-    double mu = mu_of(pr, s), k = k_of(pr, s);
+    double k = k_of(pr, s);
     B += h * h * cell.V[s] * (k * U[s][0] - nbo_rhs_f(pr, s, p));
     D += h * h * cell.V[s] * k;
     for (int f = 0; f < 6; ++f) {
-      B -= cell.A[s][f] * mu * (U[s][1 + f] - U[s][0]);
-      D += cell.A[s][f] * mu;
+      B -= cell.A[s][f] * muf[s][f] * (U[s][1 + f] - U[s][0]);
+      D += cell.A[s][f] * muf[s][f];
     }
   }
   if (has_jump) B += h * cell.S * nbo_beta(pr, cell.xg);
@@ -589,12 +667,12 @@ static void point_core(const nbo_problem* pr, const double* theta, const double 
     double cJ = scale * 2.0 * pr->lambda_jump * J;
     for (int s = 0; s < 2; ++s) {
       if (!used[s]) continue;
-      double mu = mu_of(pr, s), k = k_of(pr, s);
+      double k = k_of(pr, s);
       double c[8] = {0};
       c[0] = h * h * cell.V[s] * k;
       for (int f = 0; f < 6; ++f) {
-        c[0] += cell.A[s][f] * mu;
-        c[1 + f] = -cell.A[s][f] * mu;
+        c[0] += cell.A[s][f] * muf[s][f];
+        c[1 + f] = -cell.A[s][f] * muf[s][f];
       }
       for (int e = 0; e < 7; ++e) c[e] *= cB;
       c[7] = has_jump ? (s == 1 ? cJ : -cJ) : 0.0;
@@ -602,7 +680,7 @@ static void point_core(const nbo_problem* pr, const double* theta, const double 
         if (c[e] == 0.0) continue;
         if (e >= 1 && e <= 6 && !inside[e - 1]) continue;
         if (e == 7 && !has_jump) continue;
-        mlp_backward(pr, theta + s * Pn, Q[e], c[e], acts + ((int64_t)s * 8 + e) * L * H,
+        mlp_backward(pr, theta + s * Pn, Q[e], c[e], acts + ((int64_t)s * 8 + e) * 2 * L * H,
                      grad + s * Pn);
       }
     }
@@ -784,9 +862,11 @@ static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, gr
       double jq = nbo_alpha(pg, q);
       if (sq == 1) cq[0] = -jq; else cq[1] = jq;
     }
+    double fc[3] = {p[0], p[1], p[2]};  /* face centre, shared with the neighbour's row */
+    fc[ax] += 0.5 * sg * hg;
     double wf = 0.0;
     for (int s = 0; s < 2; ++s) {
-      double a = cell.A[s][f] * mu_of(pg, s);
+      double a = cell.A[s][f] * nbo_mu(pg, s, fc);
       wf += a;
       known -= a * (cq[s] - cp[s]);
     }

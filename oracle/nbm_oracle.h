@@ -47,6 +47,11 @@ typedef struct {
   double mu_minus, mu_plus, k_minus, k_plus;
   double h;           /* stencil spacing of the implicit cell               */
   double lambda_jump; /* weight of the value-jump row in r_p^2               */
+  int32_t solution;   /* manufactured pair: 0 the benchmark pair with constant
+                         mu_minus/mu_plus; 1 the pair of Sec. 4.1 with the
+                         variable coefficients mu- = y^2 ln(x+2) + 4,
+                         mu+ = exp(-z) (mu_minus/mu_plus unused)            */
+  int32_t activation; /* hidden-layer activation: 0 tanh, 1 sin            */
 } nbo_problem;
 
 /* Per-point terms of the residual (reading of Sec. 3). */
@@ -77,6 +82,7 @@ double nbo_phi(const nbo_problem* pr, const double x[3]);
 void nbo_grad_phi(const nbo_problem* pr, const double x[3], double g[3]);
 int nbo_phase(const nbo_problem* pr, const double x[3]); /* 0 = minus (phi<=0), 1 = plus */
 double nbo_exact_u(const nbo_problem* pr, int s, const double x[3]);
+double nbo_mu(const nbo_problem* pr, int s, const double x[3]); /* diffusion coefficient mu^s(x) */
 void nbo_exact_grad_u(const nbo_problem* pr, int s, const double x[3], double g[3]);
 double nbo_rhs_f(const nbo_problem* pr, int s, const double x[3]);
 double nbo_alpha(const nbo_problem* pr, const double x[3]);

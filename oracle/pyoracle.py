@@ -50,7 +50,11 @@ class Problem(C.Structure):
         ("mu_minus", C.c_double), ("mu_plus", C.c_double), ("k_minus", C.c_double),
         ("k_plus", C.c_double),
         ("h", C.c_double), ("lambda_jump", C.c_double),
+        ("solution", C.c_int32), ("activation", C.c_int32),
     ]
+
+SOL_BENCH, SOL_SEC41 = 0, 1
+ACT_TANH, ACT_SIN = 0, 1
 
 
 class PointTerms(C.Structure):
@@ -66,9 +70,9 @@ class Cell(C.Structure):
 
 def make_problem(geometry=GEOM_SPHERE, n_hidden=2, width=64, r0=0.5, amp=0.1, lobes_theta=5.0,
                  lobes_psi=3.0, mu_minus=1.0, mu_plus=10.0, k_minus=0.0, k_plus=0.0, h=2.0 / 32,
-                 lambda_jump=1.0) -> Problem:
+                 lambda_jump=1.0, solution=SOL_BENCH, activation=ACT_TANH) -> Problem:
     return Problem(geometry, n_hidden, width, 0, r0, amp, lobes_theta, lobes_psi, mu_minus,
-                   mu_plus, k_minus, k_plus, h, lambda_jump)
+                   mu_plus, k_minus, k_plus, h, lambda_jump, solution, activation)
 
 
 _D = C.POINTER(C.c_double)
@@ -92,6 +96,8 @@ def lib():
             L.nbo_exact_grad_u.argtypes = [_P, C.c_int, _D, _D]
             L.nbo_rhs_f.argtypes = [_P, C.c_int, _D]
             L.nbo_rhs_f.restype = C.c_double
+            L.nbo_mu.argtypes = [_P, C.c_int, _D]
+            L.nbo_mu.restype = C.c_double
             for fn in ("nbo_alpha", "nbo_beta", "nbo_dirichlet_g"):
                 getattr(L, fn).argtypes = [_P, _D]
                 getattr(L, fn).restype = C.c_double
@@ -163,6 +169,10 @@ def exact_grad_u(pr, s, x):
     g = np.zeros(3)
     lib().nbo_exact_grad_u(C.byref(pr), s, _dp(_vec(x)), _dp(g))
     return g
+
+
+def mu(pr, s, x):
+    return lib().nbo_mu(C.byref(pr), s, _dp(_vec(x)))
 
 
 def rhs_f(pr, s, x):

@@ -199,6 +199,31 @@ def test_rhs_and_jumps_match_finite_differences():
         assert abs(O.alpha(pr, p) - (O.exact_u(pr, 1, p) - O.exact_u(pr, 0, p))) < 1e-15
 
 
+def test_sec41_pair_matches_finite_differences():
+    """Sec. 4.1 pair (variable mu): f = k u - div(mu grad u) against a central
+    difference of the flux mu grad u; beta = [mu d_n u] with mu at the point."""
+    rng = np.random.default_rng(23)
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, k_minus=0.4, k_plus=1.1, solution=O.SOL_SEC41)
+    e = 1e-3
+    for _ in range(30):
+        x = rng.uniform(-0.8, 0.8, size=3)
+        for s, k in ((0, 0.4), (1, 1.1)):
+            div = 0.0
+            for ei in np.eye(3):
+                fp = O.mu(pr, s, x + 0.5 * e * ei) * (O.exact_u(pr, s, x + e * ei) - O.exact_u(pr, s, x))
+                fm = O.mu(pr, s, x - 0.5 * e * ei) * (O.exact_u(pr, s, x) - O.exact_u(pr, s, x - e * ei))
+                div += (fp - fm) / e**2
+            assert abs(O.rhs_f(pr, s, x) - (k * O.exact_u(pr, s, x) - div)) < 1e-5
+            assert np.allclose(O.exact_grad_u(pr, s, x),
+                               _fd_grad(lambda y: O.exact_u(pr, s, y), x), atol=1e-8)
+    for p in _band_points(pr, 30, 0.0, rng):
+        n = O.grad_phi(pr, p)
+        n /= np.linalg.norm(n)
+        dn = [(O.exact_u(pr, s, p + 1e-5 * n) - O.exact_u(pr, s, p - 1e-5 * n)) / 2e-5
+              for s in (0, 1)]
+        assert abs(O.beta(pr, p) - (O.mu(pr, 1, p) * dn[1] - O.mu(pr, 0, p) * dn[0])) < 1e-6
+
+
 # ------------------------------------------------ residual rows (Sec. 3) ----
 def test_balance_row_vanishes_for_quadratic_solution():
     """No interface, constant mu: the 7-point FV row is exact for quadratics."""
@@ -219,24 +244,30 @@ def test_preconditioner_is_jacobi_diagonal_of_7_point_operator():
         assert abs(t["D"] - (6 * mu + h * h * k)) < 1e-14
 
 
-def test_uncut_truncation_is_fourth_order_in_B():
+@pytest.mark.parametrize("geom,sol", [(O.GEOM_ALL_MINUS, O.SOL_BENCH),
+                                      (O.GEOM_ALL_MINUS, O.SOL_SEC41),
+                                      (O.GEOM_ALL_PLUS, O.SOL_SEC41)])
+def test_uncut_truncation_is_fourth_order_in_B(geom, sol):
     """B = h^2 x (PDE residual) so its truncation error is O(h^4) away from Gamma."""
     rng = np.random.default_rng(6)
     pts = rng.uniform(-0.8, 0.8, size=(40, 3))
     mx = []
     for h in (1 / 8, 1 / 16, 1 / 32):
-        pr = O.make_problem(geometry=O.GEOM_ALL_MINUS, mu_minus=2.0, h=h)
+        pr = O.make_problem(geometry=geom, mu_minus=2.0, h=h, solution=sol)
         mx.append(max(abs(O.point_terms(pr, None, p, mode=1)["B"]) for p in pts))
     assert mx[0] / mx[1] > 15.0 and mx[1] / mx[2] > 15.5
 
 
-def test_cut_cell_consistency_is_second_order():
+@pytest.mark.parametrize("sol", [O.SOL_BENCH, O.SOL_SEC41])
+def test_cut_cell_consistency_is_second_order(sol):
     """Exact u^+- in cut cells: B = O(h^2); this fails if the interface flux term,
-    its sign, a face fraction or a volume fraction is wrong."""
+    its sign, a face fraction or a volume fraction is wrong (and, for the Sec. 4.1
+    pair, if mu is not taken at the face centres and at x_G)."""
     rng = np.random.default_rng(8)
     mx = []
     for h in (1 / 32, 1 / 64, 1 / 128):
-        pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0, h=h)
+        pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0, h=h,
+                            solution=sol)
         res = [O.point_terms(pr, None, p, mode=1) for p in _band_points(pr, 150, 0.5 * h, rng)]
         assert all(r["cut"] for r in res)
         mx.append(max(abs(r["B"]) for r in res))
@@ -266,6 +297,10 @@ def test_mlp_textbook_cases():
     th[-1] = -0.5
     ref = 2.0 * math.tanh(1.3 * math.tanh(0.8 * x[1] + 0.1) - 0.2) - 0.5
     assert abs(O.mlp_eval(pr, th, x) - ref) < 1e-15
+    # the same path with sine activations (Sec. 4.1 networks)
+    prs = O.make_problem(n_hidden=2, width=4, activation=O.ACT_SIN)
+    ref = 2.0 * math.sin(1.3 * math.sin(0.8 * x[1] + 0.1) - 0.2) - 0.5
+    assert abs(O.mlp_eval(prs, th, x) - ref) < 1e-15
     # tiny weights: the network is linear to first order
     rng = np.random.default_rng(0)
     th = rng.normal(size=P) * 1e-4
@@ -274,15 +309,18 @@ def test_mlp_textbook_cases():
 
 
 # -------------------------------------------------------------- gradient ----
-def _small_problem(geom=O.GEOM_SPHERE):
+def _small_problem(geom=O.GEOM_SPHERE, solution=O.SOL_BENCH, activation=O.ACT_TANH):
     return O.make_problem(geometry=geom, n_hidden=3, width=8, h=2.0 / 16, mu_minus=1.0,
-                          mu_plus=10.0, k_minus=0.5, k_plus=0.2)
+                          mu_plus=10.0, k_minus=0.5, k_plus=0.2, solution=solution,
+                          activation=activation)
 
 
-@pytest.mark.parametrize("geom", [O.GEOM_SPHERE, O.GEOM_FLOWER])
-def test_hand_gradient_matches_central_differences(geom):
+@pytest.mark.parametrize("geom,sol,act", [(O.GEOM_SPHERE, O.SOL_BENCH, O.ACT_TANH),
+                                          (O.GEOM_FLOWER, O.SOL_BENCH, O.ACT_TANH),
+                                          (O.GEOM_SPHERE, O.SOL_SEC41, O.ACT_SIN)])
+def test_hand_gradient_matches_central_differences(geom, sol, act):
     """d(loss)/d(theta) by the hand-derived reverse mode vs central FD, step 1e-6."""
-    pr = _small_problem(geom)
+    pr = _small_problem(geom, sol, act)
     rng = np.random.default_rng(9)
     P = 2 * O.params_per_net(pr)
     th = rng.normal(size=P) * 0.5
@@ -393,6 +431,18 @@ def test_grid_matrix_symmetric_positive_definite_and_cg_matches_direct():
     assert st == 0 and rr <= 1e-13
     ui = u.reshape(n + 1, n + 1, n + 1)[1:-1, 1:-1, 1:-1]  # [k][j][i]
     assert np.allclose(ui.reshape(-1), x, rtol=0, atol=1e-10)
+
+
+def test_grid_matrix_with_face_centred_variable_mu_is_symmetric():
+    """Sec. 4.1 coefficients: the face coefficient mu at the face centre is the same
+    seen from both cells of the face, so the grid operator stays symmetric (a
+    cell-centred mu would break the symmetry by O(h |grad mu|))."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, solution=O.SOL_SEC41)
+    A, b = O.grid_assemble_dense(pr, 8)
+    assert np.max(np.abs(A - A.T)) <= 1e-14 * np.max(np.abs(A))
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    off = A - np.diag(np.diag(A))
+    assert np.ptp(off[off != 0]) > 0.1  # the face weights do vary
 
 
 def test_grid_second_order_without_interface():
