@@ -71,9 +71,23 @@ typedef enum {
                              (grid evaluation only)                                   */
 } nbm_precision;
 
-/* Problem descriptor (Sec. 2 problem + Sec. 3 NBM settings).  Manufactured
- * solution of the benchmark: u- = exp(x)cos(y)sin(z), u+ = x^2+y^2+z^2;
- * f, alpha, beta and the Dirichlet data g = u+ follow analytically. */
+typedef enum {
+  NBM_SOL_BENCH = 0,      /* u- = exp(x)cos(y)sin(z), u+ = x^2+y^2+z^2, constant
+                             mu_minus/mu_plus and k_minus/k_plus                       */
+  NBM_SOL_SEC41 = 1       /* the convergence study of Sec. 4.1: u- = exp(z),
+                             u+ = cos(x)sin(y), mu- = y^2 ln(x+2) + 4, mu+ = exp(-z)
+                             (mu_minus/mu_plus unused; k_minus/k_plus as given)        */
+} nbm_solution;
+
+typedef enum {
+  NBM_ACT_TANH = 0,       /* tanh hidden layers (every path)                            */
+  NBM_ACT_SIN = 1         /* sine-activated hidden layers (Sec. 4.1 networks): FP32
+                             precision and width <= 32 only                            */
+} nbm_activation;
+
+/* Problem descriptor (Sec. 2 problem + Sec. 3 NBM settings).  f, alpha, beta
+ * and the Dirichlet data g = u+ follow analytically from the manufactured
+ * pair; mu enters the rows at the face centres of the implicit cell. */
 typedef struct {
   int32_t geometry;       /* nbm_geometry                                             */
   int32_t n_hidden;       /* number of tanh layers (>= 2)                             */
@@ -92,6 +106,8 @@ typedef struct {
                              h/2^refine_levels; their rows are stacked into r_p, i.e.
                              r_p^2 = sum over the levels of (B/D)^2 + lambda J^2.  Band
                              points stay within 4h of the base spacing. */
+  int32_t solution;       /* nbm_solution: manufactured pair and coefficients          */
+  int32_t activation;     /* nbm_activation of the hidden layers                       */
 } nbm_problem_desc;
 
 typedef struct nbm_problem nbm_problem;

@@ -23,6 +23,8 @@ __all__ = ["ProblemDesc", "Problem", "NBMLoss", "load_library", "config", "param
 
 GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS = 1, 2, 3, 4
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
+SOL_BENCH, SOL_SEC41 = 0, 1
+ACT_TANH, ACT_SIN = 0, 1
 
 STATUS = {0: "NBM_OK", 1: "NBM_ERR_INVALID_ARG", 2: "NBM_ERR_CUDA", 3: "NBM_ERR_NOT_CONVERGED",
           4: "NBM_ERR_NONFINITE", 5: "NBM_ERR_OOM", 6: "NBM_ERR_DEVICE_TIMEOUT"}
@@ -41,7 +43,8 @@ class _Desc(C.Structure):
                 ("mu_minus", C.c_double), ("mu_plus", C.c_double), ("k_minus", C.c_double),
                 ("k_plus", C.c_double), ("h", C.c_double), ("lambda_jump", C.c_double),
                 ("band_fraction", C.c_double), ("fp64_stencil", C.c_int32),
-                ("refine_levels", C.c_int32)]
+                ("refine_levels", C.c_int32), ("solution", C.c_int32),
+                ("activation", C.c_int32)]
 
 
 @dataclasses.dataclass
@@ -64,12 +67,14 @@ class ProblemDesc:
     band_fraction: float = 0.0
     fp64_stencil: int = -1
     refine_levels: int = 0  # implicit refinement: also the cells of spacing h/2, ..., h/2^levels
+    solution: int = 0       # SOL_BENCH, or SOL_SEC41 (variable mu, the convergence study)
+    activation: int = 0     # ACT_TANH, or ACT_SIN (FP32 path, width <= 32)
 
     def to_c(self) -> _Desc:
         return _Desc(self.geometry, self.n_hidden, self.width, self.precision, self.r0,
                      self.amp, self.lobes_theta, self.lobes_psi, self.mu_minus, self.mu_plus,
                      self.k_minus, self.k_plus, self.h, self.lambda_jump, self.band_fraction,
-                     self.fp64_stencil, self.refine_levels)
+                     self.fp64_stencil, self.refine_levels, self.solution, self.activation)
 
 
 def config(name: str, precision: int | None = None) -> ProblemDesc:

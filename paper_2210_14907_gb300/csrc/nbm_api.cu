@@ -40,6 +40,8 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P, int level) {
   P.fp64 = d.fp64_stencil < 0 ? (h <= 2.0 / 512 + 1e-15) : (d.fp64_stencil != 0);
   P.level = level;
   P.h_band = d.h;
+  P.solution = d.solution;
+  P.activation = d.activation;
   P.r0 = d.r0;
   P.amp = d.amp;
   P.lt = d.lobes_theta;
@@ -151,6 +153,12 @@ static int check_desc(const nbm_problem_desc* d) {
   if (!(d->band_fraction >= 0.0 && d->band_fraction <= 1.0))
     return fail(NBM_ERR_INVALID_ARG, "band_fraction must be in [0, 1]");
   if (!(d->lambda_jump >= 0.0)) return fail(NBM_ERR_INVALID_ARG, "lambda_jump must be >= 0");
+  if (d->solution != NBM_SOL_BENCH && d->solution != NBM_SOL_SEC41)
+    return fail(NBM_ERR_INVALID_ARG, "unknown solution %d", d->solution);
+  if (d->activation != NBM_ACT_TANH && d->activation != NBM_ACT_SIN)
+    return fail(NBM_ERR_INVALID_ARG, "unknown activation %d", d->activation);
+  if (d->activation == NBM_ACT_SIN && (d->precision != NBM_PREC_FP32 || d->width > 32))
+    return fail(NBM_ERR_INVALID_ARG, "sine networks run on the FP32 path with width <= 32");
   if (d->refine_levels < 0 || d->refine_levels > 3)
     return fail(NBM_ERR_INVALID_ARG, "refine_levels must be 0..3 (got %d)", d->refine_levels);
   if (!(ldexp(d->h, -d->refine_levels) >= 0x1p-12))

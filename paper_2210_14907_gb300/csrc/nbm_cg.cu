@@ -45,7 +45,7 @@ __device__ inline int phase_d(const ProbDev& P, const double x[3]) {
 
 // jump correction of side s at node x of side sx: U^s(x) = u_x + corr
 __device__ inline void jump_corr(const ProbDev& P, const double x[3], int sx, double c[2]) {
-  const double jmp = alpha_d(x);
+  const double jmp = alpha_d(P, x);
   c[0] = sx == 1 ? -jmp : 0.0;
   c[1] = sx == 0 ? jmp : 0.0;
 }
@@ -79,10 +79,14 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* dia
     const bool bnd = nb[ax] == 0 || nb[ax] == G.n;
     double cq[2] = {0.0, 0.0};
     if (!bnd) jump_corr(P, q, phase_d(P, q), cq);
+    // face centre: the same point for both cells of the face, so the face
+    // weight (and the matrix) stays symmetric with variable mu
+    double fc[3] = {p[0], p[1], p[2]};
+    fc[ax] += 0.5 * sg * h;
     double wf = 0.0;
     for (int s = 0; s < 2; ++s) {
       const double A = s ? 1.0 - cg.Am[f] : cg.Am[f];
-      const double a = A * P.mu[s];
+      const double a = A * mu_at<double>(P, s, fc[0], fc[1], fc[2]);
       wf += a;
       known -= a * (cq[s] - cp[s]);
     }

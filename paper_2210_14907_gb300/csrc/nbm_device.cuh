@@ -23,6 +23,8 @@ struct ProbDev {
   double h, lambda;
   double h_band;   // base spacing: band points are drawn within 4 h_band of Gamma
   int level;       // refinement level of this pass (0: base cell; > 0 accumulates r2_out)
+  int solution;    // manufactured pair: 0 benchmark (constant mu), 1 Sec. 4.1 (variable mu)
+  int activation;  // hidden-layer activation: 0 tanh, 1 sin
   float hf, inv_hf, h2f, inv_h2f;  // h, 1/h, h^2, 1/h^2 in FP32
   float r0f, ampf, ltf, lpf;
   float muf[2], kf[2];
@@ -110,16 +112,24 @@ __device__ inline void grad_phi_d(const ProbDev& P, const double x[3], double g[
 }
 
 // ---------------------------------------------------------------------------
-// Manufactured pair: u- = e^x cos y sin z (Lap u- = -u-), u+ = |x|^2 (Lap = 6).
+// Manufactured pairs.  Solution 0 (the benchmark configurations), constant
+// mu^s:  u- = e^x cos y sin z (Lap u- = -u-),  u+ = |x|^2 (Lap u+ = 6).
+// Solution 1 (Sec. 4.1):  u- = e^z,  u+ = cos x sin y,  mu- = y^2 ln(x+2) + 4,
+// mu+ = e^-z.  (The FP32 overloads call CUDA's float functions.)
 // ---------------------------------------------------------------------------
+__device__ inline double m_exp(double v) { return exp(v); }
+__device__ inline float m_exp(float v) { return expf(v); }
+__device__ inline double m_cos(double v) { return cos(v); }
+__device__ inline float m_cos(float v) { return cosf(v); }
+__device__ inline double m_sin(double v) { return sin(v); }
+__device__ inline float m_sin(float v) { return sinf(v); }
+__device__ inline double m_log(double v) { return log(v); }
+__device__ inline float m_log(float v) { return logf(v); }
+
 template <typename T>
-__device__ inline T exact_u(int s, T x, T y, T z) {
-  if (s == 0) return exp(x) * cos(y) * sin(z);
-  return x * x + y * y + z * z;
-}
-template <>
-__device__ inline float exact_u<float>(int s, float x, float y, float z) {
-  if (s == 0) return expf(x) * cosf(y) * sinf(z);
+__device__ inline T exact_u(const ProbDev& P, int s, T x, T y, T z) {
+  if (P.solution == 1) return s == 0 ? m_exp(z) : m_cos(x) * m_sin(y);
+  if (s == 0) return m_exp(x) * m_cos(y) * m_sin(z);
   return x * x + y * y + z * z;
 }
 
@@ -139,33 +149,64 @@ __device__ __forceinline__ T pc_k(const ProbDev& P, int s) {
   if constexpr (sizeof(T) == 4) return P.kf[s]; else return P.k[s];
 }
 
+// diffusion coefficient mu^s(x)
+template <typename T>
+__device__ inline T mu_at(const ProbDev& P, int s, T x, T y, T z) {
+  if (P.solution == 1) return s == 0 ? y * y * m_log(x + (T)2) + (T)4 : m_exp(-z);
+  return pc_mu<T>(P, s);
+}
+
+// f^s = k^s u^s - div(mu^s grad u^s)
 template <typename T>
 __device__ inline T rhs_f(const ProbDev& P, int s, T x, T y, T z) {
-  T u = exact_u<T>(s, x, y, z);
-  T mu = pc_mu<T>(P, s), k = pc_k<T>(P, s);
+  const T k = pc_k<T>(P, s);
+  if (P.solution == 1) {
+    if (s == 0) {
+      // grad mu- = (y^2/(x+2), 2y ln(x+2), 0) is orthogonal to grad u- = (0, 0, e^z)
+      const T u = m_exp(z);
+      return k * u - mu_at<T>(P, 0, x, y, z) * u;
+    }
+    // grad mu+ = (0, 0, -e^-z) is orthogonal to grad u+ = (-sin x sin y, cos x cos y, 0)
+    const T u = m_cos(x) * m_sin(y);
+    return k * u + (T)2 * m_exp(-z) * u;
+  }
+  const T u = exact_u<T>(P, s, x, y, z);
+  const T mu = pc_mu<T>(P, s);
   return s == 0 ? k * u + mu * u : k * u - (T)6 * mu;
 }
 
 template <typename T>
 __device__ inline T dirichlet_g(const ProbDev& P, T x, T y, T z) {
-  return exact_u<T>(P.geometry == NBM_GEOM_ALL_MINUS ? 0 : 1, x, y, z);
+  return exact_u<T>(P, P.geometry == NBM_GEOM_ALL_MINUS ? 0 : 1, x, y, z);
 }
 
-__device__ inline void exact_grad_u_d(int s, const double x[3], double g[3]) {
+template <typename T>
+__device__ inline void exact_grad_u(const ProbDev& P, int s, const T x[3], T g[3]) {
+  if (P.solution == 1) {
+    if (s == 0) {
+      g[0] = g[1] = (T)0;
+      g[2] = m_exp(x[2]);
+    } else {
+      g[0] = -m_sin(x[0]) * m_sin(x[1]);
+      g[1] = m_cos(x[0]) * m_cos(x[1]);
+      g[2] = (T)0;
+    }
+    return;
+  }
   if (s == 0) {
-    double e = exp(x[0]);
-    g[0] = e * cos(x[1]) * sin(x[2]);
-    g[1] = -e * sin(x[1]) * sin(x[2]);
-    g[2] = e * cos(x[1]) * cos(x[2]);
+    const T e = m_exp(x[0]);
+    g[0] = e * m_cos(x[1]) * m_sin(x[2]);
+    g[1] = -e * m_sin(x[1]) * m_sin(x[2]);
+    g[2] = e * m_cos(x[1]) * m_cos(x[2]);
   } else {
-    g[0] = 2 * x[0];
-    g[1] = 2 * x[1];
-    g[2] = 2 * x[2];
+    g[0] = (T)2 * x[0];
+    g[1] = (T)2 * x[1];
+    g[2] = (T)2 * x[2];
   }
 }
 
-__device__ inline double alpha_d(const double x[3]) {
-  return exact_u<double>(1, x[0], x[1], x[2]) - exact_u<double>(0, x[0], x[1], x[2]);
+__device__ inline double alpha_d(const ProbDev& P, const double x[3]) {
+  return exact_u<double>(P, 1, x[0], x[1], x[2]) - exact_u<double>(P, 0, x[0], x[1], x[2]);
 }
 
 // FP32 versions of the level-set gradient, [u] and [mu d_n u] (the FP32 rows)
@@ -186,33 +227,33 @@ __device__ inline void grad_phi_f(const ProbDev& P, const float x[3], float g[3]
   for (int i = 0; i < 3; ++i) g[i] += a * dth[i] + b * dps[i];
 }
 
-__device__ inline float alpha_f(const float x[3]) {
-  return exact_u<float>(1, x[0], x[1], x[2]) - exact_u<float>(0, x[0], x[1], x[2]);
+__device__ inline float alpha_f(const ProbDev& P, const float x[3]) {
+  return exact_u<float>(P, 1, x[0], x[1], x[2]) - exact_u<float>(P, 0, x[0], x[1], x[2]);
 }
 
 __device__ inline float beta_f(const ProbDev& P, const float x[3]) {
-  const float e = expf(x[0]);
-  const float gm[3] = {e * cosf(x[1]) * sinf(x[2]), -e * sinf(x[1]) * sinf(x[2]),
-                       e * cosf(x[1]) * cosf(x[2])};
-  const float gp[3] = {2.f * x[0], 2.f * x[1], 2.f * x[2]};
-  float gf[3];
+  float gm[3], gp[3], gf[3];
+  exact_grad_u<float>(P, 0, x, gm);
+  exact_grad_u<float>(P, 1, x, gp);
   grad_phi_f(P, x, gf);
   const float nn = sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
   if (nn == 0.f) return 0.f;
+  const float mp = mu_at<float>(P, 1, x[0], x[1], x[2]), mm = mu_at<float>(P, 0, x[0], x[1], x[2]);
   float b = 0.f;
-  for (int i = 0; i < 3; ++i) b += (P.muf[1] * gp[i] - P.muf[0] * gm[i]) * gf[i] / nn;
+  for (int i = 0; i < 3; ++i) b += (mp * gp[i] - mm * gm[i]) * gf[i] / nn;
   return b;
 }
 
 __device__ inline double beta_d(const ProbDev& P, const double x[3]) {
   double gp[3], gm[3], gf[3];
-  exact_grad_u_d(1, x, gp);
-  exact_grad_u_d(0, x, gm);
+  exact_grad_u<double>(P, 1, x, gp);
+  exact_grad_u<double>(P, 0, x, gm);
   grad_phi_d(P, x, gf);
   double nn = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
   if (nn == 0.0) return 0.0;
+  const double mp = mu_at<double>(P, 1, x[0], x[1], x[2]), mm = mu_at<double>(P, 0, x[0], x[1], x[2]);
   double b = 0.0;
-  for (int i = 0; i < 3; ++i) b += (P.mu[1] * gp[i] - P.mu[0] * gm[i]) * gf[i] / nn;
+  for (int i = 0; i < 3; ++i) b += (mp * gp[i] - mm * gm[i]) * gf[i] / nn;
   return b;
 }
 
@@ -326,6 +367,7 @@ __device__ inline T uncut_residual(const ProbDev& P, int s, float px, float py, 
   T Bt = k * U - rhs_f<T>(P, s, x[0], x[1], x[2]);
   T dU = k;
   T dM[3], dD[3];
+  T D = h2 * k;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     dM[i] = 0;
@@ -334,19 +376,27 @@ __device__ inline T uncut_residual(const ProbDev& P, int s, float px, float py, 
     for (int sg = -1; sg <= 1; sg += 2) {
       T q[3] = {x[0], x[1], x[2]};
       q[i] += sg * h;
+      // mu at the face centre (variable coefficients of Sec. 4.1)
+      T mf = mu;
+      if (P.solution == 1) {
+        T c[3] = {x[0], x[1], x[2]};
+        c[i] += (T)0.5 * (T)sg * h;
+        mf = mu_at<T>(P, s, c[0], c[1], c[2]);
+        D += mf;
+      }
       bool bnd = fabs(q[i]) >= (T)1;
       if (bnd) {
         T g = dirichlet_g<T>(P, q[0], q[1], q[2]);
-        Bt -= mu * (g - U) / h2;
-        dU += mu / h2;
+        Bt -= mf * (g - U) / h2;
+        dU += mf / h2;
       } else {
-        Bt -= mu * ((T)out[1 + i] + (T)sg * (T)out[4 + i] / h);
-        dM[i] -= mu;
-        dD[i] -= mu * (T)sg / h;
+        Bt -= mf * ((T)out[1 + i] + (T)sg * (T)out[4 + i] / h);
+        dM[i] -= mf;
+        dD[i] -= mf * (T)sg / h;
       }
     }
   }
-  T D = (T)6 * mu + h2 * k;
+  if (P.solution != 1) D = (T)6 * mu + h2 * k;
   T r = h2 * Bt / D;
   T c = scale * (T)2 * r * h2 / D;
   seeds[0] = (float)(c * dU);
@@ -382,33 +432,45 @@ __device__ __forceinline__ T uncut_residual_pt(const ProbDev& P, int s, float px
   const T U = (T)out[0];
   const T x[3] = {(T)px, (T)py, (T)pz};
   T Bt = kk * U - fsrc;
-  T nb = 0;  // Dirichlet faces
+  T nbmu = 0;  // sum of mu over the Dirichlet faces
   T cM[3], cD[3];
+  T Dv = h2 * kk;  // Jacobi diagonal accumulated over faces (variable mu only)
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const T Mt = (T)out[1 + i], Dt = (T)out[4 + i];
     T qm[3] = {x[0], x[1], x[2]}, qp[3] = {x[0], x[1], x[2]};
     qm[i] -= h;
     qp[i] += h;
+    // mu at the two face centres (variable coefficients of Sec. 4.1)
+    T mm = mu, mp = mu;
+    if (P.solution == 1) {
+      T cm[3] = {x[0], x[1], x[2]}, cp[3] = {x[0], x[1], x[2]};
+      cm[i] -= (T)0.5 * h;
+      cp[i] += (T)0.5 * h;
+      mm = mu_at<T>(P, s, cm[0], cm[1], cm[2]);
+      mp = mu_at<T>(P, s, cp[0], cp[1], cp[2]);
+      Dv += mm + mp;
+    }
     const bool bm = fabs(qm[i]) >= (T)1, bp = fabs(qp[i]) >= (T)1;
     if (bm) {
-      Bt -= mu * (dirichlet_g<T>(P, qm[0], qm[1], qm[2]) - U) * ih2;
-      nb += (T)1;
+      Bt -= mm * (dirichlet_g<T>(P, qm[0], qm[1], qm[2]) - U) * ih2;
+      nbmu += mm;
     } else {
-      Bt -= mu * (Mt - Dt * ih);
+      Bt -= mm * (Mt - Dt * ih);
     }
     if (bp) {
-      Bt -= mu * (dirichlet_g<T>(P, qp[0], qp[1], qp[2]) - U) * ih2;
-      nb += (T)1;
+      Bt -= mp * (dirichlet_g<T>(P, qp[0], qp[1], qp[2]) - U) * ih2;
+      nbmu += mp;
     } else {
-      Bt -= mu * (Mt + Dt * ih);
+      Bt -= mp * (Mt + Dt * ih);
     }
-    cM[i] = -mu * (T)((bm ? 0 : 1) + (bp ? 0 : 1));
-    cD[i] = -mu * (T)((bp ? 0 : 1) - (bm ? 0 : 1)) * ih;
+    cM[i] = -((bm ? (T)0 : mm) + (bp ? (T)0 : mp));
+    cD[i] = -((bp ? (T)0 : mp) - (bm ? (T)0 : mm)) * ih;
   }
+  if (P.solution == 1) iD = (T)1 / Dv;
   const T r = h2 * Bt * iD;
   const T c = scale * (T)2 * r * h2 * iD;
-  sd[0] = (float)(c * (kk + nb * mu * ih2));
+  sd[0] = (float)(c * (kk + nbmu * ih2));
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     sd[1 + i] = (float)(c * cM[i]);

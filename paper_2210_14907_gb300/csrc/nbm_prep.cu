@@ -288,13 +288,13 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __
   double val = 0.0;
   if (P.fp64) {
     if (k == 0 && area > 0.0) val = beta_d(P, xg);
-    else if (k == 1 && area > 0.0) val = alpha_d(xg);
+    else if (k == 1 && area > 0.0) val = alpha_d(P, xg);
     else if (k == 2) val = rhs_f<double>(P, 0, p[0], p[1], p[2]);
     else if (k == 3) val = rhs_f<double>(P, 1, p[0], p[1], p[2]);
   } else {
     const float xf[3] = {(float)xg[0], (float)xg[1], (float)xg[2]};
     if (k == 0 && area > 0.0) val = beta_f(P, xf);
-    else if (k == 1 && area > 0.0) val = alpha_f(xf);
+    else if (k == 1 && area > 0.0) val = alpha_f(P, xf);
     else if (k == 2) val = rhs_f<float>(P, 0, (float)p[0], (float)p[1], (float)p[2]);
     else if (k == 3) val = rhs_f<float>(P, 1, (float)p[0], (float)p[1], (float)p[2]);
   }
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
     }
     for (int s = 0; s < 2; ++s) {
       const double V = s ? 1.0 - c.Vm : c.Vm;
-      const double mu = P.mu[s], k = P.k[s];
+      const double k = P.k[s];
       const double U = (double)o[8 * s];
       B += h2 * V * (k * U - c.f[s]);
       D += h2 * V * k;
@@ -363,7 +363,10 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
         const int a = f >> 1;
         const double sg = (f & 1) ? 1.0 : -1.0;
         const double A = s ? 1.0 - c.Am[f] : c.Am[f];
-        const double w = A * mu;
+        // mu^s at the face centre (constant for the benchmark pair)
+        double fc[3] = {p[0], p[1], p[2]};
+        fc[a] += 0.5 * sg * h;
+        const double w = A * mu_at<double>(P, s, fc[0], fc[1], fc[2]);
         D += w;
         if (bnd[f]) {
           // U^s(p) enters the row directly only through Dirichlet faces: the
