@@ -138,10 +138,14 @@ static int check_desc(const nbm_problem_desc* d) {
   if (!d) return fail(NBM_ERR_INVALID_ARG, "descriptor is NULL");
   if (d->geometry < NBM_GEOM_SPHERE || d->geometry > NBM_GEOM_ALL_MINUS)
     return fail(NBM_ERR_INVALID_ARG, "unknown geometry %d", d->geometry);
-  if (d->n_hidden < 2 || d->n_hidden > 4)
-    return fail(NBM_ERR_INVALID_ARG, "n_hidden must be 2..4 (got %d)", d->n_hidden);
-  if (d->width != 64 && d->width != 128)
-    return fail(NBM_ERR_INVALID_ARG, "width must be 64 or 128 (got %d)", d->width);
+  const bool narrow = d->width >= 1 && d->width <= 32;  // the narrow FP32 kernels
+  if (d->n_hidden < 2 || d->n_hidden > (narrow ? 5 : 4))
+    return fail(NBM_ERR_INVALID_ARG, "n_hidden must be 2..4 (2..5 for width <= 32; got %d)",
+                d->n_hidden);
+  if (d->width != 64 && d->width != 128 && !narrow)
+    return fail(NBM_ERR_INVALID_ARG, "width must be 1..32, 64 or 128 (got %d)", d->width);
+  if (narrow && d->precision != NBM_PREC_FP32)
+    return fail(NBM_ERR_INVALID_ARG, "widths <= 32 run on the FP32 path");
   if (d->precision != NBM_PREC_FP32 && d->precision != NBM_PREC_BF16)
     return fail(NBM_ERR_INVALID_ARG, "training precision must be FP32 or BF16 (got %d)",
                 d->precision);

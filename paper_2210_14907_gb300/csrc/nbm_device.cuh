@@ -328,6 +328,56 @@ __device__ __forceinline__ void tanh_stencil_fwd0(float t, float dt, float h, fl
   dout = (sw * Td * r2) * inv_h;
 }
 
+// ---------------------------------------------------------------------------
+// Difference-form sine layer (the sine-activated networks of Sec. 4.1).  Same
+// column convention as the tanh layer (mt = mu/h^2, dt = del/h); with
+// w = z + mu the outputs are
+//   [sin(w+d) + sin(w-d)]/2 - sin z = [cos z sin mu - 2 sin z sin^2(mu/2)] cos d
+//                                     - 2 sin z sin^2(d/2),
+//   [sin(w+d) - sin(w-d)]/2         = cos w sin d,
+// cos w = cos z (1 - 2 sin^2(mu/2)) - sin z sin mu: no O(1) values are
+// subtracted.  sz, cz = sin z, cos z of the centre column.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sin_stencil_fwd(float sz, float cz, float mt, float dt, float h,
+                                                float h2, float inv_h, float inv_h2, float& mo,
+                                                float& dout) {
+  float sh, ch, shd, chd;
+  sincosf(0.5f * mt * h2, &sh, &ch);
+  sincosf(0.5f * dt * h, &shd, &chd);
+  const float sm = 2.f * sh * ch, sh2 = sh * sh;
+  const float sd = 2.f * shd * chd, shd2 = shd * shd, cd = fmaf(-2.f, shd2, 1.f);
+  const float dsw = fmaf(cz, sm, -2.f * sz * sh2);  // sin w - sin z
+  const float cw = fmaf(cz, fmaf(-2.f, sh2, 1.f), -sz * sm);
+  mo = fmaf(dsw, cd, -2.f * sz * shd2) * inv_h2;
+  dout = cw * sd * inv_h;
+}
+
+// Adjoint of one axis of the sine layer: inputs z (via sz, cz), mt, dt and the
+// upstream gradients with respect to the scaled outputs (Gm_s, Gd_s).  Writes
+// the gradients with respect to the scaled inputs and returns the contribution
+// to d/dz.  With M = sin w cos d - sin z and D = cos w sin d:
+//   dM/dz = (cos w - cos z) cos d - cos z (1 - cos d), dM/dmu = cos w cos d,
+//   dM/dd = dD/dz = dD/dmu = -sin w sin d, dD/dd = cos w cos d,
+// cos w - cos z = -2 cos z sin^2(mu/2) - sin z sin mu.
+__device__ __forceinline__ float sin_stencil_bwd(float sz, float cz, float mt, float dt,
+                                                 float Gm_s, float Gd_s, float h, float h2,
+                                                 float inv_h, float inv_h2, float& gmu_s,
+                                                 float& gdel_s) {
+  float sh, ch, shd, chd;
+  sincosf(0.5f * mt * h2, &sh, &ch);
+  sincosf(0.5f * dt * h, &shd, &chd);
+  const float sm = 2.f * sh * ch, sh2 = sh * sh;
+  const float sd = 2.f * shd * chd, shd2 = shd * shd, cd = fmaf(-2.f, shd2, 1.f);
+  const float cmu = fmaf(-2.f, sh2, 1.f);
+  const float cw = fmaf(cz, cmu, -sz * sm), sw = fmaf(sz, cmu, cz * sm);
+  const float Gm = Gm_s * inv_h2, Gd = Gd_s * inv_h;
+  const float dMdz = fmaf(fmaf(-2.f * cz, sh2, -sz * sm), cd, -2.f * cz * shd2);
+  const float cc = cw * cd, ss = -sw * sd;
+  gmu_s = fmaf(Gm, cc, Gd * ss) * h2;
+  gdel_s = fmaf(Gm, ss, Gd * cc) * h;
+  return fmaf(Gm, dMdz, Gd * ss);
+}
+
 // Adjoint of one stencil axis.  Inputs: forward outputs t (centre), mo, dout
 // (scaled), upstream gradients with respect to the scaled outputs (Gm, Gd).
 // Writes the gradients with respect to the scaled inputs (gmu, gdel) and

@@ -283,6 +283,73 @@ __global__ void __launch_bounds__(128) k_eval_fp32(ProbDev P, const float* __res
   if (id < total) u_out[id] = result;
 }
 
+// Narrow networks (width <= 32, up to five layers; tanh or the sine layers of
+// Sec. 4.1): the same per-node evaluation with the width and depth at run time.
+template <int ACT>
+__global__ void __launch_bounds__(128) k_eval_small(ProbDev P, const float* __restrict__ params,
+                                                    int n, const float* __restrict__ pts,
+                                                    int64_t npts, float* __restrict__ u_out) {
+  __shared__ float act[2][32 * 128];
+  const int tid = threadIdx.x, H = P.H, L = P.L;
+  const int64_t N1 = n + 1, total = pts ? npts : N1 * N1 * N1;
+  const int64_t id = (int64_t)blockIdx.x * 128 + tid;
+  const float hg = 2.0f / (float)n;
+  float x = 0.f, y = 0.f, z = 0.f;
+  int s = 0;
+  if (id < total) {
+    if (pts) {
+      x = pts[3 * id];
+      y = pts[3 * id + 1];
+      z = pts[3 * id + 2];
+    } else {
+      const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
+      x = -1.f + hg * (float)i;
+      y = -1.f + hg * (float)j;
+      z = -1.f + hg * (float)k;
+    }
+    s = node_phase(P, x, y, z);
+  }
+  auto actf = [](float v) { return ACT == NBM_ACT_SIN ? sinf(v) : tanhf(v); };
+  float result = 0.f;
+  for (int net = 0; net < 2; ++net) {
+    const float* th = params + net * P.p_net;
+    float* a0 = act[0];
+    float* a1 = act[1];
+    for (int j = 0; j < H; ++j)
+      a0[j * 128 + tid] = actf(fmaf(__ldg(th + 3 * j), x,
+                                    fmaf(__ldg(th + 3 * j + 1), y,
+                                         fmaf(__ldg(th + 3 * j + 2), z, __ldg(th + 3 * H + j)))));
+    const float* Wl = th + 4 * H;
+    for (int g = 1; g < L; ++g) {
+      for (int j = 0; j < H; ++j) {
+        float acc = __ldg(Wl + (int64_t)H * H + j);
+        for (int k = 0; k < H; ++k) acc = fmaf(__ldg(Wl + (int64_t)j * H + k), a0[k * 128 + tid], acc);
+        a1[j * 128 + tid] = actf(acc);
+      }
+      float* tmp = a0;
+      a0 = a1;
+      a1 = tmp;
+      Wl += (int64_t)H * H + H;
+    }
+    float o = __ldg(Wl + H);
+    for (int k = 0; k < H; ++k) o = fmaf(__ldg(Wl + k), a0[k * 128 + tid], o);
+    if (net == s) result = o;
+  }
+  if (id < total) u_out[id] = result;
+}
+
+cudaError_t launch_eval_small(const ProbDev& P, const float* params, int n, const float* pts,
+                              int64_t npts, float* u, cudaStream_t st) {
+  if (P.H < 1 || P.H > 32 || P.L < 2 || P.L > 5) return cudaErrorInvalidValue;
+  const int64_t total = pts ? npts : (int64_t)(n + 1) * (n + 1) * (n + 1);
+  const int nb = (int)((total + 127) / 128);
+  if (P.activation == NBM_ACT_SIN)
+    k_eval_small<NBM_ACT_SIN><<<nb, 128, 0, st>>>(P, params, n, pts, npts, u);
+  else
+    k_eval_small<NBM_ACT_TANH><<<nb, 128, 0, st>>>(P, params, n, pts, npts, u);
+  return cudaGetLastError();
+}
+
 template <int L, bool BF>
 cudaError_t launch_eval_tc_t(const ProbDev& P, const float* params, const unsigned char* wimg,
                              int n, const float* pts, int64_t npts, float* u, int grid, int* status,
@@ -340,7 +407,8 @@ static int eval_common(nbm_problem* p, const float* params, int n, const float* 
   if (precision == NBM_PREC_FP32) {
 #define NBM_EVAL32(HH, LL) \
   else if (d.width == HH && d.n_hidden == LL) e = launch_eval_fp32_t<HH, LL>(P, params, n, pts, npts, u_out, st);
-    if (false) {
+    if (d.width <= 32) {
+      e = launch_eval_small(P, params, n, pts, npts, u_out, st);
     }
     NBM_EVAL32(64, 2) NBM_EVAL32(64, 3) NBM_EVAL32(64, 4) NBM_EVAL32(128, 2) NBM_EVAL32(128, 3)
     NBM_EVAL32(128, 4)

@@ -11,6 +11,7 @@
 // this CTA's slice of the partial-gradient buffer (no atomics: the final
 // reduction over CTAs runs in a fixed order).
 #include "nbm_device.cuh"
+#include "nbm_host.h"
 
 namespace nbm {
 
@@ -434,6 +435,7 @@ static cudaError_t launch_fp32_t(const ProbDev& P, const StepArgs& a, int grid, 
 }
 
 cudaError_t launch_step_fp32(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st) {
+  if (P.H <= 32) return launch_step_small(P, a, grid, st);  // narrow networks (nbm_small.cu)
 #define NBM_FP32_CASE(HH, LL) \
   if (P.H == HH && P.L == LL) return launch_fp32_t<HH, LL>(P, a, grid, st);
   NBM_FP32_CASE(64, 2)

@@ -131,6 +131,8 @@ cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool w
 cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,
                                 cudaStream_t st);
 cudaError_t launch_step_fp32(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_step_small(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st);
+size_t small_smem_bytes(int L);
 cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int prec, cudaStream_t st);
 cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,

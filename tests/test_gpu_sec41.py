@@ -75,3 +75,68 @@ def test_variable_mu_training_decreases_the_loss():
     prob.train_steps(params, m, v, 0, 200, 32768, lr=1e-3, seed=3, loss_hist=hist)
     h = hist.cpu().numpy()
     assert np.all(np.isfinite(h)) and h[-20:].mean() < 0.2 * h[:5].mean()
+
+
+@pytest.mark.parametrize("sol,act,H,L,h,geom", [
+    (1, 1, 10, 5, 2 / 32, O.GEOM_SPHERE),   # the paper's 5 x 10 sine pair (982 parameters)
+    (1, 1, 10, 5, 2 / 128, O.GEOM_SPHERE),
+    (0, 0, 16, 3, 2 / 64, O.GEOM_FLOWER),   # narrow tanh networks
+    (1, 1, 32, 2, 2 / 16, O.GEOM_SPHERE),
+], ids=["sin10x5-h32", "sin10x5-h128", "tanh16x3", "sin32x2"])
+def test_narrow_networks_match_oracle(sol, act, H, L, h, geom):
+    import paper_2210_14907_gb300 as nbm
+    d = nbm.ProblemDesc(geometry=geom, n_hidden=L, width=H, precision=nbm.PREC_FP32, h=h,
+                        solution=sol, activation=act)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=geom, n_hidden=L, width=H, h=h, solution=sol, activation=act)
+    if H == 10 and L == 5:
+        assert nbm.param_count(d) == 982
+    pts = inputs.mixed_points(600, 400, seed=H + L)
+    th = inputs.glorot_params(H, L, seed=29, bias_scale=0.2)
+    L_ref, r2_ref = O.loss(o, th.astype(np.float64), pts, want_r2=True)
+    _, g_ref = O.loss_grad(o, th.astype(np.float64), pts)
+    tp = torch.from_numpy(th).cuda()
+    tx = torch.from_numpy(pts.astype(np.float32)).cuda()
+    loss, r2 = prob.residual(tp, tx)
+    loss2, g = prob.loss_grad(tp, tx)
+    er = _rel(np.sqrt(r2.cpu().numpy()), np.sqrt(r2_ref))
+    eg = _rel(g.cpu().numpy(), g_ref)
+    print(f"narrow H {H} L {L} act {act} h {h}: residual {er:.2e} "
+          f"loss {abs(loss - L_ref) / L_ref:.2e} grad {eg:.2e}")
+    assert er <= 1e-5 and abs(loss - L_ref) <= 1e-5 * L_ref and abs(loss2 - L_ref) <= 1e-5 * L_ref
+    assert eg <= 1e-4
+    n = 14
+    ref = O.eval_grid(o, th.astype(np.float64), n)
+    got = prob.eval_grid(tp, n, precision=nbm.PREC_FP32).cpu().numpy()
+    assert _rel(got, ref) <= 1e-5
+
+
+def test_sec41_sine_pair_trains_and_is_deterministic():
+    import paper_2210_14907_gb300 as nbm
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, n_hidden=5, width=10, precision=nbm.PREC_FP32,
+                        h=2 / 32, solution=nbm.SOL_SEC41, activation=nbm.ACT_SIN)
+    prob = nbm.Problem(d)
+    runs = []
+    for _ in range(2):
+        params = nbm.xavier_init(d, seed=1, device="cuda")
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        hist = torch.zeros(300, device="cuda")
+        prob.train_steps(params, m, v, 0, 300, 4096, lr=3e-3, seed=2, loss_hist=hist)
+        runs.append((params.clone(), hist.cpu().numpy()))
+    assert torch.equal(runs[0][0], runs[1][0])
+    h = runs[0][1]
+    assert np.all(np.isfinite(h)) and h[-20:].mean() < 0.1 * h[:5].mean()
+
+
+def test_narrow_and_sine_limits():
+    import paper_2210_14907_gb300 as nbm
+    bad = [dict(width=10, n_hidden=5, precision=nbm.PREC_BF16),
+           dict(width=64, n_hidden=5),
+           dict(width=128, n_hidden=3, activation=nbm.ACT_SIN),
+           dict(width=10, n_hidden=6),
+           dict(solution=2), dict(activation=2)]
+    for kw in bad:
+        with pytest.raises(nbm.NBMError) as e:
+            nbm.Problem(nbm.ProblemDesc(**kw))
+        assert e.value.code == 1, kw
