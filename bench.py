@@ -183,13 +183,21 @@ def sphere_exact(x):
     return np.where(r <= 0.5, um, (x ** 2).sum(1))
 
 
-def node_errors(u, n):
+def sec41_exact(x):
+    """Manufactured solution of the Sec. 4.1 study (u- = e^z inside r <= 1/2,
+    u+ = cos x sin y outside)."""
+    import numpy as np
+    r = np.sqrt((x ** 2).sum(1))
+    return np.where(r <= 0.5, np.exp(x[:, 2]), np.cos(x[:, 0]) * np.sin(x[:, 1]))
+
+
+def node_errors(u, n, exact=sphere_exact):
     """L-infinity and RMS error over the interior nodes of the (n+1)^3 grid."""
     import numpy as np
     g = -1.0 + np.arange(n + 1) * 2.0 / n
     Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
     x = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
-    e = np.abs(np.asarray(u, np.float64) - sphere_exact(x)).reshape(n + 1, n + 1, n + 1)
+    e = np.abs(np.asarray(u, np.float64) - exact(x)).reshape(n + 1, n + 1, n + 1)
     e = e[1:-1, 1:-1, 1:-1]
     return float(e.max()), float(np.sqrt((e ** 2).mean()))
 
@@ -281,6 +289,59 @@ def accuracy(dev, steps=2000):
     return out
 
 
+# Table 1 of the paper (Sec. 4.1, JAX on one A6000, 10,000 epochs): N -> (RMSE,
+# L-infinity, seconds per epoch)
+PAPER_TABLE1 = {8: (3.7e-2, 3.25e-1, 0.0306), 16: (7.1e-3, 1.10e-1, 0.056),
+                32: (5.9e-3, 8.36e-2, 0.053), 64: (4.1e-3, 6.44e-2, 0.287),
+                128: (2.64e-3, 3.53e-2, 2.125)}
+
+
+def table1(dev, epochs, resolutions, lr=1e-3):
+    """The convergence study of Sec. 4.1 (Table 1): sphere of radius 1/2,
+    u- = e^z, u+ = cos x sin y, mu- = y^2 ln(x+2) + 4, mu+ = e^-z, two sine
+    networks of 5 hidden layers x 10 units (982 parameters), Glorot init, Adam.
+    Per resolution N (h = 2/N): one epoch is N^3 freshly drawn uniform
+    collocation points in mini-batches of at most 32 x 32 x 16 (the batch size
+    the paper states for its scaling runs); errors at the interior nodes of the
+    (N+1)^3 grid against the exact solution of each node's side."""
+    import numpy as np
+    import torch
+
+    import paper_2210_14907_gb300 as nbm
+    rows = []
+    for N in resolutions:
+        d = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, n_hidden=5, width=10,
+                            precision=nbm.PREC_FP32, h=2.0 / N, solution=nbm.SOL_SEC41,
+                            activation=nbm.ACT_SIN)
+        prob = nbm.Problem(d)
+        params = nbm.xavier_init(d, seed=0, device=dev)
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        batch = min(N ** 3, 32 * 32 * 16)
+        steps = epochs * ((N ** 3 + batch - 1) // batch)
+        hist = torch.zeros(min(steps, 1000), device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done, chunk = 0, 1000
+        while done < steps:
+            k = min(chunk, steps - done)
+            prob.train_steps(params, m, v, done, k, batch, lr=lr, seed=1, loss_hist=hist[:k])
+            done += k
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        u = prob.eval_grid(params, N, precision=nbm.PREC_FP32).cpu().numpy()
+        linf, rmse = node_errors(u, N, sec41_exact)
+        ref = PAPER_TABLE1.get(N)
+        rows.append({"N": N, "h": f"2/{N}", "batch": batch, "steps": steps, "rmse": rmse,
+                     "linf": linf, "s_per_epoch": wall / epochs,
+                     "final_loss": float(hist[:k].mean()),
+                     "paper_rmse": ref[0] if ref else None, "paper_linf": ref[1] if ref else None,
+                     "paper_s_per_epoch": ref[2] if ref else None})
+    return {"metric": "Sec. 4.1 convergence study (Table 1 of the paper)", "epochs": epochs,
+            "lr": lr, "networks": "2 x (3 -> 5 x 10 sine -> 1), 982 parameters, FP32",
+            "rows": rows}
+
+
 def secondary(dev, hbm_peak, peak_src):
     """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
     flower-interface 3->128x4->1 architecture) and the FP64 grid CG solve of the
@@ -359,10 +420,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--table1", action="store_true",
+                    help="run the Sec. 4.1 convergence study instead of the benchmark")
+    ap.add_argument("--table1-epochs", type=int, default=10000)
+    ap.add_argument("--table1-n", default="8,16,32,64")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.table1:
+        import torch
+        torch.cuda.set_device(0)
+        out = table1(torch.device("cuda", 0), args.table1_epochs,
+                     [int(v) for v in args.table1_n.split(",")])
+        print(json.dumps(out))
+        return 0
 
     import numpy as np
     import torch

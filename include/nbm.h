@@ -90,8 +90,9 @@ typedef enum {
  * pair; mu enters the rows at the face centres of the implicit cell. */
 typedef struct {
   int32_t geometry;       /* nbm_geometry                                             */
-  int32_t n_hidden;       /* number of tanh layers (>= 2)                             */
-  int32_t width;          /* H: 64 or 128 (FP32 path), 128 (tcgen05 path)             */
+  int32_t n_hidden;       /* number of activation layers: 2..4 (2..5 for width <= 32)  */
+  int32_t width;          /* H: 64 or 128 (FP32 path), 128 (tcgen05 path), or 1..32
+                             (narrow FP32 path, e.g. the 5 x 10 networks of Sec. 4.1)  */
   int32_t precision;      /* nbm_precision of the training/residual path              */
   double r0, amp, lobes_theta, lobes_psi;
   double mu_minus, mu_plus; /* constant diffusion coefficients, > 0                    */
