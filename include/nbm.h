@@ -61,7 +61,11 @@ typedef enum {
   NBM_GEOM_FLOWER = 2,    /* phi = r - r0 - amp sin(lobes_theta*theta) cos(lobes_psi*psi),
                              theta = polar angle from +z, psi = azimuth                */
   NBM_GEOM_ALL_PLUS = 3,  /* no interface; the whole cube is Omega+                   */
-  NBM_GEOM_ALL_MINUS = 4  /* no interface; the whole cube is Omega-                   */
+  NBM_GEOM_ALL_MINUS = 4, /* no interface; the whole cube is Omega-                   */
+  NBM_GEOM_GRID = 5       /* phi stored on a coarse mesh (Sec. 3: "a separate coarse
+                             mesh encapsulates a level-set function"), trilinearly
+                             interpolated; set with nbm_set_level_set before any
+                             computation.  No band points (band_fraction must be 0). */
 } nbm_geometry;
 
 typedef enum {
@@ -124,6 +128,17 @@ int nbm_init_problem(const nbm_problem_desc* d, nbm_problem** out);
 /* Frees the problem and its workspace.  Safe on NULL.  The caller must make
  * sure no work of this problem is still running on any stream. */
 int nbm_destroy(nbm_problem* p);
+
+/* Level set on a coarse mesh for an NBM_GEOM_GRID problem (Sec. 3): phi is a
+ * caller-owned DEVICE array of (n+1)^3 FP64 node values, node (i,j,k) at
+ * x = (-1 + 2i/n, -1 + 2j/n, -1 + 2k/n) stored at i + (n+1)(j + (n+1)k); phi is
+ * the trilinear interpolant of those values in each mesh cell, Omega- = {phi <= 0}.
+ * The values are copied into the problem (asynchronously on `stream`), so the
+ * caller may free phi once the stream has passed the copy.  1 <= n <= 1024.
+ * Returns NBM_ERR_INVALID_ARG for another geometry or a bad n.  Calling it again
+ * replaces the level set; the caller makes sure no work of this problem is
+ * still running. */
+int nbm_set_level_set(nbm_problem* p, const double* phi, int n, nbm_stream_t stream);
 
 /* Number of FP32 parameters P of the network pair. */
 int64_t nbm_param_count(const nbm_problem* p);

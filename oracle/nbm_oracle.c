@@ -54,7 +54,44 @@ void nbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * Geometry (Sec. 3: "a separate coarse mesh encapsulates a level-set
  * function"; here the level set is analytic).
  * ==================================================================== */
+/* Level set stored on a coarse mesh (Sec. 3): the trilinear interpolant of the
+ * node values in the mesh cell that contains x (cell index floor((x+1) n/2),
+ * clamped to the last cell on the upper faces); g (if not NULL) receives its
+ * gradient in that cell. */
+static double grid_phi(const nbo_problem* pr, const double x[3], double g[3]) {
+  const int n = pr->phi_n;
+  const int64_t N1 = n + 1;
+  const double sc = 0.5 * n;
+  int i[3];
+  double f[3];
+  for (int a = 0; a < 3; ++a) {
+    double t = (x[a] + 1.0) * sc;
+    int c = (int)floor(t);
+    if (c < 0) c = 0;
+    if (c > n - 1) c = n - 1;
+    i[a] = c;
+    f[a] = t - c;
+  }
+  const double* c = pr->phi_grid;
+#define NBO_C(di, dj, dk) c[(i[0] + (di)) + N1 * ((i[1] + (dj)) + N1 * (int64_t)(i[2] + (dk)))]
+  const double c000 = NBO_C(0, 0, 0), c100 = NBO_C(1, 0, 0), c010 = NBO_C(0, 1, 0),
+               c110 = NBO_C(1, 1, 0), c001 = NBO_C(0, 0, 1), c101 = NBO_C(1, 0, 1),
+               c011 = NBO_C(0, 1, 1), c111 = NBO_C(1, 1, 1);
+#undef NBO_C
+  const double c00 = c000 * (1.0 - f[0]) + c100 * f[0], c10 = c010 * (1.0 - f[0]) + c110 * f[0];
+  const double c01 = c001 * (1.0 - f[0]) + c101 * f[0], c11 = c011 * (1.0 - f[0]) + c111 * f[0];
+  const double c0 = c00 * (1.0 - f[1]) + c10 * f[1], c1 = c01 * (1.0 - f[1]) + c11 * f[1];
+  if (g) {
+    g[0] = sc * (((c100 - c000) * (1.0 - f[1]) + (c110 - c010) * f[1]) * (1.0 - f[2]) +
+                 ((c101 - c001) * (1.0 - f[1]) + (c111 - c011) * f[1]) * f[2]);
+    g[1] = sc * ((c10 - c00) * (1.0 - f[2]) + (c11 - c01) * f[2]);
+    g[2] = sc * (c1 - c0);
+  }
+  return c0 * (1.0 - f[2]) + c1 * f[2];
+}
+
 double nbo_phi(const nbo_problem* pr, const double x[3]) {
+  if (pr->geometry == NBO_GEOM_GRID) return grid_phi(pr, x, NULL);
   double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   switch (pr->geometry) {
     case NBO_GEOM_SPHERE:
@@ -76,6 +113,10 @@ double nbo_phi(const nbo_problem* pr, const double x[3]) {
 }
 
 void nbo_grad_phi(const nbo_problem* pr, const double x[3], double g[3]) {
+  if (pr->geometry == NBO_GEOM_GRID) {
+    grid_phi(pr, x, g);
+    return;
+  }
   double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   g[0] = g[1] = g[2] = 0.0;
   if (pr->geometry == NBO_GEOM_ALL_PLUS || pr->geometry == NBO_GEOM_ALL_MINUS) return;

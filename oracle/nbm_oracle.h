@@ -35,7 +35,10 @@ enum {
   NBO_GEOM_SPHERE = 1,    /* phi = |x| - r0                                     */
   NBO_GEOM_FLOWER = 2,    /* phi = r - r0 - amp sin(lt*theta) cos(lp*psi)       */
   NBO_GEOM_ALL_PLUS = 3,  /* phi = +1 everywhere: no interface, all of Omega+  */
-  NBO_GEOM_ALL_MINUS = 4  /* phi = -1 everywhere: no interface, all of Omega-  */
+  NBO_GEOM_ALL_MINUS = 4, /* phi = -1 everywhere: no interface, all of Omega-  */
+  NBO_GEOM_GRID = 5       /* phi = trilinear interpolant of the node values
+                             phi_grid on the (phi_n+1)^3 grid of [-1,1]^3
+                             (Sec. 3: a coarse mesh holds the level set)      */
 };
 
 typedef struct {
@@ -52,6 +55,10 @@ typedef struct {
                          variable coefficients mu- = y^2 ln(x+2) + 4,
                          mu+ = exp(-z) (mu_minus/mu_plus unused)            */
   int32_t activation; /* hidden-layer activation: 0 tanh, 1 sin            */
+  int32_t phi_n;      /* NBO_GEOM_GRID: cells per axis of the level-set mesh */
+  int32_t pad1;
+  const double* phi_grid; /* NBO_GEOM_GRID: node values, node (i,j,k) at
+                             i + (phi_n+1)(j + (phi_n+1)k), x_i = -1 + 2i/phi_n */
 } nbo_problem;
 
 /* Per-point terms of the residual (reading of Sec. 3). */

@@ -22,7 +22,7 @@ HDR = os.path.join(HERE, "nbm_oracle.h")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnbm_oracle.so")
 
-GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS = 1, 2, 3, 4
+GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS, GEOM_GRID = 1, 2, 3, 4, 5
 
 _lock = threading.Lock()
 _lib = None
@@ -51,6 +51,7 @@ class Problem(C.Structure):
         ("k_plus", C.c_double),
         ("h", C.c_double), ("lambda_jump", C.c_double),
         ("solution", C.c_int32), ("activation", C.c_int32),
+        ("phi_n", C.c_int32), ("pad1", C.c_int32), ("phi_grid", C.POINTER(C.c_double)),
     ]
 
 SOL_BENCH, SOL_SEC41 = 0, 1
@@ -70,9 +71,19 @@ class Cell(C.Structure):
 
 def make_problem(geometry=GEOM_SPHERE, n_hidden=2, width=64, r0=0.5, amp=0.1, lobes_theta=5.0,
                  lobes_psi=3.0, mu_minus=1.0, mu_plus=10.0, k_minus=0.0, k_plus=0.0, h=2.0 / 32,
-                 lambda_jump=1.0, solution=SOL_BENCH, activation=ACT_TANH) -> Problem:
-    return Problem(geometry, n_hidden, width, 0, r0, amp, lobes_theta, lobes_psi, mu_minus,
-                   mu_plus, k_minus, k_plus, h, lambda_jump, solution, activation)
+                 lambda_jump=1.0, solution=SOL_BENCH, activation=ACT_TANH,
+                 phi_grid=None) -> Problem:
+    """phi_grid: for GEOM_GRID, the (n+1)^3 node values of the level set (x fastest)."""
+    pr = Problem(geometry, n_hidden, width, 0, r0, amp, lobes_theta, lobes_psi, mu_minus,
+                 mu_plus, k_minus, k_plus, h, lambda_jump, solution, activation)
+    if phi_grid is not None:
+        g = np.ascontiguousarray(phi_grid, dtype=np.float64).reshape(-1)
+        n = round(len(g) ** (1.0 / 3.0)) - 1
+        assert (n + 1) ** 3 == len(g) and n >= 1
+        pr.phi_n = n
+        pr.phi_grid = g.ctypes.data_as(C.POINTER(C.c_double))
+        pr._phi_keep = g  # the array must outlive the problem
+    return pr
 
 
 _D = C.POINTER(C.c_double)
@@ -245,6 +256,8 @@ def level_problem(pr, level):
     """Copy of `pr` whose implicit cell has spacing h / 2^level."""
     q = Problem.from_buffer_copy(pr)
     q.h = pr.h / 2.0 ** level
+    if hasattr(pr, "_phi_keep"):
+        q._phi_keep = pr._phi_keep
     return q
 
 

@@ -21,7 +21,7 @@ __all__ = ["ProblemDesc", "Problem", "NBMLoss", "load_library", "config", "param
            "xavier_init", "GEOM_SPHERE", "GEOM_FLOWER", "GEOM_ALL_PLUS", "GEOM_ALL_MINUS",
            "PREC_FP32", "PREC_BF16", "PREC_FP16", "NBMError"]
 
-GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS = 1, 2, 3, 4
+GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS, GEOM_GRID = 1, 2, 3, 4, 5
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 SOL_BENCH, SOL_SEC41 = 0, 1
 ACT_TANH, ACT_SIN = 0, 1
@@ -145,6 +145,7 @@ def load_library(build_if_missing: bool = True):
                                 C.POINTER(C.c_double), P]
     L.nbm_train_steps.argtypes = [P, P, P, P, C.POINTER(C.c_int64), C.c_int, C.c_int64,
                                   C.c_float, C.c_float, C.c_float, C.c_float, C.c_uint64, P, P, P]
+    L.nbm_set_level_set.argtypes = [P, P, C.c_int, P]
     L.nbm_profile.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.nbm_profile.restype = C.c_int
     L.nbm_eval_grid.argtypes = [P, P, C.c_int, C.c_int, P, P]
@@ -203,6 +204,13 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+    def set_level_set(self, phi, n, stream=None):
+        """Level set on a coarse mesh (GEOM_GRID): the (n+1)^3 node values, x fastest."""
+        phi = _dev(phi, torch.float64)
+        if phi.numel() != (n + 1) ** 3:
+            raise ValueError("phi needs (n+1)^3 node values")
+        _check(self.lib.nbm_set_level_set(self.handle, _ptr(phi), n, _stream(stream)))
 
     def sample_points(self, n, seed=1, step=1, stream=None):
         out = torch.empty(n, 3, device="cuda", dtype=torch.float32)

@@ -136,7 +136,7 @@ static int ws_reserve(Problem& pb, int64_t n) {
 
 static int check_desc(const nbm_problem_desc* d) {
   if (!d) return fail(NBM_ERR_INVALID_ARG, "descriptor is NULL");
-  if (d->geometry < NBM_GEOM_SPHERE || d->geometry > NBM_GEOM_ALL_MINUS)
+  if (d->geometry < NBM_GEOM_SPHERE || d->geometry > NBM_GEOM_GRID)
     return fail(NBM_ERR_INVALID_ARG, "unknown geometry %d", d->geometry);
   const bool narrow = d->width >= 1 && d->width <= 32;  // the narrow FP32 kernels
   if (d->n_hidden < 2 || d->n_hidden > (narrow ? 5 : 4))
@@ -157,6 +157,8 @@ static int check_desc(const nbm_problem_desc* d) {
   if (!(d->band_fraction >= 0.0 && d->band_fraction <= 1.0))
     return fail(NBM_ERR_INVALID_ARG, "band_fraction must be in [0, 1]");
   if (!(d->lambda_jump >= 0.0)) return fail(NBM_ERR_INVALID_ARG, "lambda_jump must be >= 0");
+  if (d->geometry == NBM_GEOM_GRID && d->band_fraction != 0.0)
+    return fail(NBM_ERR_INVALID_ARG, "band points need an analytic level set (band_fraction 0)");
   if (d->solution != NBM_SOL_BENCH && d->solution != NBM_SOL_SEC41)
     return fail(NBM_ERR_INVALID_ARG, "unknown solution %d", d->solution);
   if (d->activation != NBM_ACT_TANH && d->activation != NBM_ACT_SIN)
@@ -279,6 +281,13 @@ namespace nbm {
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 const nbm_problem_desc& problem_desc(const nbm_problem* p) { return p->pb.desc; }
 int problem_num_sms(const nbm_problem* p) { return p->pb.num_sms; }
+int attach_level_set(const nbm_problem* p, ProbDev& P) {
+  P.phi_grid = p->pb.phi_grid;
+  P.phi_n = p->pb.phi_n;
+  if (P.geometry == NBM_GEOM_GRID && !P.phi_grid)
+    return fail(NBM_ERR_INVALID_ARG, "the mesh level set is not set (nbm_set_level_set)");
+  return NBM_OK;
+}
 }  // namespace nbm
 
 extern "C" {
@@ -310,6 +319,7 @@ int nbm_init_problem(const nbm_problem_desc* d, nbm_problem** out) {
 int nbm_destroy(nbm_problem* p) {
   if (!p) return NBM_OK;
   ws_free(p->pb.ws);
+  if (p->pb.phi_grid) cudaFree(p->pb.phi_grid);
   for (cudaEvent_t& e : p->pb.prof.ev)
     if (e) cudaEventDestroy(e);
   delete p;
@@ -317,6 +327,30 @@ int nbm_destroy(nbm_problem* p) {
 }
 
 int64_t nbm_param_count(const nbm_problem* p) { return p ? 2 * p->pb.p_net : -1; }
+
+int nbm_set_level_set(nbm_problem* p, const double* phi, int n, nbm_stream_t stream) {
+  if (!p || !phi) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  Problem& pb = p->pb;
+  if (pb.desc.geometry != NBM_GEOM_GRID)
+    return fail(NBM_ERR_INVALID_ARG, "the problem's geometry is not NBM_GEOM_GRID");
+  if (n < 1 || n > 1024) return fail(NBM_ERR_INVALID_ARG, "mesh level set needs 1 <= n <= 1024");
+  const size_t count = (size_t)(n + 1) * (n + 1) * (n + 1);
+  if (pb.phi_grid && pb.phi_n != n) {
+    NBM_CUDA(cudaFree(pb.phi_grid));
+    pb.phi_grid = nullptr;
+  }
+  if (!pb.phi_grid) {
+    cudaError_t e = cudaMalloc((void**)&pb.phi_grid, count * sizeof(double));
+    if (e != cudaSuccess) {
+      pb.phi_grid = nullptr;
+      return fail(NBM_ERR_OOM, "level-set mesh allocation failed");
+    }
+  }
+  pb.phi_n = n;
+  NBM_CUDA(cudaMemcpyAsync(pb.phi_grid, phi, count * sizeof(double), cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+  return NBM_OK;
+}
 
 int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused_launches_out) {
   if (!p) return fail(NBM_ERR_INVALID_ARG, "NULL problem");
@@ -349,6 +383,7 @@ int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, fl
   if (rc) return rc;
   ProbDev P;
   make_prob_dev(pb.desc, P);
+  if ((rc = attach_level_set(p, P))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   NBM_CUDA(launch_sample_classify(P, nullptr, seed, nullptr, step, n, band_count(pb.desc, n),
                                   pb.ws, st));
@@ -374,10 +409,12 @@ int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t 
   const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
   ProbDev P0;
   make_prob_dev(pb.desc, P0, 0);
+  if ((rc = attach_level_set(p, P0))) return rc;
   NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
   for (int lv = 0; lv < nlev; ++lv) {  // refinement levels: the same points, spacing h/2^lv
     ProbDev P;
     make_prob_dev(pb.desc, P, lv);
+    if ((rc = attach_level_set(p, P))) return rc;
     rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, false, r2_out, st);
     if (rc) return rc;
     StepArgs a = base_args(pb, params, MODE_RESIDUAL, 1.0f / (float)n);
@@ -402,10 +439,12 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
   const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
   ProbDev P0;
   make_prob_dev(pb.desc, P0, 0);
+  if ((rc = attach_level_set(p, P0))) return rc;
   NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
   for (int lv = 0; lv < nlev; ++lv) {
     ProbDev P;
     make_prob_dev(pb.desc, P, lv);
+    if ((rc = attach_level_set(p, P))) return rc;
     rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st);
     if (rc) return rc;
     StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)n);
@@ -437,7 +476,10 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
   const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
   const int64_t base = *step_io;
   ProbDev PL[4];
-  for (int lv = 0; lv < nlev; ++lv) make_prob_dev(pb.desc, PL[lv], lv);
+  for (int lv = 0; lv < nlev; ++lv) {
+    make_prob_dev(pb.desc, PL[lv], lv);
+    if ((rc = attach_level_set(p, PL[lv]))) return rc;
+  }
   NBM_CUDA(cudaMemcpyAsync(pb.ws.step, step_io, sizeof(int64_t), cudaMemcpyHostToDevice, st));
   NBM_CUDA(launch_prep_weights(PL[0], params, prec, pb.ws, st));
   for (int k = 0; k < n_steps; ++k) {

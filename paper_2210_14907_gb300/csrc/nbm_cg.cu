@@ -254,6 +254,7 @@ extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_ite
   d.h = 2.0 / n;
   ProbDev P;
   make_prob_dev(d, P);
+  if (int rc = attach_level_set(p, P)) return rc;
   Grid G;
   G.n = n;
   G.m1 = n - 1;

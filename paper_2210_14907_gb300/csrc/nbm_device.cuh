@@ -25,6 +25,8 @@ struct ProbDev {
   int level;       // refinement level of this pass (0: base cell; > 0 accumulates r2_out)
   int solution;    // manufactured pair: 0 benchmark (constant mu), 1 Sec. 4.1 (variable mu)
   int activation;  // hidden-layer activation: 0 tanh, 1 sin
+  int phi_n;              // NBM_GEOM_GRID: cells per axis of the level-set mesh
+  const double* phi_grid; // NBM_GEOM_GRID: (phi_n+1)^3 node values, x fastest
   float hf, inv_hf, h2f, inv_h2f;  // h, 1/h, h^2, 1/h^2 in FP32
   float r0f, ampf, ltf, lpf;
   float muf[2], kf[2];
@@ -72,7 +74,42 @@ constexpr uint32_t kPointStream = 0x4E424D31u;  // 4th counter word of point dra
 // Level sets (Sec. 3: the level set gives the cell/interface crossings).
 // theta = atan2(rho, z) is the polar angle, psi = atan2(y, x) the azimuth.
 // ---------------------------------------------------------------------------
+// Level set stored on a coarse mesh (NBM_GEOM_GRID): the trilinear interpolant
+// of the node values in the mesh cell containing x (index floor((x+1) n/2),
+// clamped to the last cell on the upper faces), and its gradient in that cell.
+template <typename T>
+__device__ inline T grid_phi(const ProbDev& P, T x, T y, T z, T* g) {
+  const int n = P.phi_n;
+  const int64_t N1 = n + 1;
+  const T sc = (T)0.5 * (T)n;
+  const T t[3] = {(x + (T)1) * sc, (y + (T)1) * sc, (z + (T)1) * sc};
+  int i[3];
+  T f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int c = (int)floor(t[a]);
+    c = c < 0 ? 0 : (c > n - 1 ? n - 1 : c);
+    i[a] = c;
+    f[a] = t[a] - (T)c;
+  }
+  const double* cg = P.phi_grid + i[0] + N1 * (i[1] + N1 * (int64_t)i[2]);
+  const int64_t sy = N1, sz = N1 * N1;
+  const T c000 = (T)cg[0], c100 = (T)cg[1], c010 = (T)cg[sy], c110 = (T)cg[sy + 1];
+  const T c001 = (T)cg[sz], c101 = (T)cg[sz + 1], c011 = (T)cg[sz + sy], c111 = (T)cg[sz + sy + 1];
+  const T c00 = c000 * ((T)1 - f[0]) + c100 * f[0], c10 = c010 * ((T)1 - f[0]) + c110 * f[0];
+  const T c01 = c001 * ((T)1 - f[0]) + c101 * f[0], c11 = c011 * ((T)1 - f[0]) + c111 * f[0];
+  const T c0 = c00 * ((T)1 - f[1]) + c10 * f[1], c1 = c01 * ((T)1 - f[1]) + c11 * f[1];
+  if (g) {
+    g[0] = sc * (((c100 - c000) * ((T)1 - f[1]) + (c110 - c010) * f[1]) * ((T)1 - f[2]) +
+                 ((c101 - c001) * ((T)1 - f[1]) + (c111 - c011) * f[1]) * f[2]);
+    g[1] = sc * ((c10 - c00) * ((T)1 - f[2]) + (c11 - c01) * f[2]);
+    g[2] = sc * (c1 - c0);
+  }
+  return c0 * ((T)1 - f[2]) + c1 * f[2];
+}
+
 __device__ inline float phi_f(const ProbDev& P, float x, float y, float z) {
+  if (P.geometry == NBM_GEOM_GRID) return grid_phi<float>(P, x, y, z, nullptr);
   if (P.geometry == NBM_GEOM_ALL_PLUS) return 1.f;
   if (P.geometry == NBM_GEOM_ALL_MINUS) return -1.f;
   float rho2 = x * x + y * y;
@@ -84,6 +121,7 @@ __device__ inline float phi_f(const ProbDev& P, float x, float y, float z) {
 }
 
 __device__ inline double phi_d(const ProbDev& P, double x, double y, double z) {
+  if (P.geometry == NBM_GEOM_GRID) return grid_phi<double>(P, x, y, z, nullptr);
   if (P.geometry == NBM_GEOM_ALL_PLUS) return 1.0;
   if (P.geometry == NBM_GEOM_ALL_MINUS) return -1.0;
   double rho2 = x * x + y * y;
@@ -95,6 +133,10 @@ __device__ inline double phi_d(const ProbDev& P, double x, double y, double z) {
 }
 
 __device__ inline void grad_phi_d(const ProbDev& P, const double x[3], double g[3]) {
+  if (P.geometry == NBM_GEOM_GRID) {
+    grid_phi<double>(P, x[0], x[1], x[2], g);
+    return;
+  }
   g[0] = g[1] = g[2] = 0.0;
   if (P.geometry == NBM_GEOM_ALL_PLUS || P.geometry == NBM_GEOM_ALL_MINUS) return;
   double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
@@ -211,6 +253,10 @@ __device__ inline double alpha_d(const ProbDev& P, const double x[3]) {
 
 // FP32 versions of the level-set gradient, [u] and [mu d_n u] (the FP32 rows)
 __device__ inline void grad_phi_f(const ProbDev& P, const float x[3], float g[3]) {
+  if (P.geometry == NBM_GEOM_GRID) {
+    grid_phi<float>(P, x[0], x[1], x[2], g);
+    return;
+  }
   g[0] = g[1] = g[2] = 0.f;
   if (P.geometry == NBM_GEOM_ALL_PLUS || P.geometry == NBM_GEOM_ALL_MINUS) return;
   const float rho = sqrtf(x[0] * x[0] + x[1] * x[1]);

@@ -402,6 +402,7 @@ static int eval_common(nbm_problem* p, const float* params, int n, const float* 
   }
   ProbDev P;
   make_prob_dev(d, P);
+  if (int rc = attach_level_set(p, P)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   if (precision == NBM_PREC_FP32) {

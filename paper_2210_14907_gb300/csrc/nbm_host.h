@@ -111,6 +111,8 @@ struct Problem {
   int num_sms = 0;
   int64_t p_net = 0;
   Workspace ws;
+  double* phi_grid = nullptr;  // NBM_GEOM_GRID: node values of the mesh level set
+  int phi_n = 0;
 };
 
 // Device constants of refinement level `level` (cell spacing h / 2^level).
@@ -119,6 +121,9 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P, int level = 0);
 void set_error_message(const char* msg);
 const nbm_problem_desc& problem_desc(const nbm_problem* p);
 int problem_num_sms(const nbm_problem* p);
+// Gives P the problem's mesh level set; NBM_ERR_INVALID_ARG (with the message
+// set) for an NBM_GEOM_GRID problem whose level set has not been set.
+int attach_level_set(const nbm_problem* p, ProbDev& P);
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,

@@ -104,6 +104,7 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   const int num_sms = problem_num_sms(p);
   ProbDev P;
   make_prob_dev(d, P);
+  if (int rc = attach_level_set(p, P)) return rc;
   if (d.width > 128 || d.n_hidden - 1 > kStaticMaxHidden || P.gstride > kStaticMaxPNetStride)
     return fail_static(NBM_ERR_INVALID_ARG, "network larger than the static-scratch limit");
   if (d.refine_levels != 0)

@@ -114,6 +114,84 @@ def test_sphere_volume_and_area_converge():
     assert errs_v[0] / errs_v[1] > 3.8 and errs_a[0] / errs_a[1] > 3.8  # second order
 
 
+def _grid_nodes(n):
+    g = -1.0 + np.arange(n + 1) * 2.0 / n
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)  # x fastest
+
+
+def test_mesh_level_set_reproduces_trilinear_functions():
+    """Sec. 3 level set on a coarse mesh: trilinear interpolation of the node
+    values is exact for every trilinear function, and so is its gradient."""
+    rng = np.random.default_rng(31)
+    a = rng.normal(size=8)
+
+    def f(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return (a[0] + a[1] * X + a[2] * Y + a[3] * Z + a[4] * X * Y + a[5] * X * Z
+                + a[6] * Y * Z + a[7] * X * Y * Z)
+
+    def grad(x):
+        X, Y, Z = x
+        return np.array([a[1] + a[4] * Y + a[5] * Z + a[7] * Y * Z,
+                         a[2] + a[4] * X + a[6] * Z + a[7] * X * Z,
+                         a[3] + a[5] * X + a[6] * Y + a[7] * X * Y])
+
+    pr = O.make_problem(geometry=O.GEOM_GRID, phi_grid=f(_grid_nodes(6)))
+    for x in np.concatenate([rng.uniform(-1, 1, size=(200, 3)), [[1.0, 1.0, 1.0], [-1, 0.2, 1]]]):
+        assert abs(O.phi(pr, x) - f(x)) < 1e-13
+        assert np.allclose(O.grad_phi(pr, x), grad(x), atol=1e-12)
+
+
+def test_mesh_level_set_of_the_sphere_converges():
+    """The sphere's level set stored at the nodes of 8^3, 16^3 and 32^3 meshes: the
+    enclosed volume and the interface area (cells of spacing 1/32) approach the
+    sphere's at second order in the mesh spacing."""
+    h = 2.0 / 64
+    c = -1.0 + h * (np.arange(64) + 0.5)
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    R = np.sqrt(X**2 + Y**2 + Z**2)
+    band = np.abs(R - 0.5) < 0.2
+    pts = np.stack([X[band], Y[band], Z[band]], axis=1)
+    errs_v, errs_a = [], []
+    for n in (8, 16, 32):
+        x = _grid_nodes(n)
+        pr = O.make_problem(geometry=O.GEOM_GRID, h=h,
+                            phi_grid=np.sqrt((x ** 2).sum(1)) - 0.5)
+        vol = float(np.sum(R[~band] < 0.5)) * h**3
+        area = 0.0
+        for p in pts:
+            g = O.cell_geometry(pr, p, h)
+            vol += g["V"][0] * h**3
+            area += g["S"] * h**2
+        errs_v.append(abs(vol - 4.0 / 3.0 * math.pi / 8.0))
+        errs_a.append(abs(area - math.pi))
+    assert errs_v[0] / errs_v[1] > 3.0 and errs_v[1] / errs_v[2] > 3.0
+    assert errs_a[2] < 0.02 and errs_a[0] / errs_a[2] > 6.0
+
+
+def test_cut_cell_consistency_on_a_mesh_level_set():
+    """A plane stored on a coarse mesh (represented exactly): with the exact u^+-,
+    cut-cell rows are O(h^2) and the value jump is met exactly."""
+    x = _grid_nodes(4)
+    plane = 0.3 * x[:, 0] - 0.2 * x[:, 1] + 0.9 * x[:, 2] - 0.1
+    rng = np.random.default_rng(32)
+    mx = []
+    for h in (1 / 32, 1 / 64, 1 / 128):
+        pr = O.make_problem(geometry=O.GEOM_GRID, h=h, mu_minus=1.0, mu_plus=10.0,
+                            phi_grid=plane)
+        res = []
+        while len(res) < 100:
+            p = rng.uniform(-0.8, 0.8, size=3)
+            q = p - (O.phi(pr, p) + rng.uniform(-0.3, 0.3) * h) * np.array([0.3, -0.2, 0.9]) / 0.94
+            t = O.point_terms(pr, None, q, mode=1)
+            if t["cut"]:
+                res.append(t)
+        mx.append(max(abs(r["B"]) for r in res))
+        assert max(abs(r["J"]) for r in res) < 1e-13
+    assert mx[0] / mx[1] > 3.4 and mx[1] / mx[2] > 3.4
+
+
 def test_uncut_cells_are_exactly_zero_one():
     pr = O.make_problem(geometry=O.GEOM_SPHERE, h=1.0 / 16)
     for p, s in (([0.0, 0.0, 0.0], 0), ([0.9, 0.9, 0.9], 1), ([0.2, -0.1, 0.05], 0)):
