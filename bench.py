@@ -344,9 +344,9 @@ def table1(dev, epochs, resolutions, lr=1e-3):
 
 def secondary(dev, hbm_peak, peak_src):
     """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
-    flower-interface 3->128x4->1 architecture) and the FP64 grid CG solve of the
-    same discretization at 128^3 and 256^3 (the plain method the NBM lifts off
-    its grid)."""
+    flower-interface 3->128x4->1 architecture), the mixed training step of the C3
+    and C4 workloads, and the FP64 grid CG solve of the same discretization at
+    128^3 and 256^3 (the plain method the NBM lifts off its grid)."""
     import torch
 
     import paper_2210_14907_gb300 as nbm
@@ -373,6 +373,27 @@ def secondary(dev, hbm_peak, peak_src):
                         "ms": ms, "tensor_tflops": flops / ms / 1e9}
     del u
     torch.cuda.empty_cache()
+    # the other training workloads: flower with 30 % band points (C3) and the
+    # fine-resolution sphere with FP64 rows (C4), mixed path, full batches
+    for name, steps in (("C3", 20), ("C4", 6)):
+        dt = nbm.config(name)
+        pt = nbm.Problem(dt)
+        params = nbm.xavier_init(dt, seed=0, device=dev)
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        B = nbm.BATCH[name]
+        pt.train_steps(params, m, v, 0, 2, B, lr=1e-3, seed=1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pt.train_steps(params, m, v, 2, steps, B, lr=1e-3, seed=1)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        flops = B * 21 * (dt.n_hidden - 1) * 2 * 128 * 128
+        out[f"train_{name}"] = {"points_per_s": B / ms * 1e3, "ms_per_step": ms, "batch": B,
+                                "tensor_tflops": flops / ms / 1e9, "steps": steps}
+        del pt, params, m, v
+        torch.cuda.empty_cache()
     for n in (128, 256):
         dcg = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
         pcg = nbm.Problem(dcg)
