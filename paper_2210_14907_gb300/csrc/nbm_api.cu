@@ -248,7 +248,12 @@ static int front_stages(Problem& pb, const ProbDev& P, const float* params, cons
   NBM_CUDA(launch_cut_geometry(P, n, w, st));
   if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(P, n, w, st));
   StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)n);
-  NBM_CUDA(launch_step(pb, P, a, st));
+  // The fine-h mode (FP64 rows) evaluates the cut cells' networks on the FP32
+  // path: their jump rows U+(x_G) - U-(x_G) - alpha difference two O(1) network
+  // values, which 16-bit GEMM operands would carry with ~2^-9 relative error.
+  // Cut cells are a small share of the points, so the cost is small.
+  if (P.fp64 && pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_step_fp32(P, a, w.grid, st));
+  else NBM_CUDA(launch_step(pb, P, a, st));
   NBM_CUDA(launch_cut_residual(P, n, (float)(1.0 / (double)n), want_seeds, r2_out, w, st));
   return NBM_OK;
 }

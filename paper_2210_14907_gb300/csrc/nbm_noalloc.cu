@@ -185,7 +185,12 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
     return prec == NBM_PREC_FP32 ? launch_step_fp32(P, a, grid, st)
                                  : launch_step_tc(P, a, grid, prec, st);
   };
-  if (e == cudaSuccess) e = step_launch(MODE_CUT_FWD);
+  if (e == cudaSuccess) {
+    // fine-h mode: the cut cells' networks on the FP32 path (as nbm_loss_grad)
+    a.mode = MODE_CUT_FWD;
+    e = (P.fp64 && prec != NBM_PREC_FP32) ? launch_step_fp32(P, a, grid, st)
+                                           : step_launch(MODE_CUT_FWD);
+  }
   if (e == cudaSuccess) e = launch_cut_residual(P, n, (float)(1.0 / (double)n), true, nullptr, w, st);
   if (e == cudaSuccess) e = step_launch(MODE_TRAIN);
   if (e == cudaSuccess)
