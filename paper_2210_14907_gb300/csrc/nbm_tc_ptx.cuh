@@ -199,13 +199,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same with a suspend-time hint: the thread may sleep up to `hint_ns`
+// nanoseconds and is woken when the phase completes, instead of spinning on
+// issue slots that other warps could use.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t mbar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: gives up after ~`budget` clock cycles and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity,
                                                   long long budget = 4000000000LL) {
   if (mbar_try_wait(mbar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try_wait(mbar, parity)) return true;
+    if (mbar_try_wait_sleep(mbar, parity, 20000u)) return true;
     if (clock64() - t0 > budget) return false;
   }
 }
