@@ -446,9 +446,14 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
           float o[8];
           const float t = act_tanh<FAST>(c[0] + bb);
           o[0] = t;
+          // symmetric increments small in every lane: their series (see tanh_stencil_fwd)
+          const bool small_mu =
+              FAST && __all_sync(0xffffffffu,
+                                 fmaxf(fabsf(c[1]), fmaxf(fabsf(c[2]), fabsf(c[3]))) * h2s <= kSmallMu);
 #pragma unroll
           for (int i = 0; i < 3; ++i)
-            tanh_stencil_fwd<FAST>(t, c[1 + i], c[4 + i], hs, h2s, ihs, ih2s, o[1 + i], o[4 + i]);
+            tanh_stencil_fwd<FAST>(t, c[1 + i], c[4 + i], hs, h2s, ihs, ih2s, o[1 + i], o[4 + i],
+                                   small_mu);
           o[7] = act_tanh<FAST>(c[7] + bb);
           if (g < NG) {
             store8o<BF>(Aimg + g * kImgH, poff(j), o);
