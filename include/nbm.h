@@ -140,6 +140,16 @@ int nbm_destroy(nbm_problem* p);
  * still running. */
 int nbm_set_level_set(nbm_problem* p, const double* phi, int n, nbm_stream_t stream);
 
+/* Diagnostics for the failure handling of the device code: one warp waits,
+ * with the bounded wait that every kernel of the library uses (mbarrier waits
+ * that give up after a clock-cycle budget and set a status bit instead of
+ * spinning), on a barrier that nothing completes.  Returns
+ * NBM_ERR_DEVICE_TIMEOUT once the wait has given up after about budget_cycles
+ * clock cycles (1e3..1e10) -- the error a computation reports when one of its
+ * device waits runs out -- or NBM_OK if the barrier completed.  No fault, no
+ * trap: the context stays usable.  Synchronizes the stream. */
+int nbm_selftest_bounded_wait(int64_t budget_cycles, nbm_stream_t stream);
+
 /* Number of FP32 parameters P of the network pair. */
 int64_t nbm_param_count(const nbm_problem* p);
 

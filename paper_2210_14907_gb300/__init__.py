@@ -146,6 +146,7 @@ def load_library(build_if_missing: bool = True):
     L.nbm_train_steps.argtypes = [P, P, P, P, C.POINTER(C.c_int64), C.c_int, C.c_int64,
                                   C.c_float, C.c_float, C.c_float, C.c_float, C.c_uint64, P, P, P]
     L.nbm_set_level_set.argtypes = [P, P, C.c_int, P]
+    L.nbm_selftest_bounded_wait.argtypes = [C.c_int64, P]
     L.nbm_profile.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.nbm_profile.restype = C.c_int
     L.nbm_eval_grid.argtypes = [P, P, C.c_int, C.c_int, P, P]
@@ -154,7 +155,8 @@ def load_library(build_if_missing: bool = True):
     L.nbm_grid_cg_solve.argtypes = [P, C.c_int, C.c_double, C.c_int, P, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double), P]
     for fn in ("nbm_init_problem", "nbm_destroy", "nbm_sample_points", "nbm_residual",
-               "nbm_loss_grad", "nbm_train_steps", "nbm_eval_grid", "nbm_grid_cg_solve"):
+               "nbm_loss_grad", "nbm_train_steps", "nbm_eval_grid", "nbm_grid_cg_solve",
+               "nbm_set_level_set", "nbm_selftest_bounded_wait"):
         getattr(L, fn).restype = C.c_int
     _lib = L
     return L

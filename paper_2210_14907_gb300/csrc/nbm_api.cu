@@ -286,6 +286,12 @@ namespace nbm {
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 const nbm_problem_desc& problem_desc(const nbm_problem* p) { return p->pb.desc; }
 int problem_num_sms(const nbm_problem* p) { return p->pb.num_sms; }
+int check_aligned(const void* ptr, size_t align, const char* name) {
+  if (ptr && ((uintptr_t)ptr & (align - 1)) != 0)
+    return fail(NBM_ERR_INVALID_ARG, "%s is not %zu-byte aligned", name, align);
+  return NBM_OK;
+}
+
 int attach_level_set(const nbm_problem* p, ProbDev& P) {
   P.phi_grid = p->pb.phi_grid;
   P.phi_n = p->pb.phi_n;
@@ -333,8 +339,25 @@ int nbm_destroy(nbm_problem* p) {
 
 int64_t nbm_param_count(const nbm_problem* p) { return p ? 2 * p->pb.p_net : -1; }
 
+int nbm_selftest_bounded_wait(int64_t budget_cycles, nbm_stream_t stream) {
+  if (budget_cycles < 1000 || budget_cycles > 10000000000LL)
+    return fail(NBM_ERR_INVALID_ARG, "budget_cycles must be in [1e3, 1e10]");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d_out = nullptr;
+  NBM_CUDA(cudaMalloc((void**)&d_out, sizeof(int)));
+  int h_out = -1;
+  cudaError_t e = launch_selftest_wait((long long)budget_cycles, d_out, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_out, d_out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(NBM_ERR_CUDA, "self-test: %s", cudaGetErrorString(e));
+  if (h_out & 2) return fail(NBM_ERR_DEVICE_TIMEOUT, "the bounded wait gave up (as intended)");
+  return NBM_OK;
+}
+
 int nbm_set_level_set(nbm_problem* p, const double* phi, int n, nbm_stream_t stream) {
   if (!p || !phi) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  if (int rc = check_aligned(phi, 8, "phi")) return rc;
   Problem& pb = p->pb;
   if (pb.desc.geometry != NBM_GEOM_GRID)
     return fail(NBM_ERR_INVALID_ARG, "the problem's geometry is not NBM_GEOM_GRID");
@@ -382,6 +405,7 @@ int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, fl
                       nbm_stream_t stream) {
   if (!p || !pts_out) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
   int rc = check_n(n);
+  if (!rc) rc = check_aligned(pts_out, 4, "pts_out");
   if (rc) return rc;
   Problem& pb = p->pb;
   rc = ws_reserve(pb, n);
@@ -406,6 +430,9 @@ int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t 
                  int64_t step, float* r2_out, double* loss_out, nbm_stream_t stream) {
   if (!p || !params) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
   int rc = check_n(n);
+  if (!rc) rc = check_aligned(params, 4, "params");
+  if (!rc) rc = check_aligned(pts, 4, "pts");
+  if (!rc) rc = check_aligned(r2_out, 4, "r2_out");
   if (rc) return rc;
   Problem& pb = p->pb;
   rc = ws_reserve(pb, n);
@@ -436,6 +463,9 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
                   int64_t step, float* grad_out, double* loss_out, nbm_stream_t stream) {
   if (!p || !params || !grad_out) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
   int rc = check_n(n);
+  if (!rc) rc = check_aligned(params, 4, "params");
+  if (!rc) rc = check_aligned(pts, 4, "pts");
+  if (!rc) rc = check_aligned(grad_out, 4, "grad_out");
   if (rc) return rc;
   Problem& pb = p->pb;
   rc = ws_reserve(pb, n);
@@ -472,6 +502,11 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
       !(eps > 0.f))
     return fail(NBM_ERR_INVALID_ARG, "bad Adam hyper-parameters");
   int rc = check_n(batch);
+  if (!rc) rc = check_aligned(params, 4, "params");
+  if (!rc) rc = check_aligned(adam_m, 4, "adam_m");
+  if (!rc) rc = check_aligned(adam_v, 4, "adam_v");
+  if (!rc) rc = check_aligned(pts, 4, "pts");
+  if (!rc) rc = check_aligned(loss_hist, 4, "loss_hist");
   if (rc) return rc;
   if (n_steps == 0) return NBM_OK;
   Problem& pb = p->pb;

@@ -245,6 +245,7 @@ extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_ite
     set_error_message("NULL argument");
     return NBM_ERR_INVALID_ARG;
   }
+  if (int rc = check_aligned(u_out, 8, "u_out")) return rc;
   if (n < 2 || n > 2048 || !(rtol > 0.0) || max_iter < 0) {
     snprintf(msg, sizeof(msg), "grid CG needs 2 <= n <= 2048, rtol > 0, max_iter >= 0 (n=%d)", n);
     set_error_message(msg);

@@ -386,6 +386,9 @@ static int eval_common(nbm_problem* p, const float* params, int n, const float* 
     set_error_message("NULL argument");
     return NBM_ERR_INVALID_ARG;
   }
+  if (int rc = check_aligned(params, 4, "params")) return rc;
+  if (int rc = check_aligned(pts, 4, "pts")) return rc;
+  if (int rc = check_aligned(u_out, 4, "u_out")) return rc;
   const nbm_problem_desc& d = problem_desc(p);
   if (!pts && (n < 1 || n > 4096)) {
     snprintf(msg, sizeof(msg), "grid evaluation needs 1 <= n <= 4096 (n=%d)", n);

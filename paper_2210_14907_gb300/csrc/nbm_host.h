@@ -32,8 +32,9 @@ struct CutRec {
   int has_jump;    // S > 0
 };
 
-// One collocation point of a tensor-core tile, gathered in list order so that a
-// tile's 16 records are one contiguous 512-byte block.
+// One collocation point of a tensor-core tile, gathered in list order (each list
+// padded to a multiple of 16) so that a half-tile's 8 records are one
+// contiguous 256-byte block.
 struct PRec {
   float x, y, z;     // point
   float gx, gy, gz;  // cut cell: interface point.  Uncut point: gx = f^s(p) in
@@ -124,6 +125,9 @@ int problem_num_sms(const nbm_problem* p);
 // Gives P the problem's mesh level set; NBM_ERR_INVALID_ARG (with the message
 // set) for an NBM_GEOM_GRID problem whose level set has not been set.
 int attach_level_set(const nbm_problem* p, ProbDev& P);
+// NBM_ERR_INVALID_ARG (with the message set) when a non-NULL pointer is not
+// aligned to `align` bytes (its element size).
+int check_aligned(const void* ptr, size_t align, const char* name);
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
@@ -144,6 +148,7 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
                           Workspace& ws, cudaStream_t st, int level = 0, int n_levels = 1);
 size_t tc_smem_bytes(int L);
+cudaError_t launch_selftest_wait(long long budget, int* out, cudaStream_t st);
 size_t fp32_smem_bytes(int H, int L);
 int tc_supported(int H, int L);
 

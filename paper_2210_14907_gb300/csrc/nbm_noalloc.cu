@@ -96,6 +96,9 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
                                     int64_t n, uint64_t seed, int64_t step, float* grad_out,
                                     double* loss_out, nbm_stream_t stream) {
   if (!p || !params || !grad_out) return fail_static(NBM_ERR_INVALID_ARG, "NULL argument");
+  if (int rc = check_aligned(params, 4, "params")) return rc;
+  if (int rc = check_aligned(pts, 4, "pts")) return rc;
+  if (int rc = check_aligned(grad_out, 4, "grad_out")) return rc;
   if (n <= 0 || n > kStaticMaxPoints)
     return fail_static(NBM_ERR_INVALID_ARG,
                        "batch %lld outside the static-scratch limit [1, %lld]", (long long)n,

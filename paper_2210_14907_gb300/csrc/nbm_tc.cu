@@ -682,6 +682,27 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
   if (w == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// Diagnostics: one warp waits, with the bounded wait every kernel of the
+// library uses, on a barrier that nothing completes.  Every thread's wait must
+// give up after about `budget` clock cycles; *out = 2 (the status bit of a
+// wait that ran out) if all gave up, 0 if the barrier completed.
+__global__ void k_selftest_wait(long long budget, int* out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(smem_u32(&bar), 0, budget);
+  const bool any = __syncthreads_or(ok);
+  if (threadIdx.x == 0) *out = any ? 0 : 2;
+}
+
+cudaError_t launch_selftest_wait(long long budget, int* out, cudaStream_t st) {
+  k_selftest_wait<<<1, 32, 0, st>>>(budget, out);
+  return cudaGetLastError();
+}
+
 template <int L, bool BF, bool FAST>
 static cudaError_t launch_tc_t(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st) {
   constexpr bool SCALED = !BF;  // FP16 operands need the 1/h^2, 1/h column scaling
