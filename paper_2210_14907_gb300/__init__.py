@@ -18,8 +18,9 @@ import torch
 from . import build as _build
 
 __all__ = ["ProblemDesc", "Problem", "NBMLoss", "load_library", "config", "param_count",
-           "xavier_init", "GEOM_SPHERE", "GEOM_FLOWER", "GEOM_ALL_PLUS", "GEOM_ALL_MINUS",
-           "PREC_FP32", "PREC_BF16", "PREC_FP16", "NBMError"]
+           "xavier_init", "save_checkpoint", "load_checkpoint", "GEOM_SPHERE", "GEOM_FLOWER",
+           "GEOM_ALL_PLUS", "GEOM_ALL_MINUS", "GEOM_GRID", "PREC_FP32", "PREC_BF16",
+           "PREC_FP16", "SOL_BENCH", "SOL_SEC41", "ACT_TANH", "ACT_SIN", "NBMError"]
 
 GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS, GEOM_GRID = 1, 2, 3, 4, 5
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
@@ -102,6 +103,22 @@ BATCH = {"C1": 4096, "C2": 262_144, "C3": 1_048_576, "C4": 4_194_304, "C5": 1_04
 def param_count(d: ProblemDesc) -> int:
     H = d.width
     return 2 * (4 * H + (d.n_hidden - 1) * (H * H + H) + H + 1)
+
+
+def save_checkpoint(path, desc: ProblemDesc, params, m, v, step: int, seed: int) -> None:
+    """Everything a training run needs to continue bitwise: the descriptor, the
+    parameters, Adam's m and v, the number of steps taken and the Philox key (the
+    points of step t are drawn at counter t, so no generator state is kept)."""
+    torch.save({"desc": dataclasses.asdict(desc), "params": params.detach().cpu(),
+                "m": m.detach().cpu(), "v": v.detach().cpu(), "step": int(step),
+                "seed": int(seed)}, path)
+
+
+def load_checkpoint(path, device="cuda"):
+    """Returns (desc, params, m, v, step, seed) as saved by save_checkpoint."""
+    c = torch.load(path, map_location="cpu")
+    return (ProblemDesc(**c["desc"]), c["params"].to(device), c["m"].to(device),
+            c["v"].to(device), c["step"], c["seed"])
 
 
 def xavier_init(d: ProblemDesc, seed: int = 0, device="cpu") -> torch.Tensor:

@@ -108,3 +108,27 @@ def test_bf16_deterministic_and_resumable():
         outs.append((tp, m, v))
     for x, y in zip(outs[0], outs[1]):
         assert torch.equal(x, y)
+
+
+def test_checkpoint_resume_in_a_new_problem_is_bitwise(tmp_path):
+    """Elastic recovery is resume from a checkpoint: 10 steps equal 5 steps, a
+    checkpoint written to disk, a fresh problem object and 5 more steps."""
+    nbm = _nbm()
+    d = nbm.config("C2")
+    full = nbm.Problem(d)
+    p = nbm.xavier_init(d, seed=4, device="cuda")
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    full.train_steps(p, m, v, 0, 10, 16384, seed=9)
+    a = nbm.Problem(d)
+    q = nbm.xavier_init(d, seed=4, device="cuda")
+    mq = torch.zeros_like(q)
+    vq = torch.zeros_like(q)
+    s = a.train_steps(q, mq, vq, 0, 5, 16384, seed=9)
+    nbm.save_checkpoint(tmp_path / "ck.pt", d, q, mq, vq, s, 9)
+    del a, q, mq, vq
+    d2, q, mq, vq, s, seed = nbm.load_checkpoint(tmp_path / "ck.pt")
+    b = nbm.Problem(d2)
+    b.train_steps(q, mq, vq, s, 5, 16384, seed=seed)
+    for x, y in ((p, q), (m, mq), (v, vq)):
+        assert torch.equal(x, y)
