@@ -372,9 +372,10 @@ __device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, fl
   }
   float sw = fmaf(-tw, tw, 1.0f);
   float Td2 = Td * Td;
-  float r2 = rcp<FAST>(fmaf(-tw * tw, Td2, 1.0f));
-  float m = fmaf(-tw * sw * Td2, r2, dm);
-  float d = sw * Td * r2;
+  float r2 = rcp<FAST>(fmaf(sw - 1.0f, Td2, 1.0f));  // 1 / (1 - tw^2 Td^2)
+  float k = sw * r2;
+  float m = fmaf(-tw * Td2, k, dm);
+  float d = k * Td;
   mo = m * inv_h2;
   dout = d * inv_h;
 }
