@@ -132,3 +132,42 @@ def test_checkpoint_resume_in_a_new_problem_is_bitwise(tmp_path):
     b.train_steps(q, mq, vq, s, 5, 16384, seed=seed)
     for x, y in ((p, q), (m, mq), (v, vq)):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("prec,H,L,tol_r,tol_g", [(0, 64, 2, 1e-5, 1e-4), (1, 128, 3, 2e-3, 5e-3)],
+                         ids=["fp32", "bf16"])
+def test_extreme_points_and_corners_on_the_interface(prec, H, L, tol_r, tol_g):
+    """Points at the lattice extremes +-(1 - 2^-22) (stencil neighbours leave the
+    cube on up to three axes: Dirichlet faces) and cells with a corner exactly on
+    the sphere (phi = 0 counts as Omega-), mixed with ordinary points."""
+    nbm = _nbm()
+    h = 2 / 16
+    d = nbm.ProblemDesc(geometry=O.GEOM_SPHERE, n_hidden=L, width=H, precision=prec,
+                        mu_minus=1.0, mu_plus=10.0, h=h)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_SPHERE, n_hidden=L, width=H, mu_minus=1.0, mu_plus=10.0,
+                       h=h)
+    e = 1.0 - 2.0 ** -22
+    corners = [[sx * e, sy * e, sz * e] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]
+    edges = [[e, 0.3, -e], [-e, 0.0, 0.5], [0.25, e, 0.0]]
+    hh = h / 2
+    on_gamma = [[0.5 - hh, hh, hh], [-0.5 + hh, -hh, hh], [hh, 0.5 - hh, -hh], [hh, hh, 0.5 + hh],
+                [-hh, -hh, -0.5 - hh]]  # one corner of each cell at a pole of the sphere
+    for p in on_gamma:
+        t = O.cell_geometry(o, np.array(p), h)
+        assert t["cut"] in (0, 1)
+    pts = np.concatenate([np.array(corners + edges + on_gamma),
+                          inputs.mixed_points(200, 100, seed=77)]).astype(np.float32)
+    th = inputs.glorot_params(H, L, seed=19, bias_scale=0.1)
+    L_ref, r2_ref = O.loss(o, th.astype(np.float64), pts, want_r2=True)
+    _, g_ref = O.loss_grad(o, th.astype(np.float64), pts)
+    tp = torch.from_numpy(th).cuda()
+    tx = torch.from_numpy(pts).cuda()
+    loss, r2 = prob.residual(tp, tx)
+    _, g = prob.loss_grad(tp, tx)
+    r2 = r2.cpu().numpy()
+    assert np.all(np.isfinite(r2))
+    assert _rel(np.sqrt(r2), np.sqrt(r2_ref)) <= tol_r
+    assert _rel(np.sqrt(r2[:16]), np.sqrt(r2_ref[:16])) <= tol_r  # the special points alone
+    assert abs(loss - L_ref) <= tol_r * L_ref
+    assert _rel(g.cpu().numpy(), g_ref) <= tol_g
