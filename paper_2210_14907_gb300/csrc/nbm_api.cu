@@ -9,9 +9,21 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nbm_device.cuh"
 
 namespace nbm {
+
+// Named host-side ranges (NVTX v3, header only): a profiler attached to the
+// process sees each stage of a call; without one they cost a function call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 static thread_local char g_err[512] = "no error";
 
@@ -221,6 +233,7 @@ static cudaError_t launch_step(Problem& pb, const ProbDev& P, const StepArgs& a,
 
 // the fused MODE_TRAIN launch, bracketed by events while profiling is on
 static cudaError_t launch_timed(Problem& pb, const ProbDev& P, const StepArgs& a, cudaStream_t st) {
+  NvtxRange r("nbm.fused (forward, rows, backward)");
   Profiler& pr = pb.prof;
   const bool rec = pr.on && pr.n < Profiler::kMax;
   if (rec) {
@@ -243,6 +256,7 @@ static int front_stages(Problem& pb, const ProbDev& P, const float* params, cons
                         int64_t n, uint64_t seed, const int64_t* step_dev, int64_t step_host,
                         bool want_seeds, float* r2_out, cudaStream_t st) {
   Workspace& w = pb.ws;
+  NvtxRange r("nbm.front (sample, cell geometry, cut rows)");
   NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, n), w,
                                   st));
   NBM_CUDA(launch_cut_geometry(P, n, w, st));
@@ -524,6 +538,7 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
   NBM_CUDA(launch_prep_weights(PL[0], params, prec, pb.ws, st));
   for (int k = 0; k < n_steps; ++k) {
     const float* pk = pts ? pts + (int64_t)k * batch * 3 : nullptr;
+    NvtxRange step_range("nbm.train_step");
     // refinement levels: the same points (the device step counter advances
     // after the last level), spacing h/2^lv; one Adam update per step
     for (int lv = 0; lv < nlev; ++lv) {
