@@ -345,8 +345,9 @@ def table1(dev, epochs, resolutions, lr=1e-3):
 def secondary(dev, hbm_peak, peak_src):
     """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
     flower-interface 3->128x4->1 architecture), the mixed training step of the C3
-    and C4 workloads, and the FP64 grid CG solve of the same discretization at
-    128^3 and 256^3 (the plain method the NBM lifts off its grid)."""
+    and C4 workloads, and the grid solve of the same discretization at 128^3 and
+    256^3 (the plain method the NBM lifts off its grid): FP64 CG, and the
+    refined solve with FP32 inner corrections to the same FP64 residual test."""
     import torch
 
     import paper_2210_14907_gb300 as nbm
@@ -410,6 +411,20 @@ def secondary(dev, hbm_peak, peak_src):
                                "hbm_frac": gbs / hbm_peak, "hbm_peak": f"{hbm_peak} GB/s {peak_src} copy",
                                "linf_exact": linf, "rmse_exact": rmse}
         del ucg
+        torch.cuda.empty_cache()
+        # the same system to the same FP64 residual test by FP32 inner corrections
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uref, it, rr, ok = pcg.grid_solve_refined(n, rtol=1e-10, max_iter=100000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        gbs = it * 68 * m / wall / 1e9  # FP32 inner iteration: SpMV 24 + update 28 + direction 16 B
+        linf, rmse = node_errors(uref.cpu().numpy(), n)
+        out[f"grid_refined_{n}"] = {"unknowns": m, "inner_iterations": it, "relres": rr,
+                                    "converged": ok, "wall_s": wall, "achieved_gbs": gbs,
+                                    "hbm_frac": gbs / hbm_peak, "linf_exact": linf,
+                                    "rmse_exact": rmse}
+        del uref
         torch.cuda.empty_cache()
     return out
 

@@ -217,6 +217,24 @@ int nbm_eval_points(nbm_problem* p, const float* params, const float* pts, int64
 int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
                       int* iters_out, double* relres_out, nbm_stream_t stream);
 
+/* The same grid system as nbm_grid_cg_solve (Sec. 1, Sec. 3), solved to the
+ * same FP64 stopping test ||b - A x|| <= rtol ||b|| by mixed-precision
+ * iterative refinement: the rows, the solution x and every residual
+ * b - A x are FP64; each correction e of A e = r is a Jacobi-preconditioned
+ * CG solve in FP32 (operator rounded to FP32) of the normalised residual
+ * r / ||r||, stopped at relative residual 1e-5 or where the outer target needs
+ * no more, and x += ||r|| e in FP64.  The FP32 iterations move half the bytes
+ * of FP64 ones and avoid GB300's narrow FP64 pipe.
+ *   Arguments and u_out as nbm_grid_cg_solve; iters_out = FP32 inner
+ *   iterations over all corrections (max_iter bounds that total); relres_out =
+ *   the final FP64 ||b - A x|| / ||b||.
+ *   Returns NBM_ERR_NOT_CONVERGED (u_out filled) at max_iter, or when three
+ *   corrections in a row reduce ||b - A x|| by less than 10 % (an operator too
+ *   ill-conditioned for FP32 corrections: use nbm_grid_cg_solve).
+ * Synchronizes the stream. */
+int nbm_grid_solve_refined(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
+                           int* iters_out, double* relres_out, nbm_stream_t stream);
+
 /* Optional timing of the fused stencil-step kernel (the dominant kernel of a
  * training step).  enable = 1 clears the counters and brackets every later
  * launch of that kernel with CUDA events on its own stream; enable = 0 stops

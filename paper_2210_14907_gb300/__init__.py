@@ -171,8 +171,10 @@ def load_library(build_if_missing: bool = True):
     L.nbm_eval_points.restype = C.c_int
     L.nbm_grid_cg_solve.argtypes = [P, C.c_int, C.c_double, C.c_int, P, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double), P]
+    L.nbm_grid_solve_refined.argtypes = L.nbm_grid_cg_solve.argtypes
     for fn in ("nbm_init_problem", "nbm_destroy", "nbm_sample_points", "nbm_residual",
                "nbm_loss_grad", "nbm_train_steps", "nbm_eval_grid", "nbm_grid_cg_solve",
+               "nbm_grid_solve_refined",
                "nbm_set_level_set", "nbm_selftest_bounded_wait"):
         getattr(L, fn).restype = C.c_int
     _lib = L
@@ -301,6 +303,19 @@ class Problem:
         rr = C.c_double(0.0)
         rc = self.lib.nbm_grid_cg_solve(self.handle, n, rtol, max_iter, _ptr(out), C.byref(it),
                                         C.byref(rr), _stream(stream))
+        if rc not in (0, 3):
+            _check(rc)
+        return out, it.value, rr.value, rc == 0
+
+    def grid_solve_refined(self, n, rtol=1e-10, max_iter=20000, out=None, stream=None):
+        """The grid system of grid_cg_solve to the same FP64 residual test, by
+        FP32 inner PCG corrections of FP64 residuals (iterative refinement)."""
+        if out is None:
+            out = torch.empty((n + 1) ** 3, device="cuda", dtype=torch.float64)
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        rc = self.lib.nbm_grid_solve_refined(self.handle, n, rtol, max_iter, _ptr(out),
+                                             C.byref(it), C.byref(rr), _stream(stream))
         if rc not in (0, 3):
             _check(rc)
         return out, it.value, rr.value, rc == 0

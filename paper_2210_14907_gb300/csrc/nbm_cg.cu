@@ -103,46 +103,76 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* dia
   rhs[r] = -known;
 }
 
-// y = A v on the interior nodes; block partial of v . y.  Launched on a 3-D
-// grid (x: runs of 256 nodes of one row, y: row j, z: plane k), so node
-// indices need no integer division.
-__global__ void __launch_bounds__(kB) k_spmv_dot(Grid G, const double* __restrict__ diag,
-                                                 const double* __restrict__ wx,
-                                                 const double* __restrict__ wy,
-                                                 const double* __restrict__ wz,
-                                                 const double* __restrict__ v, double* y,
-                                                 double* part) {
-  __shared__ double red[kB / 32];
-  const int i = blockIdx.x * kB + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-  const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
-  double d = 0.0;
-  if (i < G.m1) {
-    const int64_t r = i + s1 * j + s2 * k;
-    const double vr = v[r];
-    double acc = diag[r] * vr;
-    if (i + 1 < G.m1) acc -= wx[r] * v[r + 1];
-    if (i > 0) acc -= wx[r - 1] * v[r - 1];
-    if (j + 1 < G.m1) acc -= wy[r] * v[r + s1];
-    if (j > 0) acc -= wy[r - s1] * v[r - s1];
-    if (k + 1 < G.m1) acc -= wz[r] * v[r + s2];
-    if (k > 0) acc -= wz[r - s2] * v[r - s2];
-    y[r] = acc;
-    d = vr * acc;
-  }
+// Block partial sums: each thread's NV values are summed over the warp in T
+// (FP32 or FP64), then over the block's warps in FP64 by thread 0, which
+// writes part[v * stride + idx].
+template <typename T, int NV>
+__device__ inline void block_partials(T (&v)[NV], double* part, int64_t idx, int64_t stride) {
+  __shared__ double red[NV][kB / 32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q][threadIdx.x >> 5] = (double)v[q];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kB / 32; ++w) s += red[w];
-    part[blockIdx.x + gridDim.x * ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = s;
-  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < kB / 32; ++w) s += red[q][w];
+      part[q * stride + idx] = s;
+    }
 }
 
-// scalars[]: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 rr, 5 beta
-__global__ void k_reduce_parts(const double* __restrict__ part, int nparts, int nvec,
-                               double* out) {
+// y = A v on the interior nodes; block partial of v . y.  Grid: x = runs of
+// 256 nodes of one row, y = row j, z = a slab of kz planes.  Each thread walks
+// its (i, j) column through the slab, keeping the z neighbours in registers,
+// so node indices need no integer division and each thread reduces once.
+template <typename T>
+__global__ void __launch_bounds__(kB) k_spmv_dot(Grid G, int kz, const T* __restrict__ diag,
+                                                 const T* __restrict__ wx,
+                                                 const T* __restrict__ wy,
+                                                 const T* __restrict__ wz,
+                                                 const T* __restrict__ v, T* y,
+                                                 double* part) {
+  const int i = blockIdx.x * kB + threadIdx.x, j = blockIdx.y;
+  const int k0 = blockIdx.z * kz, k1 = min(k0 + kz, G.m1);
+  const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
+  T d[1] = {T(0)};
+  if (i < G.m1) {
+    int64_t r = i + s1 * j + s2 * k0;
+    T vm = k0 > 0 ? v[r - s2] : T(0), wzm = k0 > 0 ? wz[r - s2] : T(0);
+    T vc = v[r];
+    for (int k = k0; k < k1; ++k, r += s2) {
+      const T vp = k + 1 < G.m1 ? v[r + s2] : T(0);
+      const T wzc = wz[r];  // zero on the last interior plane
+      T acc = diag[r] * vc;
+      if (i + 1 < G.m1) acc -= wx[r] * v[r + 1];
+      if (i > 0) acc -= wx[r - 1] * v[r - 1];
+      if (j + 1 < G.m1) acc -= wy[r] * v[r + s1];
+      if (j > 0) acc -= wy[r - s1] * v[r - s1];
+      acc -= wzc * vp;
+      acc -= wzm * vm;
+      y[r] = acc;
+      d[0] += vc * acc;
+      vm = vc;
+      vc = vp;
+      wzm = wzc;
+    }
+  }
+  block_partials<T, 1>(d, part, blockIdx.x + gridDim.x * ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z), 0);
+}
+
+// scalars[]: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 rr, 5 beta (the CG recurrence)
+// and, for the refined solve, 6 ||r||, 7 1/||r||, 8 r.r of the FP64 residual.
+// After the sum, POST_ALPHA sets alpha = rz / pAp and POST_BETA sets
+// beta = rz_new / rz, rz = rz_new.
+enum { POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_NORM = 3 };
+template <int POST>
+__global__ void k_reduce_parts(const double* __restrict__ part, int nparts, int nvec, double* sc,
+                               int slot) {
   __shared__ double red[2][256];
   double s0 = 0.0, s1 = 0.0;
   for (int b = threadIdx.x; b < nparts; b += 256) {
@@ -160,64 +190,109 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nparts, int 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = red[0][0];
-    if (nvec > 1) out[1] = red[1][0];
-  }
-}
-
-__global__ void k_alpha(double* sc) { sc[2] = sc[0] / sc[1]; }
-
-__global__ void k_beta(double* sc) {
-  sc[5] = sc[3] / sc[0];
-  sc[0] = sc[3];
-}
-
-// x += alpha p; r -= alpha Ap; partials of r.z and r.r (z = r / diag)
-__global__ void __launch_bounds__(kB) k_update(Grid G, const double* __restrict__ sc,
-                                               const double* __restrict__ inv_diag,
-                                               const double* __restrict__ p,
-                                               const double* __restrict__ Ap, double* x, double* r,
-                                               double* part, int nparts) {
-  __shared__ double red[2][kB / 32];
-  const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
-  if (i < G.m) {
-    const double a = sc[2];
-    x[i] += a * p[i];
-    const double ri = r[i] - a * Ap[i];
-    r[i] = ri;
-    rz = ri * ri * inv_diag[i];
-    rr = ri * ri;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    rz += __shfl_xor_sync(0xffffffffu, rz, o);
-    rr += __shfl_xor_sync(0xffffffffu, rr, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = rz;
-    red[1][threadIdx.x >> 5] = rr;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int w = 0; w < kB / 32; ++w) {
-      s0 += red[0][w];
-      s1 += red[1][w];
+    sc[slot] = red[0][0];
+    if (nvec > 1) sc[slot + 1] = red[1][0];
+    if (POST == POST_ALPHA) sc[2] = sc[0] / sc[1];
+    if (POST == POST_BETA) {
+      sc[5] = sc[3] / sc[0];
+      sc[0] = sc[3];
     }
-    part[blockIdx.x] = s0;
-    part[nparts + blockIdx.x] = s1;
+    if (POST == POST_NORM) {  // outer residual norm of the refined solve
+      sc[6] = sqrt(sc[8]);
+      sc[7] = 1.0 / sc[6];
+    }
   }
+}
+
+// x += alpha p; r -= alpha Ap; partials of r.z and r.r (z = r / diag).  The
+// scalars stay FP64 and each thread strides over the nodes, reducing once.
+template <typename T>
+__global__ void __launch_bounds__(kB) k_update(Grid G, const double* __restrict__ sc,
+                                               const T* __restrict__ inv_diag,
+                                               const T* __restrict__ p,
+                                               const T* __restrict__ Ap, T* x, T* r,
+                                               double* part) {
+  T acc[2] = {T(0), T(0)};
+  const T a = (T)sc[2];
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * Ap[i];
+    r[i] = ri;
+    acc[0] += ri * ri * inv_diag[i];
+    acc[1] += ri * ri;
+  }
+  block_partials<T, 2>(acc, part, blockIdx.x, gridDim.x);
 }
 
 // p = r / diag + beta p   (beta = 0: p = z for the first direction)
+template <typename T>
 __global__ void __launch_bounds__(kB) k_pupdate(Grid G, const double* __restrict__ sc, int first,
-                                                const double* __restrict__ inv_diag,
-                                                const double* __restrict__ r, double* p) {
-  const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
-  if (i >= G.m) return;
-  const double z = r[i] * inv_diag[i];
-  p[i] = first ? z : z + sc[5] * p[i];
+                                                const T* __restrict__ inv_diag,
+                                                const T* __restrict__ r, T* p) {
+  const T beta = first ? T(0) : (T)sc[5];
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
+    const T z = r[i] * inv_diag[i];
+    p[i] = first ? z : z + beta * p[i];
+  }
+}
+
+// ---- refined solve: FP64 residuals, FP32 inner PCG ----
+
+// FP32 copies of the FP64 operator and preconditioner
+__global__ void __launch_bounds__(kB) k_to_f32(Grid G, const double* __restrict__ diag,
+                                               const double* __restrict__ wx,
+                                               const double* __restrict__ wy,
+                                               const double* __restrict__ wz,
+                                               const double* __restrict__ idg, float* d32,
+                                               float* wx32, float* wy32, float* wz32,
+                                               float* idg32) {
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
+    d32[i] = (float)diag[i];
+    wx32[i] = (float)wx[i];
+    wy32[i] = (float)wy[i];
+    wz32[i] = (float)wz[i];
+    idg32[i] = (float)idg[i];
+  }
+}
+
+// r = b - r (r holds A x on entry); partial of r.r
+__global__ void __launch_bounds__(kB) k_defect(Grid G, const double* __restrict__ b, double* r,
+                                               double* part) {
+  double acc[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
+    const double ri = b[i] - r[i];
+    r[i] = ri;
+    acc[0] += ri * ri;
+  }
+  block_partials<double, 1>(acc, part, blockIdx.x, gridDim.x);
+}
+
+// start of an inner solve of A e = r / ||r||: e = 0, r32 = r / ||r||,
+// p = r32 / diag; partials of r32.p and r32.r32
+__global__ void __launch_bounds__(kB) k_inner_init(Grid G, const double* __restrict__ sc,
+                                                   const double* __restrict__ r64,
+                                                   const float* __restrict__ idg32, float* r32,
+                                                   float* e32, float* p32, double* part) {
+  float acc[2] = {0.f, 0.f};
+  const double inv = sc[7];
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
+    const float ri = (float)(r64[i] * inv);
+    const float z = ri * idg32[i];
+    r32[i] = ri;
+    e32[i] = 0.f;
+    p32[i] = z;
+    acc[0] += ri * z;
+    acc[1] += ri * ri;
+  }
+  block_partials<float, 2>(acc, part, blockIdx.x, gridDim.x);
+}
+
+// x += ||r|| e   (FP64)
+__global__ void __launch_bounds__(kB) k_correct(Grid G, const double* __restrict__ sc,
+                                                const float* __restrict__ e32, double* x) {
+  const double s = sc[6];
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB)
+    x[i] += s * (double)e32[i];
 }
 
 __global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const double* __restrict__ x,
@@ -238,8 +313,23 @@ __global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const dou
 
 using namespace nbm;
 
-extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
-                                 int* iters_out, double* relres_out, nbm_stream_t stream) {
+namespace nbm {
+namespace {
+
+// problem, grid and launch shapes shared by the two solvers
+struct CgSetup {
+  ProbDev P;
+  Grid G;
+  int nb;      // one-node-per-thread blocks (row assembly)
+  int nu;      // blocks of the strided vector kernels
+  int kz;      // planes per thread in the SpMV
+  dim3 sgrid;  // SpMV grid
+  int nsp;     // SpMV partials
+  int64_t nodes;
+};
+
+int cg_setup(nbm_problem* p, int n, double rtol, int max_iter, const double* u_out, const char* who,
+             CgSetup& S) {
   char msg[256];
   if (!p || !u_out) {
     set_error_message("NULL argument");
@@ -247,100 +337,216 @@ extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_ite
   }
   if (int rc = check_aligned(u_out, 8, "u_out")) return rc;
   if (n < 2 || n > 2048 || !(rtol > 0.0) || max_iter < 0) {
-    snprintf(msg, sizeof(msg), "grid CG needs 2 <= n <= 2048, rtol > 0, max_iter >= 0 (n=%d)", n);
+    snprintf(msg, sizeof(msg), "%s needs 2 <= n <= 2048, rtol > 0, max_iter >= 0 (n=%d)", who, n);
     set_error_message(msg);
     return NBM_ERR_INVALID_ARG;
   }
   nbm_problem_desc d = problem_desc(p);
   d.h = 2.0 / n;
-  ProbDev P;
-  make_prob_dev(d, P);
-  if (int rc = attach_level_set(p, P)) return rc;
-  Grid G;
+  make_prob_dev(d, S.P);
+  if (int rc = attach_level_set(p, S.P)) return rc;
+  Grid& G = S.G;
   G.n = n;
   G.m1 = n - 1;
   G.m = (int64_t)G.m1 * G.m1 * G.m1;
   G.h = 2.0 / n;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int nb = (int)((G.m + kB - 1) / kB);
-  const int64_t nodes = (int64_t)(n + 1) * (n + 1) * (n + 1);
-  double *diag = nullptr, *wx = nullptr, *wy = nullptr, *wz = nullptr, *r = nullptr, *x = nullptr,
-         *pv = nullptr, *Ap = nullptr, *idg = nullptr, *part = nullptr, *sc = nullptr;
-  double** bufs[] = {&diag, &wx, &wy, &wz, &r, &x, &pv, &Ap, &idg};
-  const dim3 sgrid((unsigned)((G.m1 + kB - 1) / kB), (unsigned)G.m1, (unsigned)G.m1);
-  const int nsp = (int)(sgrid.x * sgrid.y * sgrid.z);  // SpMV partials
-  cudaError_t e = cudaSuccess;
-  for (double** b : bufs)
-    if (e == cudaSuccess) e = cudaMalloc((void**)b, sizeof(double) * (size_t)(G.m > 0 ? G.m : 1));
-  if (e == cudaSuccess)
-    e = cudaMalloc((void**)&part, sizeof(double) * 2 * (size_t)(nb > nsp ? nb : nsp));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&sc, sizeof(double) * 8);
-  auto cleanup = [&]() {
-    for (double** b : bufs)
-      if (*b) cudaFree(*b);
-    if (part) cudaFree(part);
-    if (sc) cudaFree(sc);
-  };
-  auto cuda_fail = [&](cudaError_t err) {
-    snprintf(msg, sizeof(msg), "grid CG: %s", cudaGetErrorString(err));
-    set_error_message(msg);
-    cleanup();
-    return err == cudaErrorMemoryAllocation ? (int)NBM_ERR_OOM : (int)NBM_ERR_CUDA;
-  };
-  if (e != cudaSuccess) return cuda_fail(e);
+  S.nb = (int)((G.m + kB - 1) / kB);
+  const int resident = 8 * problem_num_sms(p);  // 2048 threads per SM
+  S.nu = S.nb < resident ? S.nb : resident;
+  const int gx = (G.m1 + kB - 1) / kB;
+  const int64_t cols = (int64_t)gx * G.m1;  // (run, row) pairs
+  int64_t kz = cols * G.m1 / resident;       // keep >= `resident` SpMV blocks
+  S.kz = (int)(kz < 1 ? 1 : kz > 16 ? 16 : kz);
+  S.sgrid = dim3((unsigned)gx, (unsigned)G.m1, (unsigned)((G.m1 + S.kz - 1) / S.kz));
+  S.nsp = (int)(S.sgrid.x * S.sgrid.y * S.sgrid.z);
+  S.nodes = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  return NBM_OK;
+}
 
-  k_grid_rows<<<nb, kB, 0, st>>>(P, G, diag, wx, wy, wz, r, idg);
-  cudaMemsetAsync(x, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(sc, 0, sizeof(double) * 8, st);
-  // r = b: rz = r.(r/diag), rr = r.r (an update with alpha = 0)
-  k_update<<<nb, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part, nb);
-  k_reduce_parts<<<1, 256, 0, st>>>(part, nb, 2, sc + 3);
-  k_beta<<<1, 1, 0, st>>>(sc);
-  k_pupdate<<<nb, kB, 0, st>>>(G, sc, 1, idg, r, pv);
-  double host_sc[8];
-  e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e);
-  const double bnorm = sqrt(host_sc[4]);
-  int it = 0;
-  double rnorm = bnorm;
-  bool converged = bnorm == 0.0;
-  while (!converged && it < max_iter) {
-    k_spmv_dot<<<sgrid, kB, 0, st>>>(G, diag, wx, wy, wz, pv, Ap, part);
-    k_reduce_parts<<<1, 256, 0, st>>>(part, nsp, 1, sc + 1);
-    k_alpha<<<1, 1, 0, st>>>(sc);
-    k_update<<<nb, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part, nb);
-    k_reduce_parts<<<1, 256, 0, st>>>(part, nb, 2, sc + 3);
-    k_beta<<<1, 1, 0, st>>>(sc);
-    k_pupdate<<<nb, kB, 0, st>>>(G, sc, 0, idg, r, pv);
-    ++it;
-    if (it % 10 == 0 || it == max_iter) {
-      e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return cuda_fail(e);
-      rnorm = sqrt(host_sc[4]);
-      if (!(rnorm == rnorm)) break;  // NaN: stop, report below
-      converged = rnorm <= rtol * bnorm;
-    }
+// device buffers of one solve, freed together
+struct CgBuffers {
+  void* ptr[24] = {};
+  int n = 0;
+  cudaError_t err = cudaSuccess;
+  template <typename T>
+  T* get(size_t count) {
+    void* q = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1));
+    if (err == cudaSuccess) ptr[n++] = q;
+    return (T*)q;
   }
-  k_write_nodes<<<(int)((nodes + kB - 1) / kB), kB, 0, st>>>(P, G, x, u_out);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e);
-  cleanup();
+  ~CgBuffers() {
+    for (int i = 0; i < n; ++i) cudaFree(ptr[i]);
+  }
+};
+
+int cg_cuda_fail(const char* who, cudaError_t err) {
+  char msg[256];
+  snprintf(msg, sizeof(msg), "%s: %s", who, cudaGetErrorString(err));
+  set_error_message(msg);
+  return err == cudaErrorMemoryAllocation ? (int)NBM_ERR_OOM : (int)NBM_ERR_CUDA;
+}
+
+int cg_report(const char* who, bool converged, int it, double rnorm, double bnorm, double rtol,
+              int* iters_out, double* relres_out) {
+  char msg[256];
   if (iters_out) *iters_out = it;
   if (relres_out) *relres_out = bnorm > 0.0 ? rnorm / bnorm : 0.0;
   if (!(rnorm == rnorm)) {
-    set_error_message("grid CG: residual is not finite");
+    snprintf(msg, sizeof(msg), "%s: residual is not finite", who);
+    set_error_message(msg);
     return NBM_ERR_NONFINITE;
   }
   if (!converged) {
-    snprintf(msg, sizeof(msg), "grid CG: %d iterations, relative residual %.3e > %.3e", it,
+    snprintf(msg, sizeof(msg), "%s: %d iterations, relative residual %.3e > %.3e", who, it,
              bnorm > 0 ? rnorm / bnorm : 0.0, rtol);
     set_error_message(msg);
     return NBM_ERR_NOT_CONVERGED;
   }
   return NBM_OK;
+}
+
+}  // namespace
+}  // namespace nbm
+
+using namespace nbm;
+
+extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
+                                 int* iters_out, double* relres_out, nbm_stream_t stream) {
+  const char* who = "grid CG";
+  CgSetup S;
+  if (int rc = cg_setup(p, n, rtol, max_iter, u_out, who, S)) return rc;
+  const Grid& G = S.G;
+  cudaStream_t st = (cudaStream_t)stream;
+  CgBuffers B;
+  double *diag = B.get<double>(G.m), *wx = B.get<double>(G.m), *wy = B.get<double>(G.m),
+         *wz = B.get<double>(G.m), *r = B.get<double>(G.m), *x = B.get<double>(G.m),
+         *pv = B.get<double>(G.m), *Ap = B.get<double>(G.m), *idg = B.get<double>(G.m);
+  double* part = B.get<double>(2 * (size_t)(S.nu > S.nsp ? S.nu : S.nsp));
+  double* sc = B.get<double>(16);
+  if (B.err != cudaSuccess) return cg_cuda_fail(who, B.err);
+
+  k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, G, diag, wx, wy, wz, r, idg);
+  cudaMemsetAsync(x, 0, sizeof(double) * G.m, st);
+  cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
+  cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
+  cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
+  // r = b: rz = r.(r/diag), rr = r.r (an update with alpha = 0)
+  k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part);
+  k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+  k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 1, idg, r, pv);
+  double host_sc[16];
+  cudaError_t e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cg_cuda_fail(who, e);
+  const double bnorm = sqrt(host_sc[4]);
+  int it = 0;
+  double rnorm = bnorm;
+  bool converged = bnorm == 0.0;
+  while (!converged && it < max_iter) {
+    k_spmv_dot<double><<<S.sgrid, kB, 0, st>>>(G, S.kz, diag, wx, wy, wz, pv, Ap, part);
+    k_reduce_parts<POST_ALPHA><<<1, 256, 0, st>>>(part, S.nsp, 1, sc, 1);
+    k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part);
+    k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+    k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 0, idg, r, pv);
+    ++it;
+    if (it % 10 == 0 || it == max_iter) {
+      e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cg_cuda_fail(who, e);
+      rnorm = sqrt(host_sc[4]);
+      if (!(rnorm == rnorm)) break;  // NaN: stop, report below
+      converged = rnorm <= rtol * bnorm;
+    }
+  }
+  k_write_nodes<<<(int)((S.nodes + kB - 1) / kB), kB, 0, st>>>(S.P, G, x, u_out);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cg_cuda_fail(who, e);
+  return cg_report(who, converged, it, rnorm, bnorm, rtol, iters_out, relres_out);
+}
+
+namespace nbm {
+namespace {
+constexpr double kInnerTol = 1e-5;  // relative residual target of one FP32 inner solve
+constexpr int kCheckEvery = 10;     // inner iterations between host convergence checks
+constexpr int kMaxStall = 3;        // outer steps in a row that gain less than 10 %
+}  // namespace
+}  // namespace nbm
+
+extern "C" int nbm_grid_solve_refined(nbm_problem* p, int n, double rtol, int max_iter,
+                                      double* u_out, int* iters_out, double* relres_out,
+                                      nbm_stream_t stream) {
+  const char* who = "refined grid solve";
+  CgSetup S;
+  if (int rc = cg_setup(p, n, rtol, max_iter, u_out, who, S)) return rc;
+  const Grid& G = S.G;
+  cudaStream_t st = (cudaStream_t)stream;
+  CgBuffers B;
+  double *diag = B.get<double>(G.m), *wx = B.get<double>(G.m), *wy = B.get<double>(G.m),
+         *wz = B.get<double>(G.m), *b = B.get<double>(G.m), *x = B.get<double>(G.m),
+         *r64 = B.get<double>(G.m), *idg = B.get<double>(G.m);
+  float *d32 = B.get<float>(G.m), *wx32 = B.get<float>(G.m), *wy32 = B.get<float>(G.m),
+        *wz32 = B.get<float>(G.m), *idg32 = B.get<float>(G.m), *r32 = B.get<float>(G.m),
+        *e32 = B.get<float>(G.m), *p32 = B.get<float>(G.m), *Ap32 = B.get<float>(G.m);
+  double* part = B.get<double>(2 * (size_t)(S.nu > S.nsp ? S.nu : S.nsp));
+  double* sc = B.get<double>(16);
+  if (B.err != cudaSuccess) return cg_cuda_fail(who, B.err);
+
+  k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, G, diag, wx, wy, wz, b, idg);
+  k_to_f32<<<S.nu, kB, 0, st>>>(G, diag, wx, wy, wz, idg, d32, wx32, wy32, wz32, idg32);
+  cudaMemsetAsync(x, 0, sizeof(double) * G.m, st);
+  cudaMemsetAsync(r64, 0, sizeof(double) * G.m, st);
+  cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
+  // residual of x = 0
+  k_defect<<<S.nu, kB, 0, st>>>(G, b, r64, part);
+  k_reduce_parts<POST_NORM><<<1, 256, 0, st>>>(part, S.nu, 1, sc, 8);
+  double host_sc[16];
+  auto read_sc = [&]() {
+    cudaError_t err = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    return err;
+  };
+  cudaError_t e = read_sc();
+  if (e != cudaSuccess) return cg_cuda_fail(who, e);
+  const double bnorm = sqrt(host_sc[8]);
+  double rnorm = bnorm;
+  int it = 0, stall = 0;
+  bool converged = bnorm == 0.0;
+  while (!converged && it < max_iter && rnorm == rnorm && stall < kMaxStall) {
+    // inner FP32 PCG on A e = r / ||r|| (so its initial residual norm is 1),
+    // stopped at kInnerTol or where the outer target needs no more
+    double tau = 0.5 * rtol * bnorm / rnorm;
+    tau = tau < kInnerTol ? kInnerTol : tau > 0.5 ? 0.5 : tau;
+    k_inner_init<<<S.nu, kB, 0, st>>>(G, sc, r64, idg32, r32, e32, p32, part);
+    k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+    for (int inner = 1; it < max_iter; ++inner) {
+      k_spmv_dot<float><<<S.sgrid, kB, 0, st>>>(G, S.kz, d32, wx32, wy32, wz32, p32, Ap32, part);
+      k_reduce_parts<POST_ALPHA><<<1, 256, 0, st>>>(part, S.nsp, 1, sc, 1);
+      k_update<float><<<S.nu, kB, 0, st>>>(G, sc, idg32, p32, Ap32, e32, r32, part);
+      k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+      k_pupdate<float><<<S.nu, kB, 0, st>>>(G, sc, 0, idg32, r32, p32);
+      ++it;
+      if (inner % kCheckEvery == 0 || it == max_iter) {
+        if ((e = read_sc()) != cudaSuccess) return cg_cuda_fail(who, e);
+        const double rin = sqrt(host_sc[4]);
+        if (!(rin == rin) || rin <= tau) break;
+      }
+    }
+    // x += ||r|| e in FP64, then the FP64 residual r = b - A x
+    k_correct<<<S.nu, kB, 0, st>>>(G, sc, e32, x);
+    k_spmv_dot<double><<<S.sgrid, kB, 0, st>>>(G, S.kz, diag, wx, wy, wz, x, r64, part);
+    k_defect<<<S.nu, kB, 0, st>>>(G, b, r64, part);
+    k_reduce_parts<POST_NORM><<<1, 256, 0, st>>>(part, S.nu, 1, sc, 8);
+    if ((e = read_sc()) != cudaSuccess) return cg_cuda_fail(who, e);
+    const double rnew = sqrt(host_sc[8]);
+    stall = rnew > 0.9 * rnorm ? stall + 1 : 0;
+    rnorm = rnew;
+    converged = rnorm <= rtol * bnorm;
+  }
+  k_write_nodes<<<(int)((S.nodes + kB - 1) / kB), kB, 0, st>>>(S.P, G, x, u_out);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cg_cuda_fail(who, e);
+  return cg_report(who, converged, it, rnorm, bnorm, rtol, iters_out, relres_out);
 }

@@ -106,3 +106,61 @@ def test_grid_cg_reports_non_convergence():
     with pytest.raises(nbm.NBMError) as e:
         prob.grid_cg_solve(1, rtol=1e-10)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("geom,mu_p,n", [(O.GEOM_SPHERE, 10.0, 16), (O.GEOM_FLOWER, 100.0, 14),
+                                         (O.GEOM_FLOWER, 1000.0, 22), (O.GEOM_ALL_MINUS, 10.0, 9)])
+def test_refined_solve_matches_oracle(geom, mu_p, n):
+    """FP32 inner corrections of FP64 residuals reach the oracle's FP64 CG
+    solution of the same rows (the stopping test is the true FP64 residual)."""
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=geom, mu_minus=1.0, mu_plus=mu_p, k_minus=0.5)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=geom, mu_minus=1.0, mu_plus=mu_p, k_minus=0.5)
+    if geom == O.GEOM_FLOWER:
+        assert _clear_of_interface(o, n)
+    st, ref, it_ref, rr_ref = O.grid_cg_solve(o, n, rtol=1e-13, max_iter=50000)
+    assert st == 0
+    u, it, rr, ok = prob.grid_solve_refined(n, rtol=1e-12, max_iter=50000)
+    assert ok and rr <= 1e-12
+    u = u.cpu().numpy()
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    print(f"refined geom {geom} mu+ {mu_p} n {n}: {it} inner iterations (FP64 CG {it_ref}), "
+          f"max err {err:.2e}")
+    assert err <= 1e-8
+
+
+@pytest.mark.parametrize("n", [42, 97])
+def test_refined_solve_agrees_with_fp64_cg(n):
+    """Beyond the oracle's sizes: the refined and the FP64 CG solutions of the
+    same system agree to the accuracy their residual tests allow, and the
+    refined solve needs at most twice the FP64 iterations."""
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_FLOWER, mu_minus=1.0, mu_plus=10.0)
+    prob = nbm.Problem(d)
+    a, it_a, rr_a, ok_a = prob.grid_cg_solve(n, rtol=1e-12, max_iter=100000)
+    b, it_b, rr_b, ok_b = prob.grid_solve_refined(n, rtol=1e-12, max_iter=100000)
+    assert ok_a and ok_b and rr_b <= 1e-12
+    err = (torch.max(torch.abs(a - b)) / torch.max(torch.abs(a))).item()
+    print(f"n {n}: FP64 CG {it_a} it, refined {it_b} inner it, max diff {err:.2e}")
+    assert err <= 1e-9
+    assert it_b <= 2 * it_a
+    if n == 42:  # small enough for the oracle's CG
+        o = O.make_problem(geometry=O.GEOM_FLOWER, mu_minus=1.0, mu_plus=10.0)
+        st, ref, _, _ = O.grid_cg_solve(o, n, rtol=1e-13, max_iter=50000)
+        assert st == 0
+        assert np.max(np.abs(b.cpu().numpy() - ref)) <= 1e-8 * np.max(np.abs(ref))
+
+
+def test_refined_solve_reports_non_convergence_and_bad_arguments():
+    nbm = _nbm()
+    prob = nbm.Problem(nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE))
+    u, it, rr, ok = prob.grid_solve_refined(32, rtol=1e-12, max_iter=3)
+    assert not ok and it == 3 and 0 < rr < 1.0
+    assert torch.isfinite(u).all()
+    with pytest.raises(nbm.NBMError) as e:
+        prob.grid_solve_refined(1, rtol=1e-10)
+    assert e.value.code == 1
+    with pytest.raises(nbm.NBMError) as e:
+        prob.grid_solve_refined(8, rtol=0.0)
+    assert e.value.code == 1
