@@ -860,16 +860,19 @@ void nbo_eval_grid(const nbo_problem* pr, const double* theta, int n, double* u_
 
 /* Grid rows: the same balance row B_p at every interior node, with one
  * unknown u_q per node.  A net-s value at a node of the other phase is
- * u_q +- J(q) (reading: J(q) = u+(q) - u-(q) of the manufactured pair,
- * the "exact jump" extension), which moves every jump term to the RHS and
- * leaves A symmetric: A_pp = D_p, A_pq = -w_f, w_f = sum_s A^s_f mu^s. */
+ * u_q +- J(q), J(q) the value jump u+ - u- carried to the node: with Jn ==
+ * NULL the manufactured pair's own u+(q) - u-(q) (the "exact jump"
+ * extension), else Jn[node] (the extrapolated jump below).  Every jump term
+ * moves to the RHS and A stays symmetric: A_pp = D_p, A_pq = -w_f,
+ * w_f = sum_s A^s_f mu^s. */
 typedef struct {
   double diag;
   double w[6];
   double rhs;
 } grid_row;
 
-static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, grid_row* row) {
+static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, const double* Jn,
+                           grid_row* row) {
   double hg = pg->h;
   int idx[3] = {i, j, k};
   double p[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};
@@ -879,7 +882,7 @@ static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, gr
   /* c^s(q): correction so that U^s(q) = u_q + c^s(q) */
   double cp[2] = {0, 0};
   {
-    double jmp = nbo_alpha(pg, p);
+    double jmp = Jn ? Jn[node_id(n, i, j, k)] : nbo_alpha(pg, p);
     if (sp == 1) cp[0] = -jmp; else cp[1] = jmp;
   }
   row->diag = 0.0;
@@ -900,7 +903,7 @@ static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, gr
     double cq[2] = {0, 0};
     if (!bnd) {
       /* boundary neighbours carry g(q) for both networks, as in B_p */
-      double jq = nbo_alpha(pg, q);
+      double jq = Jn ? Jn[node_id(n, nb[0], nb[1], nb[2])] : nbo_alpha(pg, q);
       if (sq == 1) cq[0] = -jq; else cq[1] = jq;
     }
     double fc[3] = {p[0], p[1], p[2]};  /* face centre, shared with the neighbour's row */
@@ -935,7 +938,7 @@ int nbo_grid_assemble_dense(const nbo_problem* pr, int n, double* A, double* b) 
     for (int j = 1; j < n; ++j)
       for (int i = 1; i < n; ++i) {
         grid_row row;
-        grid_row_build(&pg, n, i, j, k, &row);
+        grid_row_build(&pg, n, i, j, k, NULL, &row);
         int64_t r = (i - 1) + (int64_t)m1 * ((j - 1) + (int64_t)m1 * (k - 1));
         A[r * m + r] = row.diag;
         b[r] = row.rhs;
@@ -951,43 +954,36 @@ int nbo_grid_assemble_dense(const nbo_problem* pr, int n, double* A, double* b) 
   return 0;
 }
 
-/* Jacobi-preconditioned conjugate gradients on the interior nodes;
- * stops at ||r|| <= rtol ||b||.  Returns 0 on convergence, 1 otherwise. */
-int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter, double* u_out,
-                      int* iters_out, double* relres_out, int n_threads) {
-  nbo_problem pg = *pr;
-  pg.h = 2.0 / n;
-  int nt = pick_threads(n_threads);
-  int m1 = n - 1;
+/* Jacobi-preconditioned conjugate gradients on the interior nodes from the
+ * start vector x (warm start); stops at ||b - A x|| <= rtol ||b|| with the
+ * recursively updated residual.  Returns 0 on convergence, 1 otherwise. */
+static int grid_cg_core(const grid_row* rows, int m1, double* x, double rtol, int max_iter,
+                        int nt, int* iters_out, double* relres_out) {
   int64_t m = (int64_t)m1 * m1 * m1;
-  grid_row* rows = (grid_row*)malloc(sizeof(grid_row) * m);
-#pragma omp parallel for schedule(static) num_threads(nt)
-  for (int64_t r = 0; r < m; ++r) {
-    int i = 1 + (int)(r % m1), j = 1 + (int)((r / m1) % m1), k = 1 + (int)(r / ((int64_t)m1 * m1));
-    grid_row_build(&pg, n, i, j, k, &rows[r]);
-  }
-  double* x = (double*)calloc(m, sizeof(double));
+  int64_t strides[3] = {1, m1, (int64_t)m1 * m1};
   double* rr = (double*)malloc(sizeof(double) * m);
   double* z = (double*)malloc(sizeof(double) * m);
   double* pp = (double*)malloc(sizeof(double) * m);
   double* Ap = (double*)malloc(sizeof(double) * m);
-  int64_t strides[3] = {1, m1, (int64_t)m1 * m1};
   double bnorm2 = 0.0;
   for (int64_t r = 0; r < m; ++r) {
-    rr[r] = rows[r].rhs;
-    bnorm2 += rr[r] * rr[r];
+    double s = rows[r].diag * x[r];
+    for (int f = 0; f < 6; ++f)
+      if (rows[r].w[f] != 0.0) s -= rows[r].w[f] * x[r + ((f & 1) ? 1 : -1) * strides[f / 2]];
+    rr[r] = rows[r].rhs - s;
+    bnorm2 += rows[r].rhs * rows[r].rhs;
   }
   double bnorm = sqrt(bnorm2);
-  double rz = 0.0;
+  double rz = 0.0, rn2 = 0.0;
   for (int64_t r = 0; r < m; ++r) {
     z[r] = rr[r] / rows[r].diag;
     pp[r] = z[r];
     rz += rr[r] * z[r];
+    rn2 += rr[r] * rr[r];
   }
   int it = 0;
-  double rnorm = bnorm;
-  int status = 1;
-  if (bnorm == 0.0) status = 0;
+  double rnorm = sqrt(rn2);
+  int status = rnorm <= rtol * bnorm ? 0 : 1;
   while (status != 0 && it < max_iter) {
     double pAp = 0.0;
 #pragma omp parallel for schedule(static) reduction(+ : pAp) num_threads(nt)
@@ -999,7 +995,8 @@ int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter, d
       pAp += pp[r] * s;
     }
     double alpha = rz / pAp;
-    double rz_new = 0.0, rn2 = 0.0;
+    double rz_new = 0.0;
+    rn2 = 0.0;
 #pragma omp parallel for schedule(static) reduction(+ : rz_new, rn2) num_threads(nt)
     for (int64_t r = 0; r < m; ++r) {
       x[r] += alpha * pp[r];
@@ -1018,27 +1015,266 @@ int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter, d
     rz = rz_new;
     for (int64_t r = 0; r < m; ++r) pp[r] = z[r] + beta * pp[r];
   }
-  /* write the full node array: Dirichlet data on the boundary */
-  double hg = pg.h;
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = bnorm > 0 ? rnorm / bnorm : 0.0;
+  free(rr);
+  free(z);
+  free(pp);
+  free(Ap);
+  return status;
+}
+
+static void grid_rows_all(const nbo_problem* pg, int n, const double* Jn, grid_row* rows, int nt) {
+  int m1 = n - 1;
+  int64_t m = (int64_t)m1 * m1 * m1;
+#pragma omp parallel for schedule(static) num_threads(nt)
+  for (int64_t r = 0; r < m; ++r) {
+    int i = 1 + (int)(r % m1), j = 1 + (int)((r / m1) % m1), k = 1 + (int)(r / ((int64_t)m1 * m1));
+    grid_row_build(pg, n, i, j, k, Jn, &rows[r]);
+  }
+}
+
+/* the full node array: interior unknowns, Dirichlet data on the boundary */
+static void grid_write_nodes(const nbo_problem* pg, int n, const double* x, double* u_out) {
+  int m1 = n - 1;
+  double hg = 2.0 / n;
   for (int k = 0; k <= n; ++k)
     for (int j = 0; j <= n; ++j)
       for (int i = 0; i <= n; ++i) {
         int64_t id = node_id(n, i, j, k);
         if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) {
           double q[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};
-          u_out[id] = nbo_dirichlet_g(&pg, q);
+          u_out[id] = nbo_dirichlet_g(pg, q);
         } else {
           u_out[id] = x[(i - 1) + (int64_t)m1 * ((j - 1) + (int64_t)m1 * (k - 1))];
         }
       }
-  if (iters_out) *iters_out = it;
-  if (relres_out) *relres_out = bnorm > 0 ? rnorm / bnorm : 0.0;
+}
+
+int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter, double* u_out,
+                      int* iters_out, double* relres_out, int n_threads) {
+  nbo_problem pg = *pr;
+  pg.h = 2.0 / n;
+  int nt = pick_threads(n_threads);
+  int m1 = n - 1;
+  int64_t m = (int64_t)m1 * m1 * m1;
+  grid_row* rows = (grid_row*)malloc(sizeof(grid_row) * m);
+  grid_rows_all(&pg, n, NULL, rows, nt);
+  double* x = (double*)calloc(m, sizeof(double));
+  int status = grid_cg_core(rows, m1, x, rtol, max_iter, nt, iters_out, relres_out);
+  grid_write_nodes(&pg, n, x, u_out);
   free(rows);
   free(x);
-  free(rr);
-  free(z);
-  free(pp);
-  free(Ap);
+  return status;
+}
+
+/* ======================================================================
+ * Extrapolated value jump at the grid nodes (the grid scheme's reading of
+ * carrying u+ - u- off Gamma to a node of the other side).  For a node x:
+ *   x_G = x moved onto phi = 0 by three Newton steps along grad phi,
+ *   d   = phi(x) / |grad phi(x)|   (signed distance, > 0 in Omega+),
+ *   n   = grad phi(x_G) / |grad phi(x_G)|,
+ *   J(x) = alpha(x_G) + d G,   G = [d_n u] = d_n u+ - d_n u-  at x_G
+ * (Taylor in d: J(x) - (u+(x) - u-(x)) = O(d^2)).  The flux jump
+ * beta = mu+ d_n u+ - mu- d_n u- fixes G once the normal derivative of one
+ * side is known; the side with the smaller mu, s*, is lagged:
+ *   mu- <= mu+:  G = beta/mu+ - (1 - mu-/mu+) d_n u-
+ *   mu+ <  mu-:  G = beta/mu- + (1 - mu+/mu-) d_n u+
+ * (all coefficients at x_G).  Dropping the lag term gives G = beta/mu_big,
+ * which is first order in h.  Nodes with |d| > 3h, or where grad phi
+ * vanishes, get J = 0: no row weights them (a face or cell touches the
+ * other phase only within about h of Gamma).
+ * ==================================================================== */
+int nbo_jump_extrap(const nbo_problem* pr, const double x[3], double h, int use_lag,
+                    double dn_small, double* J, double xg[3], double nrm[3], int* small_side) {
+  double g[3];
+  double ph = nbo_phi(pr, x);
+  nbo_grad_phi(pr, x, g);
+  double gn = norm3(g);
+  *J = 0.0;
+  *small_side = 0;
+  for (int i = 0; i < 3; ++i) xg[i] = x[i], nrm[i] = 0.0;
+  if (!(gn > 1e-300) || fabs(ph / gn) > 3.0 * h) return 1;
+  double d = ph / gn;
+  for (int it = 0; it < 3; ++it) {
+    double gg[3];
+    double f = nbo_phi(pr, xg);
+    nbo_grad_phi(pr, xg, gg);
+    double q = gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2];
+    if (q <= 1e-300) break;
+    for (int i = 0; i < 3; ++i) xg[i] -= f * gg[i] / q;
+  }
+  double gx[3];
+  nbo_grad_phi(pr, xg, gx);
+  double gxn = norm3(gx);
+  if (!(gxn > 1e-300)) return 1;
+  for (int i = 0; i < 3; ++i) nrm[i] = gx[i] / gxn;
+  double mum = nbo_mu(pr, 0, xg), mup = nbo_mu(pr, 1, xg), beta = nbo_beta(pr, xg);
+  double G;
+  if (mum <= mup) {
+    *small_side = 0;
+    G = beta / mup - (use_lag ? (1.0 - mum / mup) * dn_small : 0.0);
+  } else {
+    *small_side = 1;
+    G = beta / mum + (use_lag ? (1.0 - mup / mum) * dn_small : 0.0);
+  }
+  *J = nbo_alpha(pr, xg) + d * G;
+  return 0;
+}
+
+/* Normal derivative of side s at x_G from the node values u (the full
+ * (n+1)^3 array of an iterate): least-squares fit of a linear function
+ * a + g.(q - x_G) to the interior nodes q of phase s in the 3x3x3 block
+ * around the node nearest x_G - h n (s = minus) or x_G + h n (s = plus),
+ * i.e. one spacing into side s, so that the block holds at least two layers
+ * of side-s nodes (normal equations, Cholesky), dn = g . nrm.
+ * Returns 1 (no value) with fewer than 4 such nodes or a degenerate fit. */
+int nbo_fit_dn(const nbo_problem* pr, int n, const double* u, int s, const double xg[3],
+               const double nrm[3], double* dn) {
+  double hg = 2.0 / n;
+  int c[3];
+  for (int i = 0; i < 3; ++i) {
+    double xc = xg[i] + (s == 0 ? -hg : hg) * nrm[i];
+    c[i] = (int)floor((xc + 1.0) / hg + 0.5);
+    if (c[i] < 2) c[i] = 2;
+    if (c[i] > n - 2) c[i] = n - 2;
+  }
+  double M[4][4] = {{0}}, rhs[4] = {0};
+  int cnt = 0;
+  for (int dk = -1; dk <= 1; ++dk)
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        int q[3] = {c[0] + di, c[1] + dj, c[2] + dk};
+        double xq[3] = {-1.0 + q[0] * hg, -1.0 + q[1] * hg, -1.0 + q[2] * hg};
+        if (nbo_phase(pr, xq) != s) continue;
+        double bv[4] = {1.0, (xq[0] - xg[0]) / hg, (xq[1] - xg[1]) / hg, (xq[2] - xg[2]) / hg};
+        double uq = u[node_id(n, q[0], q[1], q[2])];
+        for (int a = 0; a < 4; ++a) {
+          rhs[a] += bv[a] * uq;
+          for (int b = 0; b < 4; ++b) M[a][b] += bv[a] * bv[b];
+        }
+        ++cnt;
+      }
+  if (cnt < 4) return 1;
+  /* Cholesky M = L L^T (M is SPD when the nodes span an affine basis) */
+  double L[4][4] = {{0}};
+  for (int a = 0; a < 4; ++a) {
+    for (int b = 0; b <= a; ++b) {
+      double t = M[a][b];
+      for (int k = 0; k < b; ++k) t -= L[a][k] * L[b][k];
+      if (a == b) {
+        if (!(t > 1e-8 * M[0][0])) return 1;
+        L[a][a] = sqrt(t);
+      } else {
+        L[a][b] = t / L[b][b];
+      }
+    }
+  }
+  double y[4], cf[4];
+  for (int a = 0; a < 4; ++a) {
+    double t = rhs[a];
+    for (int k = 0; k < a; ++k) t -= L[a][k] * y[k];
+    y[a] = t / L[a][a];
+  }
+  for (int a = 3; a >= 0; --a) {
+    double t = y[a];
+    for (int k = a + 1; k < 4; ++k) t -= L[k][a] * cf[k];
+    cf[a] = t / L[a][a];
+  }
+  *dn = (cf[1] * nrm[0] + cf[2] * nrm[1] + cf[3] * nrm[2]) / hg;
+  return 0;
+}
+
+/* J at every node: lagged from the iterate u (u != NULL), or first order */
+static void grid_jumps(const nbo_problem* pg, int n, const double* u, double* Jn, int nt) {
+  int64_t N1 = n + 1, total = N1 * N1 * N1;
+  double hg = 2.0 / n;
+#pragma omp parallel for schedule(static) num_threads(nt)
+  for (int64_t id = 0; id < total; ++id) {
+    int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
+    Jn[id] = 0.0;
+    if (i == 0 || j == 0 || k == 0 || i == n || j == n || k == n) continue;
+    double x[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg}, xg[3], nrm[3], J, dn = 0.0;
+    int ss;
+    if (nbo_jump_extrap(pg, x, hg, 0, 0.0, &J, xg, nrm, &ss)) continue;
+    if (u && nbo_fit_dn(pg, n, u, ss, xg, nrm, &dn) == 0)
+      nbo_jump_extrap(pg, x, hg, 1, dn, &J, xg, nrm, &ss);
+    Jn[id] = J;
+  }
+}
+
+/* Grid solve with a choice of node jump (jump_mode): 0 exact (as
+ * nbo_grid_cg_solve), 2 extrapolated first order (one solve), 1 extrapolated
+ * with the lagged normal derivative: pass 1 is the first-order solve, each
+ * later pass refits the lag from the previous solution, rebuilds the RHS and
+ * re-solves from the previous solution, until
+ *   max |J_new - J| <= jtol max(1, max |J_new|)
+ * (converged, returns 0).  If max_passes go by without that, the solve falls
+ * back to the first-order jump (re-solved from the last solution) and
+ * returns 2.  Returns 1 if a CG solve does not converge.  passes_out counts
+ * the lagged passes (1 for modes 0 and 2), dj_out the last max |J_new - J|. */
+int nbo_grid_solve_jump(const nbo_problem* pr, int n, int jump_mode, double rtol, int max_iter,
+                        int max_passes, double jtol, double* u_out, int* iters_out,
+                        double* relres_out, int* passes_out, double* dj_out, int n_threads) {
+  nbo_problem pg = *pr;
+  pg.h = 2.0 / n;
+  int nt = pick_threads(n_threads);
+  int m1 = n - 1;
+  int64_t m = (int64_t)m1 * m1 * m1, total = (int64_t)(n + 1) * (n + 1) * (n + 1);
+  grid_row* rows = (grid_row*)malloc(sizeof(grid_row) * m);
+  double* x = (double*)calloc(m, sizeof(double));
+  double* Jn = NULL;
+  double* Jnew = NULL;
+  if (jump_mode != 0) {
+    Jn = (double*)malloc(sizeof(double) * total);
+    Jnew = (double*)malloc(sizeof(double) * total);
+    grid_jumps(&pg, n, NULL, Jn, nt);
+  }
+  grid_rows_all(&pg, n, Jn, rows, nt);
+  int it_total = 0, it = 0, passes = 1;
+  double rr = 0.0, dj = 0.0;
+  int status = grid_cg_core(rows, m1, x, rtol, max_iter, nt, &it, &rr);
+  it_total += it;
+  grid_write_nodes(&pg, n, x, u_out);
+  if (jump_mode == 1 && status == 0) {
+    int converged = 0;
+    while (passes < max_passes && !converged) {
+      grid_jumps(&pg, n, u_out, Jnew, nt);
+      double jmax = 0.0;
+      dj = 0.0;
+      for (int64_t id = 0; id < total; ++id) {
+        double e = fabs(Jnew[id] - Jn[id]);
+        if (e > dj) dj = e;
+        if (fabs(Jnew[id]) > jmax) jmax = fabs(Jnew[id]);
+      }
+      double* t = Jn;
+      Jn = Jnew;
+      Jnew = t;
+      grid_rows_all(&pg, n, Jn, rows, nt);
+      ++passes;
+      status = grid_cg_core(rows, m1, x, rtol, max_iter, nt, &it, &rr);
+      it_total += it;
+      grid_write_nodes(&pg, n, x, u_out);
+      if (status != 0) break;
+      converged = dj <= jtol * (jmax > 1.0 ? jmax : 1.0);
+    }
+    if (status == 0 && !converged) {  /* stalled: the first-order jump instead */
+      grid_jumps(&pg, n, NULL, Jn, nt);
+      grid_rows_all(&pg, n, Jn, rows, nt);
+      status = grid_cg_core(rows, m1, x, rtol, max_iter, nt, &it, &rr);
+      it_total += it;
+      grid_write_nodes(&pg, n, x, u_out);
+      status = status == 0 ? 2 : 1;
+    }
+  }
+  if (iters_out) *iters_out = it_total;
+  if (relres_out) *relres_out = rr;
+  if (passes_out) *passes_out = passes;
+  if (dj_out) *dj_out = dj;
+  free(rows);
+  free(x);
+  free(Jn);
+  free(Jnew);
   return status;
 }
 

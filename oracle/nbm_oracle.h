@@ -133,6 +133,19 @@ int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter,
                       double* u_out /*(n+1)^3*/, int* iters_out, double* relres_out, int n_threads);
 void nbo_grid_error(const nbo_problem* pr, int n, const double* u /*(n+1)^3*/, double* linf,
                     double* rmse);
+/* Extrapolated node jump J(x) = alpha(x_G) + d G (use_lag 0: G = beta/mu_big;
+ * 1: G with the small-mu side's normal derivative dn_small).  Returns 1 and
+ * J = 0 for nodes farther than 3h from Gamma. */
+int nbo_jump_extrap(const nbo_problem* pr, const double x[3], double h, int use_lag,
+                    double dn_small, double* J, double xg[3], double nrm[3], int* small_side);
+/* d_n u_s at xg from node values u by a least-squares linear fit (1: no fit). */
+int nbo_fit_dn(const nbo_problem* pr, int n, const double* u /*(n+1)^3*/, int s,
+               const double xg[3], const double nrm[3], double* dn);
+/* Grid solve with node jump mode 0 exact, 1 extrapolated + lagged fixed point,
+ * 2 extrapolated first order.  Returns 0, 1 (CG not converged), 2 (passes out). */
+int nbo_grid_solve_jump(const nbo_problem* pr, int n, int jump_mode, double rtol, int max_iter,
+                        int max_passes, double jtol, double* u_out, int* iters_out,
+                        double* relres_out, int* passes_out, double* dj_out, int n_threads);
 
 #ifdef __cplusplus
 }

@@ -137,6 +137,12 @@ def lib():
             L.nbo_grid_cg_solve.argtypes = [_P, C.c_int, C.c_double, C.c_int, _D,
                                             C.POINTER(C.c_int), _D, C.c_int]
             L.nbo_grid_error.argtypes = [_P, C.c_int, _D, _D, _D]
+            L.nbo_jump_extrap.argtypes = [_P, _D, C.c_double, C.c_int, C.c_double, _D, _D, _D,
+                                          C.POINTER(C.c_int)]
+            L.nbo_fit_dn.argtypes = [_P, C.c_int, _D, C.c_int, _D, _D, _D]
+            L.nbo_grid_solve_jump.argtypes = [_P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
+                                              C.c_double, _D, C.POINTER(C.c_int), _D,
+                                              C.POINTER(C.c_int), _D, C.c_int]
             _lib = L
     return _lib
 
@@ -328,3 +334,38 @@ def grid_error(pr, n, u):
     b = C.c_double(0)
     lib().nbo_grid_error(C.byref(pr), n, _dp(_vec(u)), C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+JUMP_EXACT, JUMP_EXTRAP, JUMP_FIRST_ORDER = 0, 1, 2
+
+
+def jump_extrap(pr, x, h, dn_small=None):
+    """Extrapolated node jump at x: (in_band, J, x_G, n, small side); dn_small
+    None drops the lag term (G = beta / mu_big)."""
+    J = C.c_double(0)
+    xg = np.zeros(3)
+    nrm = np.zeros(3)
+    ss = C.c_int(0)
+    rc = lib().nbo_jump_extrap(C.byref(pr), _dp(_vec(x)), h, 0 if dn_small is None else 1,
+                               0.0 if dn_small is None else float(dn_small), C.byref(J), _dp(xg),
+                               _dp(nrm), C.byref(ss))
+    return rc == 0, J.value, xg, nrm, ss.value
+
+
+def fit_dn(pr, n, u, s, xg, nrm):
+    dn = C.c_double(0)
+    rc = lib().nbo_fit_dn(C.byref(pr), n, _dp(_vec(u)), s, _dp(_vec(xg)), _dp(_vec(nrm)),
+                          C.byref(dn))
+    return (dn.value if rc == 0 else None)
+
+
+def grid_solve_jump(pr, n, mode, rtol=1e-10, max_iter=10000, max_passes=10, jtol=1e-6,
+                    n_threads=0):
+    u = np.zeros((n + 1) ** 3)
+    it = C.c_int(0)
+    rr = C.c_double(0)
+    ps = C.c_int(0)
+    dj = C.c_double(0)
+    st = lib().nbo_grid_solve_jump(C.byref(pr), n, mode, rtol, max_iter, max_passes, jtol, _dp(u),
+                                   C.byref(it), C.byref(rr), C.byref(ps), C.byref(dj), n_threads)
+    return st, u, it.value, rr.value, ps.value, dj.value

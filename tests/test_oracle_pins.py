@@ -542,3 +542,139 @@ def test_grid_with_interface_converges():
         assert st == 0
         errs.append(O.grid_error(pr, n, u)[0])
     assert errs[0] / errs[1] > 2.0
+
+
+# ------------------------------- extrapolated node jump of the grid scheme ----
+# The benchmark pair written out here (not through the oracle): u- = e^x cos y
+# sin z, u+ = x^2 + y^2 + z^2, on the sphere |x| = 1/2 (normal x / |x|).
+def _um(x):
+    return math.exp(x[0]) * math.cos(x[1]) * math.sin(x[2])
+
+
+def _up(x):
+    return float(x[0] ** 2 + x[1] ** 2 + x[2] ** 2)
+
+
+def _sphere_nodes_near_interface(n, width):
+    h = 2.0 / n
+    g = -1.0 + np.arange(1, n) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    x = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    r = np.linalg.norm(x, axis=1)
+    return x[np.abs(r - 0.5) <= width * h]
+
+
+def test_jump_projection_and_distance_on_the_sphere():
+    """x_G = x / (2|x|), d = |x| - 1/2 and n = x / |x| in closed form."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    n = 32
+    for x in _sphere_nodes_near_interface(n, 2.5)[::7]:
+        ok, J0, xg, nrm, ss = O.jump_extrap(pr, x, 2.0 / n)
+        r = np.linalg.norm(x)
+        assert ok and ss == 0
+        assert np.allclose(xg, x / (2 * r), atol=1e-14)
+        assert np.allclose(nrm, x / r, atol=1e-14)
+    far = np.array([0.0, 0.1, 0.05])  # 0.39 from Gamma: outside the 3h band
+    assert not O.jump_extrap(pr, far, 2.0 / n)[0]
+
+
+@pytest.mark.parametrize("mu_m,mu_p", [(1.0, 10.0), (7.0, 2.0)])
+def test_jump_slope_is_the_normal_derivative_jump(mu_m, mu_p):
+    """With the small side's exact normal derivative, (J - [u](x_G)) / d is
+    d_n u+ - d_n u- at x_G for either ordering of mu (the flux-jump algebra)."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=mu_m, mu_plus=mu_p)
+    h = 2.0 / 32
+    for x in _sphere_nodes_near_interface(32, 2.0)[::11]:
+        ok, _, xg, nrm, ss = O.jump_extrap(pr, x, h)
+        d = np.linalg.norm(x) - 0.5
+        if abs(d) < 0.2 * h:
+            continue
+        dn = {0: _fd_grad(_um, xg) @ nrm, 1: _fd_grad(_up, xg) @ nrm}
+        assert ss == (0 if mu_m <= mu_p else 1)
+        _, J, *_ = O.jump_extrap(pr, x, h, dn[ss])
+        G = (J - (_up(xg) - _um(xg))) / d
+        assert abs(G - (dn[1] - dn[0])) <= 1e-7 * max(1.0, abs(dn[1] - dn[0]))
+
+
+def test_jump_extrapolation_orders():
+    """At nodes within h of Gamma: the lagged J is off u+ - u- by O(h^2), the
+    first-order J (lag dropped) by O(h)."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    e1, e2 = [], []
+    for n in (16, 32, 64):
+        h = 2.0 / n
+        a1 = a2 = 0.0
+        for x in _sphere_nodes_near_interface(n, 1.0):
+            ok, J0, xg, nrm, ss = O.jump_extrap(pr, x, h)
+            assert ok
+            Jt = _up(x) - _um(x)
+            _, J, *_ = O.jump_extrap(pr, x, h, _fd_grad(_um, xg) @ nrm)
+            a1, a2 = max(a1, abs(J0 - Jt)), max(a2, abs(J - Jt))
+        e1.append(a1)
+        e2.append(a2)
+    assert all(1.6 < e1[i] / e1[i + 1] < 2.6 for i in range(2))
+    assert all(e2[i] / e2[i + 1] > 3.5 for i in range(2))
+
+
+def test_fit_recovers_linear_data_exactly():
+    """The least-squares fit reproduces the normal derivative of any linear
+    node data, on either side and for interface points all around the sphere."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    n = 24
+    h = 2.0 / n
+    g = -1.0 + np.arange(n + 1) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    rng = np.random.default_rng(12)
+    c = rng.normal(size=3)
+    u = 0.3 + nodes @ c
+    for _ in range(40):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        xg = 0.5 * v
+        for s in (0, 1):
+            dn = O.fit_dn(pr, n, u, s, xg, v)
+            assert dn is not None and abs(dn - c @ v) <= 1e-11
+
+
+def test_grid_jump_modes():
+    """Node jump modes of the grid solve: exact (equal to the plain solve),
+    extrapolated with the lagged derivative (second order in L-inf and RMS,
+    a contracting fixed point) and first order (the lag dropped)."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    st, u0, *_ = O.grid_cg_solve(pr, 16, rtol=1e-12, max_iter=5000)
+    st0, ue, *_ = O.grid_solve_jump(pr, 16, O.JUMP_EXACT, rtol=1e-12, max_iter=5000)
+    assert st == st0 == 0 and np.max(np.abs(u0 - ue)) <= 1e-12 * np.max(np.abs(u0))
+    lag, first = [], []
+    for n in (16, 32, 64):
+        st1, u1, it, rr, passes, dj = O.grid_solve_jump(pr, n, O.JUMP_EXTRAP, rtol=1e-12,
+                                                        max_iter=20000)
+        assert st1 == 0 and 2 <= passes <= 10 and rr <= 1e-12
+        st2, u2, *_ = O.grid_solve_jump(pr, n, O.JUMP_FIRST_ORDER, rtol=1e-12, max_iter=20000)
+        assert st2 == 0
+        lag.append(O.grid_error(pr, n, u1))
+        first.append(O.grid_error(pr, n, u2))
+    for i in range(2):
+        assert lag[i][0] / lag[i + 1][0] > 3.0 and lag[i][1] / lag[i + 1][1] > 3.5
+        assert 1.5 < first[i][0] / first[i + 1][0] < 3.0
+    # the fixed point contracts: max |J_new - J| falls by > 5x per pass
+    djs = [O.grid_solve_jump(pr, 32, O.JUMP_EXTRAP, rtol=1e-12, max_iter=20000, max_passes=k,
+                             jtol=0.0)[5] for k in (2, 3, 4, 5)]
+    assert all(djs[i] / djs[i + 1] > 5.0 for i in range(3))
+
+
+def test_grid_jump_equal_mu_and_fallback():
+    """Equal mu: G = beta / mu needs no lag, so the second pass changes
+    nothing.  A fixed point stopped early falls back to the first-order jump."""
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=3.0, mu_plus=3.0)
+    st, u1, it, rr, passes, dj = O.grid_solve_jump(pr, 16, O.JUMP_EXTRAP, rtol=1e-12,
+                                                   max_iter=5000)
+    _, u2, *_ = O.grid_solve_jump(pr, 16, O.JUMP_FIRST_ORDER, rtol=1e-12, max_iter=5000)
+    assert st == 0 and passes == 2 and dj == 0.0
+    assert np.max(np.abs(u1 - u2)) <= 1e-10 * np.max(np.abs(u2))
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    st, u1, it, rr, passes, dj = O.grid_solve_jump(pr, 16, O.JUMP_EXTRAP, rtol=1e-12,
+                                                   max_iter=5000, max_passes=2, jtol=1e-12)
+    _, u2, *_ = O.grid_solve_jump(pr, 16, O.JUMP_FIRST_ORDER, rtol=1e-12, max_iter=5000)
+    assert st == 2 and passes == 2 and dj > 1e-12
+    assert np.max(np.abs(u1 - u2)) <= 1e-9 * np.max(np.abs(u2))
