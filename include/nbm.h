@@ -84,6 +84,13 @@ typedef enum {
 } nbm_solution;
 
 typedef enum {
+  NBM_JUMP_EXACT = 0,       /* the manufactured pair's own u+(x) - u-(x) at the node      */
+  NBM_JUMP_EXTRAP = 1,      /* alpha(x_G) + d [d_n u], the small-mu side's d_n u lagged
+                               from the previous solve (fixed-point passes, see below)   */
+  NBM_JUMP_FIRST_ORDER = 2  /* alpha(x_G) + d beta(x_G) / mu_big: the lag term dropped    */
+} nbm_grid_jump;
+
+typedef enum {
   NBM_ACT_TANH = 0,       /* tanh hidden layers (every path)                            */
   NBM_ACT_SIN = 1         /* sine-activated hidden layers (Sec. 4.1 networks): FP32
                              precision and width <= 32 only                            */
@@ -113,6 +120,8 @@ typedef struct {
                              points stay within 4h of the base spacing. */
   int32_t solution;       /* nbm_solution: manufactured pair and coefficients          */
   int32_t activation;     /* nbm_activation of the hidden layers                       */
+  int32_t grid_jump;      /* nbm_grid_jump: value jump carried to the grid solvers' nodes */
+  int32_t reserved0;      /* must be 0                                                 */
 } nbm_problem_desc;
 
 typedef struct nbm_problem nbm_problem;
@@ -209,11 +218,28 @@ int nbm_eval_points(nbm_problem* p, const float* params, const float* pts, int64
 /* The plain mesh-based method the NBM is bootstrapped from: the same
  * finite-volume rows assembled on the grid of spacing 2/n, one unknown per
  * interior node, solved in FP64 by Jacobi-preconditioned conjugate gradients
- * until ||r|| <= rtol ||b|| or max_iter.  The other side's value at a node
- * across Gamma is the node value plus the exact jump u+ - u- of the
- * manufactured pair.  u_out [(n+1)^3] FP64 (boundary nodes = Dirichlet data).
- * iters_out, relres_out (host) or NULL.  Synchronizes the stream.
- * Returns NBM_ERR_NOT_CONVERGED (with u_out filled) if max_iter is reached. */
+ * until ||r|| <= rtol ||b|| or max_iter.  u_out [(n+1)^3] FP64 (boundary
+ * nodes = Dirichlet data).  iters_out (summed over the passes below),
+ * relres_out (last solve) or NULL.  Synchronizes the stream.
+ *   The other side's value at a node x across Gamma is u_x +- J(x), J chosen
+ *   by the descriptor's grid_jump:
+ *   NBM_JUMP_EXACT: J = u+(x) - u-(x) of the manufactured pair.
+ *   NBM_JUMP_FIRST_ORDER / NBM_JUMP_EXTRAP: J = alpha(x_G) + d G, with x_G
+ *     the node moved onto phi = 0 by three Newton steps, d = phi/|grad phi|
+ *     at the node, n the normal at x_G, G = [d_n u] from the flux jump beta:
+ *     G = beta/mu+ - (1 - mu-/mu+) d_n u- if mu- <= mu+, else
+ *     G = beta/mu- + (1 - mu+/mu-) d_n u+ (coefficients at x_G).  The first-
+ *     order mode drops the d_n term.  NBM_JUMP_EXTRAP takes d_n of the
+ *     small-mu side from the previous solve (least-squares linear fit over
+ *     that side's interior nodes in the 3x3x3 block around the node nearest
+ *     one spacing into that side): pass 1 is the first-order solve, each
+ *     later pass refits, rebuilds the right-hand side and re-solves from the
+ *     previous solution, until max |J_new - J| <= 1e-6 max(1, max |J|).
+ *     After 10 passes without that, it falls back to the first-order jump
+ *     (re-solved; see nbm_grid_last_jump_info).  Nodes farther than 3h from
+ *     Gamma carry J = 0 (no row weights them).
+ * Returns NBM_ERR_NOT_CONVERGED (with u_out filled) if a solve reaches
+ * max_iter. */
 int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
                       int* iters_out, double* relres_out, nbm_stream_t stream);
 
@@ -234,6 +260,13 @@ int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* 
  * Synchronizes the stream. */
 int nbm_grid_solve_refined(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
                            int* iters_out, double* relres_out, nbm_stream_t stream);
+
+/* Outer-loop record of the calling thread's last nbm_grid_cg_solve or
+ * nbm_grid_solve_refined: passes_out = solves with a lagged jump (1 for
+ * NBM_JUMP_EXACT and NBM_JUMP_FIRST_ORDER), max_dj_out = max |J_new - J| of
+ * the last pass (0 for one pass), fell_back_out = 1 if NBM_JUMP_EXTRAP used
+ * its first-order fallback.  Any pointer may be NULL.  Host only. */
+int nbm_grid_last_jump_info(int* passes_out, double* max_dj_out, int* fell_back_out);
 
 /* Optional timing of the fused stencil-step kernel (the dominant kernel of a
  * training step).  enable = 1 clears the counters and brackets every later

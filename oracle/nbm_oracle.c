@@ -1094,7 +1094,9 @@ int nbo_jump_extrap(const nbo_problem* pr, const double x[3], double h, int use_
   *J = 0.0;
   *small_side = 0;
   for (int i = 0; i < 3; ++i) xg[i] = x[i], nrm[i] = 0.0;
-  if (!(gn > 1e-300) || fabs(ph / gn) > 3.0 * h) return 1;
+  /* the band edge sits 1e-9 outside 3h so that nodes at exactly 3h (lattice
+   * points on a sphere) fall inside whatever the rounding of d */
+  if (!(gn > 1e-300) || fabs(ph / gn) > 3.0 * h * (1.0 + 1e-9)) return 1;
   double d = ph / gn;
   for (int it = 0; it < 3; ++it) {
     double gg[3];
@@ -1125,7 +1127,8 @@ int nbo_jump_extrap(const nbo_problem* pr, const double x[3], double h, int use_
 /* Normal derivative of side s at x_G from the node values u (the full
  * (n+1)^3 array of an iterate): least-squares fit of a linear function
  * a + g.(q - x_G) to the interior nodes q of phase s in the 3x3x3 block
- * around the node nearest x_G - h n (s = minus) or x_G + h n (s = plus),
+ * around the node nearest x_G - h n (s = minus) or x_G + h n (s = plus)
+ * (a midway point takes the upper node),
  * i.e. one spacing into side s, so that the block holds at least two layers
  * of side-s nodes (normal equations, Cholesky), dn = g . nrm.
  * Returns 1 (no value) with fewer than 4 such nodes or a degenerate fit. */
@@ -1135,7 +1138,9 @@ int nbo_fit_dn(const nbo_problem* pr, int n, const double* u, int s, const doubl
   int c[3];
   for (int i = 0; i < 3; ++i) {
     double xc = xg[i] + (s == 0 ? -hg : hg) * nrm[i];
-    c[i] = (int)floor((xc + 1.0) / hg + 0.5);
+    /* nearest node; a point midway between two nodes (symmetric interfaces
+     * put x_G there) takes the upper one, by a margin far above rounding */
+    c[i] = (int)floor((xc + 1.0) / hg + 0.5 + 1e-6);
     if (c[i] < 2) c[i] = 2;
     if (c[i] > n - 2) c[i] = n - 2;
   }
@@ -1145,6 +1150,8 @@ int nbo_fit_dn(const nbo_problem* pr, int n, const double* u, int s, const doubl
     for (int dj = -1; dj <= 1; ++dj)
       for (int di = -1; di <= 1; ++di) {
         int q[3] = {c[0] + di, c[1] + dj, c[2] + dk};
+        if (q[0] < 1 || q[1] < 1 || q[2] < 1 || q[0] > n - 1 || q[1] > n - 1 || q[2] > n - 1)
+          continue;  /* interior nodes only (reached for n < 4) */
         double xq[3] = {-1.0 + q[0] * hg, -1.0 + q[1] * hg, -1.0 + q[2] * hg};
         if (nbo_phase(pr, xq) != s) continue;
         double bv[4] = {1.0, (xq[0] - xg[0]) / hg, (xq[1] - xg[1]) / hg, (xq[2] - xg[2]) / hg};

@@ -20,12 +20,14 @@ from . import build as _build
 __all__ = ["ProblemDesc", "Problem", "NBMLoss", "load_library", "config", "param_count",
            "xavier_init", "save_checkpoint", "load_checkpoint", "GEOM_SPHERE", "GEOM_FLOWER",
            "GEOM_ALL_PLUS", "GEOM_ALL_MINUS", "GEOM_GRID", "PREC_FP32", "PREC_BF16",
-           "PREC_FP16", "SOL_BENCH", "SOL_SEC41", "ACT_TANH", "ACT_SIN", "NBMError"]
+           "PREC_FP16", "SOL_BENCH", "SOL_SEC41", "ACT_TANH", "ACT_SIN", "JUMP_EXACT",
+           "JUMP_EXTRAP", "JUMP_FIRST_ORDER", "NBMError"]
 
 GEOM_SPHERE, GEOM_FLOWER, GEOM_ALL_PLUS, GEOM_ALL_MINUS, GEOM_GRID = 1, 2, 3, 4, 5
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 SOL_BENCH, SOL_SEC41 = 0, 1
 ACT_TANH, ACT_SIN = 0, 1
+JUMP_EXACT, JUMP_EXTRAP, JUMP_FIRST_ORDER = 0, 1, 2
 
 STATUS = {0: "NBM_OK", 1: "NBM_ERR_INVALID_ARG", 2: "NBM_ERR_CUDA", 3: "NBM_ERR_NOT_CONVERGED",
           4: "NBM_ERR_NONFINITE", 5: "NBM_ERR_OOM", 6: "NBM_ERR_DEVICE_TIMEOUT"}
@@ -45,7 +47,7 @@ class _Desc(C.Structure):
                 ("k_plus", C.c_double), ("h", C.c_double), ("lambda_jump", C.c_double),
                 ("band_fraction", C.c_double), ("fp64_stencil", C.c_int32),
                 ("refine_levels", C.c_int32), ("solution", C.c_int32),
-                ("activation", C.c_int32)]
+                ("activation", C.c_int32), ("grid_jump", C.c_int32), ("reserved0", C.c_int32)]
 
 
 @dataclasses.dataclass
@@ -70,12 +72,14 @@ class ProblemDesc:
     refine_levels: int = 0  # implicit refinement: also the cells of spacing h/2, ..., h/2^levels
     solution: int = 0       # SOL_BENCH, or SOL_SEC41 (variable mu, the convergence study)
     activation: int = 0     # ACT_TANH, or ACT_SIN (FP32 path, width <= 32)
+    grid_jump: int = 0      # node jump of the grid solvers: JUMP_EXACT, JUMP_EXTRAP, JUMP_FIRST_ORDER
 
     def to_c(self) -> _Desc:
         return _Desc(self.geometry, self.n_hidden, self.width, self.precision, self.r0,
                      self.amp, self.lobes_theta, self.lobes_psi, self.mu_minus, self.mu_plus,
                      self.k_minus, self.k_plus, self.h, self.lambda_jump, self.band_fraction,
-                     self.fp64_stencil, self.refine_levels, self.solution, self.activation)
+                     self.fp64_stencil, self.refine_levels, self.solution, self.activation,
+                     self.grid_jump, 0)
 
 
 def config(name: str, precision: int | None = None) -> ProblemDesc:
@@ -172,6 +176,9 @@ def load_library(build_if_missing: bool = True):
     L.nbm_grid_cg_solve.argtypes = [P, C.c_int, C.c_double, C.c_int, P, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double), P]
     L.nbm_grid_solve_refined.argtypes = L.nbm_grid_cg_solve.argtypes
+    L.nbm_grid_last_jump_info.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int)]
+    L.nbm_grid_last_jump_info.restype = C.c_int
     for fn in ("nbm_init_problem", "nbm_destroy", "nbm_sample_points", "nbm_residual",
                "nbm_loss_grad", "nbm_train_steps", "nbm_eval_grid", "nbm_grid_cg_solve",
                "nbm_grid_solve_refined",
@@ -306,6 +313,14 @@ class Problem:
         if rc not in (0, 3):
             _check(rc)
         return out, it.value, rr.value, rc == 0
+
+    @staticmethod
+    def grid_jump_info():
+        """(passes, max |J_new - J| of the last pass, fell_back) of this thread's
+        last grid solve; passes is 1 for the exact and first-order jumps."""
+        ps, dj, fb = C.c_int(0), C.c_double(0.0), C.c_int(0)
+        _check(load_library().nbm_grid_last_jump_info(C.byref(ps), C.byref(dj), C.byref(fb)))
+        return ps.value, dj.value, bool(fb.value)
 
     def grid_solve_refined(self, n, rtol=1e-10, max_iter=20000, out=None, stream=None):
         """The grid system of grid_cg_solve to the same FP64 residual test, by

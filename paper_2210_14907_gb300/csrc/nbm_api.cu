@@ -177,6 +177,10 @@ static int check_desc(const nbm_problem_desc* d) {
     return fail(NBM_ERR_INVALID_ARG, "unknown activation %d", d->activation);
   if (d->activation == NBM_ACT_SIN && (d->precision != NBM_PREC_FP32 || d->width > 32))
     return fail(NBM_ERR_INVALID_ARG, "sine networks run on the FP32 path with width <= 32");
+  if (d->grid_jump != NBM_JUMP_EXACT && d->grid_jump != NBM_JUMP_EXTRAP &&
+      d->grid_jump != NBM_JUMP_FIRST_ORDER)
+    return fail(NBM_ERR_INVALID_ARG, "unknown grid_jump %d", d->grid_jump);
+  if (d->reserved0 != 0) return fail(NBM_ERR_INVALID_ARG, "reserved0 must be 0");
   if (d->refine_levels < 0 || d->refine_levels > 3)
     return fail(NBM_ERR_INVALID_ARG, "refine_levels must be 0..3 (got %d)", d->refine_levels);
   if (!(ldexp(d->h, -d->refine_levels) >= 0x1p-12))

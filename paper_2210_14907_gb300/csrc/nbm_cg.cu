@@ -30,29 +30,36 @@ struct Grid {
   double h;
 };
 
+// grid node coordinate -1 + i h with the product rounded before the sum (no
+// fused multiply-add), so that nodes on a symmetry plane of the level set
+// (x = 0 at i = n/2) lie exactly on it
+__device__ inline double node_coord(int i, double h) { return __dadd_rn(-1.0, __dmul_rn((double)i, h)); }
+
 __device__ inline void node_xyz(const Grid& G, int64_t r, int& i, int& j, int& k, double x[3]) {
   i = 1 + (int)(r % G.m1);
   j = 1 + (int)((r / G.m1) % G.m1);
   k = 1 + (int)(r / ((int64_t)G.m1 * G.m1));
-  x[0] = -1.0 + i * G.h;
-  x[1] = -1.0 + j * G.h;
-  x[2] = -1.0 + k * G.h;
+  x[0] = node_coord(i, G.h);
+  x[1] = node_coord(j, G.h);
+  x[2] = node_coord(k, G.h);
 }
 
 __device__ inline int phase_d(const ProbDev& P, const double x[3]) {
   return phi_d(P, x[0], x[1], x[2]) <= 0.0 ? 0 : 1;
 }
 
-// jump correction of side s at node x of side sx: U^s(x) = u_x + corr
-__device__ inline void jump_corr(const ProbDev& P, const double x[3], int sx, double c[2]) {
-  const double jmp = alpha_d(P, x);
+// jump correction of side s at a node of side sx: U^s = u + c[s]
+__device__ inline void jump_corr(double jmp, int sx, double c[2]) {
   c[0] = sx == 1 ? -jmp : 0.0;
   c[1] = sx == 0 ? jmp : 0.0;
 }
 
-__global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* diag, double* wx,
-                                                  double* wy, double* wz, double* rhs,
-                                                  double* inv_diag) {
+// Rows of every interior node.  Jn (interior-node array) holds the node jump
+// J = u+ - u- carried to each node; NULL takes the manufactured pair's own
+// u+(x) - u-(x) (the exact jump).
+__global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, const double* __restrict__ Jn,
+                                                  double* diag, double* wx, double* wy, double* wz,
+                                                  double* rhs, double* inv_diag) {
   const int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (r >= G.m) return;
   int idx[3];
@@ -63,7 +70,7 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* dia
   cell_geometry_d(P, p, h, cg);
   const int sp = phase_d(P, p);
   double cp[2];
-  jump_corr(P, p, sp, cp);
+  jump_corr(Jn ? Jn[r] : alpha_d(P, p), sp, cp);
   double dg = 0.0, known = 0.0;
   for (int s = 0; s < 2; ++s) {
     const double V = s ? 1.0 - cg.Vm : cg.Vm;
@@ -75,10 +82,13 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, double* dia
     const int ax = f >> 1, sg = (f & 1) ? 1 : -1;
     int nb[3] = {idx[0], idx[1], idx[2]};
     nb[ax] += sg;
-    const double q[3] = {-1.0 + nb[0] * h, -1.0 + nb[1] * h, -1.0 + nb[2] * h};
+    const double q[3] = {node_coord(nb[0], h), node_coord(nb[1], h), node_coord(nb[2], h)};
     const bool bnd = nb[ax] == 0 || nb[ax] == G.n;
     double cq[2] = {0.0, 0.0};
-    if (!bnd) jump_corr(P, q, phase_d(P, q), cq);
+    if (!bnd) {
+      const int64_t rq = (nb[0] - 1) + (int64_t)G.m1 * ((nb[1] - 1) + (int64_t)G.m1 * (nb[2] - 1));
+      jump_corr(Jn ? Jn[rq] : alpha_d(P, q), phase_d(P, q), cq);
+    }
     // face centre: the same point for both cells of the face, so the face
     // weight (and the matrix) stays symmetric with variable mu
     double fc[3] = {p[0], p[1], p[2]};
@@ -255,16 +265,17 @@ __global__ void __launch_bounds__(kB) k_to_f32(Grid G, const double* __restrict_
   }
 }
 
-// r = b - r (r holds A x on entry); partial of r.r
+// r = b - r (r holds A x on entry); partials of r.r and b.b
 __global__ void __launch_bounds__(kB) k_defect(Grid G, const double* __restrict__ b, double* r,
                                                double* part) {
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
-    const double ri = b[i] - r[i];
+    const double bi = b[i], ri = bi - r[i];
     r[i] = ri;
     acc[0] += ri * ri;
+    acc[1] += bi * bi;
   }
-  block_partials<double, 1>(acc, part, blockIdx.x, gridDim.x);
+  block_partials<double, 2>(acc, part, blockIdx.x, gridDim.x);
 }
 
 // start of an inner solve of A e = r / ||r||: e = 0, r32 = r / ||r||,
@@ -287,6 +298,158 @@ __global__ void __launch_bounds__(kB) k_inner_init(Grid G, const double* __restr
   block_partials<float, 2>(acc, part, blockIdx.x, gridDim.x);
 }
 
+// ---- extrapolated node jump ----
+
+// d_n u_s at x_G from the interior iterate x: least-squares fit of
+// a + g.(q - x_G) over the interior side-s nodes of the 3x3x3 block around
+// the node nearest x_G -+ h n (one spacing into side s; a midway point takes
+// the upper node), normal equations by
+// Cholesky; false with fewer than 4 such nodes or a degenerate fit.
+__device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict__ x, int s,
+                       const double xg[3], const double nrm[3], double* dn) {
+  const double h = G.h;
+  int c[3];
+  for (int a = 0; a < 3; ++a) {
+    const double xc = xg[a] + (s == 0 ? -h : h) * nrm[a];
+    int ci = (int)floor((xc + 1.0) / h + 0.5 + 1e-6);  // a midway point takes the upper node
+    ci = ci < 2 ? 2 : ci;
+    c[a] = ci > G.n - 2 ? G.n - 2 : ci;
+  }
+  double M[4][4] = {}, rhs[4] = {};
+  int cnt = 0;
+  for (int dk = -1; dk <= 1; ++dk)
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int q[3] = {c[0] + di, c[1] + dj, c[2] + dk};
+        if (q[0] < 1 || q[1] < 1 || q[2] < 1 || q[0] > G.n - 1 || q[1] > G.n - 1 ||
+            q[2] > G.n - 1)
+          continue;
+        const double xq[3] = {node_coord(q[0], h), node_coord(q[1], h), node_coord(q[2], h)};
+        if (phase_d(P, xq) != s) continue;
+        const double bv[4] = {1.0, (xq[0] - xg[0]) / h, (xq[1] - xg[1]) / h, (xq[2] - xg[2]) / h};
+        const double uq = x[(q[0] - 1) + (int64_t)G.m1 * ((q[1] - 1) + (int64_t)G.m1 * (q[2] - 1))];
+        for (int a = 0; a < 4; ++a) {
+          rhs[a] += bv[a] * uq;
+          for (int b = 0; b < 4; ++b) M[a][b] += bv[a] * bv[b];
+        }
+        ++cnt;
+      }
+  if (cnt < 4) return false;
+  double L[4][4] = {};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double t = M[a][b];
+      for (int k = 0; k < b; ++k) t -= L[a][k] * L[b][k];
+      if (a == b) {
+        if (!(t > 1e-8 * M[0][0])) return false;
+        L[a][a] = sqrt(t);
+      } else {
+        L[a][b] = t / L[b][b];
+      }
+    }
+  double y[4], cf[4];
+  for (int a = 0; a < 4; ++a) {
+    double t = rhs[a];
+    for (int k = 0; k < a; ++k) t -= L[a][k] * y[k];
+    y[a] = t / L[a][a];
+  }
+  for (int a = 3; a >= 0; --a) {
+    double t = y[a];
+    for (int k = a + 1; k < 4; ++k) t -= L[k][a] * cf[k];
+    cf[a] = t / L[a][a];
+  }
+  *dn = (cf[1] * nrm[0] + cf[2] * nrm[1] + cf[3] * nrm[2]) / h;
+  return true;
+}
+
+// Node jump J(x) = alpha(x_G) + d G on every interior node within 3h of Gamma
+// (0 elsewhere), updated in place: x_G by three Newton steps from the node,
+// d = phi / |grad phi| at the node, G = [d_n u] from the flux jump with the
+// small-mu side's d_n from the iterate (lag = 1, fitted) or dropped (lag = 0).
+// Block partials of max |J_new - J| and max |J_new| go to part[] and
+// part[gridDim.x + ...].
+__global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
+                                                  const double* __restrict__ x, double* J,
+                                                  double* part) {
+  __shared__ double red[2][kB / 32];
+  double mx[2] = {0.0, 0.0};
+  for (int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x; r < G.m; r += (int64_t)gridDim.x * kB) {
+    int i, j, k;
+    double p[3], g[3];
+    node_xyz(G, r, i, j, k, p);
+    const double ph = phi_d(P, p[0], p[1], p[2]);
+    grad_phi_d(P, p, g);
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double jn = 0.0;
+    if (gn > 1e-300 && fabs(ph / gn) <= 3.0 * G.h * (1.0 + 1e-9)) {  // nodes at 3h: inside
+      const double d = ph / gn;
+      double xg[3] = {p[0], p[1], p[2]};
+      for (int it = 0; it < 3; ++it) {
+        double gg[3];
+        const double f = phi_d(P, xg[0], xg[1], xg[2]);
+        grad_phi_d(P, xg, gg);
+        const double q = gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2];
+        if (q <= 1e-300) break;
+        for (int a = 0; a < 3; ++a) xg[a] -= f * gg[a] / q;
+      }
+      double gx[3];
+      grad_phi_d(P, xg, gx);
+      const double gxn = sqrt(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
+      if (gxn > 1e-300) {
+        const double nrm[3] = {gx[0] / gxn, gx[1] / gxn, gx[2] / gxn};
+        const double mum = mu_at<double>(P, 0, xg[0], xg[1], xg[2]);
+        const double mup = mu_at<double>(P, 1, xg[0], xg[1], xg[2]);
+        const double beta = beta_d(P, xg);
+        const int ss = mum <= mup ? 0 : 1;
+        double dn = 0.0;
+        const bool have = lag && fit_dn(P, G, x, ss, xg, nrm, &dn);
+        const double Gj = ss == 0 ? beta / mup - (have ? (1.0 - mum / mup) * dn : 0.0)
+                                  : beta / mum + (have ? (1.0 - mup / mum) * dn : 0.0);
+        jn = alpha_d(P, xg) + d * Gj;
+      }
+    }
+    mx[0] = fmax(mx[0], fabs(jn - J[r]));
+    mx[1] = fmax(mx[1], fabs(jn));
+    J[r] = jn;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    for (int q = 0; q < 2; ++q) mx[q] = fmax(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 2; ++q) red[q][threadIdx.x >> 5] = mx[q];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2; ++q) {
+      double m = 0.0;
+      for (int w = 0; w < kB / 32; ++w) m = fmax(m, red[q][w]);
+      part[q * (int64_t)gridDim.x + blockIdx.x] = m;
+    }
+}
+
+// sc[slot], sc[slot + 1] = maxima of the two partial vectors
+__global__ void k_reduce_max2(const double* __restrict__ part, int nparts, double* sc, int slot) {
+  __shared__ double red[2][256];
+  double m0 = 0.0, m1 = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += 256) {
+    m0 = fmax(m0, part[b]);
+    m1 = fmax(m1, part[nparts + b]);
+  }
+  red[0][threadIdx.x] = m0;
+  red[1][threadIdx.x] = m1;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + o]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sc[slot] = red[0][0];
+    sc[slot + 1] = red[1][0];
+  }
+}
+
 // x += ||r|| e   (FP64)
 __global__ void __launch_bounds__(kB) k_correct(Grid G, const double* __restrict__ sc,
                                                 const float* __restrict__ e32, double* x) {
@@ -302,7 +465,7 @@ __global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const dou
   if (id >= N1 * N1 * N1) return;
   const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
   if (i == 0 || j == 0 || k == 0 || i == G.n || j == G.n || k == G.n) {
-    u[id] = dirichlet_g<double>(P, -1.0 + i * G.h, -1.0 + j * G.h, -1.0 + k * G.h);
+    u[id] = dirichlet_g<double>(P, node_coord(i, G.h), node_coord(j, G.h), node_coord(k, G.h));
   } else {
     u[id] = x[(i - 1) + (int64_t)G.m1 * ((j - 1) + (int64_t)G.m1 * (k - 1))];
   }
@@ -411,142 +574,248 @@ int cg_report(const char* who, bool converged, int it, double rnorm, double bnor
 
 using namespace nbm;
 
-extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
-                                 int* iters_out, double* relres_out, nbm_stream_t stream) {
-  const char* who = "grid CG";
-  CgSetup S;
-  if (int rc = cg_setup(p, n, rtol, max_iter, u_out, who, S)) return rc;
-  const Grid& G = S.G;
-  cudaStream_t st = (cudaStream_t)stream;
-  CgBuffers B;
-  double *diag = B.get<double>(G.m), *wx = B.get<double>(G.m), *wy = B.get<double>(G.m),
-         *wz = B.get<double>(G.m), *r = B.get<double>(G.m), *x = B.get<double>(G.m),
-         *pv = B.get<double>(G.m), *Ap = B.get<double>(G.m), *idg = B.get<double>(G.m);
-  double* part = B.get<double>(2 * (size_t)(S.nu > S.nsp ? S.nu : S.nsp));
-  double* sc = B.get<double>(16);
-  if (B.err != cudaSuccess) return cg_cuda_fail(who, B.err);
-
-  k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, G, diag, wx, wy, wz, r, idg);
-  cudaMemsetAsync(x, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
-  // r = b: rz = r.(r/diag), rr = r.r (an update with alpha = 0)
-  k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part);
-  k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
-  k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 1, idg, r, pv);
-  double host_sc[16];
-  cudaError_t e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cg_cuda_fail(who, e);
-  const double bnorm = sqrt(host_sc[4]);
-  int it = 0;
-  double rnorm = bnorm;
-  bool converged = bnorm == 0.0;
-  while (!converged && it < max_iter) {
-    k_spmv_dot<double><<<S.sgrid, kB, 0, st>>>(G, S.kz, diag, wx, wy, wz, pv, Ap, part);
-    k_reduce_parts<POST_ALPHA><<<1, 256, 0, st>>>(part, S.nsp, 1, sc, 1);
-    k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part);
-    k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
-    k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 0, idg, r, pv);
-    ++it;
-    if (it % 10 == 0 || it == max_iter) {
-      e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return cg_cuda_fail(who, e);
-      rnorm = sqrt(host_sc[4]);
-      if (!(rnorm == rnorm)) break;  // NaN: stop, report below
-      converged = rnorm <= rtol * bnorm;
-    }
-  }
-  k_write_nodes<<<(int)((S.nodes + kB - 1) / kB), kB, 0, st>>>(S.P, G, x, u_out);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cg_cuda_fail(who, e);
-  return cg_report(who, converged, it, rnorm, bnorm, rtol, iters_out, relres_out);
-}
-
 namespace nbm {
 namespace {
+
 constexpr double kInnerTol = 1e-5;  // relative residual target of one FP32 inner solve
 constexpr int kCheckEvery = 10;     // inner iterations between host convergence checks
 constexpr int kMaxStall = 3;        // outer steps in a row that gain less than 10 %
+constexpr int kMaxPasses = 10;      // solves with a lagged jump
+constexpr double kJumpTol = 1e-6;   // max |J_new - J| <= kJumpTol max(1, max |J|)
+
+struct JumpInfo {
+  int passes = 0;
+  double dj = 0.0;
+  int fell_back = 0;
+};
+thread_local JumpInfo g_jump_info;
+
+// Device state of one grid solve (either solver) and its outer jump loop.
+struct GridSolve {
+  const char* who;
+  CgSetup S;
+  cudaStream_t st;
+  CgBuffers B;
+  bool refined;
+  double *diag, *wx, *wy, *wz, *b, *x, *r, *idg, *J = nullptr, *part, *sc;
+  double *pv = nullptr, *Ap = nullptr;                        // FP64 CG
+  float *d32 = nullptr, *wx32 = nullptr, *wy32 = nullptr, *wz32 = nullptr, *idg32 = nullptr,
+        *r32 = nullptr, *e32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;  // refined
+  double host_sc[16];
+  double rnorm = 0.0, bnorm = 0.0;
+  int iters = 0;
+
+  cudaError_t read_sc() {
+    cudaError_t e = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  }
+
+  // r = b - A x for the current x; sc cleared, sc[8] = r.r, sc[9] = b.b
+  // (POST_NORM also sets sc[6] = ||r||, sc[7] = 1 / ||r||)
+  void defect() {
+    const Grid& G = S.G;
+    cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
+    k_spmv_dot<double><<<S.sgrid, kB, 0, st>>>(G, S.kz, diag, wx, wy, wz, x, r, part);
+    k_defect<<<S.nu, kB, 0, st>>>(G, b, r, part);
+    k_reduce_parts<POST_NORM><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 8);
+  }
+
+  // FP64 Jacobi PCG from the current x.  0, NBM_ERR_NOT_CONVERGED or NONFINITE,
+  // or -1 for a CUDA error (message in `e`).
+  int solve_fp64(double rtol, int max_iter, cudaError_t& e) {
+    const Grid& G = S.G;
+    defect();
+    cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
+    cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
+    // rz = r.(r/diag), rr = r.r (an update with alpha = sc[2] = 0), p = z
+    k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part);
+    k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+    k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 1, idg, r, pv);
+    if ((e = read_sc()) != cudaSuccess) return -1;
+    bnorm = sqrt(host_sc[9]);
+    rnorm = sqrt(host_sc[4]);
+    int it = 0;
+    bool converged = rnorm <= rtol * bnorm;
+    while (!converged && it < max_iter && rnorm == rnorm) {
+      k_spmv_dot<double><<<S.sgrid, kB, 0, st>>>(G, S.kz, diag, wx, wy, wz, pv, Ap, part);
+      k_reduce_parts<POST_ALPHA><<<1, 256, 0, st>>>(part, S.nsp, 1, sc, 1);
+      k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part);
+      k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+      k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 0, idg, r, pv);
+      ++it;
+      if (it % kCheckEvery == 0 || it == max_iter) {
+        if ((e = read_sc()) != cudaSuccess) return -1;
+        rnorm = sqrt(host_sc[4]);
+        converged = rnorm <= rtol * bnorm;
+      }
+    }
+    iters += it;
+    if (!(rnorm == rnorm)) return NBM_ERR_NONFINITE;
+    return converged ? NBM_OK : NBM_ERR_NOT_CONVERGED;
+  }
+
+  // FP64 residuals, FP32 inner PCG corrections, from the current x
+  int solve_refined(double rtol, int max_iter, cudaError_t& e) {
+    const Grid& G = S.G;
+    defect();
+    if ((e = read_sc()) != cudaSuccess) return -1;
+    bnorm = sqrt(host_sc[9]);
+    rnorm = sqrt(host_sc[8]);
+    int it = 0, stall = 0;
+    bool converged = rnorm <= rtol * bnorm;
+    while (!converged && it < max_iter && rnorm == rnorm && stall < kMaxStall) {
+      // inner FP32 PCG on A e = r / ||r|| (initial residual norm 1), stopped at
+      // kInnerTol or where the outer target needs no more
+      double tau = 0.5 * rtol * bnorm / rnorm;
+      tau = tau < kInnerTol ? kInnerTol : tau > 0.5 ? 0.5 : tau;
+      k_inner_init<<<S.nu, kB, 0, st>>>(G, sc, r, idg32, r32, e32, p32, part);
+      k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+      for (int inner = 1; it < max_iter; ++inner) {
+        k_spmv_dot<float><<<S.sgrid, kB, 0, st>>>(G, S.kz, d32, wx32, wy32, wz32, p32, Ap32, part);
+        k_reduce_parts<POST_ALPHA><<<1, 256, 0, st>>>(part, S.nsp, 1, sc, 1);
+        k_update<float><<<S.nu, kB, 0, st>>>(G, sc, idg32, p32, Ap32, e32, r32, part);
+        k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
+        k_pupdate<float><<<S.nu, kB, 0, st>>>(G, sc, 0, idg32, r32, p32);
+        ++it;
+        if (inner % kCheckEvery == 0 || it == max_iter) {
+          if ((e = read_sc()) != cudaSuccess) return -1;
+          const double rin = sqrt(host_sc[4]);
+          if (!(rin == rin) || rin <= tau) break;
+        }
+      }
+      // x += ||r|| e in FP64, then the FP64 residual r = b - A x
+      k_correct<<<S.nu, kB, 0, st>>>(G, sc, e32, x);
+      defect();
+      if ((e = read_sc()) != cudaSuccess) return -1;
+      const double rnew = sqrt(host_sc[8]);
+      stall = rnew > 0.9 * rnorm ? stall + 1 : 0;
+      rnorm = rnew;
+      converged = rnorm <= rtol * bnorm;
+    }
+    iters += it;
+    if (!(rnorm == rnorm)) return NBM_ERR_NONFINITE;
+    return converged ? NBM_OK : NBM_ERR_NOT_CONVERGED;
+  }
+
+  int solve(double rtol, int max_iter, cudaError_t& e) {
+    return refined ? solve_refined(rtol, max_iter, e) : solve_fp64(rtol, max_iter, e);
+  }
+
+  void rows() {
+    k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, S.G, J, diag, wx, wy, wz, b, idg);
+  }
+
+  // J from the current x (lag 1) or first order (lag 0); sc[10] = max |dJ|,
+  // sc[11] = max |J|
+  void jumps(int lag) {
+    k_node_jump<<<S.nu, kB, 0, st>>>(S.P, S.G, lag, x, J, part);
+    k_reduce_max2<<<1, 256, 0, st>>>(part, S.nu, sc, 10);
+  }
+};
+
+int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, int* iters_out,
+               double* relres_out, nbm_stream_t stream, bool refined) {
+  GridSolve W;
+  W.who = refined ? "refined grid solve" : "grid CG";
+  W.refined = refined;
+  g_jump_info = JumpInfo();
+  if (int rc = cg_setup(p, n, rtol, max_iter, u_out, W.who, W.S)) return rc;
+  const Grid& G = W.S.G;
+  const int mode = problem_desc(p).grid_jump;
+  W.st = (cudaStream_t)stream;
+  CgBuffers& B = W.B;
+  W.diag = B.get<double>(G.m);
+  W.wx = B.get<double>(G.m);
+  W.wy = B.get<double>(G.m);
+  W.wz = B.get<double>(G.m);
+  W.b = B.get<double>(G.m);
+  W.x = B.get<double>(G.m);
+  W.r = B.get<double>(G.m);
+  W.idg = B.get<double>(G.m);
+  if (mode != NBM_JUMP_EXACT) W.J = B.get<double>(G.m);
+  if (refined) {
+    W.d32 = B.get<float>(G.m);
+    W.wx32 = B.get<float>(G.m);
+    W.wy32 = B.get<float>(G.m);
+    W.wz32 = B.get<float>(G.m);
+    W.idg32 = B.get<float>(G.m);
+    W.r32 = B.get<float>(G.m);
+    W.e32 = B.get<float>(G.m);
+    W.p32 = B.get<float>(G.m);
+    W.Ap32 = B.get<float>(G.m);
+  } else {
+    W.pv = B.get<double>(G.m);
+    W.Ap = B.get<double>(G.m);
+  }
+  W.part = B.get<double>(2 * (size_t)(W.S.nu > W.S.nsp ? W.S.nu : W.S.nsp));
+  W.sc = B.get<double>(16);
+  if (B.err != cudaSuccess) return cg_cuda_fail(W.who, B.err);
+
+  cudaStream_t st = W.st;
+  cudaMemsetAsync(W.x, 0, sizeof(double) * G.m, st);
+  if (W.J) {
+    cudaMemsetAsync(W.J, 0, sizeof(double) * G.m, st);
+    W.jumps(0);
+  }
+  W.rows();
+  if (refined)  // the operator is the same for every pass: round it once
+    k_to_f32<<<W.S.nu, kB, 0, st>>>(G, W.diag, W.wx, W.wy, W.wz, W.idg, W.d32, W.wx32, W.wy32,
+                                     W.wz32, W.idg32);
+  cudaError_t e = cudaSuccess;
+  int status = W.solve(rtol, max_iter, e);
+  JumpInfo info;
+  info.passes = 1;
+  if (mode == NBM_JUMP_EXTRAP && status == NBM_OK) {
+    bool converged = false;
+    while (info.passes < kMaxPasses && !converged) {
+      W.jumps(1);
+      if ((e = W.read_sc()) != cudaSuccess) {
+        status = -1;
+        break;
+      }
+      info.dj = W.host_sc[10];
+      const double jmax = W.host_sc[11];
+      W.rows();
+      ++info.passes;
+      status = W.solve(rtol, max_iter, e);
+      if (status != NBM_OK) break;
+      converged = info.dj <= kJumpTol * (jmax > 1.0 ? jmax : 1.0);
+    }
+    if (status == NBM_OK && !converged) {  // stalled: the first-order jump instead
+      W.jumps(0);
+      W.rows();
+      status = W.solve(rtol, max_iter, e);
+      info.fell_back = 1;
+    }
+  }
+  if (status < 0) return cg_cuda_fail(W.who, e);
+  k_write_nodes<<<(int)((W.S.nodes + kB - 1) / kB), kB, 0, st>>>(W.S.P, G, W.x, u_out);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cg_cuda_fail(W.who, e);
+  g_jump_info = info;
+  const bool converged = status == NBM_OK;
+  return cg_report(W.who, converged, W.iters, W.rnorm, W.bnorm, rtol, iters_out, relres_out);
+}
+
 }  // namespace
 }  // namespace nbm
+
+extern "C" int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
+                                 int* iters_out, double* relres_out, nbm_stream_t stream) {
+  return grid_solve(p, n, rtol, max_iter, u_out, iters_out, relres_out, stream, false);
+}
 
 extern "C" int nbm_grid_solve_refined(nbm_problem* p, int n, double rtol, int max_iter,
                                       double* u_out, int* iters_out, double* relres_out,
                                       nbm_stream_t stream) {
-  const char* who = "refined grid solve";
-  CgSetup S;
-  if (int rc = cg_setup(p, n, rtol, max_iter, u_out, who, S)) return rc;
-  const Grid& G = S.G;
-  cudaStream_t st = (cudaStream_t)stream;
-  CgBuffers B;
-  double *diag = B.get<double>(G.m), *wx = B.get<double>(G.m), *wy = B.get<double>(G.m),
-         *wz = B.get<double>(G.m), *b = B.get<double>(G.m), *x = B.get<double>(G.m),
-         *r64 = B.get<double>(G.m), *idg = B.get<double>(G.m);
-  float *d32 = B.get<float>(G.m), *wx32 = B.get<float>(G.m), *wy32 = B.get<float>(G.m),
-        *wz32 = B.get<float>(G.m), *idg32 = B.get<float>(G.m), *r32 = B.get<float>(G.m),
-        *e32 = B.get<float>(G.m), *p32 = B.get<float>(G.m), *Ap32 = B.get<float>(G.m);
-  double* part = B.get<double>(2 * (size_t)(S.nu > S.nsp ? S.nu : S.nsp));
-  double* sc = B.get<double>(16);
-  if (B.err != cudaSuccess) return cg_cuda_fail(who, B.err);
+  return grid_solve(p, n, rtol, max_iter, u_out, iters_out, relres_out, stream, true);
+}
 
-  k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, G, diag, wx, wy, wz, b, idg);
-  k_to_f32<<<S.nu, kB, 0, st>>>(G, diag, wx, wy, wz, idg, d32, wx32, wy32, wz32, idg32);
-  cudaMemsetAsync(x, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(r64, 0, sizeof(double) * G.m, st);
-  cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
-  // residual of x = 0
-  k_defect<<<S.nu, kB, 0, st>>>(G, b, r64, part);
-  k_reduce_parts<POST_NORM><<<1, 256, 0, st>>>(part, S.nu, 1, sc, 8);
-  double host_sc[16];
-  auto read_sc = [&]() {
-    cudaError_t err = cudaMemcpyAsync(host_sc, sc, sizeof(host_sc), cudaMemcpyDeviceToHost, st);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    return err;
-  };
-  cudaError_t e = read_sc();
-  if (e != cudaSuccess) return cg_cuda_fail(who, e);
-  const double bnorm = sqrt(host_sc[8]);
-  double rnorm = bnorm;
-  int it = 0, stall = 0;
-  bool converged = bnorm == 0.0;
-  while (!converged && it < max_iter && rnorm == rnorm && stall < kMaxStall) {
-    // inner FP32 PCG on A e = r / ||r|| (so its initial residual norm is 1),
-    // stopped at kInnerTol or where the outer target needs no more
-    double tau = 0.5 * rtol * bnorm / rnorm;
-    tau = tau < kInnerTol ? kInnerTol : tau > 0.5 ? 0.5 : tau;
-    k_inner_init<<<S.nu, kB, 0, st>>>(G, sc, r64, idg32, r32, e32, p32, part);
-    k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
-    for (int inner = 1; it < max_iter; ++inner) {
-      k_spmv_dot<float><<<S.sgrid, kB, 0, st>>>(G, S.kz, d32, wx32, wy32, wz32, p32, Ap32, part);
-      k_reduce_parts<POST_ALPHA><<<1, 256, 0, st>>>(part, S.nsp, 1, sc, 1);
-      k_update<float><<<S.nu, kB, 0, st>>>(G, sc, idg32, p32, Ap32, e32, r32, part);
-      k_reduce_parts<POST_BETA><<<1, 256, 0, st>>>(part, S.nu, 2, sc, 3);
-      k_pupdate<float><<<S.nu, kB, 0, st>>>(G, sc, 0, idg32, r32, p32);
-      ++it;
-      if (inner % kCheckEvery == 0 || it == max_iter) {
-        if ((e = read_sc()) != cudaSuccess) return cg_cuda_fail(who, e);
-        const double rin = sqrt(host_sc[4]);
-        if (!(rin == rin) || rin <= tau) break;
-      }
-    }
-    // x += ||r|| e in FP64, then the FP64 residual r = b - A x
-    k_correct<<<S.nu, kB, 0, st>>>(G, sc, e32, x);
-    k_spmv_dot<double><<<S.sgrid, kB, 0, st>>>(G, S.kz, diag, wx, wy, wz, x, r64, part);
-    k_defect<<<S.nu, kB, 0, st>>>(G, b, r64, part);
-    k_reduce_parts<POST_NORM><<<1, 256, 0, st>>>(part, S.nu, 1, sc, 8);
-    if ((e = read_sc()) != cudaSuccess) return cg_cuda_fail(who, e);
-    const double rnew = sqrt(host_sc[8]);
-    stall = rnew > 0.9 * rnorm ? stall + 1 : 0;
-    rnorm = rnew;
-    converged = rnorm <= rtol * bnorm;
-  }
-  k_write_nodes<<<(int)((S.nodes + kB - 1) / kB), kB, 0, st>>>(S.P, G, x, u_out);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cg_cuda_fail(who, e);
-  return cg_report(who, converged, it, rnorm, bnorm, rtol, iters_out, relres_out);
+extern "C" int nbm_grid_last_jump_info(int* passes_out, double* max_dj_out, int* fell_back_out) {
+  if (passes_out) *passes_out = g_jump_info.passes;
+  if (max_dj_out) *max_dj_out = g_jump_info.dj;
+  if (fell_back_out) *fell_back_out = g_jump_info.fell_back;
+  return NBM_OK;
 }

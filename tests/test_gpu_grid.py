@@ -164,3 +164,52 @@ def test_refined_solve_reports_non_convergence_and_bad_arguments():
     with pytest.raises(nbm.NBMError) as e:
         prob.grid_solve_refined(8, rtol=0.0)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("geom,mu_p,n", [(O.GEOM_SPHERE, 10.0, 16), (O.GEOM_FLOWER, 100.0, 14),
+                                         (O.GEOM_SPHERE, 1000.0, 22)])
+@pytest.mark.parametrize("mode", [1, 2], ids=["extrap", "first_order"])
+@pytest.mark.parametrize("solver", ["cg", "refined"])
+def test_grid_jump_modes_match_oracle(geom, mu_p, n, mode, solver):
+    """Extrapolated node jump (lagged small-mu derivative, or first order): the
+    GPU solve equals the oracle's, pass for pass."""
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=geom, mu_minus=1.0, mu_plus=mu_p, grid_jump=mode)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=geom, mu_minus=1.0, mu_plus=mu_p)
+    if geom == O.GEOM_FLOWER:
+        assert _clear_of_interface(o, n)
+    st, ref, it_ref, rr_ref, passes_ref, dj_ref = O.grid_solve_jump(o, n, mode, rtol=1e-12,
+                                                                    max_iter=50000)
+    assert st == 0
+    f = prob.grid_cg_solve if solver == "cg" else prob.grid_solve_refined
+    u, it, rr, ok = f(n, rtol=1e-12, max_iter=50000)
+    passes, dj, fell_back = prob.grid_jump_info()
+    assert ok and rr <= 1e-12 and not fell_back
+    assert passes == passes_ref
+    err = np.max(np.abs(u.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    print(f"jump mode {mode} {solver} geom {geom} mu+ {mu_p} n {n}: {passes} passes, "
+          f"max err {err:.2e}")
+    assert err <= 1e-8
+
+
+@pytest.mark.parametrize("solver", ["cg", "refined"])
+def test_grid_lagged_jump_second_order(solver):
+    """At GPU sizes the lagged jump keeps the grid scheme second order (RMS and
+    L-inf, n = 32, 64, 128); the first-order jump is first order."""
+    nbm = _nbm()
+    o = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    errs = {1: [], 2: []}
+    for mode in (1, 2):
+        prob = nbm.Problem(nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0,
+                                           grid_jump=mode))
+        f = prob.grid_cg_solve if solver == "cg" else prob.grid_solve_refined
+        for n in (32, 64, 128):
+            u, it, rr, ok = f(n, rtol=1e-11, max_iter=100000)
+            passes, dj, fell_back = prob.grid_jump_info()
+            assert ok and not fell_back and (passes == 1) == (mode == 2)
+            errs[mode].append(O.grid_error(o, n, u.cpu().numpy()))
+    print(solver, errs)
+    for i in range(2):
+        assert errs[1][i][0] / errs[1][i + 1][0] > 3.0 and errs[1][i][1] / errs[1][i + 1][1] > 3.5
+        assert 1.5 < errs[2][i][0] / errs[2][i + 1][0] < 3.0

@@ -126,3 +126,23 @@ def test_mesh_level_set_errors():
     a, _ = prob.residual(params, pts)
     b, _ = ref.residual(params, pts)
     assert a == b
+
+
+def test_mesh_level_set_lagged_jump_cg_matches_oracle():
+    """The extrapolated node jump on a mesh level set (projection, normal and
+    fit all through the trilinear interpolant)."""
+    import paper_2210_14907_gb300 as nbm
+    n_phi = 13
+    x = _nodes(n_phi)
+    phi = _flower_phi(x) + 0.013
+    _, o = _pair(0, 64, 2, 2 / 32, phi, n_phi)
+    prob = nbm.Problem(nbm.ProblemDesc(geometry=nbm.GEOM_GRID, mu_minus=1.0, mu_plus=10.0,
+                                       grid_jump=nbm.JUMP_EXTRAP))
+    prob.set_level_set(torch.from_numpy(phi).cuda(), n_phi)
+    st, uref, it_ref, rr_ref, passes_ref, _ = O.grid_solve_jump(o, 14, O.JUMP_EXTRAP, rtol=1e-12,
+                                                                max_iter=20000)
+    assert st == 0
+    u, it, rr, ok = prob.grid_cg_solve(14, rtol=1e-12, max_iter=20000)
+    passes, dj, fell_back = prob.grid_jump_info()
+    assert ok and passes == passes_ref and not fell_back
+    assert np.max(np.abs(u.cpu().numpy() - uref)) <= 1e-8 * np.max(np.abs(uref))
