@@ -40,7 +40,7 @@ WORKLOAD = ("sphere interface (r0=0.5, mu-=1, mu+=10), h=2/128, 262144 uniform c
 BATCH = 262_144
 # DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture
 # summarised in profiles/fused_step_tc_C2.md; None when the kernel changed since.
-FUSED_TRAFFIC_BYTES = 8_950_000  # 8.91 MB read + 0.04 MB write per launch (ncu capture of k_step_tc, profiles/fused_step_tc_C2.md)
+FUSED_TRAFFIC_BYTES = 9_000_000  # 8.94 MB read + 0.07 MB write per launch (ncu capture of k_step_tc, profiles/fused_step_tc_C2.md)
 
 
 def _peaks():
@@ -342,6 +342,65 @@ def table1(dev, epochs, resolutions, lr=1e-3):
             "rows": rows}
 
 
+def grid_solves(hbm_peak, peak_src):
+    """The grid scheme (sphere, mu 1/10) at 128^3 and 256^3 unknown grids to
+    rtol 1e-10: FP64 Jacobi PCG and the refined solve (FP32 inner PCG on FP64
+    residuals), with the exact node jump; and at 256^3 the refined solve with
+    the extrapolated, lagged node jump."""
+    import torch
+
+    import paper_2210_14907_gb300 as nbm
+    out = {}
+    for n in (128, 256):
+        dcg = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+        pcg = nbm.Problem(dcg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ucg, it, rr, ok = pcg.grid_cg_solve(n, rtol=1e-10, max_iter=100000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        m = (n - 1) ** 3
+        gbs = it * 136 * m / wall / 1e9  # algorithmic bytes: SpMV 48 + update 56 + direction 32 per unknown
+        linf, rmse = node_errors(ucg.cpu().numpy(), n)
+        out[f"grid_cg_{n}"] = {"unknowns": m, "iterations": it, "relres": rr, "converged": ok,
+                               "wall_s": wall, "achieved_gbs": gbs,
+                               "hbm_frac": gbs / hbm_peak, "hbm_peak": f"{hbm_peak} GB/s {peak_src} copy",
+                               "linf_exact": linf, "rmse_exact": rmse}
+        del ucg
+        torch.cuda.empty_cache()
+        # the same system to the same FP64 residual test by FP32 inner corrections
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uref, it, rr, ok = pcg.grid_solve_refined(n, rtol=1e-10, max_iter=100000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        gbs = it * 68 * m / wall / 1e9  # FP32 inner iteration: SpMV 24 + update 28 + direction 16 B
+        linf, rmse = node_errors(uref.cpu().numpy(), n)
+        out[f"grid_refined_{n}"] = {"unknowns": m, "inner_iterations": it, "relres": rr,
+                                    "converged": ok, "wall_s": wall, "achieved_gbs": gbs,
+                                    "hbm_frac": gbs / hbm_peak, "linf_exact": linf,
+                                    "rmse_exact": rmse}
+        del uref
+        torch.cuda.empty_cache()
+    dj = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0,
+                         grid_jump=nbm.JUMP_EXTRAP)
+    pj = nbm.Problem(dj)
+    n, m = 256, 255 ** 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    uj, it, rr, ok = pj.grid_solve_refined(n, rtol=1e-10, max_iter=100000)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    passes, djump, fell_back = pj.grid_jump_info()
+    linf, rmse = node_errors(uj.cpu().numpy(), n)
+    out["grid_refined_256_lagged_jump"] = {"unknowns": m, "passes": passes, "fell_back": fell_back,
+                                           "inner_iterations": it, "relres": rr, "converged": ok,
+                                           "wall_s": wall, "linf_exact": linf, "rmse_exact": rmse}
+    del uj
+    torch.cuda.empty_cache()
+    return out
+
+
 def secondary(dev, hbm_peak, peak_src):
     """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
     flower-interface 3->128x4->1 architecture), the mixed training step of the C3
@@ -395,37 +454,7 @@ def secondary(dev, hbm_peak, peak_src):
                                 "tensor_tflops": flops / ms / 1e9, "steps": steps}
         del pt, params, m, v
         torch.cuda.empty_cache()
-    for n in (128, 256):
-        dcg = nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
-        pcg = nbm.Problem(dcg)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ucg, it, rr, ok = pcg.grid_cg_solve(n, rtol=1e-10, max_iter=100000)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        m = (n - 1) ** 3
-        gbs = it * 136 * m / wall / 1e9  # algorithmic bytes: SpMV 48 + update 56 + direction 32 per unknown
-        linf, rmse = node_errors(ucg.cpu().numpy(), n)
-        out[f"grid_cg_{n}"] = {"unknowns": m, "iterations": it, "relres": rr, "converged": ok,
-                               "wall_s": wall, "achieved_gbs": gbs,
-                               "hbm_frac": gbs / hbm_peak, "hbm_peak": f"{hbm_peak} GB/s {peak_src} copy",
-                               "linf_exact": linf, "rmse_exact": rmse}
-        del ucg
-        torch.cuda.empty_cache()
-        # the same system to the same FP64 residual test by FP32 inner corrections
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        uref, it, rr, ok = pcg.grid_solve_refined(n, rtol=1e-10, max_iter=100000)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        gbs = it * 68 * m / wall / 1e9  # FP32 inner iteration: SpMV 24 + update 28 + direction 16 B
-        linf, rmse = node_errors(uref.cpu().numpy(), n)
-        out[f"grid_refined_{n}"] = {"unknowns": m, "inner_iterations": it, "relres": rr,
-                                    "converged": ok, "wall_s": wall, "achieved_gbs": gbs,
-                                    "hbm_frac": gbs / hbm_peak, "linf_exact": linf,
-                                    "rmse_exact": rmse}
-        del uref
-        torch.cuda.empty_cache()
+    out.update(grid_solves(hbm_peak, peak_src))
     return out
 
 
@@ -460,10 +489,18 @@ def main():
                     help="run the Sec. 4.1 convergence study instead of the benchmark")
     ap.add_argument("--table1-epochs", type=int, default=10000)
     ap.add_argument("--table1-n", default="8,16,32,64")
+    ap.add_argument("--grid-only", action="store_true",
+                    help="run only the grid solves (128^3, 256^3) and print their JSON")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.grid_only:
+        import torch
+        torch.cuda.set_device(0)
+        _, _, hbm, peak_src = _peaks()
+        print(json.dumps(grid_solves(hbm, peak_src)))
+        return 0
     if args.table1:
         import torch
         torch.cuda.set_device(0)
@@ -540,6 +577,10 @@ def main():
     dpts = torch.empty(BATCH, 3, device=dev)
     hist = torch.zeros(1, device=dev)
     hloss = torch.zeros(1).pin_memory()
+    for k in range(2):  # untimed: first touch of the pinned buffers and the copy path
+        dpts.copy_(host[k], non_blocking=True)
+        st = prob.train_steps(params, m, v, st, 1, BATCH, seed=1 + rank, pts=dpts, loss_hist=hist)
+        hloss.copy_(hist, non_blocking=True)
     torch.cuda.synchronize()
     _barrier(ws)
     t0 = time.perf_counter()
