@@ -61,24 +61,51 @@ __device__ __forceinline__ void reduce32(float (&v)[32], int lane, float& s) {
   s = v[0];
 }
 
+// tanh of two values into one packed 16-bit pair.  FP16: the pair is packed
+// first and tanh.approx.f16x2 takes both in one SFU operation (the result is
+// the GEMM operand, rounded to FP16 either way).  BF16 keeps the FP32 tanh:
+// a BF16 argument would lose 3 more bits than the output rounding.
+template <bool BF>
+__device__ __forceinline__ uint32_t tanh_pack2(float a, float b) {
+  if constexpr (BF) {
+    return pack2<true>(fast_tanh(a), fast_tanh(b));
+  } else {
+    uint32_t x = pack2<false>(a, b), y;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
+  }
+}
+
 // Points: the (n+1)^3 grid nodes, or (pts != nullptr) npts points pts[3i..3i+2].
+//
+// Two tiles of 128 points are in flight per CTA.  Tile X (0, 1) has its own
+// TMEM accumulator (columns 128 X .. 128 X + 127), activation image,
+// coordinates, flags, output partials and MMA barrier, so the tensor core
+// runs one tile's layer-g GEMM while the CUDA cores run the other tile's
+// epilogue.  Thread (q = warp & 3, cg = warp >> 2) owns unit 32 q + lane
+// (its TMEM lane) and the tile's columns 32 cg .. 32 cg + 31.
+//
+// Pass 0 (the minus network) decides every point's side and keeps it as a
+// 128-bit mask per tile in `side` (bit c: point c is in Omega-); pass 1 reads
+// the mask back instead of evaluating the level set again.
 template <int L, bool BF>
 __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __restrict__ params,
                                                     const unsigned char* __restrict__ wimg, int n,
                                                     const float* __restrict__ pts, int64_t npts,
-                                                    float* __restrict__ u_out, int* status) {
+                                                    float* __restrict__ u_out, uint4* side,
+                                                    int* status) {
   constexpr int H = 128, NG = L - 1;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* Wimg = sm;                       // [NG]
-  unsigned char* Aimg = sm + NG * kImgE;          // [2] ping-pong activations
+  unsigned char* Aimg = sm + NG * kImgE;          // [2] one activation image per tile
   unsigned char* misc = sm + (NG + 2) * kImgE;
   uint64_t* bar_w = (uint64_t*)misc;
-  uint64_t* bar_mma = (uint64_t*)(misc + 8);
-  uint32_t* tslot = (uint32_t*)(misc + 16);
-  float* red = (float*)(misc + 64);               // [4][128]
-  float* xs = red + 512;                          // [3][128] node coordinates
-  int* flag = (int*)(xs + 384);                   // [128]
+  uint64_t* bar_mma = (uint64_t*)(misc + 8);      // [2]
+  uint32_t* tslot = (uint32_t*)(misc + 24);
+  float* red = (float*)(misc + 64);               // [2][4][128] output partials
+  float* xs = red + 1024;                         // [2][3][128] coordinates
+  int* flag = (int*)(xs + 768);                   // [2][128]
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int q = w & 3, cg = w >> 2, u = 32 * q + lane, col0 = 32 * cg;
@@ -87,19 +114,44 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
   if (tid == 0) {
     mbar_init(smem_u32(bar_w), 1);
     mbar_init(smem_u32(bar_mma), 1);
+    mbar_init(smem_u32(bar_mma + 1), 1);
     fence_mbar_init();
   }
-  if (w == 0) tmem_alloc(smem_u32(tslot), 128);
+  if (w == 0) tmem_alloc(smem_u32(tslot), 256);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  uint32_t ph_w = 0, ph_mma = 0;
+  // per-tile state as bit X of a register: MMA barrier phase, and a commit on
+  // bar_mma[X] not yet waited for
+  uint32_t ph_w = 0, ph_bits = 0, pending_bits = 0;
   const int64_t N1 = n + 1, total = pts ? npts : N1 * N1 * N1;
   const int64_t T = (total + 127) / 128;
   const int64_t tb = (int64_t)blockIdx.x * T / gridDim.x, te = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
   const float hg = 2.0f / (float)n;
   bool aborted = false;
+
+  // the layer-g GEMM of tile X: weights g (K-major) x image X (MN-major)
+  auto issue = [&](int X, int g) {
+    if (tid == 0) {
+      fence_after_sync();
+      const uint32_t wa = smem_u32(Wimg + g * kImgE);
+      const uint32_t ab = smem_u32(Aimg + X * kImgE);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        mma_f16(tmem + 128 * X, desc_kmajor(wa, k), desc_mnmajor(ab, k), idf, k > 0);
+      mma_commit(smem_u32(bar_mma + X));
+    }
+    pending_bits |= 1u << X;
+  };
+  // bounded wait for tile X's GEMM; false (every thread) if any thread gave up
+  auto wait_mma = [&](int X) {
+    const bool ok = mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u);
+    ph_bits ^= 1u << X;
+    pending_bits &= ~(1u << X);
+    fence_after_sync();
+    return !__syncthreads_or(!ok);
+  };
 
   for (int s = 0; s < 2 && !aborted; ++s) {
     if (tid == 0) {
@@ -124,109 +176,142 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
         break;
       }
     }
-    for (int64_t t = tb; t < te; ++t) {
-      if (tid < 128) {
-        const int64_t id = t * 128 + tid;
-        int f = 0;
+    for (int64_t t = tb; t < te && !aborted; t += 2) {
+      // coordinates and side flags of both tiles (threads 0..255)
+      int f = 0;
+      if (tid < 256) {
+        const int X = tid >> 7, c = tid & 127;
+        const int64_t id = (t + X) * 128 + c;
+        const bool valid = t + X < te && id < total;
+        int minus = 0;
+        if (s == 1 && valid) {  // the side decided in pass 0
+          const uint4 m = side[t + X];
+          const uint32_t word = (c >> 5) == 0 ? m.x : (c >> 5) == 1 ? m.y : (c >> 5) == 2 ? m.z : m.w;
+          minus = (word >> (c & 31)) & 1u;
+          f = !minus;
+        }
         float x = 0.f, y = 0.f, z = 0.f;
-        if (id < total) {
+        if (valid && (s == 0 || f)) {
           if (pts) {
             x = pts[3 * id];
             y = pts[3 * id + 1];
             z = pts[3 * id + 2];
+          } else if (total <= 0xffffffffll) {  // 32-bit index arithmetic
+            const uint32_t id32 = (uint32_t)id, n1 = (uint32_t)N1, r = id32 / n1;
+            x = -1.f + hg * (float)(id32 - r * n1);
+            y = -1.f + hg * (float)(r % n1);
+            z = -1.f + hg * (float)(r / n1);
           } else {
             const int i = (int)(id % N1), j = (int)((id / N1) % N1), k = (int)(id / (N1 * N1));
             x = -1.f + hg * (float)i;
             y = -1.f + hg * (float)j;
             z = -1.f + hg * (float)k;
           }
-          f = node_phase(P, x, y, z) == s;
         }
-        xs[tid] = x;
-        xs[128 + tid] = y;
-        xs[256 + tid] = z;
-        flag[tid] = f;
+        if (s == 0) {
+          minus = valid && node_phase(P, x, y, z) == 0;
+          f = minus;
+          const uint32_t bits = __ballot_sync(0xffffffffu, minus);
+          if (lane == 0 && t + X < te) ((uint32_t*)&side[t + X])[c >> 5] = bits;  // own tiles only
+        }
+        xs[X * 384 + c] = x;
+        xs[X * 384 + 128 + c] = y;
+        xs[X * 384 + 256 + c] = z;
+        flag[X * 128 + c] = f;
       }
-      if (__syncthreads_count(tid < 128 && flag[tid]) == 0) continue;
-      // layer 1 (FP32) -> 16-bit image
+      const uint32_t act = (__syncthreads_count(tid < 128 && f) > 0 ? 1u : 0u) |
+                           (__syncthreads_count(tid >= 128 && tid < 256 && f) > 0 ? 2u : 0u);
+      if (!act) continue;
+      // layer 1 (FP32 K = 3) of each active tile -> its image; then its GEMM
 #pragma unroll
-      for (int c8 = 0; c8 < 4; ++c8) {
-        float o[8];
+      for (int X = 0; X < 2; ++X) {
+        if (!((act >> X) & 1u)) continue;
+        const float* xx = xs + X * 384;
+        unsigned char* dst = Aimg + X * kImgE;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int c = col0 + 8 * c8 + e;
-          o[e] = fast_tanh(fmaf(w10, xs[c], fmaf(w11, xs[128 + c], fmaf(w12, xs[256 + c], b1))));
+        for (int c8 = 0; c8 < 4; ++c8) {
+          float z[8];
+#pragma unroll
+          for (int h4 = 0; h4 < 2; ++h4) {  // four columns per 16-byte shared load
+            const int c = col0 + 8 * c8 + 4 * h4;
+            const float4 px = *reinterpret_cast<const float4*>(xx + c);
+            const float4 py = *reinterpret_cast<const float4*>(xx + 128 + c);
+            const float4 pz = *reinterpret_cast<const float4*>(xx + 256 + c);
+            z[4 * h4 + 0] = fmaf(w10, px.x, fmaf(w11, py.x, fmaf(w12, pz.x, b1)));
+            z[4 * h4 + 1] = fmaf(w10, px.y, fmaf(w11, py.y, fmaf(w12, pz.y, b1)));
+            z[4 * h4 + 2] = fmaf(w10, px.z, fmaf(w11, py.z, fmaf(w12, pz.z, b1)));
+            z[4 * h4 + 3] = fmaf(w10, px.w, fmaf(w11, py.w, fmaf(w12, pz.w, b1)));
+          }
+          *reinterpret_cast<uint4*>(dst + img_off(u, col0 + 8 * c8)) =
+              make_uint4(tanh_pack2<BF>(z[0], z[1]), tanh_pack2<BF>(z[2], z[3]),
+                         tanh_pack2<BF>(z[4], z[5]), tanh_pack2<BF>(z[6], z[7]));
         }
-        uint4 pk = make_uint4(pack2<BF>(o[0], o[1]), pack2<BF>(o[2], o[3]), pack2<BF>(o[4], o[5]),
-                              pack2<BF>(o[6], o[7]));
-        *reinterpret_cast<uint4*>(Aimg + img_off(u, col0 + 8 * c8)) = pk;
       }
       fence_proxy_async();
       __syncthreads();
-      float last[32];
+      for (int X = 0; X < 2; ++X)
+        if ((act >> X) & 1u) issue(X, 0);
+      // hidden layers: while one tile's epilogue runs, the other tile's GEMM does
 #pragma unroll 1
-      for (int g = 1; g <= NG; ++g) {
-        if (tid == 0) {
-          fence_after_sync();
-          const uint32_t wa = smem_u32(Wimg + (g - 1) * kImgE);
-          const uint32_t ab = smem_u32(Aimg + ((g - 1) & 1) * kImgE);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) mma_f16(tmem, desc_kmajor(wa, k), desc_mnmajor(ab, k), idf, k > 0);
-          mma_commit(smem_u32(bar_mma));
-        }
-        bool ok = mbar_wait_bounded(smem_u32(bar_mma), ph_mma);
-        ph_mma ^= 1u;
-        fence_after_sync();
-        if (__syncthreads_or(!ok)) {
-          if (tid == 0) atomicOr(status, 2);
-          aborted = true;
-          break;
-        }
+      for (int g = 1; g <= NG && !aborted; ++g) {
         float bb = bh[0];
 #pragma unroll
         for (int i = 1; i < NG; ++i) bb = (g - 1 == i) ? bh[i] : bb;
-        float acc[32];
-        tmem_ld32(tmem + lane_base + col0, acc);
-        if (g < NG) {
-          unsigned char* dst = Aimg + (g & 1) * kImgE;
-#pragma unroll
-          for (int c8 = 0; c8 < 4; ++c8) {
-            float o[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) o[e] = fast_tanh(acc[8 * c8 + e] + bb);
-            uint4 pk = make_uint4(pack2<BF>(o[0], o[1]), pack2<BF>(o[2], o[3]),
-                                  pack2<BF>(o[4], o[5]), pack2<BF>(o[6], o[7]));
-            *reinterpret_cast<uint4*>(dst + img_off(u, col0 + 8 * c8)) = pk;
+#pragma unroll 1
+        for (int X = 0; X < 2; ++X) {
+          if (!((act >> X) & 1u)) continue;
+          if (!wait_mma(X)) {
+            aborted = true;
+            break;
           }
-        } else {
+          float acc[32];
+          tmem_ld32(tmem + lane_base + 128 * X + col0, acc);
+          if (g < NG) {
+            unsigned char* dst = Aimg + X * kImgE;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) last[i] = fast_tanh(acc[i] + bb);
+            for (int c8 = 0; c8 < 4; ++c8) {
+              const float* a8 = acc + 8 * c8;
+              *reinterpret_cast<uint4*>(dst + img_off(u, col0 + 8 * c8)) =
+                  make_uint4(tanh_pack2<BF>(a8[0] + bb, a8[1] + bb), tanh_pack2<BF>(a8[2] + bb, a8[3] + bb),
+                             tanh_pack2<BF>(a8[4] + bb, a8[5] + bb), tanh_pack2<BF>(a8[6] + bb, a8[7] + bb));
+            }
+            fence_before_sync();
+            fence_proxy_async();
+            __syncthreads();
+            issue(X, g);
+          } else {
+            // output layer (FP32): the sum over units of wo * tanh
+            float v[32], sres;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = wo * fast_tanh(acc[i] + bb);
+            reduce32(v, lane, sres);
+            red[X * 512 + q * 128 + col0 + lane] = sres;
+          }
         }
-        fence_before_sync();
-        fence_proxy_async();
-        __syncthreads();
       }
       if (aborted) break;
-      // output layer (FP32): sum over units
-      {
-        float v[32], sres;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = wo * last[i];
-        reduce32(v, lane, sres);
-        red[q * 128 + col0 + lane] = sres;
-      }
+      fence_before_sync();
       __syncthreads();
-      if (tid < 128 && flag[tid]) {
-        const int64_t id = t * 128 + tid;
-        u_out[id] = red[tid] + red[128 + tid] + red[256 + tid] + red[384 + tid] + bo;
+      if (tid < 256) {
+        const int X = tid >> 7, c = tid & 127;
+        if (((act >> X) & 1u) && flag[X * 128 + c]) {
+          const float* r = red + X * 512;
+          u_out[(t + X) * 128 + c] = r[c] + r[128 + c] + r[256 + c] + r[384 + c] + bo;
+        }
       }
       __syncthreads();
     }
   }
+  if (aborted) {
+    if (tid == 0) atomicOr(status, 2);
+    // let any GEMM still committed finish (bounded) before TMEM is released
+    for (int X = 0; X < 2; ++X)
+      if ((pending_bits >> X) & 1u) (void)mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u);
+  }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  if (w == 0) tmem_dealloc(tmem, 128);
+  if (w == 0) tmem_dealloc(tmem, 256);
 }
 
 // Plain FP32 evaluation: one thread per node, activations in shared memory
@@ -352,13 +437,13 @@ cudaError_t launch_eval_small(const ProbDev& P, const float* params, int n, cons
 
 template <int L, bool BF>
 cudaError_t launch_eval_tc_t(const ProbDev& P, const float* params, const unsigned char* wimg,
-                             int n, const float* pts, int64_t npts, float* u, int grid, int* status,
-                             cudaStream_t st) {
-  const size_t smem = (size_t)(L + 1) * kImgE + 1024 + 8192;
+                             int n, const float* pts, int64_t npts, float* u, uint4* side,
+                             int grid, int* status, cudaStream_t st) {
+  const size_t smem = (size_t)(L + 1) * kImgE + 1024 + 12288;
   cudaError_t e = cudaFuncSetAttribute(k_eval_tc<L, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_eval_tc<L, BF><<<grid, 512, smem, st>>>(P, params, wimg, n, pts, npts, u, status);
+  k_eval_tc<L, BF><<<grid, 512, smem, st>>>(P, params, wimg, n, pts, npts, u, side, status);
   return cudaGetLastError();
 }
 
@@ -423,8 +508,11 @@ static int eval_common(nbm_problem* p, const float* params, int n, const float* 
     const size_t bytes = (size_t)2 * (d.n_hidden - 1) * kImgE;
     unsigned char* wimg = nullptr;
     int* status = nullptr;
+    uint4* side = nullptr;  // per 128-point tile: bit c set if point c is in Omega-
+    const int64_t total = pts ? npts : (int64_t)(n + 1) * (n + 1) * (n + 1);
     e = cudaMalloc((void**)&wimg, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&side, sizeof(uint4) * (size_t)((total + 127) / 128));
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
     Workspace tmp;
     tmp.wtc = wimg;
@@ -432,18 +520,19 @@ static int eval_common(nbm_problem* p, const float* params, int n, const float* 
     const int grid = problem_num_sms(p);
     const bool bf = precision == NBM_PREC_BF16;
     if (e == cudaSuccess) {
-      if (d.n_hidden == 2) e = bf ? launch_eval_tc_t<2, true>(P, params, wimg, n, pts, npts, u_out, grid, status, st)
-                                  : launch_eval_tc_t<2, false>(P, params, wimg, n, pts, npts, u_out, grid, status, st);
-      else if (d.n_hidden == 3) e = bf ? launch_eval_tc_t<3, true>(P, params, wimg, n, pts, npts, u_out, grid, status, st)
-                                       : launch_eval_tc_t<3, false>(P, params, wimg, n, pts, npts, u_out, grid, status, st);
-      else e = bf ? launch_eval_tc_t<4, true>(P, params, wimg, n, pts, npts, u_out, grid, status, st)
-                  : launch_eval_tc_t<4, false>(P, params, wimg, n, pts, npts, u_out, grid, status, st);
+      if (d.n_hidden == 2) e = bf ? launch_eval_tc_t<2, true>(P, params, wimg, n, pts, npts, u_out, side, grid, status, st)
+                                  : launch_eval_tc_t<2, false>(P, params, wimg, n, pts, npts, u_out, side, grid, status, st);
+      else if (d.n_hidden == 3) e = bf ? launch_eval_tc_t<3, true>(P, params, wimg, n, pts, npts, u_out, side, grid, status, st)
+                                       : launch_eval_tc_t<3, false>(P, params, wimg, n, pts, npts, u_out, side, grid, status, st);
+      else e = bf ? launch_eval_tc_t<4, true>(P, params, wimg, n, pts, npts, u_out, side, grid, status, st)
+                  : launch_eval_tc_t<4, false>(P, params, wimg, n, pts, npts, u_out, side, grid, status, st);
     }
     int hs = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (wimg) cudaFree(wimg);
     if (status) cudaFree(status);
+    if (side) cudaFree(side);
     if (e == cudaSuccess && (hs & 2)) {
       set_error_message("grid evaluation: a bounded device wait gave up");
       return NBM_ERR_DEVICE_TIMEOUT;

@@ -66,6 +66,30 @@ def test_eval_grid_tensor_cores_match_oracle(prec, tol, L, n):
     assert err <= tol
 
 
+@pytest.mark.parametrize("prec,tol", [(2, 2e-3), (1, 1e-2)], ids=["fp16", "bf16"])
+@pytest.mark.parametrize("L", [3, 4])
+def test_eval_grid_tensor_cores_at_size(prec, tol, L):
+    """Grids of many tiles per CTA (161^3 nodes, about 27 tile pairs per SM), so
+    both tiles of a pair are in flight, across mixed flower tiles: the 16-bit
+    tensor-core evaluation against the FP32 path (itself equal to the oracle)."""
+    nbm = _nbm()
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_FLOWER, n_hidden=L, width=128)
+    prob = nbm.Problem(d)
+    th = torch.from_numpy(inputs.glorot_params(128, L, seed=23, bias_scale=0.2)).cuda()
+    n = 160
+    ref = prob.eval_grid(th, n, precision=nbm.PREC_FP32).double()
+    got = prob.eval_grid(th, n, precision=prec).double()
+    err = (torch.linalg.norm(got - ref) / torch.linalg.norm(ref)).item()
+    mx = (torch.max(torch.abs(got - ref)) / torch.max(torch.abs(ref))).item()
+    print(f"eval at size prec {prec} L {L}: rel {err:.2e}, max {mx:.2e}")
+    assert err <= tol and mx <= 4 * tol
+    gen = torch.Generator(device="cuda").manual_seed(29)
+    pts = (torch.rand(100_003, 3, device="cuda", generator=gen) * 1.9 - 0.95).contiguous()
+    a = prob.eval_points(th, pts, precision=nbm.PREC_FP32).double()
+    b = prob.eval_points(th, pts, precision=prec).double()
+    assert (torch.linalg.norm(b - a) / torch.linalg.norm(a)).item() <= tol
+
+
 @pytest.mark.parametrize("geom,mu_p,n", [(O.GEOM_SPHERE, 10.0, 16), (O.GEOM_FLOWER, 100.0, 14),
                                          (O.GEOM_ALL_MINUS, 10.0, 9)])
 def test_grid_cg_matches_oracle(geom, mu_p, n):
