@@ -372,6 +372,9 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
     int tile_i = 0;  // index of the half-tile among this group's tiles of the segment
 #pragma unroll 1
     for (int tau = s0 + grp; tau < s1; tau += 2, ++tile_i, ++kk) {
+      // layer-1 weights of this thread's unit, loaded while the records arrive
+      const float w1[3] = {__ldg(th + 3 * u), __ldg(th + 3 * u + 1), __ldg(th + 3 * u + 2)};
+      const float b1 = __ldg(th + 3 * H + u);
       // ---- tile records (prefetched during the previous tile)
       {
         const bool ok = mbar_wait_bounded(smem_u32(bar_p), ph_p);
@@ -398,8 +401,6 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 
       // ---- layer 1 (3 -> H) in FP32; exact increments mu = 0, del_i = h W1[u][i]
       {
-        const float w1[3] = {__ldg(th + 3 * u), __ldg(th + 3 * u + 1), __ldg(th + 3 * u + 2)};
-        const float b1 = __ldg(th + 3 * H + u);
         const float dl1[3] = {SCALED ? w1[0] : w1[0] * P.hf, SCALED ? w1[1] : w1[1] * P.hf,
                               SCALED ? w1[2] : w1[2] * P.hf};
 #pragma unroll
@@ -425,6 +426,8 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       float last[32];
 #pragma unroll 1
       for (int g = 1; g <= NG; ++g) {
+        // the layer's bias, loaded while the GEMM runs
+        const float bb = __ldg(th + 4 * H + (g - 1) * (H * H + H) + H * H + u);
         if (gtid == 0 && gate(0)) {
           const uint32_t wa = smem_u32(Wimg + (g - 1) * kImg);
           const uint32_t ab = smem_u32(Aimg + (g - 1) * kImgH);
@@ -437,7 +440,6 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
           aborted = true;
           break;
         }
-        const float bb = __ldg(th + 4 * H + (g - 1) * (H * H + H) + H * H + u);
         float acc[32];
         tmem_ld32(d_tm + lane_base + col0, acc);
 #pragma unroll

@@ -40,3 +40,25 @@ def test_invalid_descriptor_is_rejected_without_a_gpu():
     rc = lib.nbm_init_problem(ctypes.byref(d), ctypes.byref(h))
     assert rc == 1 and h.value is None
     assert b"width" in lib.nbm_last_error()
+
+
+@pytest.mark.parametrize("field,value,word", [("grid_jump", 3, b"grid_jump"),
+                                              ("grid_jump", -1, b"grid_jump"),
+                                              ("reserved0", 1, b"reserved0"),
+                                              ("refine_levels", 4, b"refine_levels"),
+                                              ("activation", 2, b"activation")])
+def test_descriptor_fields_are_validated_without_a_gpu(field, value, word):
+    import paper_2210_14907_gb300 as nbm
+    lib = nbm.load_library()
+    d = nbm.ProblemDesc().to_c()
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.nbm_init_problem(ctypes.byref(d), ctypes.byref(h)) == 1 and h.value is None
+    assert word in lib.nbm_last_error()
+
+
+def test_descriptor_layout_matches_the_header():
+    """The ctypes mirror has the C struct's size: every field in order, no
+    padding surprises (int32 tail padded to 8 bytes)."""
+    import paper_2210_14907_gb300 as nbm
+    assert ctypes.sizeof(nbm._Desc) == 4 * 4 + 11 * 8 + 6 * 4
