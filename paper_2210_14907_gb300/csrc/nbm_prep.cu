@@ -332,9 +332,10 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
                                                       float* seeds, float scale, float* r2_out,
                                                       double* loss_part) {
   __shared__ double red[128];
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0;
-  if (id < counters[2]) {
+  const int nc = counters[2];
+  double r2_sum = 0.0;  // this thread's cells (grid-stride), then the block partial
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nc; id += gridDim.x * blockDim.x) {
+    double r2 = 0.0;
     CutRec c = cut[id];
     const int i = c.point;
     const double h = P.h, h2 = h * h;
@@ -398,8 +399,9 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
       }
     }
     if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
+    r2_sum += r2;
   }
-  red[threadIdx.x] = r2;
+  red[threadIdx.x] = r2_sum;
   __syncthreads();
   for (int o = 64; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -561,14 +563,28 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
                               float* m, float* v, float lr, float b1, float b2, float eps,
                               const float* corr, const double* loss, float* wt, void* wtc,
                               int prec, const float* gacc_in, float* gacc_out) {
+  // Block of 256 threads: 32 consecutive parameters (lane) x 8 groups of the
+  // per-CTA partial slices (group cg sums slices cg, cg + 8, ...); the groups
+  // are then added in a fixed order, so the sum is deterministic.
+  __shared__ float red[8][33];
   const int64_t pn = P.p_net;
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= 2 * pn) return;
-  const int s = (int)(j / pn);
+  const int lane = threadIdx.x & 31, cg = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+  const bool in = j < 2 * pn;
+  const int s = in ? (int)(j / pn) : 0;
   const int64_t jj = j - s * pn;
-  float g = 0.f;
-  for (int c = 0; c < grid; ++c)
-    if (flag[2 * c + s]) g += gpart[((int64_t)c * 2 + s) * P.gstride + jj];
+  float part = 0.f;
+  if (in) {
+#pragma unroll 4
+    for (int c = cg; c < grid; c += 8)
+      if (flag[2 * c + s]) part += gpart[((int64_t)c * 2 + s) * P.gstride + jj];
+  }
+  red[cg][lane] = part;
+  __syncthreads();
+  if (cg != 0 || !in) return;
+  float g = red[0][lane];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) g += red[q][lane];
   if (gacc_in) g += gacc_in[j];
   if (gacc_out) {
     gacc_out[j] = g;
@@ -626,9 +642,16 @@ cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cuda
   return cudaGetLastError();
 }
 
+// blocks of the cut-row kernel (grid-stride over the cut cells), i.e. the
+// number of its loss partials
+int cut_residual_blocks(int64_t n, const Workspace& ws) {
+  const int64_t worst = (n + 127) / 128, cap = 4 * (int64_t)ws.grid;
+  return (int)(worst < cap ? worst : cap);
+}
+
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
                                 float* r2_out, Workspace& ws, cudaStream_t st) {
-  int nb = (int)((n + 127) / 128);
+  int nb = cut_residual_blocks(n, ws);
   k_cut_residual<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.counters, ws.cut, ws.cut_out,
                                      want_seeds ? ws.cut_seed : nullptr, scale, r2_out,
                                      ws.cut_loss_part);
@@ -655,13 +678,13 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
                           Workspace& ws, cudaStream_t st, int level, int n_levels) {
   const bool last = level == n_levels - 1;
-  int ncb = (int)((n + 127) / 128);
+  int ncb = cut_residual_blocks(n, ws);
   k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb, 1.0 / (double)n, ws.loss,
                             adam ? ws.step : nullptr, loss_hist, hist_base, ws.status, b1, b2,
                             ws.corr, ws.loss_acc, level > 0, last);
   if (adam || want_grad) {
     int64_t tot = 2 * P.p_net;
-    k_reduce_adam<<<(int)((tot + 255) / 256), 256, 0, st>>>(
+    k_reduce_adam<<<(int)((tot + 31) / 32), 256, 0, st>>>(
         P, grid, ws.gpart, ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps,
         ws.corr, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
         level > 0 ? ws.gacc : nullptr, last ? nullptr : ws.gacc);
