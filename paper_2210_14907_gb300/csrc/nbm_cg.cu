@@ -1,17 +1,22 @@
 // nbm_cg.cu -- the plain mesh-based method the NBM is bootstrapped from
 // (arXiv 2210.14907, Sec. 1 and Sec. 3): the same finite-volume balance row on
 // the nodes of a grid of spacing h = 2/n, one unknown per interior node, solved
-// by Jacobi-preconditioned conjugate gradients in FP64.  HBM-bound: every
-// iteration streams the operator (diagonal + three face weights per node) and
-// five vectors.
+// by Jacobi-preconditioned conjugate gradients in FP64 (nbm_grid_cg_solve), or
+// to the same FP64 residual test by FP32 inner PCG corrections of FP64
+// residuals (nbm_grid_solve_refined).  Each iteration streams the operator
+// (diagonal + three face weights per node) and five vectors; in FP64 the
+// SpMV is bound by GB300's narrow FP64 pipe, in FP32 the kernels by HBM.
 //
 // Row of interior node p (cell p + [-h/2, h/2]^3, fractions as in nbm_geom.cuh):
 //   sum_f w_f (u_p - u_q) + h^2 sum_s V^s k^s u_p = -known_p,
 //   w_f = sum_s A^s_f mu^s  (shared by the two cells of the face: A is SPD),
 // where the value of network/side s at a node q of the other side is u_q plus
-// the jump u+ - u- of the manufactured pair at q (the "exact jump" extension);
-// all such terms, the source, the interface flux h S beta and the Dirichlet
-// data move to the right-hand side.
+// the value jump J(q) = u+ - u- carried to q: the manufactured pair's own
+// u+(q) - u-(q) (the exact jump), or alpha(x_G) + d [d_n u] extrapolated from
+// the interface (k_node_jump; the normal derivative of the small-mu side
+// lagged from the previous solve, or dropped); all such terms, the source,
+// the interface flux h S beta and the Dirichlet data move to the right-hand
+// side.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -142,7 +147,7 @@ __device__ inline void block_partials(T (&v)[NV], double* part, int64_t idx, int
 // residual, 10 max |dJ|, 11 max |J|.  After the sum, POST_ALPHA sets
 // alpha = rz / pAp, POST_BETA sets beta = rz_new / rz, rz = rz_new, and
 // POST_NORM sets ||r|| and its inverse; POST_SKIP leaves the partials unused.
-enum { POST_SKIP = -1, POST_NONE = 0, POST_ALPHA = 1, POST_BETA = 2, POST_NORM = 3 };
+enum { POST_SKIP = -1, POST_ALPHA = 1, POST_BETA = 2, POST_NORM = 3 };
 
 // The sum over a launch's block partials, done by its last block: each block
 // takes a ticket after a device-scope fence (its partials are written); the
