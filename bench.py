@@ -401,7 +401,7 @@ def grid_solves(hbm_peak, peak_src):
     return out
 
 
-def secondary(dev, hbm_peak, peak_src):
+def secondary(dev, hbm_peak, peak_src, tc_burst, tc_sustained):
     """Grid evaluation (a dense 513^3 node grid, FP16 tcgen05 hidden layers, the
     flower-interface 3->128x4->1 architecture), the mixed training step of the C3
     and C4 workloads, and the grid solve of the same discretization at 128^3 and
@@ -430,7 +430,9 @@ def secondary(dev, hbm_peak, peak_src):
     flops = nodes * 3 * 2 * 128 * 128  # hidden GEMMs of the node's own network
     out["eval_grid"] = {"metric": "grid points/s (trained-surrogate inference)", "value": nodes / ms * 1e3,
                         "unit": "grid points/s", "grid": "513^3 nodes", "precision": "fp16",
-                        "ms": ms, "tensor_tflops": flops / ms / 1e9}
+                        "ms": ms, "tensor_tflops": flops / ms / 1e9,
+                        "tensor_frac": flops / ms / 1e9 / tc_burst,
+                        "tensor_peak": f"{tc_burst} TFLOP/s {peak_src} dense 16-bit, burst (kernel timed alone)"}
     del u
     torch.cuda.empty_cache()
     # the other training workloads: flower with 30 % band points (C3) and the
@@ -451,7 +453,8 @@ def secondary(dev, hbm_peak, peak_src):
         ms = a.elapsed_time(b) / steps
         flops = B * 21 * (dt.n_hidden - 1) * 2 * 128 * 128
         out[f"train_{name}"] = {"points_per_s": B / ms * 1e3, "ms_per_step": ms, "batch": B,
-                                "tensor_tflops": flops / ms / 1e9, "steps": steps}
+                                "tensor_tflops": flops / ms / 1e9,
+                                "tensor_frac": flops / ms / 1e9 / tc_sustained, "steps": steps}
         del pt, params, m, v
         torch.cuda.empty_cache()
     out.update(grid_solves(hbm_peak, peak_src))
@@ -621,7 +624,7 @@ def main():
             "roofline": roof, "e2e": e2e, "gpu_launches": 9 * args.steps,
             "clocks": clk.summary(), "wall_s": wall}
     if ws == 1 and not args.no_secondary:
-        line["secondary"] = secondary(dev, hbm, peak_src)
+        line["secondary"] = secondary(dev, hbm, peak_src, burst, sustained)
     if ws == 1 and not args.no_accuracy:
         line["accuracy"] = accuracy(dev)
     if ws == 1 and not args.no_cpu_baseline:
