@@ -144,13 +144,16 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
     }
     pending_bits |= 1u << X;
   };
-  // bounded wait for tile X's GEMM; false (every thread) if any thread gave up
+  // bounded wait for tile X's GEMM (this thread's result; the CTA agrees on an
+  // abort at the barrier that ends the epilogue)
   auto wait_mma = [&](int X) {
     const bool ok = mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u);
-    ph_bits ^= 1u << X;
-    pending_bits &= ~(1u << X);
+    if (ok) {  // a wait that gave up leaves the GEMM pending for the exit path
+      ph_bits ^= 1u << X;
+      pending_bits &= ~(1u << X);
+    }
     fence_after_sync();
-    return !__syncthreads_or(!ok);
+    return ok;
   };
 
   for (int s = 0; s < 2 && !aborted; ++s) {
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
     const float wo = th[oo + u], bo = th[oo + H];
     {
       bool ok = mbar_wait_bounded(smem_u32(bar_w), ph_w);
-      ph_w ^= 1u;
+      if (ok) ph_w ^= 1u;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(status, 2);
         aborted = true;
@@ -252,6 +255,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
       for (int X = 0; X < 2; ++X)
         if ((act >> X) & 1u) issue(X, 0);
       // hidden layers: while one tile's epilogue runs, the other tile's GEMM does
+      bool ok_all = true;  // this thread's MMA waits of the pair
 #pragma unroll 1
       for (int g = 1; g <= NG && !aborted; ++g) {
         float bb = bh[0];
@@ -260,10 +264,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
 #pragma unroll 1
         for (int X = 0; X < 2; ++X) {
           if (!((act >> X) & 1u)) continue;
-          if (!wait_mma(X)) {
-            aborted = true;
-            break;
-          }
+          ok_all = wait_mma(X) && ok_all;
           float acc[32];
           tmem_ld32(tmem + lane_base + 128 * X + col0, acc);
           if (g < NG) {
@@ -277,7 +278,10 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
             }
             fence_before_sync();
             fence_proxy_async();
-            __syncthreads();
+            if (__syncthreads_or(!ok_all)) {
+              aborted = true;
+              break;
+            }
             issue(X, g);
           } else {
             // output layer (FP32): the sum over units of wo * tanh
@@ -291,7 +295,10 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
       }
       if (aborted) break;
       fence_before_sync();
-      __syncthreads();
+      if (__syncthreads_or(!ok_all)) {
+        aborted = true;
+        break;
+      }
       if (tid < 256) {
         const int X = tid >> 7, c = tid & 127;
         if (((act >> X) & 1u) && flag[X * 128 + c]) {
@@ -304,9 +311,11 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
   }
   if (aborted) {
     if (tid == 0) atomicOr(status, 2);
-    // let any GEMM still committed finish (bounded) before TMEM is released
+    // let any GEMM still committed, and a weight copy that a wait gave up on,
+    // finish (bounded) before TMEM and shared memory are released
     for (int X = 0; X < 2; ++X)
       if ((pending_bits >> X) & 1u) (void)mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u);
+    (void)mbar_wait_bounded(smem_u32(bar_w), ph_w, 2000000LL);
   }
   fence_before_sync();
   __syncthreads();

@@ -242,10 +242,22 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 
   // Completion of this group's MMA phase; false (and the CTA-wide abort flag
   // set) if the wait ran out or either group gave up.
+  // Bounded wait for the group's MMA phase (no group barrier: the one that ends
+  // the phase's epilogue agrees on an abort; until then a thread whose wait
+  // gave up only computes on undefined accumulator values).
   auto wait_mma = [&]() -> bool {
     const bool ok = mbar_wait_bounded(smem_u32(bar_mma), ph_mma);
-    ph_mma ^= 1u;
+    if (ok) ph_mma ^= 1u;  // a wait that gave up leaves the phase for the exit drain
     fence_after_sync();
+    return ok;
+  };
+  // The group barrier that ends an MMA phase's epilogue.  It orders the
+  // epilogue's shared-memory images before the next MMA, keeps every thread
+  // within one phase of bar_mma, and agrees on an abort (a wait that gave up,
+  // or the abort flag).  False: abort.
+  auto end_phase = [&](bool ok) -> bool {
+    fence_before_sync();
+    fence_proxy_async();
     const bool bad = named_sync_or(gbar, 256, !ok || *abort_f != 0);
     if (bad && gtid == 0) {
       if (!ok) atomicOr(a.status, 2);
@@ -361,7 +373,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
     }
     {
       const bool ok = mbar_wait_bounded(smem_u32(bar_w), ph_w);
-      ph_w ^= 1u;
+      if (ok) ph_w ^= 1u;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(a.status, 2);
         aborted = true;
@@ -378,7 +390,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       // ---- tile records (prefetched during the previous tile)
       {
         const bool ok = mbar_wait_bounded(smem_u32(bar_p), ph_p);
-        ph_p ^= 1u;
+        if (ok) ph_p ^= 1u;
         if (named_sync_or(gbar, 256, !ok || *abort_f != 0)) {
           if (gtid == 0) {
             if (!ok) atomicOr(a.status, 2);
@@ -436,10 +448,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
             mma_f16(d_tm, desc_kmajor(wa, k), desc_mnmajor(ab, k), id_fwd, k > 0);
           mma_commit(smem_u32(bar_mma));
         }
-        if (!wait_mma()) {
-          aborted = true;
-          break;
-        }
+        const bool ok_w = wait_mma();
         float acc[32];
         tmem_ld32(d_tm + lane_base + col0, acc);
 #pragma unroll
@@ -464,9 +473,10 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
             for (int c2 = 0; c2 < 8; ++c2) last[8 * j + c2] = o[c2];
           }
         }
-        fence_before_sync();
-        fence_proxy_async();
-        named_sync(gbar, 256);
+        if (!end_phase(ok_w)) {
+          aborted = true;
+          break;
+        }
       }
       if (aborted) break;
 
@@ -612,11 +622,8 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
                     (k > 0 || acc_w) ? 1u : 0u);
           mma_commit(smem_u32(bar_mma));
         }
-        if (!wait_mma()) {
-          aborted = true;
-          break;
-        }
-        if (gtid == 0) st_release_s32(done_cnt + grp, nph + 1);
+        const bool ok_w = wait_mma();
+        if (gtid == 0 && ok_w) st_release_s32(done_cnt + grp, nph + 1);
         unsigned char* img = Aimg + (g - 1) * kImgH;  // state of act[g-1]
         float G[16];  // two points at a time: registers are short here
 #pragma unroll
@@ -650,9 +657,10 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
             gb1 += gz[0] + gz[7];
           }
         }
-        fence_before_sync();
-        fence_proxy_async();
-        named_sync(gbar, 256);
+        if (!end_phase(ok_w)) {
+          aborted = true;
+          break;
+        }
       }
       if (aborted) break;
     }
@@ -679,6 +687,15 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       a.gpart_flag[2 * blockIdx.x] = aborted ? 0 : wrote0;
       a.gpart_flag[2 * blockIdx.x + 1] = aborted ? 0 : wrote1;
     }
+  }
+  if (aborted) {
+    // an MMA or record copy of this group may still be in flight: give it a
+    // short bounded wait (about 1 ms) before TMEM and shared memory are released
+    (void)mbar_wait_bounded(smem_u32(bar_mma), ph_mma, 2000000LL);
+    (void)mbar_wait_bounded(smem_u32(bar_p), ph_p, 2000000LL);
+    (void)mbar_wait_bounded(smem_u32(bar_w), ph_w, 2000000LL);
+    fence_before_sync();
+    __syncthreads();
   }
   fence_after_sync();
   if (w == 0) tmem_dealloc(tmem, NCOLS);
