@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
   float* red = (float*)(misc + 64);               // [2][4][128] output partials
   float* xs = red + 1024;                         // [2][3][128] coordinates
   int* flag = (int*)(xs + 768);                   // [2][128]
+  int* actw = flag + 256;  // [2][8] staging warps with a point of the side, by pair parity
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int q = w & 3, cg = w >> 2, u = 32 * q + lane, col0 = 32 * cg;
@@ -179,7 +180,10 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
         break;
       }
     }
-    for (int64_t t = tb; t < te && !aborted; t += 2) {
+    for (int64_t t = tb, pair = 0; t < te && !aborted; t += 2, ++pair) {
+      // actw alternates between two halves: a pair without active tiles has no
+      // barrier after its reads, so the next pair must not overwrite them
+      int* aw = actw + 8 * (int)(pair & 1);
       // coordinates and side flags of both tiles (threads 0..255)
       int f = 0;
       if (tid < 256) {
@@ -221,9 +225,12 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
         xs[X * 384 + 128 + c] = y;
         xs[X * 384 + 256 + c] = z;
         flag[X * 128 + c] = f;
+        const uint32_t any = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) aw[w] = any != 0u;
       }
-      const uint32_t act = (__syncthreads_count(tid < 128 && f) > 0 ? 1u : 0u) |
-                           (__syncthreads_count(tid >= 128 && tid < 256 && f) > 0 ? 2u : 0u);
+      __syncthreads();
+      const uint32_t act = ((aw[0] | aw[1] | aw[2] | aw[3]) ? 1u : 0u) |
+                           ((aw[4] | aw[5] | aw[6] | aw[7]) ? 2u : 0u);
       if (!act) continue;
       // layer 1 (FP32 K = 3) of each active tile -> its image; then its GEMM
 #pragma unroll
@@ -306,7 +313,9 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
           u_out[(t + X) * 128 + c] = r[c] + r[128 + c] + r[256 + c] + r[384 + c] + bo;
         }
       }
-      __syncthreads();
+      // no barrier here: each thread rewrites only its own flag slot in the
+      // next staging, and xs, red, the images and TMEM are next written after
+      // the next pair's barriers
     }
   }
   if (aborted) {
