@@ -40,7 +40,7 @@ WORKLOAD = ("sphere interface (r0=0.5, mu-=1, mu+=10), h=2/128, 262144 uniform c
 BATCH = 262_144
 # DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture
 # summarised in profiles/fused_step_tc_C2.md; None when the kernel changed since.
-FUSED_TRAFFIC_BYTES = 9_000_000  # 8.94 MB read + 0.07 MB write per launch (ncu capture of k_step_tc, profiles/fused_step_tc_C2.md)
+FUSED_TRAFFIC_BYTES = 9_010_000  # 8.93 MB read + 0.08 MB write per launch (ncu capture of k_step_tc, profiles/fused_step_tc_C2.md)
 
 
 def _peaks():
