@@ -3,12 +3,13 @@
 // u at the (n+1)^3 nodes -1 + i 2/n, each node with the network of its side
 // of the interface (phi <= 0: minus).
 //
-// Tensor-core path: a persistent CTA per SM walks its tiles of 128 nodes once
-// per network (the network's hidden weights are staged in shared memory once
-// per pass; tiles without a node of that side are skipped).  Layer 1 (K = 3)
-// and the output layer run in FP32; every hidden layer is one 128x128x128
-// tcgen05 MMA with 16-bit operands (FP16 or BF16) and FP32 accumulation in
-// TMEM.  The FP32 path is a plain SIMT evaluation (reference precision).
+// Tensor-core path: a persistent CTA per SM walks its tiles of 128 nodes, two
+// at a time, once per network (the network's hidden weights are staged in
+// shared memory once per pass; tiles without a node of that side are
+// skipped).  Layer 1 (K = 3) and the output layer run in FP32; every hidden
+// layer is one 128x128x128 tcgen05 MMA with 16-bit operands (FP16 or BF16)
+// and FP32 accumulation in TMEM.  The FP32 path is a plain SIMT evaluation
+// (reference precision).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
