@@ -360,7 +360,7 @@ def grid_solves(hbm_peak, peak_src):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         m = (n - 1) ** 3
-        gbs = it * 136 * m / wall / 1e9  # algorithmic bytes: SpMV 48 + update 56 + direction 32 per unknown
+        gbs = it * 120 * m / wall / 1e9  # algorithmic bytes (scaled system): SpMV 40 + update 56 + direction 24 per unknown
         linf, rmse = node_errors(ucg.cpu().numpy(), n)
         out[f"grid_cg_{n}"] = {"unknowns": m, "iterations": it, "relres": rr, "converged": ok,
                                "wall_s": wall, "achieved_gbs": gbs,

@@ -64,7 +64,7 @@ __device__ inline void jump_corr(double jmp, int sx, double c[2]) {
 // u+(x) - u-(x) (the exact jump).
 __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, const double* __restrict__ Jn,
                                                   double* diag, double* wx, double* wy, double* wz,
-                                                  double* rhs, double* inv_diag) {
+                                                  double* rhs) {
   const int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (r >= G.m) return;
   int idx[3];
@@ -111,11 +111,27 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, const doubl
   }
   if (cg.cut && cg.has_jump) known += h * cg.S * beta_d(P, cg.xg);
   diag[r] = dg;
-  inv_diag[r] = 1.0 / dg;  // the Jacobi preconditioner, applied by multiplication
   wx[r] = wplus[0];
   wy[r] = wplus[1];
   wz[r] = wplus[2];
   rhs[r] = -known;
+}
+
+// The Jacobi-scaled system D^-1/2 A D^-1/2 x^ = D^-1/2 b, x = D^-1/2 x^ (D =
+// diag A): unit diagonal, face weights w / sqrt(d_p d_q), in place.  CG on it
+// is Jacobi-preconditioned CG on A in exact arithmetic, and it reads neither
+// the diagonal nor its inverse in the SpMV or the direction update.
+__global__ void __launch_bounds__(kB) k_scale_rows(Grid G, const double* __restrict__ diag,
+                                                   double* wx, double* wy, double* wz, double* b) {
+  const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
+  for (int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x; r < G.m; r += (int64_t)gridDim.x * kB) {
+    const int i = (int)(r % G.m1), j = (int)((r / G.m1) % G.m1), k = (int)(r / s2);
+    const double dr = diag[r];
+    if (i + 1 < G.m1) wx[r] /= sqrt(dr * diag[r + 1]);
+    if (j + 1 < G.m1) wy[r] /= sqrt(dr * diag[r + s1]);
+    if (k + 1 < G.m1) wz[r] /= sqrt(dr * diag[r + s2]);
+    b[r] /= sqrt(dr);
+  }
 }
 
 // Block partial sums: each thread's NV values are summed over the warp in T
@@ -142,23 +158,60 @@ __device__ inline void block_partials(T (&v)[NV], double* part, int64_t idx, int
     }
 }
 
-// scalars[]: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 rr, 5 beta (the CG recurrence)
-// and, for the refined solve, 6 ||r||, 7 1/||r||, 8 r.r and 9 b.b of the FP64
-// residual, 10 max |dJ|, 11 max |J|.  After the sum, POST_ALPHA sets
-// alpha = rz / pAp, POST_BETA sets beta = rz_new / rz, rz = rz_new, and
+// scalars[]: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 rr, 5 beta (the CG recurrence
+// on the Jacobi-scaled system); 6 ||r|| and 7 1/||r|| (the FP64 residual of the
+// refined solve, unscaled norm), 8 sum d r^2 (= ||r||^2), 9 sum d b^2
+// (= ||b||^2), 12 max |dJ|, 13 max |J| (node jump).  After the sums, POST_ALPHA
+// sets alpha = rz / pAp, POST_BETA sets beta = rz_new / rz and rz = rz_new,
 // POST_NORM sets ||r|| and its inverse; POST_SKIP leaves the partials unused.
 enum { POST_SKIP = -1, POST_ALPHA = 1, POST_BETA = 2, POST_NORM = 3 };
+constexpr int kMaxVec = 2;
+
+// Fixed-order sum of nvec (<= 2) partial vectors of nparts entries by one
+// block of kB threads into sc[slot + q], then the post step.  `l2`: read the
+// partials from L2 (other blocks of the same launch wrote them).
+__device__ void sum_partials(const double* part, int nparts, int nvec, double* sc, int slot,
+                             int post, bool l2) {
+  __shared__ double red[kMaxVec][kB];
+  const int t = threadIdx.x + blockDim.x * threadIdx.y;
+#pragma unroll
+  for (int q = 0; q < kMaxVec; ++q) {
+    double s = 0.0;
+    if (q < nvec)
+      for (int b = t; b < nparts; b += kB)
+        s += l2 ? __ldcg(part + (int64_t)q * nparts + b) : part[(int64_t)q * nparts + b];
+    red[q][t] = s;
+  }
+  __syncthreads();
+  for (int o = kB / 2; o > 0; o >>= 1) {
+    if (t < o)
+#pragma unroll
+      for (int q = 0; q < kMaxVec; ++q) red[q][t] += red[q][t + o];
+    __syncthreads();
+  }
+  if (t == 0) {
+    for (int q = 0; q < nvec; ++q) sc[slot + q] = red[q][0];
+    if (post == POST_ALPHA) sc[2] = sc[0] / sc[1];
+    if (post == POST_BETA) {
+      sc[5] = sc[3] / sc[0];
+      sc[0] = sc[3];
+    }
+    if (post == POST_NORM) {  // residual norm of the refined solve
+      sc[6] = sqrt(sc[8]);
+      sc[7] = 1.0 / sc[6];
+    }
+  }
+}
 
 // The sum over a launch's block partials, done by its last block: each block
 // takes a ticket after a device-scope fence (its partials are written); the
-// block that draws the last ticket adds every partial in a fixed order (loads
-// from L2, where the other blocks' writes are) into sc[slot] (and
-// sc[slot + 1]), applies the post step and re-arms the ticket.
+// block that draws the last ticket adds every partial in a fixed order and
+// re-arms the ticket.  With no ticket (large grids) a separate
+// k_reduce_parts launch does the sum.
 __device__ void fold_partials(const double* part, int nparts, int nvec, double* sc, int slot,
                               int post, int* ticket) {
-  if (!ticket) return;  // large grids: a separate k_reduce_parts launch sums them
+  if (!ticket) return;
   __shared__ int last;
-  __shared__ double red[2][kB];
   const int t = threadIdx.x + blockDim.x * threadIdx.y;
   __syncthreads();  // the block's partials are written (by thread 0)
   if (t == 0) {
@@ -168,35 +221,8 @@ __device__ void fold_partials(const double* part, int nparts, int nvec, double* 
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double s0 = 0.0, s1 = 0.0;
-  for (int b = t; b < nparts; b += kB) {
-    s0 += __ldcg(part + b);
-    if (nvec > 1) s1 += __ldcg(part + nparts + b);
-  }
-  red[0][t] = s0;
-  red[1][t] = s1;
-  __syncthreads();
-  for (int o = kB / 2; o > 0; o >>= 1) {
-    if (t < o) {
-      red[0][t] += red[0][t + o];
-      red[1][t] += red[1][t + o];
-    }
-    __syncthreads();
-  }
-  if (t == 0) {
-    sc[slot] = red[0][0];
-    if (nvec > 1) sc[slot + 1] = red[1][0];
-    if (post == POST_ALPHA) sc[2] = sc[0] / sc[1];
-    if (post == POST_BETA) {
-      sc[5] = sc[3] / sc[0];
-      sc[0] = sc[3];
-    }
-    if (post == POST_NORM) {  // outer residual norm of the refined solve
-      sc[6] = sqrt(sc[8]);
-      sc[7] = 1.0 / sc[6];
-    }
-    *ticket = 0;
-  }
+  sum_partials(part, nparts, nvec, sc, slot, post, true);
+  if (t == 0) *ticket = 0;
 }
 
 // The same sum as fold_partials as a separate one-block launch.  A fold costs
@@ -204,46 +230,20 @@ __device__ void fold_partials(const double* part, int nparts, int nvec, double* 
 // costs more than the extra launch, so they use this kernel instead.
 __global__ void __launch_bounds__(kB) k_reduce_parts(const double* __restrict__ part, int nparts,
                                                      int nvec, double* sc, int slot, int post) {
-  __shared__ double red[2][kB];
-  const int t = threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
-  for (int b = t; b < nparts; b += kB) {
-    s0 += part[b];
-    if (nvec > 1) s1 += part[nparts + b];
-  }
-  red[0][t] = s0;
-  red[1][t] = s1;
-  __syncthreads();
-  for (int o = kB / 2; o > 0; o >>= 1) {
-    if (t < o) {
-      red[0][t] += red[0][t + o];
-      red[1][t] += red[1][t + o];
-    }
-    __syncthreads();
-  }
-  if (t == 0) {
-    sc[slot] = red[0][0];
-    if (nvec > 1) sc[slot + 1] = red[1][0];
-    if (post == POST_ALPHA) sc[2] = sc[0] / sc[1];
-    if (post == POST_BETA) {
-      sc[5] = sc[3] / sc[0];
-      sc[0] = sc[3];
-    }
-    if (post == POST_NORM) {
-      sc[6] = sqrt(sc[8]);
-      sc[7] = 1.0 / sc[6];
-    }
-  }
+  sum_partials(part, nparts, nvec, sc, slot, post, false);
 }
 
-// y = A v on the interior nodes; p . y summed into sc[1] (post = POST_ALPHA)
+// y = A v on the interior nodes: the Jacobi-scaled operator (UNIT: unit
+// diagonal, `diag` unused) or the unscaled one; v . y summed into sc[1]
+// (post = POST_ALPHA)
 // or not at all (POST_SKIP).  Blocks of kB threads: blockDim.x nodes of a row
 // times blockDim.y rows; grid z = slabs of kz planes.  Each thread walks its
 // (i, j) column through the slab, keeping the z neighbours in registers, so
 // node indices need no integer division and each thread reduces once.
 // (FP32: 8 blocks, i.e. 2048 threads, per SM; at most 32 registers)
-template <typename T>
-__global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 8 : 6) k_spmv_dot(Grid G, int kz, const T* __restrict__ diag,
+template <typename T, bool UNIT>
+__global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 8 : 6) k_spmv_dot(Grid G, int kz,
+                                                 const T* __restrict__ diag,
                                                  const T* __restrict__ wx,
                                                  const T* __restrict__ wy,
                                                  const T* __restrict__ wz,
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 8 : 6) k_spmv_dot(Grid G,
     for (int k = k0; k < k1; ++k, r += s2) {
       const T vp = k + 1 < G.m1 ? v[r + s2] : T(0);
       const T wzc = wz[r];  // zero on the last interior plane
-      T acc = diag[r] * vc;
+      T acc = UNIT ? vc : diag[r] * vc;
       if (i + 1 < G.m1) acc -= wx[r] * v[r + 1];
       if (i > 0) acc -= wx[r - 1] * v[r - 1];
       if (j + 1 < G.m1) acc -= wy[r] * v[r + s1];
@@ -280,10 +280,13 @@ __global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 8 : 6) k_spmv_dot(Grid G,
   fold_partials(part, nparts, 1, sc, 1, post, ticket);
 }
 
-// x += alpha p; r -= alpha Ap; partials of r.z and r.r (z = r / diag).  The
-// scalars stay FP64 and each thread strides over the nodes, reducing once.
-template <typename T>
-__global__ void __launch_bounds__(kB) k_update(Grid G, double* sc, const T* __restrict__ inv_diag,
+// x += alpha p; r -= alpha Ap; partials of the recurrence's r.z and of the
+// stopping norm ||r||^2 of the unscaled system.  UNIT (scaled system, dv = D):
+// r.z = r^.r^ and ||r||^2 = sum d r^2.  Otherwise (Jacobi PCG, dv = 1/D):
+// r.z = sum r^2 / d and ||r||^2 = r.r.  The scalars stay FP64 and each thread
+// strides over the nodes, reducing once.
+template <typename T, bool UNIT>
+__global__ void __launch_bounds__(kB) k_update(Grid G, double* sc, const T* __restrict__ dv,
                                                const T* __restrict__ p,
                                                const T* __restrict__ Ap, T* x, T* r,
                                                double* part, int* ticket) {
@@ -293,69 +296,78 @@ __global__ void __launch_bounds__(kB) k_update(Grid G, double* sc, const T* __re
     x[i] += a * p[i];
     const T ri = r[i] - a * Ap[i];
     r[i] = ri;
-    acc[0] += ri * ri * inv_diag[i];
-    acc[1] += ri * ri;
+    const T rr = ri * ri;
+    acc[0] += UNIT ? rr : rr * dv[i];
+    acc[1] += UNIT ? dv[i] * rr : rr;
   }
   block_partials<T, 2>(acc, part, blockIdx.x, gridDim.x);
   fold_partials(part, gridDim.x, 2, sc, 3, POST_BETA, ticket);
 }
 
-// p = r / diag + beta p   (beta = 0: p = z for the first direction)
-template <typename T>
+// p = z + beta p with z = r (UNIT) or r / D (`inv_diag`; Jacobi PCG)
+// (beta = 0: p = z for the first direction)
+template <typename T, bool UNIT>
 __global__ void __launch_bounds__(kB) k_pupdate(Grid G, const double* __restrict__ sc, int first,
                                                 const T* __restrict__ inv_diag,
                                                 const T* __restrict__ r, T* p) {
   const T beta = first ? T(0) : (T)sc[5];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
-    const T z = r[i] * inv_diag[i];
+    const T z = UNIT ? r[i] : r[i] * inv_diag[i];
     p[i] = first ? z : z + beta * p[i];
   }
 }
 
 // ---- refined solve: FP64 residuals, FP32 inner PCG ----
 
-// FP32 copies of the FP64 operator and preconditioner
+// FP32 copies of the unscaled operator for the inner Jacobi PCG of the
+// refined solve: D, 1/D and the face weights w = w^ sqrt(d_p d_q)
 __global__ void __launch_bounds__(kB) k_to_f32(Grid G, const double* __restrict__ diag,
                                                const double* __restrict__ wx,
                                                const double* __restrict__ wy,
-                                               const double* __restrict__ wz,
-                                               const double* __restrict__ idg, float* d32,
-                                               float* wx32, float* wy32, float* wz32,
-                                               float* idg32) {
-  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
-    d32[i] = (float)diag[i];
-    wx32[i] = (float)wx[i];
-    wy32[i] = (float)wy[i];
-    wz32[i] = (float)wz[i];
-    idg32[i] = (float)idg[i];
+                                               const double* __restrict__ wz, float* d32,
+                                               float* idg32, float* wx32, float* wy32,
+                                               float* wz32) {
+  const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
+  for (int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x; r < G.m; r += (int64_t)gridDim.x * kB) {
+    const int i = (int)(r % G.m1), j = (int)((r / G.m1) % G.m1), k = (int)(r / s2);
+    const double dr = diag[r];
+    d32[r] = (float)dr;
+    idg32[r] = (float)(1.0 / dr);
+    wx32[r] = i + 1 < G.m1 ? (float)(wx[r] * sqrt(dr * diag[r + 1])) : 0.f;
+    wy32[r] = j + 1 < G.m1 ? (float)(wy[r] * sqrt(dr * diag[r + s1])) : 0.f;
+    wz32[r] = k + 1 < G.m1 ? (float)(wz[r] * sqrt(dr * diag[r + s2])) : 0.f;
   }
 }
 
-// r = b - r (r holds A x on entry); partials of r.r and b.b
-__global__ void __launch_bounds__(kB) k_defect(Grid G, const double* __restrict__ b, double* r,
+// r^ = b^ - r^ (r^ holds A^ x^ on entry); partials of sum d r^2 (= ||r||^2)
+// and sum d b^2 (= ||b||^2), summed into sc[8], sc[9] (POST_NORM)
+__global__ void __launch_bounds__(kB) k_defect(Grid G, const double* __restrict__ d,
+                                               const double* __restrict__ b, double* r,
                                                double* part, double* sc, int* ticket) {
   double acc[2] = {0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
-    const double bi = b[i], ri = bi - r[i];
+    const double bi = b[i], ri = bi - r[i], di = d[i];
     r[i] = ri;
-    acc[0] += ri * ri;
-    acc[1] += bi * bi;
+    acc[0] += di * ri * ri;
+    acc[1] += di * bi * bi;
   }
   block_partials<double, 2>(acc, part, blockIdx.x, gridDim.x);
   fold_partials(part, gridDim.x, 2, sc, 8, POST_NORM, ticket);
 }
 
-// start of an inner solve of A e = r / ||r||: e = 0, r32 = r / ||r||,
-// p = r32 / diag; partials of r32.p and r32.r32
+// start of an inner solve (FP32 Jacobi PCG on the unscaled operator) of
+// A e = r / ||r|| with r = D^1/2 r^: e = 0, r32 = r / ||r|| (norm 1),
+// p32 = r32 / D; partials of r32.p32 and r32.r32
 __global__ void __launch_bounds__(kB) k_inner_init(Grid G, double* sc,
                                                    const double* __restrict__ r64,
+                                                   const float* __restrict__ d32,
                                                    const float* __restrict__ idg32, float* r32,
                                                    float* e32, float* p32, double* part,
                                                    int* ticket) {
   float acc[2] = {0.f, 0.f};
   const double inv = sc[7];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
-    const float ri = (float)(r64[i] * inv);
+    const float ri = (float)(r64[i] * inv) * sqrtf(d32[i]);
     const float z = ri * idg32[i];
     r32[i] = ri;
     e32[i] = 0.f;
@@ -369,13 +381,15 @@ __global__ void __launch_bounds__(kB) k_inner_init(Grid G, double* sc,
 
 // ---- extrapolated node jump ----
 
-// d_n u_s at x_G from the interior iterate x: least-squares fit of
+// d_n u_s at x_G from the interior iterate x^ of the scaled system (node
+// values x^ / sqrt(d)): least-squares fit of
 // a + g.(q - x_G) over the interior side-s nodes of the 3x3x3 block around
 // the node nearest x_G -+ h n (one spacing into side s; a midway point takes
 // the upper node), normal equations by
 // Cholesky; false with fewer than 4 such nodes or a degenerate fit.
-__device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict__ x, int s,
-                       const double xg[3], const double nrm[3], double* dn) {
+__device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict__ x,
+                       const double* __restrict__ diag, int s, const double xg[3],
+                       const double nrm[3], double* dn) {
   const double h = G.h;
   int c[3];
   for (int a = 0; a < 3; ++a) {
@@ -396,7 +410,8 @@ __device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict
         const double xq[3] = {node_coord(q[0], h), node_coord(q[1], h), node_coord(q[2], h)};
         if (phase_d(P, xq) != s) continue;
         const double bv[4] = {1.0, (xq[0] - xg[0]) / h, (xq[1] - xg[1]) / h, (xq[2] - xg[2]) / h};
-        const double uq = x[(q[0] - 1) + (int64_t)G.m1 * ((q[1] - 1) + (int64_t)G.m1 * (q[2] - 1))];
+        const int64_t rq = (q[0] - 1) + (int64_t)G.m1 * ((q[1] - 1) + (int64_t)G.m1 * (q[2] - 1));
+        const double uq = x[rq] / sqrt(diag[rq]);  // the unscaled node value
         for (int a = 0; a < 4; ++a) {
           rhs[a] += bv[a] * uq;
           for (int b = 0; b < 4; ++b) M[a][b] += bv[a] * bv[b];
@@ -438,7 +453,8 @@ __device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict
 // Block partials of max |J_new - J| and max |J_new| go to part[] and
 // part[gridDim.x + ...].
 __global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
-                                                  const double* __restrict__ x, double* J,
+                                                  const double* __restrict__ x,
+                                                  const double* __restrict__ diag, double* J,
                                                   double* part) {
   __shared__ double red[2][kB / 32];
   double mx[2] = {0.0, 0.0};
@@ -471,7 +487,7 @@ __global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
         const double beta = beta_d(P, xg);
         const int ss = mum <= mup ? 0 : 1;
         double dn = 0.0;
-        const bool have = lag && fit_dn(P, G, x, ss, xg, nrm, &dn);
+        const bool have = lag && fit_dn(P, G, x, diag, ss, xg, nrm, &dn);
         const double Gj = ss == 0 ? beta / mup - (have ? (1.0 - mum / mup) * dn : 0.0)
                                   : beta / mum + (have ? (1.0 - mup / mum) * dn : 0.0);
         jn = alpha_d(P, xg) + d * Gj;
@@ -519,16 +535,18 @@ __global__ void k_reduce_max2(const double* __restrict__ part, int nparts, doubl
   }
 }
 
-// x += ||r|| e   (FP64)
+// x^ += ||r|| D^1/2 e   (FP64; e is the inner solve's unscaled correction)
 __global__ void __launch_bounds__(kB) k_correct(Grid G, const double* __restrict__ sc,
+                                                const float* __restrict__ d32,
                                                 const float* __restrict__ e32, double* x) {
   const double s = sc[6];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB)
-    x[i] += s * (double)e32[i];
+    x[i] += s * (double)(e32[i] * sqrtf(d32[i]));
 }
 
+// the (n+1)^3 node array: x = x^ / sqrt(d) inside, Dirichlet data on the boundary
 __global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const double* __restrict__ x,
-                                                    double* u) {
+                                                    const double* __restrict__ diag, double* u) {
   const int64_t N1 = G.n + 1;
   const int64_t id = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (id >= N1 * N1 * N1) return;
@@ -536,7 +554,8 @@ __global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const dou
   if (i == 0 || j == 0 || k == 0 || i == G.n || j == G.n || k == G.n) {
     u[id] = dirichlet_g<double>(P, node_coord(i, G.h), node_coord(j, G.h), node_coord(k, G.h));
   } else {
-    u[id] = x[(i - 1) + (int64_t)G.m1 * ((j - 1) + (int64_t)G.m1 * (k - 1))];
+    const int64_t r = (i - 1) + (int64_t)G.m1 * ((j - 1) + (int64_t)G.m1 * (k - 1));
+    u[id] = x[r] / sqrt(diag[r]);
   }
 }
 
@@ -680,10 +699,12 @@ struct GridSolve {
   cudaStream_t st;
   CgBuffers B;
   bool refined;
-  double *diag, *wx, *wy, *wz, *b, *x, *r, *idg, *J = nullptr, *part, *sc;
+  // diag: D = diag A; wx, wy, wz, b, x, r: the Jacobi-scaled system's face
+  // weights, right-hand side, iterate x^ = D^1/2 x and residual
+  double *diag, *wx, *wy, *wz, *b, *x, *r, *J = nullptr, *part, *sc;
   int* ticket = nullptr;  // last-block counter of the folded reductions
   double *pv = nullptr, *Ap = nullptr;                        // FP64 CG
-  float *d32 = nullptr, *wx32 = nullptr, *wy32 = nullptr, *wz32 = nullptr, *idg32 = nullptr,
+  float *d32 = nullptr, *idg32 = nullptr, *wx32 = nullptr, *wy32 = nullptr, *wz32 = nullptr,
         *r32 = nullptr, *e32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;  // refined
   double host_sc[16];
   double rnorm = 0.0, bnorm = 0.0;
@@ -701,40 +722,41 @@ struct GridSolve {
     return e;
   }
 
-  // r = b - A x for the current x; sc cleared, sc[8] = r.r, sc[9] = b.b
-  // (POST_NORM also sets sc[6] = ||r||, sc[7] = 1 / ||r||)
+  // r^ = b^ - A^ x^ for the current x^; sc cleared, then sc[8] = ||r||^2,
+  // sc[9] = ||b||^2 and (POST_NORM) sc[6] = ||r||, sc[7] = 1 / ||r||
   void defect() {
     const Grid& G = S.G;
     cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
-    k_spmv_dot<double><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, diag, wx, wy, wz, x, r, part, sc,
-                                                      POST_SKIP, nullptr);
-    k_defect<<<S.nu, kB, 0, st>>>(G, b, r, part, sc, tk());
+    k_spmv_dot<double, true><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, nullptr, wx, wy, wz, x, r,
+                                                            part, sc, POST_SKIP, nullptr);
+    k_defect<<<S.nu, kB, 0, st>>>(G, diag, b, r, part, sc, tk());
     reduce(S.nu, 2, 8, POST_NORM);
   }
 
-  // FP64 Jacobi PCG from the current x.  0, NBM_ERR_NOT_CONVERGED or NONFINITE,
-  // or -1 for a CUDA error (message in `e`).
+  // FP64 CG on the Jacobi-scaled system (Jacobi PCG on A) from the current x^;
+  // stops at ||r|| <= rtol ||b|| in the unscaled norm.  0,
+  // NBM_ERR_NOT_CONVERGED or NONFINITE, or -1 for a CUDA error (message in `e`).
   int solve_fp64(double rtol, int max_iter, cudaError_t& e) {
     const Grid& G = S.G;
     defect();
     cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
     cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
-    // rz = r.(r/diag), rr = r.r (an update with alpha = sc[2] = 0), p = z
-    k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part, tk());
+    // rz = r^.r^, rr = ||r||^2 (an update with alpha = sc[2] = 0), p = r^
+    k_update<double, true><<<S.nu, kB, 0, st>>>(G, sc, diag, pv, Ap, x, r, part, tk());
     reduce(S.nu, 2, 3, POST_BETA);
-    k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 1, idg, r, pv);
+    k_pupdate<double, true><<<S.nu, kB, 0, st>>>(G, sc, 1, nullptr, r, pv);
     if ((e = read_sc()) != cudaSuccess) return -1;
     bnorm = sqrt(host_sc[9]);
     rnorm = sqrt(host_sc[4]);
     int it = 0;
     bool converged = rnorm <= rtol * bnorm;
     while (!converged && it < max_iter && rnorm == rnorm) {
-      k_spmv_dot<double><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, diag, wx, wy, wz, pv, Ap, part,
-                                                        sc, POST_ALPHA, tk());
+      k_spmv_dot<double, true><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, nullptr, wx, wy, wz, pv, Ap,
+                                                              part, sc, POST_ALPHA, tk());
       reduce(S.nsp, 1, 1, POST_ALPHA);
-      k_update<double><<<S.nu, kB, 0, st>>>(G, sc, idg, pv, Ap, x, r, part, tk());
+      k_update<double, true><<<S.nu, kB, 0, st>>>(G, sc, diag, pv, Ap, x, r, part, tk());
       reduce(S.nu, 2, 3, POST_BETA);
-      k_pupdate<double><<<S.nu, kB, 0, st>>>(G, sc, 0, idg, r, pv);
+      k_pupdate<double, true><<<S.nu, kB, 0, st>>>(G, sc, 0, nullptr, r, pv);
       ++it;
       if (it % kCheckEvery == 0 || it == max_iter) {
         if ((e = read_sc()) != cudaSuccess) return -1;
@@ -747,7 +769,8 @@ struct GridSolve {
     return converged ? NBM_OK : NBM_ERR_NOT_CONVERGED;
   }
 
-  // FP64 residuals, FP32 inner PCG corrections, from the current x
+  // FP64 residuals of the scaled system, FP32 inner Jacobi-PCG corrections on
+  // the unscaled operator, from the current x^
   int solve_refined(double rtol, int max_iter, cudaError_t& e) {
     const Grid& G = S.G;
     defect();
@@ -757,19 +780,20 @@ struct GridSolve {
     int it = 0, stall = 0;
     bool converged = rnorm <= rtol * bnorm;
     while (!converged && it < max_iter && rnorm == rnorm && stall < kMaxStall) {
-      // inner FP32 PCG on A e = r / ||r|| (initial residual norm 1), stopped at
-      // kInnerTol or where the outer target needs no more
+      // inner FP32 Jacobi PCG on A e = D^1/2 r^ / ||r|| (initial residual norm
+      // 1), stopped at kInnerTol or where the outer target needs no more
       double tau = 0.5 * rtol * bnorm / rnorm;
       tau = tau < kInnerTol ? kInnerTol : tau > 0.5 ? 0.5 : tau;
-      k_inner_init<<<S.nu, kB, 0, st>>>(G, sc, r, idg32, r32, e32, p32, part, tk());
+      k_inner_init<<<S.nu, kB, 0, st>>>(G, sc, r, d32, idg32, r32, e32, p32, part, tk());
       reduce(S.nu, 2, 3, POST_BETA);
       for (int inner = 1; it < max_iter; ++inner) {
-        k_spmv_dot<float><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, d32, wx32, wy32, wz32, p32, Ap32,
-                                                         part, sc, POST_ALPHA, tk());
+        k_spmv_dot<float, false><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, d32, wx32, wy32, wz32,
+                                                                p32, Ap32, part, sc, POST_ALPHA,
+                                                                tk());
         reduce(S.nsp, 1, 1, POST_ALPHA);
-        k_update<float><<<S.nu, kB, 0, st>>>(G, sc, idg32, p32, Ap32, e32, r32, part, tk());
+        k_update<float, false><<<S.nu, kB, 0, st>>>(G, sc, idg32, p32, Ap32, e32, r32, part, tk());
         reduce(S.nu, 2, 3, POST_BETA);
-        k_pupdate<float><<<S.nu, kB, 0, st>>>(G, sc, 0, idg32, r32, p32);
+        k_pupdate<float, false><<<S.nu, kB, 0, st>>>(G, sc, 0, idg32, r32, p32);
         ++it;
         if (inner % kCheckEvery == 0 || it == max_iter) {
           if ((e = read_sc()) != cudaSuccess) return -1;
@@ -777,8 +801,8 @@ struct GridSolve {
           if (!(rin == rin) || rin <= tau) break;
         }
       }
-      // x += ||r|| e in FP64, then the FP64 residual r = b - A x
-      k_correct<<<S.nu, kB, 0, st>>>(G, sc, e32, x);
+      // x^ += ||r|| D^1/2 e in FP64, then the FP64 residual r^ = b^ - A^ x^
+      k_correct<<<S.nu, kB, 0, st>>>(G, sc, d32, e32, x);
       defect();
       if ((e = read_sc()) != cudaSuccess) return -1;
       const double rnew = sqrt(host_sc[8]);
@@ -795,15 +819,17 @@ struct GridSolve {
     return refined ? solve_refined(rtol, max_iter, e) : solve_fp64(rtol, max_iter, e);
   }
 
+  // the rows of the current jumps, then the scaled system
   void rows() {
-    k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, S.G, J, diag, wx, wy, wz, b, idg);
+    k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, S.G, J, diag, wx, wy, wz, b);
+    k_scale_rows<<<S.nu, kB, 0, st>>>(S.G, diag, wx, wy, wz, b);
   }
 
-  // J from the current x (lag 1) or first order (lag 0); sc[10] = max |dJ|,
-  // sc[11] = max |J|
+  // J from the current x (lag 1) or first order (lag 0); sc[12] = max |dJ|,
+  // sc[13] = max |J|
   void jumps(int lag) {
-    k_node_jump<<<S.nu, kB, 0, st>>>(S.P, S.G, lag, x, J, part);
-    k_reduce_max2<<<1, 256, 0, st>>>(part, S.nu, sc, 10);
+    k_node_jump<<<S.nu, kB, 0, st>>>(S.P, S.G, lag, x, diag, J, part);
+    k_reduce_max2<<<1, 256, 0, st>>>(part, S.nu, sc, 12);
   }
 };
 
@@ -825,14 +851,13 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
   W.b = B.get<double>(G.m);
   W.x = B.get<double>(G.m);
   W.r = B.get<double>(G.m);
-  W.idg = B.get<double>(G.m);
   if (mode != NBM_JUMP_EXACT) W.J = B.get<double>(G.m);
   if (refined) {
     W.d32 = B.get<float>(G.m);
+    W.idg32 = B.get<float>(G.m);
     W.wx32 = B.get<float>(G.m);
     W.wy32 = B.get<float>(G.m);
     W.wz32 = B.get<float>(G.m);
-    W.idg32 = B.get<float>(G.m);
     W.r32 = B.get<float>(G.m);
     W.e32 = B.get<float>(G.m);
     W.p32 = B.get<float>(G.m);
@@ -841,7 +866,7 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
     W.pv = B.get<double>(G.m);
     W.Ap = B.get<double>(G.m);
   }
-  W.part = B.get<double>(2 * (size_t)(W.S.nu > W.S.nsp ? W.S.nu : W.S.nsp));
+  W.part = B.get<double>(kMaxVec * (size_t)(W.S.nu > W.S.nsp ? W.S.nu : W.S.nsp));
   W.sc = B.get<double>(16);
   W.ticket = B.get<int>(1);
   if (B.err != cudaSuccess) return cg_cuda_fail(W.who, B.err);
@@ -855,8 +880,8 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
   }
   W.rows();
   if (refined)  // the operator is the same for every pass: round it once
-    k_to_f32<<<W.S.nu, kB, 0, st>>>(G, W.diag, W.wx, W.wy, W.wz, W.idg, W.d32, W.wx32, W.wy32,
-                                     W.wz32, W.idg32);
+    k_to_f32<<<W.S.nu, kB, 0, st>>>(G, W.diag, W.wx, W.wy, W.wz, W.d32, W.idg32, W.wx32, W.wy32,
+                                     W.wz32);
   cudaError_t e = cudaSuccess;
   int status = W.solve(rtol, max_iter, e);
   JumpInfo info;
@@ -869,8 +894,8 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
         status = -1;
         break;
       }
-      info.dj = W.host_sc[10];
-      const double jmax = W.host_sc[11];
+      info.dj = W.host_sc[12];
+      const double jmax = W.host_sc[13];
       W.rows();
       ++info.passes;
       status = W.solve(rtol, max_iter, e);
@@ -885,7 +910,7 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
     }
   }
   if (status < 0) return cg_cuda_fail(W.who, e);
-  k_write_nodes<<<(int)((W.S.nodes + kB - 1) / kB), kB, 0, st>>>(W.S.P, G, W.x, u_out);
+  k_write_nodes<<<(int)((W.S.nodes + kB - 1) / kB), kB, 0, st>>>(W.S.P, G, W.x, W.diag, u_out);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cg_cuda_fail(W.who, e);
