@@ -1,4 +1,4 @@
-// nbm_geom.cuh -- FP64 geometry of the implicit compute cell (arXiv
+// nbm_geom.cuh -- geometry of the implicit compute cell (arXiv
 // 2210.14907, Fig. 2: "interface-cell crossings"): the level set is taken
 // linear on each tetrahedron of the Freudenthal-Kuhn six-tetrahedron split of
 // the cube, which gives closed forms for the volume fractions, the face
@@ -10,98 +10,107 @@
 
 namespace nbm {
 
-__device__ inline double frac_tri(double a, double b, double c) {
-  int na = a <= 0.0, nb = b <= 0.0, nc = c <= 0.0;
+// The closed forms below are templated on the real type T: FP64 for the grid
+// rows and the FP64-row mode; FP32 (on cell-local coordinates, where the
+// corners are exactly +-1/2) for the cut cells of the FP32-row mode.
+
+// fraction of the triangle (corner values a, b, c; phi linear) with phi <= 0
+template <typename T>
+__device__ inline T frac_tri(T a, T b, T c) {
+  int na = a <= T(0), nb = b <= T(0), nc = c <= T(0);
   int k = na + nb + nc;
-  if (k == 0) return 0.0;
-  if (k == 3) return 1.0;
+  if (k == 0) return T(0);
+  if (k == 3) return T(1);
   if (k == 1) {
-    double l = na ? a : (nb ? b : c);
-    double o1 = na ? b : a, o2 = nc ? b : c;  // the two positive values
+    T l = na ? a : (nb ? b : c);
+    T o1 = na ? b : a, o2 = nc ? b : c;  // the two positive values
     return (l / (l - o1)) * (l / (l - o2));
   }
-  double l = !na ? a : (!nb ? b : c);
-  double o1 = !na ? b : a, o2 = !nc ? b : c;  // the two non-positive values
-  return 1.0 - (l / (l - o1)) * (l / (l - o2));
+  T l = !na ? a : (!nb ? b : c);
+  T o1 = !na ? b : a, o2 = !nc ? b : c;  // the two non-positive values
+  return T(1) - (l / (l - o1)) * (l / (l - o2));
 }
 
-__device__ inline double frac_tet(const double f[4]) {
+// fraction of the tetrahedron (corner values f) with phi <= 0
+template <typename T>
+__device__ inline T frac_tet(const T f[4]) {
   int neg = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
-  if (neg == 0) return 0.0;
-  if (neg == 4) return 1.0;
+  for (int i = 0; i < 4; ++i) neg += f[i] <= T(0);
+  if (neg == 0) return T(0);
+  if (neg == 4) return T(1);
   if (neg == 1 || neg == 3) {
     bool want_neg = neg == 1;
     int lone = 0;
     for (int i = 0; i < 4; ++i)
-      if ((f[i] <= 0.0) == want_neg) lone = i;
-    double prod = 1.0;
+      if ((f[i] <= T(0)) == want_neg) lone = i;
+    T prod = T(1);
     for (int i = 0; i < 4; ++i)
       if (i != lone) prod *= f[lone] / (f[lone] - f[i]);
-    return neg == 1 ? prod : 1.0 - prod;
+    return neg == 1 ? prod : T(1) - prod;
   }
   // two on each side: A, B = -values below, C, D = values above
-  double A = -1.0, B = -1.0, C = -1.0, D = -1.0;
+  T A = T(-1), B = T(-1), C = T(-1), D = T(-1);
   for (int i = 0; i < 4; ++i) {
-    if (f[i] <= 0.0) {
-      if (A < 0.0) A = -f[i]; else B = -f[i];
+    if (f[i] <= T(0)) {
+      if (A < T(0)) A = -f[i]; else B = -f[i];
     } else {
-      if (C < 0.0) C = f[i]; else D = f[i];
+      if (C < T(0)) C = f[i]; else D = f[i];
     }
   }
-  double num = C * D * (A * A + A * B + B * B) + (C + D) * A * B * (A + B) + A * A * B * B;
+  T num = C * D * (A * A + A * B + B * B) + (C + D) * A * B * (A + B) + A * A * B * B;
   return num / ((C + A) * (D + A) * (C + B) * (D + B));
 }
 
-__device__ inline void lerp_zero(const double* xu, double fu, const double* xv, double fv,
-                                 double* o) {
-  double t = fu / (fu - fv);
+template <typename T>
+__device__ inline void lerp_zero(const T* xu, T fu, const T* xv, T fv, T* o) {
+  T t = fu / (fu - fv);
   for (int i = 0; i < 3; ++i) o[i] = xu[i] + t * (xv[i] - xu[i]);
 }
 
-__device__ inline double tri_area_acc(const double* a, const double* b, const double* c,
-                                      double* wc) {
-  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-  double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
-         cz = e1[0] * e2[1] - e1[1] * e2[0];
-  double ar = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
-  for (int i = 0; i < 3; ++i) wc[i] += ar * (a[i] + b[i] + c[i]) / 3.0;
+template <typename T>
+__device__ inline T tri_area_acc(const T* a, const T* b, const T* c, T* wc) {
+  T e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  T e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  T cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+    cz = e1[0] * e2[1] - e1[1] * e2[0];
+  T ar = T(0.5) * sqrt(cx * cx + cy * cy + cz * cz);
+  for (int i = 0; i < 3; ++i) wc[i] += ar * (a[i] + b[i] + c[i]) / T(3);
   return ar;
 }
 
 // interface polygon of one tetrahedron: returns its area, adds area*centroid
-__device__ inline double tet_iface(const double X[4][3], const double f[4], double* wc) {
+template <typename T>
+__device__ inline T tet_iface(const T X[4][3], const T f[4], T* wc) {
   int neg = 0;
-  for (int i = 0; i < 4; ++i) neg += f[i] <= 0.0;
-  if (neg == 0 || neg == 4) return 0.0;
+  for (int i = 0; i < 4; ++i) neg += f[i] <= T(0);
+  if (neg == 0 || neg == 4) return T(0);
   if (neg == 1 || neg == 3) {
     bool want_neg = neg == 1;
     int lone = 0;
     for (int i = 0; i < 4; ++i)
-      if ((f[i] <= 0.0) == want_neg) lone = i;
-    double Pp[3][3];
+      if ((f[i] <= T(0)) == want_neg) lone = i;
+    T Pp[3][3];
     int k = 0;
     for (int i = 0; i < 4; ++i) {
       if (i == lone) continue;
-      if (want_neg) lerp_zero(X[lone], f[lone], X[i], f[i], Pp[k]);
-      else lerp_zero(X[i], f[i], X[lone], f[lone], Pp[k]);
+      if (want_neg) lerp_zero<T>(X[lone], f[lone], X[i], f[i], Pp[k]);
+      else lerp_zero<T>(X[i], f[i], X[lone], f[lone], Pp[k]);
       ++k;
     }
-    return tri_area_acc(Pp[0], Pp[1], Pp[2], wc);
+    return tri_area_acc<T>(Pp[0], Pp[1], Pp[2], wc);
   }
   int a = -1, b = -1, c = -1, d = -1;
   for (int i = 0; i < 4; ++i) {
-    if (f[i] <= 0.0) { if (a < 0) a = i; else b = i; }
+    if (f[i] <= T(0)) { if (a < 0) a = i; else b = i; }
     else { if (c < 0) c = i; else d = i; }
   }
-  double Q[4][3];
-  lerp_zero(X[a], f[a], X[c], f[c], Q[0]);
-  lerp_zero(X[a], f[a], X[d], f[d], Q[1]);
-  lerp_zero(X[b], f[b], X[d], f[d], Q[2]);
-  lerp_zero(X[b], f[b], X[c], f[c], Q[3]);
-  return tri_area_acc(Q[0], Q[1], Q[2], wc) + tri_area_acc(Q[0], Q[2], Q[3], wc);
+  T Q[4][3];
+  lerp_zero<T>(X[a], f[a], X[c], f[c], Q[0]);
+  lerp_zero<T>(X[a], f[a], X[d], f[d], Q[1]);
+  lerp_zero<T>(X[b], f[b], X[d], f[d], Q[2]);
+  lerp_zero<T>(X[b], f[b], X[c], f[c], Q[3]);
+  return tri_area_acc<T>(Q[0], Q[1], Q[2], wc) + tri_area_acc<T>(Q[0], Q[2], Q[3], wc);
 }
 
 struct CellGeo {
@@ -145,8 +154,8 @@ __device__ inline void cell_geometry_d(const ProbDev& P, const double p[3], doub
       for (int a = 0; a < 3; ++a) Xt[k][a] = C[idx[k]][a];
       ft[k] = F[idx[k]];
     }
-    vneg += frac_tet(ft) / 6.0;
-    area += tet_iface(Xt, ft, wc);
+    vneg += frac_tet<double>(ft) / 6.0;
+    area += tet_iface<double>(Xt, ft, wc);
   }
   g.Vm = vneg;
   for (int a = 0; a < 3; ++a) {
@@ -155,7 +164,7 @@ __device__ inline void cell_geometry_d(const ProbDev& P, const double p[3], doub
       int b0 = sd << a;
       int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << k), c11 = c10 | (1 << k);
       g.Am[2 * a + sd] =
-          0.5 * (frac_tri(F[c00], F[c10], F[c11]) + frac_tri(F[c00], F[c01], F[c11]));
+          0.5 * (frac_tri<double>(F[c00], F[c10], F[c11]) + frac_tri<double>(F[c00], F[c01], F[c11]));
     }
   }
   g.S = area / (h * h);

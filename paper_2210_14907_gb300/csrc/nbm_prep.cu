@@ -203,63 +203,118 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* __restrict__ cl
 // transcendentals) are evaluated by four different lanes.  FP64 is narrow on
 // this part, so the per-cell dependency chain, not the operation count, sets
 // the time.
-__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __restrict__ X,
-                                                      const float* __restrict__ Y,
-                                                      const float* __restrict__ Z,
-                                                      const int* __restrict__ cut_pt,
-                                                      const int* __restrict__ counters,
-                                                      CutRec* cut) {
+// Lane k's share of a cut cell's closed forms (corner values F, corners C):
+// tetrahedron k of the Kuhn split (k < 6; volume fraction / 6, interface area,
+// area-weighted centroid) and face k (k < 6; fraction of Omega-).
+template <typename T>
+__device__ inline void cell_pieces(int k, const T F[8], const T C[8][3], T& vneg, T& area, T wc[3],
+                                   T& Afk) {
+  if (k >= 6) return;
+  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int v1 = 1 << perm[k][0];
+  const int v2 = v1 | (1 << perm[k][1]);
+  const int idx[4] = {0, v1, v2, 7};
+  T Xt[4][3], ft[4];
+  for (int t = 0; t < 4; ++t) {
+    for (int a = 0; a < 3; ++a) Xt[t][a] = C[idx[t]][a];
+    ft[t] = F[idx[t]];
+  }
+  vneg = frac_tet<T>(ft) / T(6);
+  area = tet_iface<T>(Xt, ft, wc);
+  const int a = k >> 1, sd = k & 1, j = (a + 1) % 3, kk = (a + 2) % 3;
+  const int b0 = sd << a;
+  const int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << kk), c11 = c10 | (1 << kk);
+  Afk = T(0.5) * (frac_tri<T>(F[c00], F[c10], F[c11]) + frac_tri<T>(F[c00], F[c01], F[c11]));
+}
+
+// Cut cell `id` of the list (nc cells) on the 8 lanes of a warp's quarter; the
+// whole warp calls it (full-mask shuffles), lanes past the list compute on
+// cell 0's point and store nothing.
+__device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float* __restrict__ X,
+                                                  const float* __restrict__ Y,
+                                                  const float* __restrict__ Z,
+                                                  const int* __restrict__ cut_pt, CutRec* cut,
+                                                  int id, int nc) {
   const unsigned full = 0xffffffffu;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int id = gid >> 3, k = threadIdx.x & 7, base = (threadIdx.x & 31) & ~7;
-  const int nc = counters[2];
-  if ((gid >> 5) * 4 >= nc) return;  // the whole warp (4 cells) is past the cut list
+  const int k = threadIdx.x & 7, base = (threadIdx.x & 31) & ~7;
   const bool live = id < nc;
   const int i = live ? cut_pt[id] : 0;
   const double h = P.h;
   const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
-  // corner k
-  double Ck[3];
-  for (int a = 0; a < 3; ++a) Ck[a] = p[a] + h * ((double)((k >> a) & 1) - 0.5);
-  const double Fk = phi_d(P, Ck[0], Ck[1], Ck[2]);
-  double F[8], C[8][3];
+  // Lane k < 6 takes tetrahedron k (volume fraction, interface area and
+  // area-weighted centroid) and face k; the 8 lanes then sum.  Outputs:
+  // Vm, S (area / h^2), the centroid cen and face fraction Afk of lane k.
+  double vneg_d, S_d, Afk_d, cen[3] = {p[0], p[1], p[2]};
+  bool has_area;
+  if (P.fp64) {
+    // FP64 rows: FP64 corner values and closed forms on absolute coordinates
+    double Ck[3];
+    for (int a = 0; a < 3; ++a) Ck[a] = p[a] + h * ((double)((k >> a) & 1) - 0.5);
+    const double Fk = phi_d(P, Ck[0], Ck[1], Ck[2]);
+    double F[8], C[8][3];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    F[c] = __shfl_sync(full, Fk, base + c);
-    for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
-  }
-  // tetrahedron k (k < 6): volume fraction, interface area and centroid
-  double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0};
-  if (k < 6) {
-    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    const int v1 = 1 << perm[k][0];
-    const int v2 = v1 | (1 << perm[k][1]);
-    const int idx[4] = {0, v1, v2, 7};
-    double Xt[4][3], ft[4];
-    for (int t = 0; t < 4; ++t) {
-      for (int a = 0; a < 3; ++a) Xt[t][a] = C[idx[t]][a];
-      ft[t] = F[idx[t]];
+    for (int c = 0; c < 8; ++c) {
+      F[c] = __shfl_sync(full, Fk, base + c);
+      for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
     }
-    vneg = frac_tet(ft) / 6.0;
-    area = tet_iface(Xt, ft, wc);
-  }
-  // face k (k < 6): fraction of Omega-
-  double Afk = 0.0;
-  if (k < 6) {
-    const int a = k >> 1, sd = k & 1, j = (a + 1) % 3, kk = (a + 2) % 3;
-    const int b0 = sd << a;
-    const int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << kk), c11 = c10 | (1 << kk);
-    Afk = 0.5 * (frac_tri(F[c00], F[c10], F[c11]) + frac_tri(F[c00], F[c01], F[c11]));
-  }
+    double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0}, Afk = 0.0;
+    cell_pieces<double>(k, F, C, vneg, area, wc, Afk);
 #pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    vneg += __shfl_xor_sync(full, vneg, o);
-    area += __shfl_xor_sync(full, area, o);
-    for (int a = 0; a < 3; ++a) wc[a] += __shfl_xor_sync(full, wc[a], o);
+    for (int o = 1; o < 8; o <<= 1) {
+      vneg += __shfl_xor_sync(full, vneg, o);
+      area += __shfl_xor_sync(full, area, o);
+      for (int a = 0; a < 3; ++a) wc[a] += __shfl_xor_sync(full, wc[a], o);
+    }
+    vneg_d = vneg;
+    S_d = area / (h * h);
+    Afk_d = Afk;
+    has_area = area > 0.0;
+    if (has_area)
+      for (int a = 0; a < 3; ++a) cen[a] = wc[a] / area;
+  } else {
+    // FP32 rows: corner values with the classifier's rule (FP32 at the same
+    // FP32 coordinates; every corner of the cell in FP64 when one is within
+    // the FP32 error band of 0), so the signs are those that made the cell
+    // cut; the closed forms in FP32 on cell-local coordinates (corners at
+    // exactly +-1/2, lengths in units of h), where nothing cancels
+    const float pf[3] = {X[i], Y[i], Z[i]};
+    const float hh = 0.5f * P.hf;
+    float Fk = phi_f(P, pf[0] + ((k & 1) ? hh : -hh), pf[1] + ((k & 2) ? hh : -hh),
+                     pf[2] + ((k & 4) ? hh : -hh));
+    float mn = fabsf(Fk);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) mn = fminf(mn, __shfl_xor_sync(full, mn, o));
+    if (mn < 2e-5f) {
+      const double hd = 0.5 * P.h;
+      const double fd = phi_d(P, (double)pf[0] + ((k & 1) ? hd : -hd),
+                              (double)pf[1] + ((k & 2) ? hd : -hd),
+                              (double)pf[2] + ((k & 4) ? hd : -hd));
+      Fk = (float)fd;
+      if (Fk == 0.f && fd > 0.0) Fk = __int_as_float(1);  // keep a positive sign
+    }
+    float F[8], C[8][3];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      F[c] = __shfl_sync(full, Fk, base + c);
+      for (int a = 0; a < 3; ++a) C[c][a] = (float)((c >> a) & 1) - 0.5f;
+    }
+    float vneg = 0.f, area = 0.f, wc[3] = {0.f, 0.f, 0.f}, Afk = 0.f;
+    cell_pieces<float>(k, F, C, vneg, area, wc, Afk);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      vneg += __shfl_xor_sync(full, vneg, o);
+      area += __shfl_xor_sync(full, area, o);
+      for (int a = 0; a < 3; ++a) wc[a] += __shfl_xor_sync(full, wc[a], o);
+    }
+    vneg_d = vneg;
+    S_d = area;  // already in units of h^2
+    Afk_d = Afk;
+    has_area = area > 0.f;
+    if (has_area)
+      for (int a = 0; a < 3; ++a) cen[a] = p[a] + h * (double)(wc[a] / area);
   }
-  double xg[3] = {p[0], p[1], p[2]};
-  if (area > 0.0) {
-    for (int a = 0; a < 3; ++a) xg[a] = wc[a] / area;
+  double xg[3] = {cen[0], cen[1], cen[2]};
+  if (has_area) {
     if (P.fp64) {
       for (int it = 0; it < 3; ++it) {  // Newton projection onto phi = 0
         double g[3];
@@ -287,14 +342,14 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __
   // four point functions on four lanes (FP64 for the FP64 rows, else FP32)
   double val = 0.0;
   if (P.fp64) {
-    if (k == 0 && area > 0.0) val = beta_d(P, xg);
-    else if (k == 1 && area > 0.0) val = alpha_d(P, xg);
+    if (k == 0 && has_area) val = beta_d(P, xg);
+    else if (k == 1 && has_area) val = alpha_d(P, xg);
     else if (k == 2) val = rhs_f<double>(P, 0, p[0], p[1], p[2]);
     else if (k == 3) val = rhs_f<double>(P, 1, p[0], p[1], p[2]);
   } else {
     const float xf[3] = {(float)xg[0], (float)xg[1], (float)xg[2]};
-    if (k == 0 && area > 0.0) val = beta_f(P, xf);
-    else if (k == 1 && area > 0.0) val = alpha_f(P, xf);
+    if (k == 0 && has_area) val = beta_f(P, xf);
+    else if (k == 1 && has_area) val = alpha_f(P, xf);
     else if (k == 2) val = rhs_f<float>(P, 0, (float)p[0], (float)p[1], (float)p[2]);
     else if (k == 3) val = rhs_f<float>(P, 1, (float)p[0], (float)p[1], (float)p[2]);
   }
@@ -302,17 +357,32 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __
   const double f0 = __shfl_sync(full, val, base + 2), f1 = __shfl_sync(full, val, base + 3);
   if (!live) return;
   CutRec* r = cut + id;
-  if (k < 6) r->Am[k] = Afk;
+  if (k < 6) r->Am[k] = Afk_d;
   if (k == 0) {
-    r->Vm = vneg;
-    r->S = area / (h * h);
-    r->has_jump = area > 0.0;
+    r->Vm = vneg_d;
+    r->S = S_d;
+    r->has_jump = has_area;
     for (int a = 0; a < 3; ++a) r->xg[a] = xg[a];
     r->beta = beta;
     r->alpha = alpha;
     r->f[0] = f0;
     r->f[1] = f1;
     r->point = i;
+  }
+}
+
+// Grid-stride over the cut list in groups of 16 cells (4 per warp), so that
+// the grid need not cover the worst case of every point being cut.
+__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __restrict__ X,
+                                                      const float* __restrict__ Y,
+                                                      const float* __restrict__ Z,
+                                                      const int* __restrict__ cut_pt,
+                                                      const int* __restrict__ counters,
+                                                      CutRec* cut) {
+  const int nc = counters[2];
+  for (int cell0 = blockIdx.x * 16; cell0 < nc; cell0 += gridDim.x * 16) {
+    if (cell0 + 4 * (int)(threadIdx.x >> 5) >= nc) break;  // this warp's cells are past the list
+    cut_cell_geometry(P, X, Y, Z, cut_pt, cut, cell0 + (int)(threadIdx.x >> 3), nc);
   }
 }
 
@@ -636,8 +706,10 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
 }
 
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
-  // 8 lanes per cut cell, 16 cells per block (grid sized for the worst case)
-  int nb = (int)((n + 15) / 16);
+  // 8 lanes per cut cell, 16 cells per block; at most 8 blocks per SM, each
+  // striding over the cut list
+  const int64_t worst = (n + 15) / 16, cap = 8 * (int64_t)ws.grid;
+  int nb = (int)(worst < cap ? worst : cap);
   k_cut_geometry<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
   return cudaGetLastError();
 }
