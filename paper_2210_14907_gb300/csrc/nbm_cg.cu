@@ -1,11 +1,12 @@
 // nbm_cg.cu -- the plain mesh-based method the NBM is bootstrapped from
 // (arXiv 2210.14907, Sec. 1 and Sec. 3): the same finite-volume balance row on
 // the nodes of a grid of spacing h = 2/n, one unknown per interior node, solved
-// by Jacobi-preconditioned conjugate gradients in FP64 (nbm_grid_cg_solve), or
-// to the same FP64 residual test by FP32 inner PCG corrections of FP64
-// residuals (nbm_grid_solve_refined).  Each iteration streams the operator
-// (diagonal + three face weights per node) and five vectors; in FP64 the
-// SpMV is bound by GB300's narrow FP64 pipe, in FP32 the kernels by HBM.
+// by Jacobi-preconditioned conjugate gradients in FP64 (nbm_grid_cg_solve; run
+// as CG on the Jacobi-scaled system D^-1/2 A D^-1/2, the same iterates in
+// exact arithmetic with fewer bytes), or to the same FP64 residual test by
+// FP32 inner PCG corrections of FP64 residuals (nbm_grid_solve_refined).  In
+// FP64 the SpMV is bound by GB300's narrow FP64 pipe, in FP32 the kernels by
+// HBM.
 //
 // Row of interior node p (cell p + [-h/2, h/2]^3, fractions as in nbm_geom.cuh):
 //   sum_f w_f (u_p - u_q) + h^2 sum_s V^s k^s u_p = -known_p,

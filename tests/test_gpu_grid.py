@@ -237,3 +237,27 @@ def test_grid_lagged_jump_second_order(solver):
     for i in range(2):
         assert errs[1][i][0] / errs[1][i + 1][0] > 3.0 and errs[1][i][1] / errs[1][i + 1][1] > 3.5
         assert 1.5 < errs[2][i][0] / errs[2][i + 1][0] < 3.0
+
+
+def test_large_grid_solves_with_separate_reductions():
+    """n = 202 (8.1 M unknowns): past the size where the reductions are folded
+    into the producing kernels, so every sum goes through the separate
+    reduction launch.  Both solvers reach the same solution, second-order
+    close to the exact one (2.2e-5 at n = 256, so about 3.6e-5 here)."""
+    nbm = _nbm()
+    prob = nbm.Problem(nbm.ProblemDesc(geometry=nbm.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0))
+    n = 202
+    assert (n - 1) ** 3 > 8_000_000
+    a, it_a, rr_a, ok_a = prob.grid_cg_solve(n, rtol=1e-10, max_iter=100000)
+    b, it_b, rr_b, ok_b = prob.grid_solve_refined(n, rtol=1e-10, max_iter=100000)
+    assert ok_a and ok_b and rr_a <= 1e-10 and rr_b <= 1e-10
+    diff = (torch.max(torch.abs(a - b)) / torch.max(torch.abs(a))).item()
+    g = -1.0 + torch.arange(n + 1, device="cuda", dtype=torch.float64) * (2.0 / n)
+    Z, Y, X = torch.meshgrid(g, g, g, indexing="ij")
+    r = torch.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    exact = torch.where(r <= 0.5, torch.exp(X) * torch.cos(Y) * torch.sin(Z), r ** 2).reshape(-1)
+    interior = torch.zeros((n + 1,) * 3, dtype=torch.bool, device="cuda")
+    interior[1:-1, 1:-1, 1:-1] = True
+    linf = torch.max(torch.abs(a - exact)[interior.reshape(-1)]).item()
+    print(f"n {n}: FP64 CG {it_a} it, refined {it_b} inner it, diff {diff:.2e}, L-inf {linf:.2e}")
+    assert diff <= 1e-8 and linf <= 5e-5
