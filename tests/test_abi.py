@@ -62,3 +62,15 @@ def test_descriptor_layout_matches_the_header():
     padding surprises (int32 tail padded to 8 bytes)."""
     import paper_2210_14907_gb300 as nbm
     assert ctypes.sizeof(nbm._Desc) == 4 * 4 + 11 * 8 + 6 * 4
+
+
+def test_grid_entry_points_reject_null_arguments_without_a_gpu():
+    import paper_2210_14907_gb300 as nbm
+    lib = nbm.load_library()
+    for fn in (lib.nbm_grid_cg_solve, lib.nbm_grid_solve_refined):
+        assert fn(None, 16, 1e-10, 100, None, None, None, None) == 1
+        assert b"NULL" in lib.nbm_last_error()
+    ps, dj, fb = ctypes.c_int(-1), ctypes.c_double(-1.0), ctypes.c_int(-1)
+    assert lib.nbm_grid_last_jump_info(ctypes.byref(ps), ctypes.byref(dj), ctypes.byref(fb)) == 0
+    assert ps.value >= 0 and fb.value in (0, 1)
+    assert lib.nbm_grid_last_jump_info(None, None, None) == 0
