@@ -353,6 +353,21 @@ def test_cut_cell_consistency_is_second_order(sol):
     assert mx[0] / mx[1] > 3.4 and mx[1] / mx[2] > 3.4
 
 
+
+@pytest.mark.parametrize("sol", [O.SOL_BENCH, O.SOL_SEC41])
+def test_jump_row_vanishes_for_the_exact_pair_on_the_flower(sol):
+    """The value-jump row J = U+(x_G) - U-(x_G) - alpha(x_G) is zero to rounding
+    when U is the manufactured pair, on the flower interface too (x_G from the
+    Newton projection of a non-distance level set)."""
+    rng = np.random.default_rng(9)
+    h = 1 / 64
+    pr = O.make_problem(geometry=O.GEOM_FLOWER, mu_minus=1.0, mu_plus=100.0, h=h, solution=sol)
+    res = [O.point_terms(pr, None, p, mode=1) for p in _band_points(pr, 120, 0.5 * h, rng)]
+    cut = [r for r in res if r["cut"] and r["has_jump"]]
+    assert len(cut) > 100
+    assert max(abs(r["J"]) for r in cut) < 1e-13
+
+
 # --------------------------------------------------------------- network ----
 def test_mlp_textbook_cases():
     pr = O.make_problem(n_hidden=2, width=4)
