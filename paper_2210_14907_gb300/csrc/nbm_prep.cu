@@ -3,11 +3,13 @@
 //                        implicit cell from the level set at its 8 corners
 //   scan + scatter     : stable phase partition (two networks -> two lists;
 //                        cut cells go into both and into the cut list)
-//   cut geometry       : FP64 Kuhn-split volume / face / interface fractions
-//                        and the interface point of every cut cell
+//   cut geometry       : Kuhn-split volume / face / interface fractions and
+//                        the interface point of every cut cell (FP32 on
+//                        cell-local coordinates, FP64 in the FP64-row mode)
 //   cut residual       : balance + jump rows of cut cells (both networks)
 //   weight staging     : FP32 transposed and 16-bit tensor-core copies
-//   finish             : deterministic loss / gradient reduction and Adam
+//   finish             : deterministic loss / gradient reduction (8 slice
+//                        groups per 32 parameters, fixed order) and Adam
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 

@@ -23,6 +23,9 @@
 //
 // Shared memory: (L-1) weight images of 32 KB + 2 x L operand images of 16 KB.
 // TMEM: 2 x 64 columns for D + 128 per hidden layer for the weight gradient.
+// Every wait is bounded.  The group barrier that ends each phase agrees on an
+// abort; an aborted CTA gives its MMAs and copies in flight a short bounded
+// wait before it frees TMEM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
