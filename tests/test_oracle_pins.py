@@ -693,3 +693,4 @@ def test_grid_jump_equal_mu_and_fallback():
     _, u2, *_ = O.grid_solve_jump(pr, 16, O.JUMP_FIRST_ORDER, rtol=1e-12, max_iter=5000)
     assert st == 2 and passes == 2 and dj > 1e-12
     assert np.max(np.abs(u1 - u2)) <= 1e-9 * np.max(np.abs(u2))
+
