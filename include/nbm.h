@@ -32,7 +32,12 @@
  *    (-1,1)^3.  Passing pts == NULL draws them on the device from the
  *    counter-based Philox4x32-10 stream (seed, step): uniform points on the
  *    lattice -1 + k 2^-22, plus round(band_fraction*n) points within 4h of
- *    Gamma.
+ *    Gamma (the last ones of the batch).  Point i of step t is drawn from the
+ *    block at counter (i, t mod 2^32, t div 2^32, 0x4E424D31) under the key
+ *    (seed mod 2^32, seed div 2^32); a uniform point takes coordinate j from
+ *    word j as k = 1 + floor(w_j (2^23 - 1) / 2^32).  A band point takes an
+ *    isotropic direction and an offset uniform on (-4h, 4h) from the
+ *    interface along it, rounded to the lattice.
  *  - One nbm_problem may be used by one host thread at a time.
  */
 #ifndef NBM_H
@@ -62,9 +67,8 @@ typedef enum {
                              theta = polar angle from +z, psi = azimuth                */
   NBM_GEOM_ALL_PLUS = 3,  /* no interface; the whole cube is Omega+                   */
   NBM_GEOM_ALL_MINUS = 4, /* no interface; the whole cube is Omega-                   */
-  NBM_GEOM_GRID = 5       /* phi stored on a coarse mesh (Sec. 3: "a separate coarse
-                             mesh encapsulates a level-set function"), trilinearly
-                             interpolated; set with nbm_set_level_set before any
+  NBM_GEOM_GRID = 5       /* phi stored on a separate coarse mesh (Sec. 3),
+                             trilinearly interpolated; set with nbm_set_level_set before any
                              computation.  No band points (band_fraction must be 0). */
 } nbm_geometry;
 
@@ -112,7 +116,7 @@ typedef struct {
   double lambda_jump;     /* weight of the value-jump row in r_p^2 (1 in the paper's reading) */
   double band_fraction;   /* share of sampled points drawn within 4h of Gamma         */
   int32_t fp64_stencil;   /* -1: automatic (on for h <= 2/512, per level), 0: off, 1: on */
-  int32_t refine_levels;  /* implicit refinement (Sec. 3, Fig. 2: cells "at multi-resolutions";
+  int32_t refine_levels;  /* implicit refinement (Sec. 3, Fig. 2: cells at several resolutions;
                              Sec. 4.2: a base resolution refined three times).  0..3: every
                              collocation point also gets the cells of spacing h/2, ...,
                              h/2^refine_levels; their rows are stacked into r_p, i.e.
@@ -162,7 +166,7 @@ int nbm_selftest_bounded_wait(int64_t budget_cycles, nbm_stream_t stream);
 /* Number of FP32 parameters P of the network pair. */
 int64_t nbm_param_count(const nbm_problem* p);
 
-/* Draws n collocation points (Sec. 3, "randomly sampled points") from the
+/* Draws n collocation points (Sec. 3: random points in the domain) from the
  * Philox4x32-10 stream keyed by `seed` at counter `step`; pts_out is [n][3]. */
 int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, float* pts_out,
                       nbm_stream_t stream);
@@ -179,8 +183,8 @@ int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, fl
 int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,
                  int64_t step, float* r2_out, double* loss_out, nbm_stream_t stream);
 
-/* Loss and its gradient with respect to all P parameters (Sec. 3, "the
- * automatic differentiation loop passes across the NBM kernels"), by the
+/* Loss and its gradient with respect to all P parameters (Sec. 3: gradients
+ * are taken through the NBM kernels themselves), by the
  * hand-written backward kernels.  grad_out [P] is overwritten.
  * loss_out (host) or NULL; a non-NULL loss_out synchronizes the stream. */
 int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,

@@ -51,8 +51,8 @@ void nbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 }
 
 /* ======================================================================
- * Geometry (Sec. 3: "a separate coarse mesh encapsulates a level-set
- * function"; here the level set is analytic).
+ * Geometry (Sec. 3: the level set lives on a separate coarse
+ * mesh; here it is analytic, or such a mesh).
  * ==================================================================== */
 /* Level set stored on a coarse mesh (Sec. 3): the trilinear interpolant of the
  * node values in the mesh cell that contains x (cell index floor((x+1) n/2),
@@ -248,8 +248,8 @@ double nbo_dirichlet_g(const nbo_problem* pr, const double x[3]) {
 }
 
 /* ======================================================================
- * Implicit compute cell C_p = p + [-h/2, h/2]^3 (Fig. 2: "placing implicit
- * cells ... calculating interface-cell crossings").  Reading: phi is taken
+ * Implicit compute cell C_p = p + [-h/2, h/2]^3 (Fig. 2: an implicit
+ * cell at each point, cut by the interface).  Reading: phi is taken
  * linear on each tetrahedron of the Freudenthal-Kuhn six-tetrahedron split
  * of the cube, so every fraction has a closed form.
  * ==================================================================== */
@@ -455,8 +455,8 @@ void nbo_cell_geometry(const nbo_problem* pr, const double p[3], double h, nbo_c
 }
 
 /* ======================================================================
- * Networks (Sec. 3: "two neural networks are used to represent the
- * solution on each side"): a_0 = x, z_l = W_l a_{l-1} + b_l,
+ * Networks (Sec. 3: one network for the
+ * solution on each side of the interface): a_0 = x, z_l = W_l a_{l-1} + b_l,
  * a_l = act(z_l) for the hidden layers (tanh, or sin for the sine-activated
  * networks of Sec. 4.1), u = w . a_L + b.
  * Layout per net: W1[H][3], b1[H], then (W_l[H][H], b_l[H]) for
@@ -562,7 +562,7 @@ static void mlp_backward(const nbo_problem* pr, const double* th, const double x
 }
 
 /* ======================================================================
- * Collocation points ("randomly sampled points", Sec. 3).  Uniform points
+ * Collocation points (random points, Sec. 3).  Uniform points
  * lie on the lattice -1 + k 2^-22, k in [1, 2^23-1], so p +- h is exact for
  * power-of-two h.  Band points (|phi| < 4h) are placed along rays from the
  * origin at a uniform offset t in (-4h, 4h) from the interface radius.

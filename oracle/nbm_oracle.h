@@ -15,13 +15,15 @@
  *             side), point residual r_p = ||M^-1 A u - M^-1 b||, losses
  *             aggregated over points, Adam on the network parameters.
  *   Fig. 2    (caption) one point per kernel thread, local preconditioner.
- * The discretization equation is missing from the paper's text (Sec. 3 stops
- * at "hence the loss function is"); the finite-volume reading implemented
+ * The discretization equation is missing from the paper's text (Sec. 3 breaks
+ * off where the loss would be written out); the finite-volume reading implemented
  * here is documented per function.
  *
- * Parity status: every function has a pin in tests/test_oracle_*.py
- * except the interface-cell order of the grid scheme (parity unpinned: the
- * cited Bochkov-Gibou scheme is not available to compare against).
+ * Parity status: every function has a pin in tests/test_oracle_pins.py,
+ * tests/test_oracle_conventions.py or tests/test_grid_identities.py.  No pin
+ * compares the grid rows with the cited Bochkov-Gibou scheme (not available);
+ * their order is pinned instead.  tests/oracle_mutants.py plants mistakes in
+ * copies of this file and checks that the pins catch them.
  */
 #ifndef NBM_ORACLE_H
 #define NBM_ORACLE_H

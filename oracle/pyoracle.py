@@ -267,7 +267,7 @@ def level_problem(pr, level):
     return q
 
 
-# Implicit refinement (Sec. 3 and Fig. 2: implicit cells "at multi-resolutions";
+# Implicit refinement (Sec. 3 and Fig. 2: implicit cells at several resolutions;
 # Sec. 4.2: a base resolution implicitly refined three times).  The paper does
 # not say how the levels' rows are combined; the reading taken here stacks the
 # rows of every level into the point's residual vector, so that r_p^2 (and the

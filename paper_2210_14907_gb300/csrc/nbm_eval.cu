@@ -1,5 +1,5 @@
 // nbm_eval.cu -- evaluation of the trained surrogate on a dense grid (the
-// "once trained, evaluate the simulation" use of arXiv 2210.14907, Fig. 1):
+// use of a trained model in arXiv 2210.14907, Fig. 1: train once, then evaluate):
 // u at the (n+1)^3 nodes -1 + i 2/n, each node with the network of its side
 // of the interface (phi <= 0: minus).
 //

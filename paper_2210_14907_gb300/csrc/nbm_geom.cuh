@@ -1,5 +1,5 @@
 // nbm_geom.cuh -- geometry of the implicit compute cell (arXiv
-// 2210.14907, Fig. 2: "interface-cell crossings"): the level set is taken
+// 2210.14907, Fig. 2: where the interface crosses the cell): the level set is taken
 // linear on each tetrahedron of the Freudenthal-Kuhn six-tetrahedron split of
 // the cube, which gives closed forms for the volume fractions, the face
 // fractions (each face split along the diagonal from its lowest to its

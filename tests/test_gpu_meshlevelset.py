@@ -1,5 +1,5 @@
-"""Level set stored on a coarse mesh (Sec. 3: "a separate coarse mesh
-encapsulates a level-set function"), trilinearly interpolated, on the GPU
+"""Level set stored on a coarse mesh (Sec. 3: the level set lives on a
+separate coarse mesh), trilinearly interpolated, on the GPU
 against the FP64 oracle: residual rows, gradients, grid evaluation and the
 grid CG solve of problems whose interface is given only by mesh values.
 """

@@ -4,6 +4,7 @@ import numpy as np
 
 from oracle import pyoracle as O
 
+
 def test_scaled_cg_iterates_equal_jacobi_pcg_on_the_oracle_system():
     """The identity the GPU grid solver relies on: CG on the Jacobi-scaled system
     D^-1/2 A D^-1/2 x^ = D^-1/2 b gives the iterates x = D^-1/2 x^ of Jacobi PCG
