@@ -342,6 +342,23 @@ def table1(dev, epochs, resolutions, lr=1e-3):
             "rows": rows}
 
 
+def cpu_baseline_grid():
+    """The FP64 oracle's grid solve (row assembly and Jacobi PCG, OpenMP over
+    rows, all host cores) on the grid_solves problem at 64^3 and 128^3 node
+    grids, rtol 1e-10."""
+    from oracle import pyoracle as O
+    O.build()
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
+    out = {"kind": "oracle", "cores": os.cpu_count()}
+    for n in (64, 128):
+        t0 = time.perf_counter()
+        st, _, it, rr = O.grid_cg_solve(pr, n, rtol=1e-10, max_iter=100000)
+        wall = time.perf_counter() - t0
+        out[f"grid_cg_{n}"] = {"unknowns": (n - 1) ** 3, "iterations": it, "relres": rr,
+                               "converged": st == 0, "wall_s": wall}
+    return out
+
+
 def grid_solves(hbm_peak, peak_src):
     """The grid scheme (sphere, mu 1/10) at 128^3 and 256^3 unknown grids to
     rtol 1e-10: FP64 Jacobi PCG and the refined solve (FP32 inner PCG on FP64
@@ -502,7 +519,10 @@ def main():
         import torch
         torch.cuda.set_device(0)
         _, _, hbm, peak_src = _peaks()
-        print(json.dumps(grid_solves(hbm, peak_src)))
+        out = grid_solves(hbm, peak_src)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline_grid"] = cpu_baseline_grid()
+        print(json.dumps(out))
         return 0
     if args.table1:
         import torch
@@ -629,6 +649,8 @@ def main():
         line["accuracy"] = accuracy(dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        if not args.no_secondary:
+            line["cpu_baseline_grid"] = cpu_baseline_grid()
     print(json.dumps(line), flush=True)
 
 
