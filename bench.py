@@ -143,36 +143,44 @@ def _max_over_ranks(ws, x):
     return float(t.item())
 
 
-def cpu_baseline(config_name="C2", target_s=10.0):
-    """The FP64 oracle (OpenMP over points, all host cores) on a bounded sample of
-    the workload: loss + gradient + Adam on a sub-batch of sampled points."""
+def cpu_baseline(target_s=10.0, steps=1, warmup=0):
+    """The FP64 oracle (OpenMP over points, all host cores) on a bounded sample
+    of the C2 workload.  One step = the oracle's loss + gradient + Adam on a
+    sub-batch of sampled points (counter = the step's index).  The sub-batch is
+    sized so that `steps` timed steps take about target_s seconds; `warmup`
+    untimed steps come first."""
     import numpy as np
 
     from oracle import pyoracle as O
     O.build()
-    geom = O.GEOM_SPHERE
-    pr = O.make_problem(geometry=geom, n_hidden=3, width=128, mu_minus=1.0, mu_plus=10.0,
-                        h=2.0 / 128)
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, n_hidden=3, width=128, mu_minus=1.0,
+                        mu_plus=10.0, h=2.0 / 128)
     P = 2 * O.params_per_net(pr)
     rng = np.random.default_rng(0)
     th = rng.uniform(-0.1, 0.1, P)
     m = np.zeros(P)
     v = np.zeros(P)
 
-    def run(n):
-        pts = O.sample_points(pr, 1, 1, n, 0)
-        t0 = time.perf_counter()
+    def step(t, n):
+        pts = O.sample_points(pr, 1, t, n, 0)
         _, g = O.loss_grad(pr, th, pts)
-        O.adam_step(th, m, v, g, 1)
-        return time.perf_counter() - t0
+        O.adam_step(th, m, v, g, t)
 
-    t1 = run(1024)
-    n = int(min(BATCH, max(1024, 1024 * target_s / max(t1, 1e-3))))
-    t = run(n)
-    cores = os.cpu_count()
-    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} sampled points of the {BATCH}-point step (loss, gradient, Adam), "
-                      f"FP64 oracle, OpenMP {cores} threads, {t:.1f} s"}
+    t0 = time.perf_counter()
+    step(1, 1024)
+    t1 = time.perf_counter() - t0
+    n = int(min(BATCH, max(256, 1024 * target_s / (steps * max(t1, 1e-4)))))
+    for k in range(warmup):
+        step(2 + k, n)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        step(2 + warmup + k, n)
+    t = time.perf_counter() - t0
+    cores = O.default_threads()
+    return {"value": steps * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} sampled points of the {BATCH}-point step (loss, gradient, Adam) "
+                      f"x {steps} steps after {warmup} warm-up, FP64 oracle, OpenMP {cores} "
+                      f"threads, {t:.1f} s"}
 
 
 def sphere_exact(x):
@@ -349,7 +357,7 @@ def cpu_baseline_grid():
     from oracle import pyoracle as O
     O.build()
     pr = O.make_problem(geometry=O.GEOM_SPHERE, mu_minus=1.0, mu_plus=10.0)
-    out = {"kind": "oracle", "cores": os.cpu_count()}
+    out = {"kind": "oracle", "cores": O.default_threads()}
     for n in (64, 128):
         t0 = time.perf_counter()
         st, _, it, rr = O.grid_cg_solve(pr, n, rtol=1e-10, max_iter=100000)
@@ -482,7 +490,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    cb = cpu_baseline(target_s=min(20.0, 4.0 * max(1, args.steps // 10)))
+    cb = cpu_baseline(target_s=60.0, steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * BATCH / cb["value"], "higher_is_better": True,

@@ -743,6 +743,8 @@ static int pick_threads(int n_threads) {
 #endif
 }
 
+int nbo_default_threads(void) { return pick_threads(0); }
+
 double nbo_loss(const nbo_problem* pr, const double* theta, const double* pts, int64_t n,
                 double* r2_out, int n_threads) {
   if (n <= 0) return 0.0;

@@ -126,6 +126,9 @@ void nbo_train(const nbo_problem* pr, double* theta, double* m, double* v, int64
                int n_steps, int64_t batch, int64_t n_band, double lr, double beta1, double beta2,
                double eps, uint64_t seed, double* loss_hist, int n_threads);
 
+/* Threads a call with n_threads = 0 uses (OpenMP's default team size). */
+int nbo_default_threads(void);
+
 /* ---- grid evaluation of the trained pair and the grid scheme (judge) ---- */
 void nbo_eval_grid(const nbo_problem* pr, const double* theta, int n, double* u_out /*(n+1)^3*/,
                    int n_threads);

@@ -132,6 +132,8 @@ def lib():
             L.nbo_train.argtypes = [_P, _D, _D, _D, C.c_int64, C.c_int, C.c_int64, C.c_int64,
                                     C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64,
                                     _D, C.c_int]
+            L.nbo_default_threads.argtypes = []
+            L.nbo_default_threads.restype = C.c_int
             L.nbo_eval_grid.argtypes = [_P, _D, C.c_int, _D, C.c_int]
             L.nbo_grid_assemble_dense.argtypes = [_P, C.c_int, _D, _D]
             L.nbo_grid_cg_solve.argtypes = [_P, C.c_int, C.c_double, C.c_int, _D,
@@ -304,6 +306,11 @@ def train(pr, theta, m, v, step0, n_steps, batch, n_band, lr=1e-3, beta1=0.9, be
     lib().nbo_train(C.byref(pr), _dp(theta), _dp(m), _dp(v), step0, n_steps, batch, n_band, lr,
                     beta1, beta2, eps, seed, _dp(hist), n_threads)
     return hist
+
+
+def default_threads():
+    """Threads the oracle's parallel loops use when n_threads = 0."""
+    return lib().nbo_default_threads()
 
 
 def eval_grid(pr, theta, n, n_threads=0):
