@@ -222,6 +222,17 @@ MUTANTS = [
      "        double q[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};\n"
      "        int s = nbo_phase(pr, q);\n        double e", None),
     ("py_grid_error", P, "return a.value, b.value\n", "return b.value, a.value\n", None),
+    # degenerate cases
+    ("flower_axis", C, "if (rho == 0.0) return;", "if (rho < 0.0) return;", None),
+    ("loss_empty", C,
+     "  if (n <= 0) return 0.0;\n  int nt = pick_threads(n_threads);\n"
+     "  double* part = (double*)calloc(nt, sizeof(double));\n#pragma omp",
+     "  int nt = pick_threads(n_threads);\n"
+     "  double* part = (double*)calloc(nt, sizeof(double));\n#pragma omp", None),
+    ("fit_chol_guard", C, "if (!(t > 1e-8 * M[0][0])) return 1;", "if (!(t > 0.0)) return 1;",
+     None),
+    ("fit_count", C, "if (cnt < 4) return 1;", "if (cnt < 1) return 1;",
+     "fewer than four nodes cannot span an affine basis, so the Cholesky guard refuses them"),
 ]
 
 

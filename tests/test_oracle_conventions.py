@@ -15,6 +15,8 @@ arithmetic:
 - the warm start of the lagged passes;
 - the grid error metrics and the boundary values of the grid solution.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -346,3 +348,58 @@ def test_normal_derivative_fit_is_centred_one_spacing_into_its_side(geom, s):
         dn = O.fit_dn(pr, n, u, s, xg, nrm)
         assert dn is not None
         assert abs(dn - (Hm @ c + bv) @ nrm) <= 1e-11
+
+
+# ------------------------------------------------------ degenerate cases ----
+def test_flower_gradient_on_the_polar_axis_is_radial():
+    """On the z axis the flower's angular term has no derivative (a conical
+    point: sin(5 theta) cos(3 psi) behaves like rho cos(3 psi) / z there).
+    The reading takes the radial gradient x / |x|, the average of the
+    directional derivatives around the axis."""
+    pr = O.make_problem(geometry=O.GEOM_FLOWER)
+    for z in (0.5, -0.25, 0.625):
+        g = O.grad_phi(pr, np.array([0.0, 0.0, z]))
+        assert np.array_equal(g, np.array([0.0, 0.0, math.copysign(1.0, z)]))
+
+
+def test_empty_batch_has_zero_loss_and_gradient():
+    pr = O.make_problem(geometry=O.GEOM_SPHERE, n_hidden=2, width=4, h=2.0 / 16)
+    th = np.random.default_rng(2).normal(size=2 * O.params_per_net(pr))
+    pts = np.zeros((0, 3))
+    assert O.loss(pr, th, pts) == 0.0
+    L, g = O.loss_grad(pr, th, pts)
+    assert L == 0.0 and np.all(g == 0.0) and len(g) == len(th)
+    assert O.sample_points(pr, 1, 1, 0, 0).shape == (0, 3)
+
+
+def test_normal_derivative_fit_refuses_degenerate_node_sets():
+    """The fit needs four side-s nodes that span an affine basis.  Coplanar
+    side-s nodes in the block, or fewer than four of them, give no value, and
+    the node keeps its first-order jump."""
+    m, n = 8, 16
+    h = 2.0 / n
+    gm = -1.0 + np.arange(m + 1) * (2.0 / m)
+    Zm, Ym, Xm = np.meshgrid(gm, gm, gm, indexing="ij")
+    u = np.zeros((n + 1) ** 3)
+    node = -1.0 + 9 * h
+    # phi = x - c with c a quarter spacing above the node plane x = node - h.
+    # The block centred at (node, -h, 0) (normal along y) spans the planes
+    # node - h, node, node + h, and only the first is on the minus side.
+    c = node - 0.75 * h
+    pr = O.make_problem(geometry=O.GEOM_GRID, phi_grid=Xm - c)
+    xg = np.array([node, 0.0, 0.0])
+    assert O.fit_dn(pr, n, u, 0, xg, np.array([0.0, 1.0, 0.0])) is None
+    # off the node, rounding leaves the degenerate pivot at about +2e-15
+    # instead of 0: the relative guard still refuses the set
+    xg_off = np.array([0.12632993277877888, 0.0, 0.0])
+    assert O.fit_dn(pr, n, u, 0, xg_off, np.array([0.0, 1.0, 0.0])) is None
+    # the plus side of the same block holds two planes: a valid fit (u = 0)
+    assert O.fit_dn(pr, n, u, 1, xg, np.array([0.0, -1.0, 0.0])) == 0.0
+    # a corner: x + y + z <= c3 keeps only the block's corner node
+    c3 = 3.0 * node - 2.5 * h
+    pr3 = O.make_problem(geometry=O.GEOM_GRID, phi_grid=Xm + Ym + Zm - c3)
+    d = np.full(3, 1.0 / math.sqrt(3.0))
+    assert O.fit_dn(pr3, n, u, 0, np.full(3, node) + h * d, d) is None
+    # a quarter spacing further out it keeps four nodes, a tetrahedron: a fit
+    pr4 = O.make_problem(geometry=O.GEOM_GRID, phi_grid=Xm + Ym + Zm - (c3 + 1.25 * h))
+    assert O.fit_dn(pr4, n, u, 0, np.full(3, node) + h * d, d) == 0.0
