@@ -41,6 +41,11 @@ BATCH = 262_144
 # DRAM bytes (read + write) per launch of the fused kernel, from the ncu capture
 # summarised in profiles/fused_step_tc_C2.md; None when the kernel changed since.
 FUSED_TRAFFIC_BYTES = 9_010_000  # 8.93 MB read + 0.08 MB write per launch (ncu capture of k_step_tc, profiles/fused_step_tc_C2.md)
+# libnbm kernel launches per timed step (one nbm_train_steps call of one C2
+# step): k_prep_weights; k_sample_classify, k_scan_counts, k_scatter;
+# k_cut_geometry, k_gather_tiles; k_step_tc (cut-cell forward),
+# k_cut_residual; k_step_tc (fused train step); k_loss, k_reduce_adam
+LAUNCHES_PER_STEP = 11
 
 
 def _peaks():
@@ -649,7 +654,7 @@ def main():
                        "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},
             "fp32_path": {"value": value32, "unit": UNIT, "steps": k32,
                           "ms_per_step": ms32 / k32, "mixed_speedup": value / value32},
-            "roofline": roof, "e2e": e2e, "gpu_launches": 9 * args.steps,
+            "roofline": roof, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk.summary(), "wall_s": wall}
     if ws == 1 and not args.no_secondary:
         line["secondary"] = secondary(dev, hbm, peak_src, burst, sustained)
