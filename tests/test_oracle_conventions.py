@@ -163,6 +163,31 @@ def test_grid_evaluation_takes_the_network_of_the_node_phase(n):
     assert np.any(X * X + Y * Y + Z * Z == 0.25)
 
 
+def test_grid_evaluation_orders_nodes_x_fastest():
+    """Node (i, j, k) of the evaluated grid is at (-1 + i h, -1 + j h, -1 + k h)
+    and sits at index i + (n+1)(j + (n+1) k).  Seen through a mesh level set
+    that is linear in x, y and z with different slopes: its indicator is not
+    symmetric under any swap of the axes.  phi is at least 1/40 away from 0 at
+    every node."""
+    m, n = 4, 8
+
+    def lin(x, y, z):
+        return x + 0.5 * y - 0.25 * z - 0.1
+
+    gm = -1.0 + np.arange(m + 1) * (2.0 / m)
+    Zm, Ym, Xm = np.meshgrid(gm, gm, gm, indexing="ij")
+    pr = O.make_problem(geometry=O.GEOM_GRID, n_hidden=2, width=4, phi_grid=lin(Xm, Ym, Zm))
+    Pn = O.params_per_net(pr)
+    th = np.zeros(2 * Pn)
+    th[2 * Pn - 1] = 1.0
+    u = O.eval_grid(pr, th, n)
+    g = -1.0 + np.arange(n + 1) * (2.0 / n)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    ph = lin(X, Y, Z)
+    assert np.min(np.abs(ph)) >= 0.025 - 1e-15
+    assert np.array_equal(u, (ph > 0).astype(float).reshape(-1))
+
+
 # ------------------------------------------------ point rows vs grid rows ----
 def _interior_nodes(n):
     g = -1.0 + np.arange(1, n) * (2.0 / n)
@@ -218,7 +243,7 @@ def test_point_row_is_the_grid_row_at_the_exact_solution(geom, sol):
     assert n_cut > 20
 
 
-# ------------------------------------------------------------- grid CG ----
+# ------------------------------------------------ grid CG and node jumps ----
 @pytest.mark.parametrize("mu_plus", [10.0, 1000.0])
 def test_grid_cg_is_jacobi_pcg(mu_plus):
     """The oracle's grid CG is Jacobi-preconditioned CG from x = 0 stopped at
@@ -257,29 +282,35 @@ def test_lagged_passes_restart_from_the_previous_solution():
     assert it - it1 < 0.75 * (passes - 1) * it1
 
 
-def test_grid_evaluation_orders_nodes_x_fastest():
-    """Node (i, j, k) of the evaluated grid is at (-1 + i h, -1 + j h, -1 + k h)
-    and sits at index i + (n+1)(j + (n+1) k).  Seen through a mesh level set
-    that is linear in x, y and z with different slopes: its indicator is not
-    symmetric under any swap of the axes.  phi is at least 1/40 away from 0 at
-    every node."""
-    m, n = 4, 8
-
-    def lin(x, y, z):
-        return x + 0.5 * y - 0.25 * z - 0.1
-
-    gm = -1.0 + np.arange(m + 1) * (2.0 / m)
-    Zm, Ym, Xm = np.meshgrid(gm, gm, gm, indexing="ij")
-    pr = O.make_problem(geometry=O.GEOM_GRID, n_hidden=2, width=4, phi_grid=lin(Xm, Ym, Zm))
-    Pn = O.params_per_net(pr)
-    th = np.zeros(2 * Pn)
-    th[2 * Pn - 1] = 1.0
-    u = O.eval_grid(pr, th, n)
-    g = -1.0 + np.arange(n + 1) * (2.0 / n)
+@pytest.mark.parametrize("geom,s", [(O.GEOM_ALL_MINUS, 0), (O.GEOM_ALL_PLUS, 1)])
+def test_normal_derivative_fit_is_centred_one_spacing_into_its_side(geom, s):
+    """The least-squares fit of the lagged jump uses the 3x3x3 block of nodes
+    around the node nearest x_G - h n (minus side) or x_G + h n (plus side).
+    For a quadratic u, the linear fit over a block symmetric about its centre c
+    has slope grad u(c) exactly (the even quadratic part is orthogonal to the
+    odd linear basis).  So the fitted d_n u is grad u(c) . n, and c is visible."""
+    n = 16
+    h = 2.0 / n
+    pr = O.make_problem(geometry=geom)
+    Hm = np.array([[2.0, 0.5, -0.3], [0.5, -1.0, 0.2], [-0.3, 0.2, 1.5]])
+    bv = np.array([0.3, -0.7, 0.4])
+    g = -1.0 + np.arange(n + 1) * h
     Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
-    ph = lin(X, Y, Z)
-    assert np.min(np.abs(ph)) >= 0.025 - 1e-15
-    assert np.array_equal(u, (ph > 0).astype(float).reshape(-1))
+    Q = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    u = 0.5 * np.einsum("pi,ij,pj->p", Q, Hm, Q) + Q @ bv
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        xg = rng.uniform(-0.5, 0.5, size=3)
+        nrm = rng.normal(size=3)
+        nrm /= np.linalg.norm(nrm)
+        target = xg + (h if s == 1 else -h) * nrm
+        c_idx = np.rint((target + 1.0) / h)
+        if np.any(np.abs((target + 1.0) / h - c_idx) > 0.49):
+            continue  # too close to a tie between two nodes
+        c = -1.0 + c_idx * h
+        dn = O.fit_dn(pr, n, u, s, xg, nrm)
+        assert dn is not None
+        assert abs(dn - (Hm @ c + bv) @ nrm) <= 1e-11
 
 
 # -------------------------------------------------------- grid metrics ----
@@ -317,37 +348,6 @@ def test_grid_solution_carries_the_dirichlet_data_on_the_boundary(mode):
     bnd = (np.abs(X) == 1.0) | (np.abs(Y) == 1.0) | (np.abs(Z) == 1.0)
     ref = (X * X + Y * Y + Z * Z)[bnd]
     assert np.max(np.abs(u.reshape(n + 1, n + 1, n + 1)[bnd] - ref)) <= 1e-15
-
-
-@pytest.mark.parametrize("geom,s", [(O.GEOM_ALL_MINUS, 0), (O.GEOM_ALL_PLUS, 1)])
-def test_normal_derivative_fit_is_centred_one_spacing_into_its_side(geom, s):
-    """The least-squares fit of the lagged jump uses the 3x3x3 block of nodes
-    around the node nearest x_G - h n (minus side) or x_G + h n (plus side).
-    For a quadratic u, the linear fit over a block symmetric about its centre c
-    has slope grad u(c) exactly (the even quadratic part is orthogonal to the
-    odd linear basis).  So the fitted d_n u is grad u(c) . n, and c is visible."""
-    n = 16
-    h = 2.0 / n
-    pr = O.make_problem(geometry=geom)
-    Hm = np.array([[2.0, 0.5, -0.3], [0.5, -1.0, 0.2], [-0.3, 0.2, 1.5]])
-    bv = np.array([0.3, -0.7, 0.4])
-    g = -1.0 + np.arange(n + 1) * h
-    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
-    Q = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
-    u = 0.5 * np.einsum("pi,ij,pj->p", Q, Hm, Q) + Q @ bv
-    rng = np.random.default_rng(12)
-    for _ in range(20):
-        xg = rng.uniform(-0.5, 0.5, size=3)
-        nrm = rng.normal(size=3)
-        nrm /= np.linalg.norm(nrm)
-        target = xg + (h if s == 1 else -h) * nrm
-        c_idx = np.rint((target + 1.0) / h)
-        if np.any(np.abs((target + 1.0) / h - c_idx) > 0.49):
-            continue  # too close to a tie between two nodes
-        c = -1.0 + c_idx * h
-        dn = O.fit_dn(pr, n, u, s, xg, nrm)
-        assert dn is not None
-        assert abs(dn - (Hm @ c + bv) @ nrm) <= 1e-11
 
 
 # ------------------------------------------------------ degenerate cases ----
