@@ -163,11 +163,14 @@ int nbm_set_level_set(nbm_problem* p, const double* phi, int n, nbm_stream_t str
  * trap: the context stays usable.  Synchronizes the stream. */
 int nbm_selftest_bounded_wait(int64_t budget_cycles, nbm_stream_t stream);
 
-/* Number of FP32 parameters P of the network pair. */
+/* Number of FP32 parameters P of the network pair; -1 for a NULL problem. */
 int64_t nbm_param_count(const nbm_problem* p);
 
 /* Draws n collocation points (Sec. 3: random points in the domain) from the
- * Philox4x32-10 stream keyed by `seed` at counter `step`; pts_out is [n][3]. */
+ * Philox4x32-10 stream keyed by `seed` at counter `step`, as described under
+ * "Collocation points" above; pts_out is a caller-owned DEVICE array [n][3].
+ * Returns NBM_ERR_INVALID_ARG for a NULL argument, n outside 1..2^30 or a
+ * misaligned pts_out.  Asynchronous. */
 int nbm_sample_points(nbm_problem* p, uint64_t seed, int64_t step, int64_t n, float* pts_out,
                       nbm_stream_t stream);
 
