@@ -210,15 +210,21 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
 
 /* Evaluates the trained surrogate on the (n+1)^3 nodes -1 + i*2/n of the
  * cube, each node with the network of its side of Gamma (phi <= 0: minus).
- * Node (i,j,k) is u_out[i + (n+1)(j + (n+1)k)].  `precision` selects the
- * hidden-GEMM type (nbm_precision). */
+ * Node (i,j,k) is u_out[i + (n+1)(j + (n+1)k)], a caller-owned DEVICE array.
+ * `precision` selects the hidden-GEMM type (nbm_precision): NBM_PREC_FP32
+ * (CUDA cores; asynchronous), or NBM_PREC_BF16 / NBM_PREC_FP16 (tensor cores;
+ * width 128 and 2..4 hidden layers only; these allocate their scratch,
+ * synchronize the stream and free it).
+ * Returns NBM_ERR_INVALID_ARG for a NULL or misaligned argument, n outside
+ * 1..4096 or an unsupported precision, NBM_ERR_OOM if the scratch cannot be
+ * allocated, NBM_ERR_DEVICE_TIMEOUT if a bounded device wait gave up. */
 int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision, float* u_out,
                   nbm_stream_t stream);
 
 /* The trained surrogate at n arbitrary points pts [n][3] (FP32, inside the
  * cube), each with the network of its side of the interface; u_out [n].
- * Same precision choices and kernels as nbm_eval_grid.  Synchronizes the
- * stream for the 16-bit paths. */
+ * Same precision choices, kernels, synchronization and errors as
+ * nbm_eval_grid, with 1 <= n <= 2^34 in place of the grid size. */
 int nbm_eval_points(nbm_problem* p, const float* params, const float* pts, int64_t n,
                     int precision, float* u_out, nbm_stream_t stream);
 

@@ -560,7 +560,7 @@ static int eval_common(nbm_problem* p, const float* params, int n, const float* 
   if (e != cudaSuccess) {
     snprintf(msg, sizeof(msg), "grid evaluation: %s", cudaGetErrorString(e));
     set_error_message(msg);
-    return NBM_ERR_CUDA;
+    return e == cudaErrorMemoryAllocation ? NBM_ERR_OOM : NBM_ERR_CUDA;
   }
   return NBM_OK;
 }
