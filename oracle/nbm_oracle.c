@@ -90,6 +90,9 @@ static double grid_phi(const nbo_problem* pr, const double x[3], double g[3]) {
   return c0 * (1.0 - f[2]) + c1 * f[2];
 }
 
+/* The level set, Omega- = {phi <= 0}: the sphere |x| = r0 of Sec. 4.1, the
+ * flower (that sphere with an angular perturbation amp sin(lt theta) cos(lp psi),
+ * the benchmark interface), the no-interface cases, or a mesh level set. */
 double nbo_phi(const nbo_problem* pr, const double x[3]) {
   if (pr->geometry == NBO_GEOM_GRID) return grid_phi(pr, x, NULL);
   double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
@@ -112,6 +115,8 @@ double nbo_phi(const nbo_problem* pr, const double x[3]) {
   return 1.0;
 }
 
+/* grad phi in closed form; for the flower, the radial part plus the chain
+ * rule through the polar angle theta and the azimuth psi. */
 void nbo_grad_phi(const nbo_problem* pr, const double x[3], double g[3]) {
   if (pr->geometry == NBO_GEOM_GRID) {
     grid_phi(pr, x, g);
@@ -380,6 +385,8 @@ static void tet_interface(const double X[4][3], const double f[4], double* area,
   for (int i = 0; i < 3; ++i) wc[i] = a1 * c1[i] + a2 * c2[i];
 }
 
+/* Geometry of the cell p + [-h/2, h/2]^3 (Fig. 2): volume fractions V^s, face
+ * fractions A^s_f, interface area fraction S and interface point x_G. */
 void nbo_cell_geometry(const nbo_problem* pr, const double p[3], double h, nbo_cell* out) {
   memset(out, 0, sizeof(*out));
   /* corner c has offsets ((c&1), (c>>1)&1, (c>>2)&1) - 1/2, times h */
@@ -518,6 +525,7 @@ static double mlp_forward(const nbo_problem* pr, const double* th, const double 
   return u;
 }
 
+/* one network's output at x (parameter layout as above) */
 double nbo_mlp_eval(const nbo_problem* pr, const double* theta_net, const double x[3]) {
   return mlp_forward(pr, theta_net, x, NULL);
 }
@@ -729,6 +737,7 @@ static void point_core(const nbo_problem* pr, const double* theta, const double 
   free(acts);
 }
 
+/* B, D, J and r_p^2 of one point (Sec. 3), without the gradient */
 void nbo_point_terms_eval(const nbo_problem* pr, const double* theta, const double p[3], int mode,
                           nbo_point_terms* out) {
   point_core(pr, theta, p, mode, 0.0, NULL, out);
@@ -745,6 +754,9 @@ static int pick_threads(int n_threads) {
 
 int nbo_default_threads(void) { return pick_threads(0); }
 
+/* The loss: the mean of r_p^2 over the points (Sec. 3 aggregates the point
+ * residuals into one loss; the mean of squares is the reading taken).
+ * r2_out (if not NULL) receives every r_p^2. */
 double nbo_loss(const nbo_problem* pr, const double* theta, const double* pts, int64_t n,
                 double* r2_out, int n_threads) {
   if (n <= 0) return 0.0;
@@ -772,6 +784,9 @@ double nbo_loss(const nbo_problem* pr, const double* theta, const double* pts, i
   return s / (double)n;
 }
 
+/* The loss and its gradient with respect to both networks' parameters, by
+ * the reverse mode of point_core (Sec. 3: the gradient passes through the
+ * NBM kernels). */
 double nbo_loss_grad(const nbo_problem* pr, const double* theta, const double* pts, int64_t n,
                      double* grad, int n_threads) {
   int64_t P = 2 * nbo_params_per_net(pr);
@@ -820,6 +835,9 @@ void nbo_adam_step(double* theta, double* m, double* v, const double* grad, int6
   }
 }
 
+/* n_steps training steps (Sec. 3): step t = step0 + k + 1 samples its batch
+ * at Philox counter t, takes the loss gradient there and applies Adam with
+ * the bias correction of step t. */
 void nbo_train(const nbo_problem* pr, double* theta, double* m, double* v, int64_t step0,
                int n_steps, int64_t batch, int64_t n_band, double lr, double beta1, double beta2,
                double eps, uint64_t seed, double* loss_hist, int n_threads) {
@@ -846,6 +864,9 @@ static int64_t node_id(int n, int i, int j, int k) {
   return (int64_t)i + (int64_t)(n + 1) * ((int64_t)j + (int64_t)(n + 1) * k);
 }
 
+/* The trained pair on the (n+1)^3 nodes, each node with the network of its
+ * phase (the use of a trained model in Fig. 1); node (i,j,k) at
+ * i + (n+1)(j + (n+1)k). */
 void nbo_eval_grid(const nbo_problem* pr, const double* theta, int n, double* u_out, int n_threads) {
   int64_t Pn = nbo_params_per_net(pr);
   double hg = 2.0 / n;
@@ -930,6 +951,7 @@ static void grid_row_build(const nbo_problem* pg, int n, int i, int j, int k, co
   row->rhs = -known;
 }
 
+/* the grid system as a dense matrix (small n only), exact node jump */
 int nbo_grid_assemble_dense(const nbo_problem* pr, int n, double* A, double* b) {
   nbo_problem pg = *pr;
   pg.h = 2.0 / n;
@@ -1026,6 +1048,7 @@ static int grid_cg_core(const grid_row* rows, int m1, double* x, double rtol, in
   return status;
 }
 
+/* the rows of every interior node (OpenMP over rows) */
 static void grid_rows_all(const nbo_problem* pg, int n, const double* Jn, grid_row* rows, int nt) {
   int m1 = n - 1;
   int64_t m = (int64_t)m1 * m1 * m1;
@@ -1053,6 +1076,9 @@ static void grid_write_nodes(const nbo_problem* pg, int n, const double* x, doub
       }
 }
 
+/* The grid method the NBM is bootstrapped from (Sec. 1, Sec. 3): the rows
+ * above on the grid of spacing 2/n with the exact node jump, solved by Jacobi
+ * PCG from zero to ||b - A x|| <= rtol ||b||. */
 int nbo_grid_cg_solve(const nbo_problem* pr, int n, double rtol, int max_iter, double* u_out,
                       int* iters_out, double* relres_out, int n_threads) {
   nbo_problem pg = *pr;
