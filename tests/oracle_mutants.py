@@ -135,8 +135,8 @@ MUTANTS = [
      "c[7] = has_jump ? (s == 1 ? -cJ : cJ) : 0.0;", None),
     ("grad_c0", C, "c[0] += cell.A[s][f] * muf[s][f];\n        c[1 + f]",
      "c[0] -= cell.A[s][f] * muf[s][f];\n        c[1 + f]", None),
-    ("loss_mean", C, "  free(part);\n  return s / (double)n;\n}\n\ndouble nbo_loss_grad",
-     "  free(part);\n  return s / (double)(n + 1);\n}\n\ndouble nbo_loss_grad", None),
+    ("loss_mean", C, "  free(part);\n  return s / (double)n;\n}\n\n/* The loss and its gradient",
+     "  free(part);\n  return s / (double)(n + 1);\n}\n\n/* The loss and its gradient", None),
     ("loss_grad_scale", C, "double scale = 1.0 / (double)n;", "double scale = 2.0 / (double)n;", None),
     ("levels_h", P, "q.h = pr.h / 2.0 ** level", "q.h = pr.h / 2.0 ** (level + 1)", None),
     ("levels_count", P, "for lv in range(levels + 1):\n        L, r2 = loss(",
