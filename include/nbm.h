@@ -38,8 +38,9 @@
  *    word j as k = 1 + floor(w_j (2^23 - 1) / 2^32).  A band point takes an
  *    isotropic direction and an offset uniform on (-4h, 4h) from the
  *    interface along it, rounded to the lattice.
- *  - Batch sizes n of the point calls are 1..2^30; any other n, including an
- *    empty batch, returns NBM_ERR_INVALID_ARG.
+ *  - Batch sizes n of nbm_sample_points, nbm_residual, nbm_loss_grad and
+ *    nbm_train_steps are 1..2^30; any other n, including an empty batch,
+ *    returns NBM_ERR_INVALID_ARG.
  *  - One nbm_problem may be used by one host thread at a time.
  */
 #ifndef NBM_H
