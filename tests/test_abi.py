@@ -74,3 +74,44 @@ def test_grid_entry_points_reject_null_arguments_without_a_gpu():
     assert lib.nbm_grid_last_jump_info(ctypes.byref(ps), ctypes.byref(dj), ctypes.byref(fb)) == 0
     assert ps.value >= 0 and fb.value in (0, 1)
     assert lib.nbm_grid_last_jump_info(None, None, None) == 0
+
+
+def test_header_compiles_as_c_and_agrees_with_the_binding(tmp_path):
+    """include/nbm.h is plain C: a C11 program includes it, links libnbm.so and
+    calls it.  Every field offset of nbm_problem_desc matches the ctypes mirror
+    of the Python binding, and an invalid descriptor is refused from C (status
+    NBM_ERR_INVALID_ARG, *out set to NULL) without a GPU."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import paper_2210_14907_gb300 as nbm
+    from paper_2210_14907_gb300 import build
+    libdir = os.path.dirname(build.build())
+    names = [f[0] for f in nbm._Desc._fields_]
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "nbm.h"', "int main(void) {",
+           '  printf("size %zu\\n", sizeof(nbm_problem_desc));']
+    src += [f'  printf("{n} %zu\\n", offsetof(nbm_problem_desc, {n}));' for n in names]
+    src += ["  nbm_problem_desc d = {0};", "  d.geometry = NBM_GEOM_SPHERE;", "  d.n_hidden = 2;",
+            "  d.width = 96;",
+            "  nbm_problem* p = (nbm_problem*)&d;",
+            "  int rc = nbm_init_problem(&d, &p);",
+            '  printf("rc %d %d\\n", rc, p == NULL);',
+            '  printf("count %lld\\n", (long long)nbm_param_count(NULL));',
+            '  printf("msg %s\\n", nbm_last_error());',
+            "  return 0;", "}"]
+    c = tmp_path / "abi.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(c), "-o", str(exe), "-L", libdir, "-lnbm",
+                    "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    vals = dict(line.split(" ", 1) for line in out.splitlines() if line)
+    assert int(vals["size"]) == ctypes.sizeof(nbm._Desc)
+    for n in names:
+        assert int(vals[n]) == getattr(nbm._Desc, n).offset, n
+    assert vals["rc"] == "1 1"
+    assert vals["count"] == "-1"
+    assert "width" in vals["msg"]
