@@ -423,7 +423,7 @@ void nbo_cell_geometry(const nbo_problem* pr, const double p[3], double h, nbo_c
     }
     vneg += nbo_tet_fraction(ft[0], ft[1], ft[2], ft[3]) / 6.0;
     double ta, tw[3];
-    tet_interface(Xt, ft, &ta, tw);
+    tet_interface((const double(*)[3])Xt, ft, &ta, tw);
     area += ta;
     for (int i = 0; i < 3; ++i) wc[i] += tw[i];
   }
