@@ -344,9 +344,14 @@ def table1(dev, epochs, resolutions, lr=1e-3):
         wall = time.perf_counter() - t0
         u = prob.eval_grid(params, N, precision=nbm.PREC_FP32).cpu().numpy()
         linf, rmse = node_errors(u, N, sec41_exact)
+        # the plain grid method on the same rows and grid, for comparison
+        ucg, it_cg, _, ok_cg = prob.grid_cg_solve(N, rtol=1e-10, max_iter=100000)
+        g_linf, g_rmse = node_errors(ucg.cpu().numpy(), N, sec41_exact)
         ref = PAPER_TABLE1.get(N)
         rows.append({"N": N, "h": f"2/{N}", "batch": batch, "steps": steps, "rmse": rmse,
                      "linf": linf, "s_per_epoch": wall / epochs,
+                     "grid_cg": {"rmse": g_rmse, "linf": g_linf, "iterations": it_cg,
+                                 "converged": ok_cg},
                      "final_loss": float(hist[:k].mean()),
                      "paper_rmse": ref[0] if ref else None, "paper_linf": ref[1] if ref else None,
                      "paper_s_per_epoch": ref[2] if ref else None})
