@@ -222,6 +222,13 @@ MUTANTS = [
      "        double q[3] = {-1.0 + i * hg, -1.0 + j * hg, -1.0 + k * hg};\n"
      "        int s = nbo_phase(pr, q);\n        double e", None),
     ("py_grid_error", P, "return a.value, b.value\n", "return b.value, a.value\n", None),
+    # argument marshalling of the Python wrappers
+    ("py_sample_args", P, "lib().nbo_sample_points(C.byref(pr), seed, step, n, n_band, _dp(pts))",
+     "lib().nbo_sample_points(C.byref(pr), step, seed, n, n_band, _dp(pts))", None),
+    ("py_terms_D", P, '"D": t.D,', '"D": t.B,', None),
+    ("py_adam_t", P, "len(theta), t, lr, beta1,", "len(theta), t + 1, lr, beta1,", None),
+    ("py_jump_lag", P, "0 if dn_small is None else 1,", "0,", None),
+    ("py_fit_side", P, "_dp(_vec(u)), s, _dp(_vec(xg))", "_dp(_vec(u)), 1 - s, _dp(_vec(xg))", None),
     # degenerate cases
     ("flower_axis", C, "if (rho == 0.0) return;", "if (rho < 0.0) return;", None),
     ("loss_empty", C,
