@@ -500,7 +500,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    cb = cpu_baseline(target_s=60.0, steps=args.steps, warmup=args.warmup)
+    cb = cpu_baseline(target_s=args.ref_seconds, steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * BATCH / cb["value"], "higher_is_better": True,
@@ -521,6 +521,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp32-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: about this many seconds for the K timed steps")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--table1", action="store_true",
