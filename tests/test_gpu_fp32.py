@@ -162,6 +162,13 @@ def test_invalid_arguments_fail_cleanly():
     with pytest.raises(nbm.NBMError) as e:
         prob.loss_grad(th, n=0)
     assert e.value.code == 1
+    # one point over the largest batch: refused on the host before any allocation
+    with pytest.raises(nbm.NBMError) as e:
+        prob.loss_grad(th, n=2**30 + 1)
+    assert e.value.code == 1
+    with pytest.raises(nbm.NBMError) as e:
+        prob.train_steps(th, torch.zeros_like(th), torch.zeros_like(th), 0, 1, 2**30 + 1)
+    assert e.value.code == 1
     bad = torch.full((prob.P,), float("nan"), device="cuda")
     with pytest.raises(nbm.NBMError) as e:
         prob.loss_grad(bad, n=256)
