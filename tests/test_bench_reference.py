@@ -1,6 +1,7 @@
-"""bench.py --impl reference (the FP64 oracle timed on the host cores) prints
-the one JSON line of the benchmark contract.  Runs on a CPU with a short time
-budget."""
+"""The CPU-side parts of bench.py: the reference arm (the FP64 oracle timed on
+the host cores) prints the one JSON line of the benchmark contract, and the
+helpers behind the reported exact-solution errors agree with the oracle's
+metrics.  Runs on a CPU with a short time budget."""
 import json
 import os
 import subprocess
@@ -30,3 +31,25 @@ def test_reference_arm_prints_the_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_bench_accuracy_helpers_agree_with_the_oracle_metrics():
+    """bench.py reports exact-solution errors with its own numpy helpers; they
+    give the oracle's L-inf and RMS over the interior nodes for both
+    manufactured pairs."""
+    import numpy as np
+
+    import bench
+    from oracle import pyoracle as O
+
+    rng = np.random.default_rng(3)
+    for sol, exact in ((O.SOL_BENCH, bench.sphere_exact), (O.SOL_SEC41, bench.sec41_exact)):
+        pr = O.make_problem(geometry=O.GEOM_SPHERE, solution=sol)
+        for n in (8, 16):
+            g = -1.0 + np.arange(n + 1) * (2.0 / n)
+            Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+            x = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+            u = exact(x) + rng.normal(scale=1e-3, size=len(x))
+            linf, rms = bench.node_errors(u, n, exact)
+            linf_o, rms_o = O.grid_error(pr, n, u)
+            assert abs(linf - linf_o) <= 1e-15 and abs(rms - rms_o) <= 1e-15
