@@ -53,3 +53,24 @@ def test_bench_accuracy_helpers_agree_with_the_oracle_metrics():
             linf, rms = bench.node_errors(u, n, exact)
             linf_o, rms_o = O.grid_error(pr, n, u)
             assert abs(linf - linf_o) <= 1e-15 and abs(rms - rms_o) <= 1e-15
+
+
+def test_bench_trilinear_interpolation_reproduces_multilinear_functions():
+    """bench.py's trilinear interpolation of node values (the grid method's
+    value between nodes in the gain comparison) is exact for any function
+    that is linear in each coordinate, including at the cube's faces."""
+    import numpy as np
+
+    import bench
+
+    def f(x, y, z):
+        return 0.3 - 1.2 * x + 0.7 * y + 2.0 * z + 0.5 * x * y - 0.25 * y * z + 1.5 * x * y * z
+
+    n = 12
+    g = -1.0 + np.arange(n + 1) * (2.0 / n)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    u = f(X, Y, Z).reshape(-1)
+    rng = np.random.default_rng(6)
+    pts = np.concatenate([rng.uniform(-1, 1, size=(500, 3)), [[1.0, 1.0, 1.0], [-1.0, 0.2, 1.0]]])
+    got = bench.trilinear(u, n, pts)
+    assert np.max(np.abs(got - f(pts[:, 0], pts[:, 1], pts[:, 2]))) <= 1e-13
