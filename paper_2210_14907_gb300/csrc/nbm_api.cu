@@ -255,24 +255,29 @@ static cudaError_t launch_timed(Problem& pb, const ProbDev& P, const StepArgs& a
   return e;
 }
 
-// sample/classify .. cut rows; leaves seeds of cut cells in the workspace
+// sample/classify .. cut rows; leaves seeds of cut cells in the workspace.  The
+// n points are points first .. first+n-1 of a batch of n_total (0: n) points:
+// drawn points take their counters and band decisions from the whole batch, and
+// the seeds carry the whole batch's 1/n_total.
 static int front_stages(Problem& pb, const ProbDev& P, const float* params, const float* pts,
                         int64_t n, uint64_t seed, const int64_t* step_dev, int64_t step_host,
-                        bool want_seeds, float* r2_out, cudaStream_t st) {
+                        bool want_seeds, float* r2_out, cudaStream_t st, int64_t first = 0,
+                        int64_t n_total = 0) {
   Workspace& w = pb.ws;
   NvtxRange r("nbm.front (sample, cell geometry, cut rows)");
-  NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, n), w,
-                                  st));
+  const int64_t nt = n_total > 0 ? n_total : n;
+  NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, nt), w,
+                                  st, first, nt));
   NBM_CUDA(launch_cut_geometry(P, n, w, st));
   if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(P, n, w, st));
-  StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)n);
+  StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)nt);
   // The fine-h mode (FP64 rows) evaluates the cut cells' networks on the FP32
   // path: their jump rows U+(x_G) - U-(x_G) - alpha difference two O(1) network
   // values, which 16-bit GEMM operands would carry with ~2^-9 relative error.
   // Cut cells are a small share of the points, so the cost is small.
   if (P.fp64 && pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_step_fp32(P, a, w.grid, st));
   else NBM_CUDA(launch_step(pb, P, a, st));
-  NBM_CUDA(launch_cut_residual(P, n, (float)(1.0 / (double)n), want_seeds, r2_out, w, st));
+  NBM_CUDA(launch_cut_residual(P, n, (float)(1.0 / (double)nt), want_seeds, r2_out, w, st));
   return NBM_OK;
 }
 
@@ -506,6 +511,67 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
                            0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st, lv, nlev));
   }
   if (loss_out) return read_loss(pb, loss_out, st);
+  return NBM_OK;
+}
+
+int nbm_loss_grad_shard(nbm_problem* p, const float* params, const float* pts, int64_t n_total,
+                        int64_t first, int64_t n, uint64_t seed, int64_t step, float* grad_out,
+                        double* loss_out, nbm_stream_t stream) {
+  if (!p || !params || !grad_out || !loss_out) return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  int rc = check_n(n);
+  if (!rc) rc = check_n(n_total);
+  if (!rc && (first < 0 || first > n_total - n))
+    rc = fail(NBM_ERR_INVALID_ARG, "shard [%lld, %lld) outside the batch of %lld points",
+              (long long)first, (long long)(first + n), (long long)n_total);
+  if (!rc) rc = check_aligned(params, 4, "params");
+  if (!rc) rc = check_aligned(pts, 4, "pts");
+  if (!rc) rc = check_aligned(grad_out, 4, "grad_out");
+  if (!rc) rc = check_aligned(loss_out, 8, "loss_out");
+  if (rc) return rc;
+  Problem& pb = p->pb;
+  rc = ws_reserve(pb, n);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
+  const double inv_total = 1.0 / (double)n_total;
+  ProbDev P0;
+  make_prob_dev(pb.desc, P0, 0);
+  if ((rc = attach_level_set(p, P0))) return rc;
+  NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
+  for (int lv = 0; lv < nlev; ++lv) {
+    ProbDev P;
+    make_prob_dev(pb.desc, P, lv);
+    if ((rc = attach_level_set(p, P))) return rc;
+    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st, first,
+                      n_total);
+    if (rc) return rc;
+    StepArgs a = base_args(pb, params, MODE_TRAIN, (float)inv_total);
+    NBM_CUDA(launch_timed(pb, P, a, st));
+    NBM_CUDA(launch_finish(P, n, pb.ws.grid, false, true, nullptr, nullptr, nullptr, grad_out, 0.f,
+                           0.9f, 0.999f, 0.f, nullptr, 0, prec, pb.ws, st, lv, nlev, inv_total));
+  }
+  NBM_CUDA(cudaMemcpyAsync(loss_out, pb.ws.loss, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return NBM_OK;
+}
+
+int nbm_adam_step(nbm_problem* p, float* params, float* adam_m, float* adam_v, const float* grad,
+                  int64_t* step_io, float lr, float beta1, float beta2, float eps,
+                  const double* loss, nbm_stream_t stream) {
+  if (!p || !params || !adam_m || !adam_v || !grad || !step_io)
+    return fail(NBM_ERR_INVALID_ARG, "NULL argument");
+  if (*step_io < 0) return fail(NBM_ERR_INVALID_ARG, "*step_io < 0");
+  if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps > 0.f))
+    return fail(NBM_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  int rc = check_aligned(params, 4, "params");
+  if (!rc) rc = check_aligned(adam_m, 4, "adam_m");
+  if (!rc) rc = check_aligned(adam_v, 4, "adam_v");
+  if (!rc) rc = check_aligned(grad, 4, "grad");
+  if (!rc) rc = check_aligned(loss, 8, "loss");
+  if (rc) return rc;
+  NBM_CUDA(launch_adam(2 * p->pb.p_net, params, adam_m, adam_v, grad, lr, beta1, beta2, eps,
+                       *step_io + 1, loss, (cudaStream_t)stream));
+  *step_io += 1;
   return NBM_OK;
 }
 

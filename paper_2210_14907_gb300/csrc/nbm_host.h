@@ -130,9 +130,14 @@ int attach_level_set(const nbm_problem* p, ProbDev& P);
 int check_aligned(const void* ptr, size_t align, const char* name);
 
 // ---- launchers (return cudaError_t of the launch) ----
+// Draws (pts_in == NULL) or reads n points and classifies their cells.  Drawn
+// point i is point first + i of a batch of n_total points (0: n_total = n), so
+// a shard of a batch gets the counters and band decisions the whole batch
+// would give it; n_band counts the band points of that whole batch.
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
-                                   int64_t n_band, Workspace& ws, cudaStream_t st);
+                                   int64_t n_band, Workspace& ws, cudaStream_t st,
+                                   int64_t first = 0, int64_t n_total = 0);
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
@@ -146,7 +151,14 @@ cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int pr
 cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
-                          Workspace& ws, cudaStream_t st, int level = 0, int n_levels = 1);
+                          Workspace& ws, cudaStream_t st, int level = 0, int n_levels = 1,
+                          double loss_scale = 0.0);  // 0: the loss is the mean over the n points
+// Adam update t (bias-corrected, 1-based) of n parameters with a caller-supplied
+// gradient, by the arithmetic of the fused update.  Skipped when loss != NULL
+// and *loss is not finite.
+cudaError_t launch_adam(int64_t n, float* params, float* m, float* v, const float* grad, float lr,
+                        float b1, float b2, float eps, int64_t t, const double* loss,
+                        cudaStream_t st);
 size_t tc_smem_bytes(int L);
 cudaError_t launch_selftest_wait(long long budget, int* out, cudaStream_t st);
 size_t fp32_smem_bytes(int H, int L);

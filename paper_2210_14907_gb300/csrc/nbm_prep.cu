@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float
                                                           int64_t step_host, int64_t n,
                                                           int64_t n_band, float* X, float* Y,
                                                           float* Z, uint8_t* cls, int* blockcnt,
-                                                          int nb) {
+                                                          int nb, int64_t first, int64_t n_total) {
   int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
   int c = -1;
   if (i < n) {
@@ -104,9 +104,11 @@ __global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float
       p[1] = pts_in[3 * i + 1];
       p[2] = pts_in[3 * i + 2];
     } else {
+      // point first + i of the step's n_total-point batch (band points last)
       int64_t step = step_dev ? (*step_dev + 1) : step_host;
       bool iface = P.geometry == NBM_GEOM_SPHERE || P.geometry == NBM_GEOM_FLOWER;
-      draw_point(P, seed, step, i, iface && i >= n - n_band, p);
+      const int64_t ig = first + i;
+      draw_point(P, seed, step, ig, iface && ig >= n_total - n_band, p);
     }
     X[i] = p[0];
     Y[i] = p[1];
@@ -692,15 +694,55 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
   }
 }
 
+// One Adam update (Kingma & Ba, bias-corrected) with a gradient the caller
+// supplies, e.g. the sum of the data-parallel shards' gradients (Sec. 3: the
+// locally computed gradient updates are aggregated).  Element for element the
+// arithmetic of the update in k_reduce_adam, so one shard covering the whole
+// batch reproduces nbm_train_steps bitwise.
+__global__ void k_adam(int64_t n, float* __restrict__ params, float* __restrict__ m,
+                       float* __restrict__ v, const float* __restrict__ grad, float lr, float b1,
+                       float b2, float eps, int64_t t, const double* __restrict__ loss) {
+  if (loss && !isfinite(*loss)) return;  // non-finite step: skip the update
+  // bias corrections of step t, by the expression k_loss uses for the fused update
+  __shared__ float corr[2];
+  if (threadIdx.x == 0) {
+    corr[0] = (float)(1.0 - pow((double)b1, (double)t));
+    corr[1] = (float)(1.0 - pow((double)b2, (double)t));
+  }
+  __syncthreads();
+  const float c1 = corr[0], c2 = corr[1];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const float g = grad[j];
+    const float mj = b1 * m[j] + (1.f - b1) * g;
+    const float vj = b2 * v[j] + (1.f - b2) * g * g;
+    m[j] = mj;
+    v[j] = vj;
+    const float mh = mj / c1, vh = vj / c2;
+    params[j] = params[j] - lr * mh / (sqrtf(vh) + eps);
+  }
+}
+
 // ------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------
+cudaError_t launch_adam(int64_t n, float* params, float* m, float* v, const float* grad, float lr,
+                        float b1, float b2, float eps, int64_t t, const double* loss,
+                        cudaStream_t st) {
+  const int64_t blocks = (n + 255) / 256;
+  k_adam<<<(int)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(n, params, m, v, grad, lr, b1, b2,
+                                                                eps, t, loss);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
-                                   int64_t n_band, Workspace& ws, cudaStream_t st) {
+                                   int64_t n_band, Workspace& ws, cudaStream_t st,
+                                   int64_t first, int64_t n_total) {
   int nb = (int)((n + kBlk - 1) / kBlk);
   k_sample_classify<<<nb, kBlk, 0, st>>>(P, pts_in, seed, step_dev, step_host, n, n_band, ws.x,
-                                         ws.y, ws.z, ws.cls, ws.blockcnt, nb);
+                                         ws.y, ws.z, ws.cls, ws.blockcnt, nb, first,
+                                         n_total > 0 ? n_total : n);
   k_scan_counts<<<1, 1024, 0, st>>>(ws.blockcnt, nb, ws.counters);
   k_scatter<<<nb, kBlk, 0, st>>>(ws.cls, n, ws.blockcnt, nb, ws.list_minus, ws.list_plus,
                                  ws.cut_pt);
@@ -750,10 +792,12 @@ cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec,
 cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
-                          Workspace& ws, cudaStream_t st, int level, int n_levels) {
+                          Workspace& ws, cudaStream_t st, int level, int n_levels,
+                          double loss_scale) {
   const bool last = level == n_levels - 1;
   int ncb = cut_residual_blocks(n, ws);
-  k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb, 1.0 / (double)n, ws.loss,
+  k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb,
+                            loss_scale > 0.0 ? loss_scale : 1.0 / (double)n, ws.loss,
                             adam ? ws.step : nullptr, loss_hist, hist_base, ws.status, b1, b2,
                             ws.corr, ws.loss_acc, level > 0, last);
   if (adam || want_grad) {
