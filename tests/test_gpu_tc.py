@@ -1,14 +1,17 @@
 """Parity of the BF16 tcgen05 path with the FP64 oracle (through the C ABI).
 
 Tolerances (mixed path): residual and loss relative error <= 2e-3, gradient
-relative error (2-norm) <= 5e-3.  Residual error is measured on r_p, norm-wise.
+relative error (2-norm) <= 5e-3.  The residual r_p is checked norm-wise over the
+batch against that bar and point by point against the bound of tests/parity.py
+(4 BF16 unit roundoffs relative, plus the rounding of the network values in a
+cut cell's jump row).
 """
 import numpy as np
 import pytest
 import torch
 
 from oracle import pyoracle as O
-from tests import inputs
+from tests import inputs, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +63,8 @@ def test_bf16_residual_loss_gradient_match_oracle(case):
     print(f"bf16 case {case[:3]}: residual {er:.2e} loss {el:.2e} grad {eg:.2e}")
     assert er <= RES_TOL and el <= LOSS_TOL and abs(loss2 - L_ref) / L_ref <= LOSS_TOL
     assert eg <= GRAD_TOL
+    parity.check_points(o, th, pts, r2.cpu().numpy(), r2_ref, *parity.bf16_tols(L),
+                        label=f"bf16 {case[:3]}")
 
 
 def test_bf16_ragged_and_tiny_batches():
@@ -74,22 +79,39 @@ def test_bf16_ragged_and_tiny_batches():
         assert _rel(g.cpu().numpy(), g_ref) <= GRAD_TOL, n
 
 
-def test_bf16_training_tracks_fp32_training():
-    """C2 shape, 30 steps at a reduced batch: the mixed path's loss curve follows the FP32 path."""
+def test_bf16_adam_trajectory_follows_the_oracle():
+    """C2 architecture (sphere, h = 2/128, 3 -> 128^3 -> 1), 16,384 device-drawn
+    points per step, 10 Adam steps of the mixed path against the oracle's own
+    training loop from the same parameters (nbo_train: same Philox points, FP64
+    forward, gradient and Adam)."""
     nbm = _nbm()
-    res = {}
-    for prec in (nbm.PREC_FP32, nbm.PREC_BF16):
-        d = nbm.config("C2", precision=prec)
-        prob = nbm.Problem(d)
-        tp = torch.from_numpy(inputs.glorot_params(128, 3, seed=0)).cuda()
-        m = torch.zeros_like(tp)
-        v = torch.zeros_like(tp)
-        hist = torch.zeros(30, device="cuda")
-        prob.train_steps(tp, m, v, 0, 30, 16384, lr=1e-3, seed=1, loss_hist=hist)
-        res[prec] = hist.cpu().numpy()
-    h32, h16 = res[nbm.PREC_FP32], res[nbm.PREC_BF16]
-    assert np.all(np.isfinite(h16)) and h16[-1] < h16[0]
-    assert np.max(np.abs(h16 - h32) / h32) < 2e-2
+    d = nbm.config("C2")
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_SPHERE, n_hidden=3, width=128, mu_minus=1.0,
+                       mu_plus=10.0, h=2 / 128)
+    th = inputs.glorot_params(128, 3, seed=0)
+    steps, batch, lr = 10, 16384, 1e-3
+    th_o = th.astype(np.float64)
+    m_o = np.zeros_like(th_o)
+    v_o = np.zeros_like(th_o)
+    hist_o = O.train(o, th_o, m_o, v_o, 0, steps, batch, 0, lr=lr, seed=1)
+    tp = torch.from_numpy(th).cuda()
+    m = torch.zeros_like(tp)
+    v = torch.zeros_like(tp)
+    hist = torch.zeros(steps, device="cuda")
+    prob.train_steps(tp, m, v, 0, steps, batch, lr=lr, seed=1, loss_hist=hist)
+    hist = hist.cpu().numpy()
+    got = tp.cpu().numpy().astype(np.float64)
+    # every step's loss within the mixed path's loss tolerance
+    assert np.max(np.abs(hist - hist_o) / hist_o) <= LOSS_TOL
+    # the parameters after 10 updates: Adam moves each component by about lr per
+    # step whatever its gradient's size, so a component whose gradient is within
+    # the BF16 error of zero may move the other way (measured: 0.07 % of them by
+    # more than lr/2); all together they stay within the gradient tolerance
+    assert _rel(got, th_o) <= GRAD_TOL
+    moved = np.abs((got - th) - (th_o - th))
+    assert np.mean(moved > 0.5 * lr) <= 1e-2
+    assert moved.max() <= 2 * steps * lr
 
 
 def test_bf16_deterministic_and_resumable():
@@ -168,6 +190,8 @@ def test_extreme_points_and_corners_on_the_interface(prec, H, L, tol_r, tol_g):
     r2 = r2.cpu().numpy()
     assert np.all(np.isfinite(r2))
     assert _rel(np.sqrt(r2), np.sqrt(r2_ref)) <= tol_r
-    assert _rel(np.sqrt(r2[:16]), np.sqrt(r2_ref[:16])) <= tol_r  # the special points alone
+    # every point, the 16 special ones included, within its own bound
+    tols = parity.bf16_tols(L) if prec == 1 else (tol_r, tol_r)
+    parity.check_points(o, th, pts, r2, r2_ref, *tols, label=f"extreme points prec {prec}")
     assert abs(loss - L_ref) <= tol_r * L_ref
     assert _rel(g.cpu().numpy(), g_ref) <= tol_g

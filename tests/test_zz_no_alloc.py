@@ -1,9 +1,11 @@
 """nbm_loss_grad_static, the entry point that allocates no device memory.
 
-It exists for callers that cannot call cudaMalloc while they run: code that
-executes inside a CUDA-graph capture or a caller-owned memory pool, hosts that
-forbid allocation after start-up, and plugins whose host framework owns all
-device memory.  Its scratch is one static device array inside libnbm.
+It exists for callers that cannot call cudaMalloc while they run: hosts whose
+own pool or arena owns all device memory (plugins, inference servers),
+real-time or embedded hosts that forbid allocation after start-up, and code
+that must not synchronize the device as cudaMalloc and cudaFree may.  Its
+scratch is one static device array inside libnbm.  Its results are checked
+against the FP64 oracle and against the allocating nbm_loss_grad.
 
 This file runs last (pytest collects it last), so a failure here leaves every
 other test already run.  It passes both alone in a fresh process and after the
@@ -15,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import pyoracle as O
 from tests import inputs
 
 pytestmark = pytest.mark.gpu
@@ -36,12 +39,16 @@ def test_static_scratch_matches_allocating_entry_point_twice(prec, loss_tol, gra
     d = nbm.ProblemDesc(geometry=nbm.GEOM_FLOWER, n_hidden=3, width=128, precision=prec,
                         mu_minus=1.0, mu_plus=100.0, h=2.0 / 128)
     prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_FLOWER, n_hidden=3, width=128, mu_minus=1.0,
+                       mu_plus=100.0, h=2.0 / 128)
     fn = _static_entry(prob.lib)
     stream = torch.cuda.current_stream()
     for call in range(2):
-        pts = torch.from_numpy(inputs.mixed_points(3000, 1000, seed=40 + call)
-                               .astype(np.float32)).cuda()
-        th = torch.from_numpy(inputs.glorot_params(128, 3, seed=call, bias_scale=0.1)).cuda()
+        p32 = inputs.mixed_points(3000, 1000, seed=40 + call).astype(np.float32)
+        pts = torch.from_numpy(p32).cuda()
+        th_np = inputs.glorot_params(128, 3, seed=call, bias_scale=0.1)
+        th = torch.from_numpy(th_np).cuda()
+        loss_o, g_o = O.loss_grad(o, th_np.astype(np.float64), p32.astype(np.float64))
         loss_ref, g_ref = prob.loss_grad(th, pts)
         g = torch.full((prob.P,), float("nan"), device="cuda")
         loss = ctypes.c_double(0.0)
@@ -52,6 +59,10 @@ def test_static_scratch_matches_allocating_entry_point_twice(prec, loss_tol, gra
         torch.cuda.synchronize()
         g = g.cpu().numpy().astype(np.float64)
         g_ref = g_ref.cpu().numpy().astype(np.float64)
+        # against the FP64 oracle, within the path's tolerances
+        assert abs(loss.value - loss_o) / loss_o <= loss_tol
+        assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) <= grad_tol
+        # and against the allocating entry point on the same inputs
         assert abs(loss.value - loss_ref) / loss_ref <= loss_tol
         assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= grad_tol
 
