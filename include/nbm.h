@@ -196,6 +196,45 @@ int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t 
 int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t n, uint64_t seed,
                   int64_t step, float* grad_out, double* loss_out, nbm_stream_t stream);
 
+/* One data-parallel shard of a training step's loss and gradient (Sec. 3: the
+ * collocation points of a step are distributed over processors and their
+ * locally computed gradient updates are aggregated).  The step's batch has
+ * n_total points; this call takes points first .. first+n-1 of it:
+ *   pts [n][3] or NULL   the shard's points; NULL draws them on the device as
+ *                        points first .. first+n-1 of nbm_sample_points(seed,
+ *                        step, n_total) (same counters, same band points)
+ *   grad_out [P]         overwritten with (1/n_total) sum over the shard of
+ *                        the gradient of r_p^2
+ *   loss_out [1]         DEVICE, FP64, 8-byte aligned: (1/n_total) sum over the
+ *                        shard of r_p^2
+ * Summed over shards that partition [0, n_total) (e.g. by an all-reduce),
+ * grad_out and loss_out are the whole batch's gradient and loss, up to the
+ * order of FP32 additions; nbm_adam_step then applies the update on every
+ * rank.  Fully asynchronous: nothing is read back, so a bounded device wait
+ * that gave up is reported by the next call of this problem that returns a
+ * loss on the host.
+ * Returns NBM_ERR_INVALID_ARG for a NULL or misaligned argument, n or n_total
+ * outside 1..2^30, or a shard outside [0, n_total). */
+int nbm_loss_grad_shard(nbm_problem* p, const float* params, const float* pts, int64_t n_total,
+                        int64_t first, int64_t n, uint64_t seed, int64_t step, float* grad_out,
+                        double* loss_out, nbm_stream_t stream);
+
+/* One Adam update (Kingma & Ba: bias-corrected, constant lr, the optimizer of
+ * Sec. 3) with a caller-supplied gradient grad [P], e.g. the all-reduced sum
+ * of nbm_loss_grad_shard's outputs.  Update t = *step_io + 1; *step_io += 1 on
+ * the host.  The arithmetic is that of the update inside nbm_train_steps, so a
+ * single shard covering the whole batch followed by this call reproduces
+ * nbm_train_steps bitwise.
+ *   params, adam_m, adam_v [P]  updated in place
+ *   loss  DEVICE FP64 scalar or NULL: when given and not finite, the update
+ *         is skipped (parameters, m, v unchanged), as nbm_train_steps skips a
+ *         step whose loss is not finite.
+ * Asynchronous.  Returns NBM_ERR_INVALID_ARG for a NULL or misaligned argument,
+ * *step_io < 0 or bad hyper-parameters (lr > 0, 0 <= beta < 1, eps > 0). */
+int nbm_adam_step(nbm_problem* p, float* params, float* adam_m, float* adam_v, const float* grad,
+                  int64_t* step_io, float lr, float beta1, float beta2, float eps,
+                  const double* loss, nbm_stream_t stream);
+
 /* n_steps fused training steps (sample -> cell geometry -> two-network stencil
  * forward -> residual -> backward -> Adam, Sec. 3).  Step t (1-based, t =
  * *step_io + 1, ...) samples `batch` points at Philox counter t and applies a
@@ -212,7 +251,10 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
                     uint64_t seed, const float* pts, float* loss_hist, nbm_stream_t stream);
 
 /* Evaluates the trained surrogate on the (n+1)^3 nodes -1 + i*2/n of the
- * cube, each node with the network of its side of Gamma (phi <= 0: minus).
+ * cube, each node with the network of its side of Gamma (phi <= 0: minus):
+ * the inference use of a trained NBM model (Fig. 1 caption: once trained,
+ * the networks evaluate a 1024^3-resolution simulation in under a
+ * millisecond; Sec. 4.1 measures the errors at grid nodes).
  * Node (i,j,k) is u_out[i + (n+1)(j + (n+1)k)], a caller-owned DEVICE array.
  * `precision` selects the hidden-GEMM type (nbm_precision): NBM_PREC_FP32
  * (CUDA cores; asynchronous), or NBM_PREC_BF16 / NBM_PREC_FP16 (tensor cores;
@@ -225,14 +267,18 @@ int nbm_eval_grid(nbm_problem* p, const float* params, int n, int precision, flo
                   nbm_stream_t stream);
 
 /* The trained surrogate at n arbitrary points pts [n][3] (FP32, inside the
- * cube), each with the network of its side of the interface; u_out [n].
+ * cube), each with the network of its side of the interface; u_out [n]: the
+ * mesh-free solution the networks encode everywhere in the domain (Sec. 1
+ * and the conclusion: NBM lifts a mesh-based discretization off its grid).
  * Same precision choices, kernels, synchronization and errors as
  * nbm_eval_grid, with 1 <= n <= 2^34 in place of the grid size. */
 int nbm_eval_points(nbm_problem* p, const float* params, const float* pts, int64_t n,
                     int precision, float* u_out, nbm_stream_t stream);
 
-/* The plain mesh-based method the NBM is bootstrapped from: the same
- * finite-volume rows assembled on the grid of spacing 2/n, one unknown per
+/* The plain mesh-based method the NBM is bootstrapped from (Sec. 1 and Sec. 3:
+ * the NBM evaluates a conventional finite-volume discretization of the
+ * interface problem of Sec. 2 on implicit cells; here the same rows are
+ * assembled on the grid of spacing 2/n and solved), one unknown per
  * interior node, solved in FP64 by Jacobi-preconditioned conjugate gradients
  * until ||r|| <= rtol ||b|| or max_iter.  u_out [(n+1)^3] FP64 (boundary
  * nodes = Dirichlet data).  iters_out (summed over the passes below),
@@ -277,6 +323,24 @@ int nbm_grid_cg_solve(nbm_problem* p, int n, double rtol, int max_iter, double* 
 int nbm_grid_solve_refined(nbm_problem* p, int n, double rtol, int max_iter, double* u_out,
                            int* iters_out, double* relres_out, nbm_stream_t stream);
 
+/* The value jump J(x) = u+(x) - u-(x) that the grid scheme above carries to each
+ * node x of the (n+1)^3 grid (x fastest), for grid_jump mode `mode`
+ * (nbm_grid_jump; not necessarily the descriptor's): with it the plain
+ * method's node values u_x extend across Gamma (the other side's value at x is
+ * u_x +- J(x)), e.g. to interpolate either side's solution between nodes.
+ *   NBM_JUMP_EXACT         u+(x) - u-(x) of the manufactured pair (every node)
+ *   NBM_JUMP_FIRST_ORDER   alpha(x_G) + d beta(x_G)/mu_big within 3h of Gamma
+ *   NBM_JUMP_EXTRAP        alpha(x_G) + d G with the small-mu side's d_n u
+ *                          fitted from the node values u [(n+1)^3] FP64 (e.g.
+ *                          the solution of nbm_grid_cg_solve) as in a lagged pass
+ * Nodes farther than 3h from Gamma get 0 in the two extrapolated modes (Sec. 3
+ * bootstraps the NBM from this scheme; the jump conditions are those of Sec. 2).
+ * u may be NULL except for NBM_JUMP_EXTRAP; jump_out [(n+1)^3] FP64 DEVICE.
+ * Asynchronous.  Returns NBM_ERR_INVALID_ARG for a NULL or misaligned
+ * argument, an unknown mode or n outside 2..2048. */
+int nbm_grid_node_jump(nbm_problem* p, int n, int mode, const double* u, double* jump_out,
+                       nbm_stream_t stream);
+
 /* Outer-loop record of the calling thread's last nbm_grid_cg_solve or
  * nbm_grid_solve_refined: passes_out = solves with a lagged jump (1 for
  * NBM_JUMP_EXACT and NBM_JUMP_FIRST_ORDER), max_dj_out = max |J_new - J| of
@@ -293,11 +357,12 @@ int nbm_grid_last_jump_info(int* passes_out, double* max_dj_out, int* fell_back_
 int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused_launches_out);
 
 /* nbm_loss_grad without any device allocation, for callers that cannot call
- * cudaMalloc while they run: code that executes inside a CUDA-graph capture
- * or under a caller-owned memory pool, a real-time or embedded host that
- * forbids allocation after start-up, or a plugin whose host framework owns
- * all device memory.  (The paper has no counterpart: this is a deployment
- * variant of the loss-and-gradient call.)
+ * cudaMalloc while they run: a host that owns all device memory through its
+ * own pool or arena (a plugin, an inference server), a real-time or embedded
+ * host that forbids allocation after start-up, or code that must not
+ * synchronize the device, which cudaMalloc and cudaFree may do.  (The paper
+ * has no counterpart: this is a deployment variant of the loss-and-gradient
+ * call.)
  *   Arguments, results and precision path are those of nbm_loss_grad; the
  *   caller still owns params, pts, grad_out.
  *   Scratch: one static device array of about 12 MB inside libnbm, held on
@@ -307,7 +372,11 @@ int nbm_profile(nbm_problem* p, int enable, double* fused_ms_out, int64_t* fused
  *   NBM_ERR_INVALID_ARG.
  *   No cudaMalloc, cudaFree or other allocating call is made.  The first call
  *   on a device looks up the array's device address (cudaGetSymbolAddress,
- *   once per device); make that first call before any stream capture.
+ *   once per device, with that device current) and keeps it for the life of
+ *   the process; after cudaDeviceReset of that device the kept address is
+ *   stale, so do not call this entry point again in such a process.
+ *   A non-NULL loss_out reads the loss back and synchronizes the stream, as
+ *   in nbm_loss_grad; with loss_out == NULL the call only enqueues work.
  *   Every call shares the array and leaves its contents behind (the status
  *   word is cleared at the start of each call); calls whose work overlaps on
  *   the GPU (different streams, host threads or problems) race on it and

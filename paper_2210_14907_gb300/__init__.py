@@ -166,6 +166,10 @@ def load_library(build_if_missing: bool = True):
                                 C.POINTER(C.c_double), P]
     L.nbm_train_steps.argtypes = [P, P, P, P, C.POINTER(C.c_int64), C.c_int, C.c_int64,
                                   C.c_float, C.c_float, C.c_float, C.c_float, C.c_uint64, P, P, P]
+    L.nbm_loss_grad_shard.argtypes = [P, P, P, C.c_int64, C.c_int64, C.c_int64, C.c_uint64,
+                                      C.c_int64, P, P, P]
+    L.nbm_adam_step.argtypes = [P, P, P, P, P, C.POINTER(C.c_int64), C.c_float, C.c_float,
+                                C.c_float, C.c_float, P, P]
     L.nbm_set_level_set.argtypes = [P, P, C.c_int, P]
     L.nbm_selftest_bounded_wait.argtypes = [C.c_int64, P]
     L.nbm_profile.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -178,9 +182,12 @@ def load_library(build_if_missing: bool = True):
     L.nbm_grid_solve_refined.argtypes = L.nbm_grid_cg_solve.argtypes
     L.nbm_grid_last_jump_info.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int)]
+    L.nbm_grid_node_jump.argtypes = [P, C.c_int, C.c_int, P, P, P]
+    L.nbm_grid_node_jump.restype = C.c_int
     L.nbm_grid_last_jump_info.restype = C.c_int
     for fn in ("nbm_init_problem", "nbm_destroy", "nbm_sample_points", "nbm_residual",
-               "nbm_loss_grad", "nbm_train_steps", "nbm_eval_grid", "nbm_grid_cg_solve",
+               "nbm_loss_grad", "nbm_loss_grad_shard", "nbm_adam_step", "nbm_train_steps",
+               "nbm_eval_grid", "nbm_grid_cg_solve",
                "nbm_grid_solve_refined",
                "nbm_set_level_set", "nbm_selftest_bounded_wait"):
         getattr(L, fn).restype = C.c_int
@@ -268,6 +275,38 @@ class Problem:
                                       _stream(stream)))
         return (loss.value if sync else None), grad
 
+    def loss_grad_shard(self, params, n_total, first, n, seed=1, step=1, pts=None, grad=None,
+                        loss=None, stream=None):
+        """Points first .. first+n-1 of the step's n_total-point batch: returns
+        (loss, grad), both scaled by 1/n_total and left on the device (loss is
+        a one-element FP64 tensor), so that their sums over a partition of the
+        batch are the whole batch's loss and gradient.  Asynchronous."""
+        _dev(params)
+        _dev(pts)
+        if grad is None:
+            grad = torch.empty(self.P, device=params.device, dtype=torch.float32)
+        if loss is None:
+            loss = torch.empty(1, device=params.device, dtype=torch.float64)
+        _dev(grad)
+        _dev(loss, torch.float64)
+        _check(self.lib.nbm_loss_grad_shard(self.handle, _ptr(params), _ptr(pts), n_total, first,
+                                            n, seed, step, _ptr(grad), _ptr(loss),
+                                            _stream(stream)))
+        return loss, grad
+
+    def adam_step(self, params, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  loss=None, stream=None):
+        """Adam update step+1 with the given gradient (skipped when the device
+        scalar `loss` is given and not finite); returns step + 1."""
+        for t in (params, m, v, grad):
+            _dev(t)
+        _dev(loss, torch.float64)
+        st = C.c_int64(step)
+        _check(self.lib.nbm_adam_step(self.handle, _ptr(params), _ptr(m), _ptr(v), _ptr(grad),
+                                      C.byref(st), lr, beta1, beta2, eps, _ptr(loss),
+                                      _stream(stream)))
+        return st.value
+
     def train_steps(self, params, m, v, step, n_steps, batch, lr=1e-3, beta1=0.9, beta2=0.999,
                     eps=1e-8, seed=1, loss_hist=None, pts=None, stream=None):
         for t in (params, m, v):
@@ -322,6 +361,17 @@ class Problem:
         _check(load_library().nbm_grid_last_jump_info(C.byref(ps), C.byref(dj), C.byref(fb)))
         return ps.value, dj.value, bool(fb.value)
 
+    def grid_node_jump(self, n, mode, u=None, out=None, stream=None):
+        """The grid scheme's value jump u+ - u- at the (n+1)^3 nodes for grid_jump
+        mode `mode` (JUMP_EXTRAP fits the small-mu side's normal derivative
+        from the node values u)."""
+        _dev(u, torch.float64)
+        if out is None:
+            out = torch.empty((n + 1) ** 3, device="cuda", dtype=torch.float64)
+        _check(self.lib.nbm_grid_node_jump(self.handle, n, mode, _ptr(u), _ptr(out),
+                                           _stream(stream)))
+        return out
+
     def grid_solve_refined(self, n, rtol=1e-10, max_iter=20000, out=None, stream=None):
         """The grid system of grid_cg_solve to the same FP64 residual test, by
         FP32 inner PCG corrections of FP64 residuals (iterative refinement)."""
@@ -337,13 +387,28 @@ class Problem:
 
 
 class NBMLoss(torch.autograd.Function):
-    """loss = NBMLoss.apply(problem, params, pts): mean r_p^2 of Sec. 3; the backward
-    runs libnbm's hand-written backward kernels (nbm_loss_grad)."""
+    """loss = NBMLoss.apply(problem, params, pts): mean r_p^2 of Sec. 3 as a
+    differentiable function of the network parameters.
+
+    When a gradient can be needed (grad mode on and params requiring it) the
+    forward runs nbm_loss_grad, which computes the loss and libnbm's
+    hand-written backward in one pass, and keeps the gradient for backward;
+    otherwise it runs the forward-only nbm_residual.  The loss is not
+    differentiated with respect to the collocation points: pts that require
+    a gradient are refused."""
 
     @staticmethod
     def forward(ctx, problem, params, pts):
-        loss, grad = problem.loss_grad(params.detach().contiguous(), pts.contiguous())
-        ctx.save_for_backward(grad)
+        if pts.requires_grad:
+            raise ValueError("NBMLoss does not differentiate with respect to the collocation "
+                             "points; pass pts.detach()")
+        p = params.detach().contiguous()
+        x = pts.detach().contiguous()
+        if ctx.needs_input_grad[1]:
+            loss, grad = problem.loss_grad(p, x)
+            ctx.save_for_backward(grad)
+        else:
+            loss, _ = problem.residual(p, x, want_r2=False)
         return torch.tensor(loss, dtype=torch.float64, device=params.device)
 
     @staticmethod

@@ -388,8 +388,9 @@ __global__ void __launch_bounds__(kB) k_inner_init(Grid G, double* sc,
 // the node nearest x_G -+ h n (one spacing into side s; a midway point takes
 // the upper node), normal equations by
 // Cholesky; false with fewer than 4 such nodes or a degenerate fit.
-__device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict__ x,
-                       const double* __restrict__ diag, int s, const double xg[3],
+// `val(q, rq)` returns the node value at grid node q (rq: its interior index).
+template <class Val>
+__device__ bool fit_dn(const ProbDev& P, const Grid& G, Val val, int s, const double xg[3],
                        const double nrm[3], double* dn) {
   const double h = G.h;
   int c[3];
@@ -412,7 +413,7 @@ __device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict
         if (phase_d(P, xq) != s) continue;
         const double bv[4] = {1.0, (xq[0] - xg[0]) / h, (xq[1] - xg[1]) / h, (xq[2] - xg[2]) / h};
         const int64_t rq = (q[0] - 1) + (int64_t)G.m1 * ((q[1] - 1) + (int64_t)G.m1 * (q[2] - 1));
-        const double uq = x[rq] / sqrt(diag[rq]);  // the unscaled node value
+        const double uq = val(q, rq);
         for (int a = 0; a < 4; ++a) {
           rhs[a] += bv[a] * uq;
           for (int b = 0; b < 4; ++b) M[a][b] += bv[a] * bv[b];
@@ -447,53 +448,62 @@ __device__ bool fit_dn(const ProbDev& P, const Grid& G, const double* __restrict
   return true;
 }
 
-// Node jump J(x) = alpha(x_G) + d G on every interior node within 3h of Gamma
-// (0 elsewhere), updated in place: x_G by three Newton steps from the node,
-// d = phi / |grad phi| at the node, G = [d_n u] from the flux jump with the
-// small-mu side's d_n from the iterate (lag = 1, fitted) or dropped (lag = 0).
-// Block partials of max |J_new - J| and max |J_new| go to part[] and
-// part[gridDim.x + ...].
+// Node jump J(x) = alpha(x_G) + d G at a node x within 3h of Gamma (0
+// elsewhere): x_G by three Newton steps from the node, d = phi / |grad phi| at
+// the node, G = [d_n u] from the flux jump with the small-mu side's d_n fitted
+// from the node values val (lag = 1) or dropped (lag = 0).
+template <class Val>
+__device__ double node_jump(const ProbDev& P, const Grid& G, const double p[3], int lag, Val val) {
+  double g[3];
+  const double ph = phi_d(P, p[0], p[1], p[2]);
+  grad_phi_d(P, p, g);
+  const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  double jn = 0.0;
+  if (gn > 1e-300 && fabs(ph / gn) <= 3.0 * G.h * (1.0 + 1e-9)) {  // nodes at 3h: inside
+    const double d = ph / gn;
+    double xg[3] = {p[0], p[1], p[2]};
+    for (int it = 0; it < 3; ++it) {
+      double gg[3];
+      const double f = phi_d(P, xg[0], xg[1], xg[2]);
+      grad_phi_d(P, xg, gg);
+      const double q = gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2];
+      if (q <= 1e-300) break;
+      for (int a = 0; a < 3; ++a) xg[a] -= f * gg[a] / q;
+    }
+    double gx[3];
+    grad_phi_d(P, xg, gx);
+    const double gxn = sqrt(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
+    if (gxn > 1e-300) {
+      const double nrm[3] = {gx[0] / gxn, gx[1] / gxn, gx[2] / gxn};
+      const double mum = mu_at<double>(P, 0, xg[0], xg[1], xg[2]);
+      const double mup = mu_at<double>(P, 1, xg[0], xg[1], xg[2]);
+      const double beta = beta_d(P, xg);
+      const int ss = mum <= mup ? 0 : 1;
+      double dn = 0.0;
+      const bool have = lag && fit_dn(P, G, val, ss, xg, nrm, &dn);
+      const double Gj = ss == 0 ? beta / mup - (have ? (1.0 - mum / mup) * dn : 0.0)
+                                : beta / mum + (have ? (1.0 - mup / mum) * dn : 0.0);
+      jn = alpha_d(P, xg) + d * Gj;
+    }
+  }
+  return jn;
+}
+
+// node_jump on every interior node, updated in place, from the iterate x^ of
+// the scaled system (node values x^ / sqrt(d)).  Block partials of
+// max |J_new - J| and max |J_new| go to part[] and part[gridDim.x + ...].
 __global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
                                                   const double* __restrict__ x,
                                                   const double* __restrict__ diag, double* J,
                                                   double* part) {
   __shared__ double red[2][kB / 32];
   double mx[2] = {0.0, 0.0};
+  auto val = [&](const int*, int64_t rq) { return x[rq] / sqrt(diag[rq]); };
   for (int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x; r < G.m; r += (int64_t)gridDim.x * kB) {
     int i, j, k;
-    double p[3], g[3];
+    double p[3];
     node_xyz(G, r, i, j, k, p);
-    const double ph = phi_d(P, p[0], p[1], p[2]);
-    grad_phi_d(P, p, g);
-    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-    double jn = 0.0;
-    if (gn > 1e-300 && fabs(ph / gn) <= 3.0 * G.h * (1.0 + 1e-9)) {  // nodes at 3h: inside
-      const double d = ph / gn;
-      double xg[3] = {p[0], p[1], p[2]};
-      for (int it = 0; it < 3; ++it) {
-        double gg[3];
-        const double f = phi_d(P, xg[0], xg[1], xg[2]);
-        grad_phi_d(P, xg, gg);
-        const double q = gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2];
-        if (q <= 1e-300) break;
-        for (int a = 0; a < 3; ++a) xg[a] -= f * gg[a] / q;
-      }
-      double gx[3];
-      grad_phi_d(P, xg, gx);
-      const double gxn = sqrt(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
-      if (gxn > 1e-300) {
-        const double nrm[3] = {gx[0] / gxn, gx[1] / gxn, gx[2] / gxn};
-        const double mum = mu_at<double>(P, 0, xg[0], xg[1], xg[2]);
-        const double mup = mu_at<double>(P, 1, xg[0], xg[1], xg[2]);
-        const double beta = beta_d(P, xg);
-        const int ss = mum <= mup ? 0 : 1;
-        double dn = 0.0;
-        const bool have = lag && fit_dn(P, G, x, diag, ss, xg, nrm, &dn);
-        const double Gj = ss == 0 ? beta / mup - (have ? (1.0 - mum / mup) * dn : 0.0)
-                                  : beta / mum + (have ? (1.0 - mup / mum) * dn : 0.0);
-        jn = alpha_d(P, xg) + d * Gj;
-      }
-    }
+    const double jn = node_jump(P, G, p, lag, val);
     mx[0] = fmax(mx[0], fabs(jn - J[r]));
     mx[1] = fmax(mx[1], fabs(jn));
     J[r] = jn;
@@ -510,6 +520,23 @@ __global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
       for (int w = 0; w < kB / 32; ++w) m = fmax(m, red[q][w]);
       part[q * (int64_t)gridDim.x + blockIdx.x] = m;
     }
+}
+
+// The node jump of grid_jump mode `mode` on all (n+1)^3 nodes (x fastest), from
+// the node values u (read only by the lagged mode's fit): the exact jump
+// alpha(x) = u+(x) - u-(x) of the manufactured pair, or node_jump (first
+// order: lag 0; lagged: lag 1).
+__global__ void __launch_bounds__(kB) k_node_jump_all(ProbDev P, Grid G, int mode,
+                                                      const double* __restrict__ u, double* J) {
+  const int64_t n1 = G.n + 1, nodes = n1 * n1 * n1;
+  auto val = [&](const int* q, int64_t) { return u[q[0] + n1 * (q[1] + n1 * (int64_t)q[2])]; };
+  for (int64_t e = (int64_t)blockIdx.x * kB + threadIdx.x; e < nodes;
+       e += (int64_t)gridDim.x * kB) {
+    const int i = (int)(e % n1), j = (int)((e / n1) % n1), k = (int)(e / (n1 * n1));
+    const double p[3] = {node_coord(i, G.h), node_coord(j, G.h), node_coord(k, G.h)};
+    J[e] = mode == NBM_JUMP_EXACT ? alpha_d(P, p)
+                                  : node_jump(P, G, p, mode == NBM_JUMP_EXTRAP ? 1 : 0, val);
+  }
 }
 
 // sc[slot], sc[slot + 1] = maxima of the two partial vectors
@@ -939,4 +966,24 @@ extern "C" int nbm_grid_last_jump_info(int* passes_out, double* max_dj_out, int*
   if (max_dj_out) *max_dj_out = g_jump_info.dj;
   if (fell_back_out) *fell_back_out = g_jump_info.fell_back;
   return NBM_OK;
+}
+
+extern "C" int nbm_grid_node_jump(nbm_problem* p, int n, int mode, const double* u,
+                                  double* jump_out, nbm_stream_t stream) {
+  if (!p || !jump_out || (mode == NBM_JUMP_EXTRAP && !u)) {
+    set_error_message("NULL argument");
+    return NBM_ERR_INVALID_ARG;
+  }
+  if (mode != NBM_JUMP_EXACT && mode != NBM_JUMP_EXTRAP && mode != NBM_JUMP_FIRST_ORDER) {
+    set_error_message("unknown grid_jump mode");
+    return NBM_ERR_INVALID_ARG;
+  }
+  if (int rc = check_aligned(u, 8, "u")) return rc;
+  CgSetup S;
+  if (int rc = cg_setup(p, n, 1.0, 0, jump_out, "node jump", S)) return rc;
+  const int64_t blocks = (S.nodes + kB - 1) / kB, cap = 8 * (int64_t)problem_num_sms(p);
+  k_node_jump_all<<<(int)(blocks < cap ? blocks : cap), kB, 0, (cudaStream_t)stream>>>(
+      S.P, S.G, mode, u, jump_out);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NBM_OK : cg_cuda_fail("node jump", e);
 }
