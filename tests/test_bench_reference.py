@@ -28,6 +28,11 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert "3 steps after 3 warm-up" in cb["sample"]
+    # the line describes the sub-batch it timed: steps x ms_per_step is the timed
+    # region and value is sub-batch points per second
+    assert d["config"]["batch"] == cb["sub_batch"] <= d["config"]["workload_batch"]
+    assert abs(d["steps"] * d["ms_per_step"] / 1e3 - cb["timed_s"]) <= 1e-9 * cb["timed_s"]
+    assert abs(d["value"] - d["steps"] * cb["sub_batch"] / cb["timed_s"]) <= 1e-9 * d["value"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

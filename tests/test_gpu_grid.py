@@ -261,3 +261,47 @@ def test_large_grid_solves_with_separate_reductions():
     linf = torch.max(torch.abs(a - exact)[interior.reshape(-1)]).item()
     print(f"n {n}: FP64 CG {it_a} it, refined {it_b} inner it, diff {diff:.2e}, L-inf {linf:.2e}")
     assert diff <= 1e-8 and linf <= 5e-5
+
+
+@pytest.mark.parametrize("geom, mu_p", [(O.GEOM_SPHERE, 10.0), (O.GEOM_FLOWER, 100.0)],
+                         ids=["sphere", "flower"])
+def test_grid_node_jump_matches_oracle_in_every_mode(geom, mu_p):
+    """nbm_grid_node_jump on all (n+1)^3 nodes against the oracle: the exact jump
+    u+ - u- of the manufactured pair, the first-order jump alpha + d beta/mu_big
+    within 3h of Gamma, and the lagged jump with the small side's d_n u fitted
+    from given node values (here the grid solution)."""
+    import paper_2210_14907_gb300 as nbm
+    n = 22
+    prob = nbm.Problem(nbm.ProblemDesc(geometry=geom, mu_minus=1.0, mu_plus=mu_p,
+                                       grid_jump=nbm.JUMP_EXTRAP))
+    u, _, _, ok = prob.grid_cg_solve(n, rtol=1e-10)
+    assert ok
+    uh = u.cpu().numpy()
+    o = O.make_problem(geometry=geom, mu_minus=1.0, mu_plus=mu_p)
+    h = 2.0 / n
+    g = -1.0 + np.arange(n + 1) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    assert min(abs(O.phi(o, x)) for x in nodes) > 1e-9  # no node decided by rounding
+    J = prob.grid_node_jump(n, nbm.JUMP_EXACT).cpu().numpy()
+    ref = np.array([O.exact_u(o, 1, x) - O.exact_u(o, 0, x) for x in nodes])
+    assert np.max(np.abs(J - ref)) <= 1e-12 * max(1.0, np.abs(ref).max())
+    J1 = prob.grid_node_jump(n, nbm.JUMP_FIRST_ORDER).cpu().numpy()
+    Jl = prob.grid_node_jump(n, nbm.JUMP_EXTRAP, u).cpu().numpy()
+    r1 = np.zeros(len(nodes))
+    rl = np.zeros(len(nodes))
+    band = 0
+    for e, x in enumerate(nodes):
+        inb, j1, xg, nrm, ss = O.jump_extrap(o, x, h)
+        if not inb:
+            continue
+        band += 1
+        r1[e] = j1
+        dn = O.fit_dn(o, n, uh, ss, xg, nrm)
+        rl[e] = O.jump_extrap(o, x, h, dn)[1] if dn is not None else j1
+    assert band > 100
+    assert np.max(np.abs(J1 - r1)) <= 1e-10
+    assert np.max(np.abs(Jl - rl)) <= 1e-10
+    assert np.max(np.abs(Jl - J1)) > 1e-6  # the lag term is there
+    with pytest.raises(nbm.NBMError):
+        prob.grid_node_jump(n, nbm.JUMP_EXTRAP)  # the lagged mode needs node values
