@@ -14,7 +14,9 @@
 // layer in FP32 and writes the next 16-bit operand image to shared memory.
 // The first layer (K = 3), the output layer (H -> 1, a warp
 // transpose-reduction), the residual rows and the seeds stay FP32 (FP64 rows
-// on request).  The backward reuses the stored images: per hidden layer one
+// on request).  In the BF16 training path the epilogues' FP32 arithmetic runs
+// on packed pairs (add/mul/fma .f32x2: two points per instruction, each
+// rounded as its scalar form).  The backward reuses the stored images: per hidden layer one
 // input-gradient MMA (W^T gz, into the group's D columns) and one
 // weight-gradient MMA (gz A^T, K = 64) accumulated across all half-tiles of
 // the CTA in shared TMEM columns, in a fixed order of the half-tiles, so the
@@ -31,6 +33,7 @@
 
 #include "nbm_device.cuh"
 #include "nbm_tc_ptx.cuh"
+#include "nbm_f32x2.cuh"
 
 namespace nbm {
 
@@ -139,6 +142,41 @@ __device__ __forceinline__ void warp_transpose_reduce32(const float (&x)[32], fl
     const float keep = hi ? v[1] : v[0], send = hi ? v[0] : v[1];
     s = keep + __shfl_xor_sync(0xffffffffu, send, 1);
   }
+}
+
+// Two points' tanh stencil layer on packed FP32 pairs (unscaled columns, every
+// lane's symmetric increments small): the arithmetic of tanh_stencil_fwd's
+// series path, operation for operation.
+__device__ __forceinline__ void tanh_stencil_fwd_pair(F2 T, F2 NT, F2 S0, F2 MU, F2 DE, F2& M,
+                                                      F2& D) {
+  float dA, dB;
+  f2get(DE, dA, dB);
+  const F2 TD = f2(act_tanh<true>(dA), act_tanh<true>(dB));
+  const F2 poly = fma2(fma2(T, T, f2s(-1.0f / 3.0f)), mul2(MU, MU), fma2(NT, MU, f2s(1.0f)));
+  const F2 dm = mul2(mul2(S0, MU), poly);
+  const F2 tw = add2(T, dm);
+  const F2 ntw = mul2(tw, f2s(-1.0f));
+  const F2 sw = fma2(ntw, tw, f2s(1.0f));
+  const F2 td2 = mul2(TD, TD);
+  float eA, eB;
+  f2get(fma2(add2(sw, f2s(-1.0f)), td2, f2s(1.0f)), eA, eB);
+  const F2 r2 = f2(rcp<true>(eA), rcp<true>(eB));
+  const F2 k = mul2(sw, r2);
+  M = fma2(mul2(ntw, td2), k, dm);
+  D = mul2(k, TD);
+}
+
+// Two points' adjoint of one stencil axis (unscaled columns): the arithmetic of
+// tanh_stencil_bwd on packed pairs.
+__device__ __forceinline__ F2 tanh_stencil_bwd_pair(F2 T, F2 S0, F2 MO, F2 DO, F2 GM, F2 GD,
+                                                    F2& gmu, F2& gdel) {
+  const F2 P = mul2(fma2(mul2(T, f2s(2.0f)), MO, fma2(MO, MO, mul2(DO, DO))), f2s(-1.0f));
+  const F2 Q = mul2(mul2(DO, f2s(-2.0f)), add2(T, MO));
+  const F2 S = add2(S0, P);
+  const F2 qgd = mul2(Q, GD);
+  gmu = fma2(S, GM, qgd);
+  gdel = fma2(Q, GM, mul2(S, GD));
+  return fma2(P, GM, qgd);
 }
 
 }  // namespace
@@ -418,6 +456,44 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       {
         const float dl1[3] = {SCALED ? w1[0] : w1[0] * P.hf, SCALED ? w1[1] : w1[1] * P.hf,
                               SCALED ? w1[2] : w1[2] * P.hf};
+        if constexpr (FAST && !SCALED) {
+          // two points per packed FP32 instruction; tanh(h W1[u][i]) depends on the
+          // unit only
+          float Td[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) Td[i] = act_tanh<true>(dl1[i]);
+#pragma unroll
+          for (int pp = 0; pp < kPPT; pp += 2) {
+            const PRec pa = pr[4 * cgl + pp], pb = pr[4 * cgl + pp + 1];
+            const F2 W0 = f2s(w1[0]), W1 = f2s(w1[1]), W2 = f2s(w1[2]), B1 = f2s(b1);
+            float zA, zB;
+            f2get(fma2(W0, f2(pa.x, pb.x), fma2(W1, f2(pa.y, pb.y), fma2(W2, f2(pa.z, pb.z), B1))),
+                  zA, zB);
+            const F2 T = f2(act_tanh<true>(zA), act_tanh<true>(zB));
+            const F2 NT = mul2(T, f2s(-1.0f));
+            const F2 SW = fma2(NT, T, f2s(1.0f));
+            const F2 NTT = mul2(NT, T);
+            const F2 NTS = mul2(NT, SW);
+            float oA[8], oB[8];
+            f2get(T, oA[0], oB[0]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              const F2 TD = f2s(Td[i]), TD2 = mul2(TD, TD);
+              float eA, eB;
+              f2get(fma2(NTT, TD2, f2s(1.0f)), eA, eB);
+              const F2 R2 = f2(rcp<true>(eA), rcp<true>(eB));
+              f2get(mul2(mul2(NTS, TD2), R2), oA[1 + i], oB[1 + i]);
+              f2get(mul2(mul2(SW, TD), R2), oA[4 + i], oB[4 + i]);
+            }
+            const bool ja = pa.cutj >= 0 && (pa.cutj & 1), jb = pb.cutj >= 0 && (pb.cutj & 1);
+            oA[7] = ja ? act_tanh<true>(fmaf(w1[0], pa.gx, fmaf(w1[1], pa.gy, fmaf(w1[2], pa.gz, b1))))
+                       : 0.f;
+            oB[7] = jb ? act_tanh<true>(fmaf(w1[0], pb.gx, fmaf(w1[1], pb.gy, fmaf(w1[2], pb.gz, b1))))
+                       : 0.f;
+            store8o<BF>(Aimg, poff(pp), oA);
+            store8o<BF>(Aimg, poff(pp + 1), oB);
+          }
+        } else {
 #pragma unroll
         for (int pp = 0; pp < kPPT; ++pp) {
           const int p = 4 * cgl + pp;
@@ -432,6 +508,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
           o[7] = jump ? act_tanh<FAST>(fmaf(w1[0], pi.gx, fmaf(w1[1], pi.gy, fmaf(w1[2], pi.gz, b1))))
                       : 0.f;
           store8o<BF>(Aimg, poff(pp), o);
+        }
         }
       }
       fence_proxy_async();
@@ -454,6 +531,54 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         const bool ok_w = wait_mma();
         float acc[32];
         tmem_ld32(d_tm + lane_base + col0, acc);
+        if constexpr (FAST && !SCALED) {
+          // two points per packed FP32 instruction
+#pragma unroll
+          for (int jp = 0; jp < kPPT; jp += 2) {
+            const float* cA = acc + 8 * jp;
+            const float* cB = cA + 8;
+            float oA[8], oB[8];
+            const float tA = act_tanh<true>(cA[0] + bb), tB = act_tanh<true>(cB[0] + bb);
+            oA[0] = tA;
+            oB[0] = tB;
+            const bool smA = __all_sync(
+                0xffffffffu, fmaxf(fabsf(cA[1]), fmaxf(fabsf(cA[2]), fabsf(cA[3]))) <= kSmallMu);
+            const bool smB = __all_sync(
+                0xffffffffu, fmaxf(fabsf(cB[1]), fmaxf(fabsf(cB[2]), fabsf(cB[3]))) <= kSmallMu);
+            if (smA && smB) {
+              const F2 T = f2(tA, tB), NT = mul2(T, f2s(-1.0f));
+              const F2 S0 = fma2(NT, T, f2s(1.0f));
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                F2 M, D;
+                tanh_stencil_fwd_pair(T, NT, S0, f2(cA[1 + i], cB[1 + i]), f2(cA[4 + i], cB[4 + i]),
+                                      M, D);
+                f2get(M, oA[1 + i], oB[1 + i]);
+                f2get(D, oA[4 + i], oB[4 + i]);
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                tanh_stencil_fwd<true>(tA, cA[1 + i], cA[4 + i], 1.f, 1.f, 1.f, 1.f, oA[1 + i],
+                                       oA[4 + i], smA);
+                tanh_stencil_fwd<true>(tB, cB[1 + i], cB[4 + i], 1.f, 1.f, 1.f, 1.f, oB[1 + i],
+                                       oB[4 + i], smB);
+              }
+            }
+            oA[7] = act_tanh<true>(cA[7] + bb);
+            oB[7] = act_tanh<true>(cB[7] + bb);
+            if (g < NG) {
+              store8o<BF>(Aimg + g * kImgH, poff(jp), oA);
+              store8o<BF>(Aimg + g * kImgH, poff(jp + 1), oB);
+            } else {
+#pragma unroll
+              for (int c2 = 0; c2 < 8; ++c2) {
+                last[8 * jp + c2] = oA[c2];
+                last[8 * jp + 8 + c2] = oB[c2];
+              }
+            }
+          }
+        } else {
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
           const float* c = acc + 8 * j;
@@ -475,6 +600,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 #pragma unroll
             for (int c2 = 0; c2 < 8; ++c2) last[8 * j + c2] = o[c2];
           }
+        }
         }
         if (!end_phase(ok_w)) {
           aborted = true;
@@ -567,6 +693,55 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       if (!train) continue;
 
       // ---- backward: adjoint of the last tanh layer (FP32 state in registers)
+      if constexpr (!SCALED) {
+        // two points per packed FP32 instruction
+#pragma unroll
+        for (int pp = 0; pp < kPPT; pp += 2) {
+          float sA[8], sB[8];
+          {
+            const float4* s4 = reinterpret_cast<const float4*>(seeds + 8 * (4 * cgl + pp));
+            const float4 a0 = s4[0], a1 = s4[1], b0 = s4[2], b1v = s4[3];
+            sA[0] = a0.x; sA[1] = a0.y; sA[2] = a0.z; sA[3] = a0.w;
+            sA[4] = a1.x; sA[5] = a1.y; sA[6] = a1.z; sA[7] = a1.w;
+            sB[0] = b0.x; sB[1] = b0.y; sB[2] = b0.z; sB[3] = b0.w;
+            sB[4] = b1v.x; sB[5] = b1v.y; sB[6] = b1v.z; sB[7] = b1v.w;
+          }
+          const float* stA = last + 8 * pp;
+          const float* stB = stA + 8;
+          F2 sw = mul2(f2(sA[0], sB[0]), f2(stA[0], stB[0]));
+#pragma unroll
+          for (int c = 1; c < 8; ++c) sw = fma2(f2(sA[c], sB[c]), f2(stA[c], stB[c]), sw);
+          {
+            float x, y;
+            f2get(sw, x, y);
+            gwo += x;
+            gwo += y;
+          }
+          const F2 WO = f2s(wo);
+          const F2 T = f2(stA[0], stB[0]);
+          const F2 S0 = fma2(mul2(T, f2s(-1.0f)), T, f2s(1.0f));
+          float gA[8], gB[8];
+          F2 gzc = mul2(S0, mul2(WO, f2(sA[0], sB[0])));
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            F2 gm, gd;
+            gzc = add2(gzc, tanh_stencil_bwd_pair(T, S0, f2(stA[1 + i], stB[1 + i]),
+                                                  f2(stA[4 + i], stB[4 + i]),
+                                                  mul2(WO, f2(sA[1 + i], sB[1 + i])),
+                                                  mul2(WO, f2(sA[4 + i], sB[4 + i])), gm, gd));
+            f2get(gm, gA[1 + i], gB[1 + i]);
+            f2get(gd, gA[4 + i], gB[4 + i]);
+          }
+          f2get(gzc, gA[0], gB[0]);
+          const F2 T7 = f2(stA[7], stB[7]);
+          f2get(mul2(fma2(mul2(T7, f2s(-1.0f)), T7, f2s(1.0f)), mul2(WO, f2(sA[7], sB[7]))), gA[7],
+                gB[7]);
+          gbh[NG - 1] += gA[0] + gA[7];
+          gbh[NG - 1] += gB[0] + gB[7];
+          store8o<BF>(Aimg + (L - 1) * kImgH, poff(pp), gA);
+          store8o<BF>(Aimg + (L - 1) * kImgH, poff(pp + 1), gB);
+        }
+      } else {
 #pragma unroll
       for (int pp = 0; pp < kPPT; ++pp) {
         const int p = 4 * cgl + pp;
@@ -593,6 +768,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         gz[7] = fmaf(-st[7], st[7], 1.f) * (wo * sd[7]);
         gbh[NG - 1] += gz[0] + gz[7];
         store8o<BF>(Aimg + (L - 1) * kImgH, poff(pp), gz);
+      }
       }
       if (gtid == 0) {
         float s = 0.f;
@@ -629,15 +805,42 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         if (gtid == 0 && ok_w) st_release_s32(done_cnt + grp, nph + 1);
         unsigned char* img = Aimg + (g - 1) * kImgH;  // state of act[g-1]
         float G[16];  // two points at a time: registers are short here
+        float gzP[8];  // the second point's adjoint of a packed pair
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
           if ((j & 1) == 0) tmem_ld16(d_tm + lane_base + col0 + 8 * j, G);
           const int p = 4 * cgl + j;
           float st[8];
           load8o<BF>(img, poff(j), st);
+          float gz[8];
+          if constexpr (!SCALED) {
+            if ((j & 1) == 0) {
+              // this point and the next one on packed FP32 pairs
+              float sB[8];
+              load8o<BF>(img, poff(j + 1), sB);
+              const F2 T = f2(st[0], sB[0]);
+              const F2 S0 = fma2(mul2(T, f2s(-1.0f)), T, f2s(1.0f));
+              F2 gzc = mul2(S0, f2(G[0], G[8]));
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                F2 gm, gd;
+                gzc = add2(gzc, tanh_stencil_bwd_pair(T, S0, f2(st[1 + i], sB[1 + i]),
+                                                      f2(st[4 + i], sB[4 + i]),
+                                                      f2(G[1 + i], G[9 + i]),
+                                                      f2(G[4 + i], G[12 + i]), gm, gd));
+                f2get(gm, gz[1 + i], gzP[1 + i]);
+                f2get(gd, gz[4 + i], gzP[4 + i]);
+              }
+              f2get(gzc, gz[0], gzP[0]);
+              const F2 T7 = f2(st[7], sB[7]);
+              f2get(mul2(fma2(mul2(T7, f2s(-1.0f)), T7, f2s(1.0f)), f2(G[7], G[15])), gz[7], gzP[7]);
+            } else {
+#pragma unroll
+              for (int c2 = 0; c2 < 8; ++c2) gz[c2] = gzP[c2];
+            }
+          } else {
           const float* Gp = G + 8 * (j & 1);
           const float t = st[0], s0 = fmaf(-t, t, 1.f);
-          float gz[8];
           float gzc = s0 * Gp[0];
 #pragma unroll
           for (int i = 0; i < 3; ++i)
@@ -645,6 +848,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
                                     ihs, ih2s, gz[1 + i], gz[4 + i]);
           gz[0] = gzc;
           gz[7] = fmaf(-st[7], st[7], 1.f) * Gp[7];
+          }
           if (g > 1) {
             const float gsum = gz[0] + gz[7];
 #pragma unroll

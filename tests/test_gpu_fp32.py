@@ -154,8 +154,18 @@ def test_autograd_function_backward_is_libnbm_gradient():
     th = torch.from_numpy(inputs.glorot_params(64, 2, seed=2)).cuda().requires_grad_(True)
     loss = nbm.NBMLoss.apply(prob, th, pts)
     loss.backward()
-    _, g = prob.loss_grad(th.detach(), pts)
+    l2, g = prob.loss_grad(th.detach(), pts)
     assert torch.equal(th.grad, g)
+    # no gradient needed: the forward alone (nbm_residual), the same loss
+    with torch.no_grad():
+        l0 = nbm.NBMLoss.apply(prob, th, pts)
+    l1 = nbm.NBMLoss.apply(prob, th.detach(), pts)
+    assert not l0.requires_grad and not l1.requires_grad
+    assert float(l0) == float(l1) == prob.residual(th.detach(), pts, want_r2=False)[0]
+    assert abs(float(l0) - l2) <= 1e-6 * l2
+    # the points are not differentiated
+    with pytest.raises(ValueError):
+        nbm.NBMLoss.apply(prob, th, pts.clone().requires_grad_(True))
 
 
 def test_invalid_arguments_fail_cleanly():
