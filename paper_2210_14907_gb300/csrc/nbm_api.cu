@@ -109,7 +109,7 @@ static int ws_reserve(Problem& pb, int64_t n) {
   ws_free(w);
   const int64_t cap = n < 1024 ? 1024 : n;
   const int nb = (int)((cap + 255) / 256);
-  const int ncb = (int)((cap + 127) / 128);
+  const int ncb = (int)((cap + 31) / 32);  // cut-row blocks (one warp each)
   const int grid = pb.num_sms;
   const int64_t H = pb.desc.width, L = pb.desc.n_hidden;
   NBM_CUDA(dalloc(w.x, cap));

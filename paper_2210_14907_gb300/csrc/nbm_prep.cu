@@ -397,7 +397,9 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __
 //   D = sum_s sum_f A^s_f mu^s + h^2 sum_s V^s k^s,   J = U+(xg) - U-(xg) - alpha,
 //   r^2 = (B/D)^2 + lambda J^2;   seeds = d(scale r^2)/d(outputs).
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __restrict__ X,
+// One warp per block: the cut list (a few thousand cells) spreads over many SMs,
+// each cell's FP64 row on one thread, since GB300's FP64 pipe is narrow.
+__global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* __restrict__ X,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ Z,
                                                       const int* __restrict__ counters,
@@ -405,7 +407,6 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
                                                       const float* __restrict__ out,
                                                       float* seeds, float scale, float* r2_out,
                                                       double* loss_part) {
-  __shared__ double red[128];
   const int nc = counters[2];
   double r2_sum = 0.0;  // this thread's cells (grid-stride), then the block partial
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nc; id += gridDim.x * blockDim.x) {
@@ -475,13 +476,9 @@ __global__ void __launch_bounds__(128) k_cut_residual(ProbDev P, const float* __
     if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
     r2_sum += r2;
   }
-  red[threadIdx.x] = r2_sum;
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r2_sum += __shfl_xor_sync(0xffffffffu, r2_sum, o);
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = r2_sum;
 }
 
 // ------------------------------------------------------------------------
@@ -761,14 +758,14 @@ cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cuda
 // blocks of the cut-row kernel (grid-stride over the cut cells), i.e. the
 // number of its loss partials
 int cut_residual_blocks(int64_t n, const Workspace& ws) {
-  const int64_t worst = (n + 127) / 128, cap = 4 * (int64_t)ws.grid;
+  const int64_t worst = (n + 31) / 32, cap = 8 * (int64_t)ws.grid;
   return (int)(worst < cap ? worst : cap);
 }
 
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
                                 float* r2_out, Workspace& ws, cudaStream_t st) {
   int nb = cut_residual_blocks(n, ws);
-  k_cut_residual<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.counters, ws.cut, ws.cut_out,
+  k_cut_residual<<<nb, 32, 0, st>>>(P, ws.x, ws.y, ws.z, ws.counters, ws.cut, ws.cut_out,
                                      want_seeds ? ws.cut_seed : nullptr, scale, r2_out,
                                      ws.cut_loss_part);
   return cudaGetLastError();
