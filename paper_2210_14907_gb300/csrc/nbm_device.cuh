@@ -345,13 +345,16 @@ __device__ __forceinline__ float rcp(float x) {
 // independent evaluations; it only changes the rounding.
 // ---------------------------------------------------------------------------
 //
-// small_mu (fast path, every lane of the warp has |mu| <= kSmallMu): the
+// small_mu (every lane of the warp has |mu| below the path's threshold): the
 // symmetric part from its Taylor series instead of the addition identity,
 //   tanh(z+mu) - tanh z = (1-t^2) mu (1 - t mu + (t^2 - 1/3) mu^2) + R,
 //   |R| <= (1-t^2) mu^4 / 2,
-// i.e. a relative error below mu^3/2 = 6.3e-5 (the outputs are rounded to
-// 16 bits next), two SFU operations fewer per axis.
+// i.e. a relative error below mu^3/2: 6.3e-5 at the SFU path's threshold
+// kSmallMu (its outputs are rounded to 16 bits next), 3e-8 (below FP32
+// rounding) at the accurate path's kSmallMuAccurate = 2^-8.  It saves the
+// tanh of mu and a reciprocal per axis.
 constexpr float kSmallMu = 0.05f;
+constexpr float kSmallMuAccurate = 0.00390625f;
 
 template <bool FAST>
 __device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, float h, float h2,
@@ -360,7 +363,7 @@ __device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, fl
   float mu = mt * h2, de = dt * h;
   float Td = act_tanh<FAST>(de);
   float tw, dm;
-  if (FAST && small_mu) {
+  if (small_mu) {
     const float poly = fmaf(fmaf(t, t, -1.0f / 3.0f), mu * mu, fmaf(-t, mu, 1.0f));
     dm = fmaf(-t, t, 1.0f) * mu * poly;
     tw = t + dm;

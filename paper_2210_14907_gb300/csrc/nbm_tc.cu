@@ -147,11 +147,12 @@ __device__ __forceinline__ void warp_transpose_reduce32(const float (&x)[32], fl
 // Two points' tanh stencil layer on packed FP32 pairs (unscaled columns, every
 // lane's symmetric increments small): the arithmetic of tanh_stencil_fwd's
 // series path, operation for operation.
+template <bool FAST>
 __device__ __forceinline__ void tanh_stencil_fwd_pair(F2 T, F2 NT, F2 S0, F2 MU, F2 DE, F2& M,
                                                       F2& D) {
   float dA, dB;
   f2get(DE, dA, dB);
-  const F2 TD = f2(act_tanh<true>(dA), act_tanh<true>(dB));
+  const F2 TD = f2(act_tanh<FAST>(dA), act_tanh<FAST>(dB));
   const F2 poly = fma2(fma2(T, T, f2s(-1.0f / 3.0f)), mul2(MU, MU), fma2(NT, MU, f2s(1.0f)));
   const F2 dm = mul2(mul2(S0, MU), poly);
   const F2 tw = add2(T, dm);
@@ -160,7 +161,7 @@ __device__ __forceinline__ void tanh_stencil_fwd_pair(F2 T, F2 NT, F2 S0, F2 MU,
   const F2 td2 = mul2(TD, TD);
   float eA, eB;
   f2get(fma2(add2(sw, f2s(-1.0f)), td2, f2s(1.0f)), eA, eB);
-  const F2 r2 = f2(rcp<true>(eA), rcp<true>(eB));
+  const F2 r2 = f2(rcp<FAST>(eA), rcp<FAST>(eB));
   const F2 k = mul2(sw, r2);
   M = fma2(mul2(ntw, td2), k, dm);
   D = mul2(k, TD);
@@ -456,12 +457,12 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       {
         const float dl1[3] = {SCALED ? w1[0] : w1[0] * P.hf, SCALED ? w1[1] : w1[1] * P.hf,
                               SCALED ? w1[2] : w1[2] * P.hf};
-        if constexpr (FAST && !SCALED) {
+        if constexpr (!SCALED) {
           // two points per packed FP32 instruction; tanh(h W1[u][i]) depends on the
           // unit only
           float Td[3];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) Td[i] = act_tanh<true>(dl1[i]);
+          for (int i = 0; i < 3; ++i) Td[i] = act_tanh<FAST>(dl1[i]);
 #pragma unroll
           for (int pp = 0; pp < kPPT; pp += 2) {
             const PRec pa = pr[4 * cgl + pp], pb = pr[4 * cgl + pp + 1];
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
             float zA, zB;
             f2get(fma2(W0, f2(pa.x, pb.x), fma2(W1, f2(pa.y, pb.y), fma2(W2, f2(pa.z, pb.z), B1))),
                   zA, zB);
-            const F2 T = f2(act_tanh<true>(zA), act_tanh<true>(zB));
+            const F2 T = f2(act_tanh<FAST>(zA), act_tanh<FAST>(zB));
             const F2 NT = mul2(T, f2s(-1.0f));
             const F2 SW = fma2(NT, T, f2s(1.0f));
             const F2 NTT = mul2(NT, T);
@@ -481,14 +482,14 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
               const F2 TD = f2s(Td[i]), TD2 = mul2(TD, TD);
               float eA, eB;
               f2get(fma2(NTT, TD2, f2s(1.0f)), eA, eB);
-              const F2 R2 = f2(rcp<true>(eA), rcp<true>(eB));
+              const F2 R2 = f2(rcp<FAST>(eA), rcp<FAST>(eB));
               f2get(mul2(mul2(NTS, TD2), R2), oA[1 + i], oB[1 + i]);
               f2get(mul2(mul2(SW, TD), R2), oA[4 + i], oB[4 + i]);
             }
             const bool ja = pa.cutj >= 0 && (pa.cutj & 1), jb = pb.cutj >= 0 && (pb.cutj & 1);
-            oA[7] = ja ? act_tanh<true>(fmaf(w1[0], pa.gx, fmaf(w1[1], pa.gy, fmaf(w1[2], pa.gz, b1))))
+            oA[7] = ja ? act_tanh<FAST>(fmaf(w1[0], pa.gx, fmaf(w1[1], pa.gy, fmaf(w1[2], pa.gz, b1))))
                        : 0.f;
-            oB[7] = jb ? act_tanh<true>(fmaf(w1[0], pb.gx, fmaf(w1[1], pb.gy, fmaf(w1[2], pb.gz, b1))))
+            oB[7] = jb ? act_tanh<FAST>(fmaf(w1[0], pb.gx, fmaf(w1[1], pb.gy, fmaf(w1[2], pb.gz, b1))))
                        : 0.f;
             store8o<BF>(Aimg, poff(pp), oA);
             store8o<BF>(Aimg, poff(pp + 1), oB);
@@ -531,42 +532,43 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         const bool ok_w = wait_mma();
         float acc[32];
         tmem_ld32(d_tm + lane_base + col0, acc);
-        if constexpr (FAST && !SCALED) {
+        if constexpr (!SCALED) {
           // two points per packed FP32 instruction
+          constexpr float kSmall = FAST ? kSmallMu : kSmallMuAccurate;
 #pragma unroll
           for (int jp = 0; jp < kPPT; jp += 2) {
             const float* cA = acc + 8 * jp;
             const float* cB = cA + 8;
             float oA[8], oB[8];
-            const float tA = act_tanh<true>(cA[0] + bb), tB = act_tanh<true>(cB[0] + bb);
+            const float tA = act_tanh<FAST>(cA[0] + bb), tB = act_tanh<FAST>(cB[0] + bb);
             oA[0] = tA;
             oB[0] = tB;
             const bool smA = __all_sync(
-                0xffffffffu, fmaxf(fabsf(cA[1]), fmaxf(fabsf(cA[2]), fabsf(cA[3]))) <= kSmallMu);
+                0xffffffffu, fmaxf(fabsf(cA[1]), fmaxf(fabsf(cA[2]), fabsf(cA[3]))) <= kSmall);
             const bool smB = __all_sync(
-                0xffffffffu, fmaxf(fabsf(cB[1]), fmaxf(fabsf(cB[2]), fabsf(cB[3]))) <= kSmallMu);
+                0xffffffffu, fmaxf(fabsf(cB[1]), fmaxf(fabsf(cB[2]), fabsf(cB[3]))) <= kSmall);
             if (smA && smB) {
               const F2 T = f2(tA, tB), NT = mul2(T, f2s(-1.0f));
               const F2 S0 = fma2(NT, T, f2s(1.0f));
 #pragma unroll
               for (int i = 0; i < 3; ++i) {
                 F2 M, D;
-                tanh_stencil_fwd_pair(T, NT, S0, f2(cA[1 + i], cB[1 + i]), f2(cA[4 + i], cB[4 + i]),
-                                      M, D);
+                tanh_stencil_fwd_pair<FAST>(T, NT, S0, f2(cA[1 + i], cB[1 + i]),
+                                            f2(cA[4 + i], cB[4 + i]), M, D);
                 f2get(M, oA[1 + i], oB[1 + i]);
                 f2get(D, oA[4 + i], oB[4 + i]);
               }
             } else {
 #pragma unroll
               for (int i = 0; i < 3; ++i) {
-                tanh_stencil_fwd<true>(tA, cA[1 + i], cA[4 + i], 1.f, 1.f, 1.f, 1.f, oA[1 + i],
+                tanh_stencil_fwd<FAST>(tA, cA[1 + i], cA[4 + i], 1.f, 1.f, 1.f, 1.f, oA[1 + i],
                                        oA[4 + i], smA);
-                tanh_stencil_fwd<true>(tB, cB[1 + i], cB[4 + i], 1.f, 1.f, 1.f, 1.f, oB[1 + i],
+                tanh_stencil_fwd<FAST>(tB, cB[1 + i], cB[4 + i], 1.f, 1.f, 1.f, 1.f, oB[1 + i],
                                        oB[4 + i], smB);
               }
             }
-            oA[7] = act_tanh<true>(cA[7] + bb);
-            oB[7] = act_tanh<true>(cB[7] + bb);
+            oA[7] = act_tanh<FAST>(cA[7] + bb);
+            oB[7] = act_tanh<FAST>(cB[7] + bb);
             if (g < NG) {
               store8o<BF>(Aimg + g * kImgH, poff(jp), oA);
               store8o<BF>(Aimg + g * kImgH, poff(jp + 1), oB);
