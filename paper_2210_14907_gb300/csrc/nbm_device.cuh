@@ -598,4 +598,78 @@ __device__ __forceinline__ T uncut_residual_pt(const ProbDev& P, int s, float px
   return r * r;
 }
 
+// The row of uncut_residual_pt spread over the 8 lanes c = 0..7 of an aligned
+// group of a warp (all 8 call it for the same point; `mask` covers the
+// calling lanes).  Lane c < 6 takes face c (axis c/2, side c%2), lane 6 the
+// reaction and source term; the balance row and the Dirichlet and face sums
+// are added over the group by shuffles.  Every lane returns r^2 and lane c
+// writes seed c.  The same terms as the one-thread row, added in a different
+// order: for the FP64 rows, whose chain on a single thread is bound by the
+// narrow FP64 pipe, this runs each FP64 instruction on 8 lanes instead of 1.
+template <typename T>
+__device__ __forceinline__ T uncut_residual_lanes(const ProbDev& P, int s, float px, float py,
+                                                  float pz, T fsrc, const float out[8], T scale,
+                                                  int c, unsigned mask, float& sd_c) {
+  const T h = pc_h<T>(P), h2 = h * h, mu = pc_mu<T>(P, s), kk = pc_k<T>(P, s);
+  T ih, ih2, iD;
+  if constexpr (sizeof(T) == 4) {
+    ih = P.inv_hf;
+    ih2 = P.inv_h2f;
+    iD = P.inv_Df[s];
+  } else {
+    ih = P.inv_h;
+    ih2 = P.inv_h2;
+    iD = P.inv_D[s];
+  }
+  const T U = (T)out[0];
+  const T x[3] = {(T)px, (T)py, (T)pz};
+  T term = (T)0, nb = (T)0, cm = (T)0, dv = (T)0;
+  if (c < 6) {
+    // (selects, not indexing: the columns and coordinates stay in registers)
+    const int i = c >> 1;
+    const bool plus = c & 1;
+    const T Mt = (T)(i == 0 ? out[1] : i == 1 ? out[2] : out[3]);
+    const T Dt = (T)(i == 0 ? out[4] : i == 1 ? out[5] : out[6]);
+    const T dq = plus ? h : -h;
+    const T q0 = i == 0 ? x[0] + dq : x[0], q1 = i == 1 ? x[1] + dq : x[1],
+            q2 = i == 2 ? x[2] + dq : x[2];
+    T mf = mu;
+    if (P.solution == 1) {
+      const T dc = plus ? (T)0.5 * h : -(T)0.5 * h;
+      mf = mu_at<T>(P, s, i == 0 ? x[0] + dc : x[0], i == 1 ? x[1] + dc : x[1],
+                    i == 2 ? x[2] + dc : x[2]);
+      dv = mf;
+    }
+    if (fabs(i == 0 ? q0 : i == 1 ? q1 : q2) >= (T)1) {
+      term = -mf * (dirichlet_g<T>(P, q0, q1, q2) - U) * ih2;
+      nb = mf;
+    } else {
+      term = -mf * (plus ? Mt + Dt * ih : Mt - Dt * ih);
+      cm = mf;
+    }
+  } else if (c == 6) {
+    term = kk * U - fsrc;
+  }
+  T Bt = term, nbmu = nb, Dv = dv;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    Bt += __shfl_xor_sync(mask, Bt, o, 8);
+    nbmu += __shfl_xor_sync(mask, nbmu, o, 8);
+    Dv += __shfl_xor_sync(mask, Dv, o, 8);
+  }
+  // the two faces of the axis of seed c (c = 1..3: symmetric, 4..6: antisymmetric)
+  const int ax = c >= 4 ? c - 4 : c - 1;
+  const int fa = ax < 0 || ax > 2 ? 0 : 2 * ax;
+  const T cmm = __shfl_sync(mask, cm, fa, 8), cmp = __shfl_sync(mask, cm, fa + 1, 8);
+  if (P.solution == 1) iD = (T)1 / (Dv + h2 * kk);
+  const T r = h2 * Bt * iD;
+  const T cf = scale * (T)2 * r * h2 * iD;
+  T sd = (T)0;
+  if (c == 0) sd = cf * (kk + nbmu * ih2);
+  else if (c <= 3) sd = cf * -(cmm + cmp);
+  else if (c <= 6) sd = cf * (-(cmp - cmm) * ih);
+  sd_c = (float)sd;
+  return r * r;
+}
+
 }  // namespace nbm

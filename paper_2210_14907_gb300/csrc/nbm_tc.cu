@@ -622,7 +622,43 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       named_sync(gbar, 256);
       // ---- output columns and residual rows: thread p of the group's first
       // warp owns point p and its 8 columns
-      if (gtid < kHP) {
+      // (the FP64 rows only occur in the accurate, !FAST, instances)
+      if (!FAST && P.fp64 && gtid < 8 * kHP) {
+        // FP64 rows: lane c of the 8 lanes gtid = 8 p + c takes column c of
+        // point p; the row is spread over the 8 lanes (uncut_residual_lanes)
+        const int p = gtid >> 3, c = gtid & 7;
+        const unsigned gmask = 0xFFu << (gtid & 24);
+        float oc = red[8 * p + c];
+#pragma unroll
+        for (int qq = 1; qq < 4; ++qq) oc += red[64 * qq + 8 * p + c];
+        if (c == 0 || c == 7) oc += bo;
+        const float csc = SCALED ? 1.f : (c >= 1 && c <= 3) ? P.inv_h2f
+                                       : (c >= 4 && c <= 6) ? P.inv_hf : 1.f;
+        oc *= csc;  // the scaled convention of the rows
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = __shfl_sync(gmask, oc, k, 8);
+        const PRec pi = pr[p];
+        const bool valid = pi.pt >= 0, is_cut = pi.cutj >= 0;
+        float* sdp = seeds + 8 * p;
+        if (cutfwd) {
+          if (valid) a.cut_out[(int64_t)(pi.cutj >> 1) * 16 + net * 8 + c] = oc;
+        } else if (valid && !is_cut) {
+          float sdc;
+          const double r2d = uncut_residual_lanes<double>(P, net, pi.x, pi.y, pi.z,
+                                                          (double)pi.gx + (double)pi.gy, o,
+                                                          (double)a.scale, c, gmask, sdc);
+          if (c == 0) {
+            loss_acc_d += r2d;
+            if (a.r2_out) a.r2_out[pi.pt] = (P.level ? a.r2_out[pi.pt] : 0.f) + (float)r2d;
+          }
+          sdp[c] = sdc * csc;  // seeds in this kernel's column convention
+        } else if (valid && train) {
+          sdp[c] *= csc;  // cut point: the seeds copied at the start of the tile, rescaled
+        } else {
+          sdp[c] = 0.f;
+        }
+      } else if ((FAST || !P.fp64) && gtid < kHP) {
         const int p = gtid;
         float o[8];
         {
