@@ -3,19 +3,21 @@
 // u at the (n+1)^3 nodes -1 + i 2/n, each node with the network of its side
 // of the interface (phi <= 0: minus).
 //
-// Tensor-core path: a persistent CTA per SM walks its tiles of 128 nodes, two
-// at a time, once per network (the network's hidden weights are staged in
-// shared memory once per pass; tiles without a node of that side are
-// skipped).  Layer 1 (K = 3) and the output layer run in FP32; every hidden
-// layer is one 128x128x128 tcgen05 MMA with 16-bit operands (FP16 or BF16)
-// and FP32 accumulation in TMEM.  The FP32 path is a plain SIMT evaluation
-// (reference precision).
+// Tensor-core path: a persistent CTA per SM walks its tiles of 64 nodes once
+// per network (the network's hidden weights are staged in shared memory once
+// per pass; tiles without a node of that side are skipped), in two
+// independent warp groups with three tiles in flight each.  Layer 1 (K = 3)
+// and the output layer run in FP32; every hidden layer is one 128x64x128
+// tcgen05 MMA per tile with 16-bit operands (FP16 or BF16) and FP32
+// accumulation in TMEM.  The FP32 path is a plain SIMT evaluation (reference
+// precision).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstdio>
 
 #include "nbm_device.cuh"
+#include "nbm_f32x2.cuh"
 #include "nbm_tc_ptx.cuh"
 
 namespace nbm {
@@ -24,6 +26,10 @@ namespace {
 using namespace tc;
 
 constexpr int kImgE = 32768;
+// 64-point tiles in flight per warp group of the tensor-core evaluation, and the
+// TMEM columns they take (2 groups x kEvalTiles x 64, rounded up to a power of 2)
+constexpr int kEvalTiles = 3;
+constexpr int kEvalTmemCols = 2 * kEvalTiles * 64 <= 256 ? 256 : 512;
 
 // side of a grid node, decided as the FP64 level set would (FP32 first)
 __device__ inline int node_phase(const ProbDev& P, float x, float y, float z) {
@@ -79,76 +85,82 @@ __device__ __forceinline__ uint32_t tanh_pack2(float a, float b) {
 
 // Points: the (n+1)^3 grid nodes, or (pts != nullptr) npts points pts[3i..3i+2].
 //
-// Two tiles of 128 points are in flight per CTA.  Tile X (0, 1) has its own
-// TMEM accumulator (columns 128 X .. 128 X + 127), activation image,
-// coordinates, flags, output partials and MMA barrier, so the tensor core
-// runs one tile's layer-g GEMM while the CUDA cores run the other tile's
-// epilogue.  Thread (q = warp & 3, cg = warp >> 2) owns unit 32 q + lane
-// (its TMEM lane) and the tile's columns 32 cg .. 32 cg + 31.
+// Two warp groups of 8 warps run independently, each on its own sets of kX
+// 64-point tiles (the CTA's tiles alternate between the groups: group g takes
+// tiles tb + g, tb + g + 2, ..., kX at a time).  Each tile X (0 .. kX-1) of a group
+// has its own activation image (128 units x 64 points, 16 KB), 64 TMEM
+// accumulator columns and MMA barrier, so the tensor pipe runs one tile's
+// 128 x 64 x 128 GEMM while the CUDA cores run the other tile's epilogue, and
+// the two groups (each on its own named barrier) fill each other's waits.  In
+// a group, thread (q = warp & 3, cg = (warp >> 2) & 1) owns unit 32 q + lane
+// (its TMEM lane) and the tile's points 32 cg .. 32 cg + 31.
 //
-// Pass 0 (the minus network) decides every point's side and keeps it as a
-// 128-bit mask per tile in `side` (bit c: point c is in Omega-); pass 1 reads
-// the mask back instead of evaluating the level set again.
+// Pass 0 (the minus network) decides every point's side and keeps it in
+// `side` (per 128 points, bit c: point c is in Omega-; each 64-point tile owns
+// two of the four words); pass 1 reads it back instead of evaluating the
+// level set again.  A tile without a point of the pass's side is skipped.
 template <int L, bool BF>
 __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __restrict__ params,
                                                     const unsigned char* __restrict__ wimg, int n,
                                                     const float* __restrict__ pts, int64_t npts,
                                                     float* __restrict__ u_out, uint4* side,
                                                     int* status) {
-  constexpr int H = 128, NG = L - 1;
+  constexpr int H = 128, NG = L - 1, kTP = 64, kImgG = 16384, kX = kEvalTiles;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* Wimg = sm;                       // [NG]
-  unsigned char* Aimg = sm + NG * kImgE;          // [2] one activation image per tile
-  unsigned char* misc = sm + (NG + 2) * kImgE;
-  uint64_t* bar_w = (uint64_t*)misc;
-  uint64_t* bar_mma = (uint64_t*)(misc + 8);      // [2]
-  uint32_t* tslot = (uint32_t*)(misc + 24);
-  float* red = (float*)(misc + 64);               // [2][4][128] output partials
-  float* xs = red + 1024;                         // [2][3][128] coordinates
-  int* flag = (int*)(xs + 768);                   // [2][128]
-  int* actw = flag + 256;  // [2][8] staging warps with a point of the side, by pair parity
-
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int q = w & 3, cg = w >> 2, u = 32 * q + lane, col0 = 32 * cg;
-  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-  const uint32_t idf = idesc_f16(BF, false, true);
+  const int grp = tid >> 8, gtid = tid & 255, gw = gtid >> 5;
+  const int q = w & 3, cg = (w >> 2) & 1, u = 32 * q + lane, col0 = 32 * cg;
+  const uint32_t gbar = 1u + (uint32_t)grp;
+  unsigned char* Wimg = sm;                                    // [NG] 32 KB
+  unsigned char* Aimg = sm + NG * kImgE + grp * kX * kImgG;    // this group's [kX] images
+  unsigned char* misc = sm + NG * kImgE + 2 * kX * kImgG;
+  uint64_t* bar_w = (uint64_t*)misc;
+  uint64_t* bar_mma = (uint64_t*)(misc + 8) + kX * grp;        // this group's [kX]
+  uint32_t* tslot = (uint32_t*)(misc + 8 + 16 * kX);
+  volatile int* abort_f = (volatile int*)(misc + 12 + 16 * kX);
+  int* actw = (int*)(misc + 128) + grp * 4 * kX;               // [2 set parities][2 kX warps]
+  constexpr int kRed = 256, kXs = kRed + 2 * kX * 4 * kTP * 4, kFlag = kXs + 2 * kX * 3 * kTP * 4;
+  float* red = (float*)(misc + kRed) + grp * kX * 4 * kTP;     // [kX][4][64] output partials
+  float* xs = (float*)(misc + kXs) + grp * kX * 3 * kTP;       // [kX][3][64] coordinates
+  int* flag = (int*)(misc + kFlag) + grp * kX * kTP;           // [kX][64]
+
+  const uint32_t idf = idesc_f16_n(BF, false, true, kTP);
   if (tid == 0) {
     mbar_init(smem_u32(bar_w), 1);
-    mbar_init(smem_u32(bar_mma), 1);
-    mbar_init(smem_u32(bar_mma + 1), 1);
+    for (int b = 0; b < 2 * kX; ++b) mbar_init(smem_u32((uint64_t*)(misc + 8) + b), 1);
+    *abort_f = 0;
     fence_mbar_init();
   }
-  if (w == 0) tmem_alloc(smem_u32(tslot), 256);
+  if (w == 0) tmem_alloc(smem_u32(tslot), kEvalTmemCols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  // per-tile state as bit X of a register: MMA barrier phase, and a commit on
-  // bar_mma[X] not yet waited for
+  const uint32_t d_tm = tmem + (uint32_t)(kX * kTP * grp);  // tile X: d_tm + 64 X
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+  // per-tile state as bit X: MMA barrier phase, and a commit not yet waited for
   uint32_t ph_w = 0, ph_bits = 0, pending_bits = 0;
   const int64_t N1 = n + 1, total = pts ? npts : N1 * N1 * N1;
-  const int64_t T = (total + 127) / 128;
+  const int64_t T = (total + kTP - 1) / kTP;
   const int64_t tb = (int64_t)blockIdx.x * T / gridDim.x, te = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
   const float hg = 2.0f / (float)n;
   bool aborted = false;
 
   // the layer-g GEMM of tile X: weights g (K-major) x image X (MN-major)
   auto issue = [&](int X, int g) {
-    if (tid == 0) {
+    if (gtid == 0) {
       fence_after_sync();
-      const uint32_t wa = smem_u32(Wimg + g * kImgE);
-      const uint32_t ab = smem_u32(Aimg + X * kImgE);
+      const uint32_t wa = smem_u32(Wimg + g * kImgE), ab = smem_u32(Aimg + X * kImgG);
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        mma_f16(tmem + 128 * X, desc_kmajor(wa, k), desc_mnmajor(ab, k), idf, k > 0);
+        mma_f16(d_tm + kTP * X, desc_kmajor(wa, k), desc_mnmajor(ab, k), idf, k > 0);
       mma_commit(smem_u32(bar_mma + X));
     }
     pending_bits |= 1u << X;
   };
-  // bounded wait for tile X's GEMM (this thread's result; the CTA agrees on an
-  // abort at the barrier that ends the epilogue)
-  auto wait_mma = [&](int X) {
+  // bounded wait for tile X's GEMM; false if it gave up
+  auto wait_mma = [&](int X) -> bool {
     const bool ok = mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u);
     if (ok) {  // a wait that gave up leaves the GEMM pending for the exit path
       ph_bits ^= 1u << X;
@@ -156,6 +168,17 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
     }
     fence_after_sync();
     return ok;
+  };
+  // the group barrier that ends a phase; it agrees on an abort.  False: abort.
+  auto end_phase = [&](bool ok) -> bool {
+    fence_before_sync();
+    fence_proxy_async();
+    const bool bad = named_sync_or(gbar, 256, !ok || *abort_f != 0);
+    if (bad && gtid == 0) {
+      if (!ok) atomicOr(status, 2);
+      *abort_f = 1;
+    }
+    return !bad;
   };
 
   for (int s = 0; s < 2 && !aborted; ++s) {
@@ -181,21 +204,23 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
         break;
       }
     }
-    for (int64_t t = tb, pair = 0; t < te && !aborted; t += 2, ++pair) {
-      // actw alternates between two halves: a pair without active tiles has no
-      // barrier after its reads, so the next pair must not overwrite them
-      int* aw = actw + 8 * (int)(pair & 1);
-      // coordinates and side flags of both tiles (threads 0..255)
-      int f = 0;
-      if (tid < 256) {
-        const int X = tid >> 7, c = tid & 127;
-        const int64_t id = (t + X) * 128 + c;
-        const bool valid = t + X < te && id < total;
-        int minus = 0;
+    int set = 0;
+#pragma unroll 1
+    for (int64_t t = tb + grp; t < te; t += 2 * kX, ++set) {
+      // tile X of this set is t + 2 X; actw alternates between two halves: a
+      // set without active tiles has no barrier after its reads
+      int* aw = actw + 2 * kX * (set & 1);
+      // coordinates and side flags of the tiles' 64 points (threads 0 .. 64 kX - 1)
+      if (gtid < kX * kTP) {
+        const int X = gtid >> 6, c = gtid & 63;
+        const int64_t tx = t + 2 * X;
+        const int64_t id = tx * kTP + c;
+        const bool valid = tx < te && id < total;
+        int f = 0, minus = 0;
+        uint32_t* sw = valid ? reinterpret_cast<uint32_t*>(&side[tx >> 1]) + 2 * (tx & 1) + (c >> 5)
+                             : nullptr;
         if (s == 1 && valid) {  // the side decided in pass 0
-          const uint4 m = side[t + X];
-          const uint32_t word = (c >> 5) == 0 ? m.x : (c >> 5) == 1 ? m.y : (c >> 5) == 2 ? m.z : m.w;
-          minus = (word >> (c & 31)) & 1u;
+          minus = (*sw >> (c & 31)) & 1u;
           f = !minus;
         }
         float x = 0.f, y = 0.f, z = 0.f;
@@ -220,34 +245,36 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
           minus = valid && node_phase(P, x, y, z) == 0;
           f = minus;
           const uint32_t bits = __ballot_sync(0xffffffffu, minus);
-          if (lane == 0 && t + X < te) ((uint32_t*)&side[t + X])[c >> 5] = bits;  // own tiles only
+          if (lane == 0 && valid) *sw = bits;
         }
-        xs[X * 384 + c] = x;
-        xs[X * 384 + 128 + c] = y;
-        xs[X * 384 + 256 + c] = z;
-        flag[X * 128 + c] = f;
+        float* xx = xs + X * 3 * kTP;
+        xx[c] = x;
+        xx[kTP + c] = y;
+        xx[2 * kTP + c] = z;
+        flag[X * kTP + c] = f;
         const uint32_t any = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) aw[w] = any != 0u;
+        if (lane == 0) aw[gw] = any != 0u;
       }
-      __syncthreads();
-      const uint32_t act = ((aw[0] | aw[1] | aw[2] | aw[3]) ? 1u : 0u) |
-                           ((aw[4] | aw[5] | aw[6] | aw[7]) ? 2u : 0u);
-      if (!act) continue;
-      // layer 1 (FP32 K = 3) of each active tile -> its image; then its GEMM
+      named_sync(gbar, 256);
+      uint32_t act = 0;
 #pragma unroll
-      for (int X = 0; X < 2; ++X) {
+      for (int X = 0; X < kX; ++X) act |= ((aw[2 * X] | aw[2 * X + 1]) ? 1u : 0u) << X;
+      if (!act) continue;
+      // layer 1 (FP32, K = 3) of each active tile -> its image; then its GEMM
+#pragma unroll
+      for (int X = 0; X < kX; ++X) {
         if (!((act >> X) & 1u)) continue;
-        const float* xx = xs + X * 384;
-        unsigned char* dst = Aimg + X * kImgE;
+        const float* xx = xs + X * 3 * kTP;
+        unsigned char* dst = Aimg + X * kImgG;
 #pragma unroll
         for (int c8 = 0; c8 < 4; ++c8) {
           float z[8];
 #pragma unroll
-          for (int h4 = 0; h4 < 2; ++h4) {  // four columns per 16-byte shared load
+          for (int h4 = 0; h4 < 2; ++h4) {  // four points per 16-byte shared load
             const int c = col0 + 8 * c8 + 4 * h4;
             const float4 px = *reinterpret_cast<const float4*>(xx + c);
-            const float4 py = *reinterpret_cast<const float4*>(xx + 128 + c);
-            const float4 pz = *reinterpret_cast<const float4*>(xx + 256 + c);
+            const float4 py = *reinterpret_cast<const float4*>(xx + kTP + c);
+            const float4 pz = *reinterpret_cast<const float4*>(xx + 2 * kTP + c);
             z[4 * h4 + 0] = fmaf(w10, px.x, fmaf(w11, py.x, fmaf(w12, pz.x, b1)));
             z[4 * h4 + 1] = fmaf(w10, px.y, fmaf(w11, py.y, fmaf(w12, pz.y, b1)));
             z[4 * h4 + 2] = fmaf(w10, px.z, fmaf(w11, py.z, fmaf(w12, pz.z, b1)));
@@ -258,9 +285,11 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
                          tanh_pack2<BF>(z[4], z[5]), tanh_pack2<BF>(z[6], z[7]));
         }
       }
-      fence_proxy_async();
-      __syncthreads();
-      for (int X = 0; X < 2; ++X)
+      if (!end_phase(true)) {
+        aborted = true;
+        break;
+      }
+      for (int X = 0; X < kX; ++X)
         if ((act >> X) & 1u) issue(X, 0);
       // hidden layers: while one tile's epilogue runs, the other tile's GEMM does
       bool ok_all = true;  // this thread's MMA waits of the pair
@@ -270,23 +299,26 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
 #pragma unroll
         for (int i = 1; i < NG; ++i) bb = (g - 1 == i) ? bh[i] : bb;
 #pragma unroll 1
-        for (int X = 0; X < 2; ++X) {
+        for (int X = 0; X < kX; ++X) {
           if (!((act >> X) & 1u)) continue;
           ok_all = wait_mma(X) && ok_all;
           float acc[32];
-          tmem_ld32(tmem + lane_base + 128 * X + col0, acc);
+          tmem_ld32(d_tm + kTP * X + lane_base + col0, acc);
+          const F2 BB = f2s(bb);
           if (g < NG) {
-            unsigned char* dst = Aimg + X * kImgE;
+            unsigned char* dst = Aimg + X * kImgG;
 #pragma unroll
             for (int c8 = 0; c8 < 4; ++c8) {
-              const float* a8 = acc + 8 * c8;
+              // the bias on packed FP32 pairs, then tanh and the 16-bit operand
+              float z[8];
+#pragma unroll
+              for (int i = 0; i < 8; i += 2)
+                f2get(add2(f2(acc[8 * c8 + i], acc[8 * c8 + i + 1]), BB), z[i], z[i + 1]);
               *reinterpret_cast<uint4*>(dst + img_off(u, col0 + 8 * c8)) =
-                  make_uint4(tanh_pack2<BF>(a8[0] + bb, a8[1] + bb), tanh_pack2<BF>(a8[2] + bb, a8[3] + bb),
-                             tanh_pack2<BF>(a8[4] + bb, a8[5] + bb), tanh_pack2<BF>(a8[6] + bb, a8[7] + bb));
+                  make_uint4(tanh_pack2<BF>(z[0], z[1]), tanh_pack2<BF>(z[2], z[3]),
+                             tanh_pack2<BF>(z[4], z[5]), tanh_pack2<BF>(z[6], z[7]));
             }
-            fence_before_sync();
-            fence_proxy_async();
-            if (__syncthreads_or(!ok_all)) {
+            if (!end_phase(ok_all)) {
               aborted = true;
               break;
             }
@@ -294,43 +326,50 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
           } else {
             // output layer (FP32): the sum over units of wo * tanh
             float v[32], sres;
+            const F2 WO = f2s(wo);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = wo * fast_tanh(acc[i] + bb);
+            for (int i = 0; i < 32; i += 2) {
+              float za, zb;
+              f2get(add2(f2(acc[i], acc[i + 1]), BB), za, zb);
+              f2get(mul2(WO, f2(fast_tanh(za), fast_tanh(zb))), v[i], v[i + 1]);
+            }
             reduce32(v, lane, sres);
-            red[X * 512 + q * 128 + col0 + lane] = sres;
+            red[(X * 4 + q) * kTP + col0 + lane] = sres;
           }
         }
       }
       if (aborted) break;
-      fence_before_sync();
-      if (__syncthreads_or(!ok_all)) {
+      if (!end_phase(ok_all)) {
         aborted = true;
         break;
       }
-      if (tid < 256) {
-        const int X = tid >> 7, c = tid & 127;
-        if (((act >> X) & 1u) && flag[X * 128 + c]) {
-          const float* r = red + X * 512;
-          u_out[(t + X) * 128 + c] = r[c] + r[128 + c] + r[256 + c] + r[384 + c] + bo;
+      if (gtid < kX * kTP) {
+        const int X = gtid >> 6, c = gtid & 63;
+        if (((act >> X) & 1u) && flag[X * kTP + c]) {
+          const float* r = red + X * 4 * kTP;
+          u_out[(t + 2 * X) * kTP + c] = r[c] + r[kTP + c] + r[2 * kTP + c] + r[3 * kTP + c] + bo;
         }
       }
-      // no barrier here: each thread rewrites only its own flag slot in the
-      // next staging, and xs, red, the images and TMEM are next written after
-      // the next pair's barriers
+      // no barrier here: each thread rewrites only its own coordinate and flag
+      // slots in the next staging, and red, the images and TMEM are next
+      // written after the next pair's barriers
     }
+    // both groups are done with this network before its weights are replaced
+    if (__syncthreads_or(aborted)) aborted = true;
   }
   if (aborted) {
     if (tid == 0) atomicOr(status, 2);
     // let any GEMM still committed, and a weight copy that a wait gave up on,
     // finish (bounded) before TMEM and shared memory are released
-    for (int X = 0; X < 2; ++X)
-      if ((pending_bits >> X) & 1u) (void)mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u);
+    for (int X = 0; X < kX; ++X)
+      if ((pending_bits >> X) & 1u)
+        (void)mbar_wait_bounded(smem_u32(bar_mma + X), (ph_bits >> X) & 1u, 2000000LL);
     (void)mbar_wait_bounded(smem_u32(bar_w), ph_w, 2000000LL);
   }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  if (w == 0) tmem_dealloc(tmem, 256);
+  if (w == 0) tmem_dealloc(tmem, kEvalTmemCols);
 }
 
 // Plain FP32 evaluation: one thread per node, activations in shared memory
@@ -458,7 +497,10 @@ template <int L, bool BF>
 cudaError_t launch_eval_tc_t(const ProbDev& P, const float* params, const unsigned char* wimg,
                              int n, const float* pts, int64_t npts, float* u, uint4* side,
                              int grid, int* status, cudaStream_t st) {
-  const size_t smem = (size_t)(L + 1) * kImgE + 1024 + 12288;
+  // weights (L-1) x 32 KB, 2 kEvalTiles 16 KB tile images, barriers, partials,
+  // coordinates and flags (256 + 4608 kEvalTiles bytes), 1 KB of alignment slack
+  const size_t smem = (size_t)(L - 1) * kImgE + 2 * kEvalTiles * 16384 + 256 +
+                      4608 * kEvalTiles + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_eval_tc<L, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
