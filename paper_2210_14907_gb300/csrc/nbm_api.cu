@@ -91,7 +91,7 @@ static void ws_free(Workspace& w) {
   void* ptrs[] = {w.x, w.y, w.z, w.cls, w.blockcnt, w.list_minus, w.list_plus, w.cut_pt, w.rec,
                   w.rec_cut,
                   w.counters, w.cut, w.cut_out, w.cut_seed, w.loss_part, w.cut_loss_part, w.loss,
-                  w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.corr, w.status, w.loss_acc,
+                  w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.status, w.loss_acc,
                   w.gacc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -137,7 +137,6 @@ static int ws_reserve(Problem& pb, int64_t n) {
   NBM_CUDA(dalloc((uint16_t*&)w.wtc, 2 * (size_t)(L - 1) * H * H));
   NBM_CUDA(dalloc(w.grad, 2 * (size_t)pb.p_net));
   NBM_CUDA(dalloc(w.step, 1));
-  NBM_CUDA(dalloc(w.corr, 2));
   NBM_CUDA(dalloc(w.status, 1));
   NBM_CUDA(cudaMemset(w.status, 0, sizeof(int)));
   NBM_CUDA(cudaMemset(w.step, 0, sizeof(int64_t)));
@@ -618,7 +617,8 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
       StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)batch);
       NBM_CUDA(launch_timed(pb, P, a, st));
       NBM_CUDA(launch_finish(P, batch, pb.ws.grid, true, false, params, adam_m, adam_v, nullptr,
-                             lr, beta1, beta2, eps, loss_hist, base, prec, pb.ws, st, lv, nlev));
+                             lr, beta1, beta2, eps, loss_hist, base, prec, pb.ws, st, lv, nlev,
+                             0.0, base + k + 1));
     }
   }
   *step_io = base + n_steps;

@@ -94,7 +94,6 @@ struct Workspace {
   void* wtc = nullptr;              // 16-bit hidden weights
   float* grad = nullptr;            // [P]
   int64_t* step = nullptr;          // [1] device step counter
-  float* corr = nullptr;            // [2] Adam bias corrections of the current step
   int* status = nullptr;            // [1]
 };
 
@@ -152,7 +151,11 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
                           Workspace& ws, cudaStream_t st, int level = 0, int n_levels = 1,
-                          double loss_scale = 0.0);  // 0: the loss is the mean over the n points
+                          double loss_scale = 0.0,  // 0: the loss is the mean over the n points
+                          int64_t adam_t = 0);      // the Adam step (1-based) of this update
+// Adam's bias correction 1 - beta^t of step t, in FP64 rounded to FP32 (on the
+// host, where t of every enqueued step is known; both update kernels take it)
+float adam_correction(float beta, int64_t t);
 // Adam update t (bias-corrected, 1-based) of n parameters with a caller-supplied
 // gradient, by the arithmetic of the fused update.  Skipped when loss != NULL
 // and *loss is not finite.

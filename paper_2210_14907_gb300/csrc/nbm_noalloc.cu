@@ -42,7 +42,7 @@ constexpr size_t kScratchBytes =
     + align256(2 * kStaticMaxGrid * 4)                     // partial flags
     + align256((size_t)2 * kStaticMaxHidden * 128 * 128 * 4)  // FP32 transposed weights
     + align256((size_t)2 * kStaticMaxHidden * 128 * 128 * 2)  // 16-bit weight images
-    + align256(8) + align256(8) + align256(4);             // step, corr, status
+    + align256(8) + align256(4);                           // step, status
 
 // The scratch.  In host code `g_static_scratch` only names the symbol; its
 // device address comes from cudaGetSymbolAddress below.
@@ -144,7 +144,6 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   w.wt = carve<float>(cur, (size_t)2 * kStaticMaxHidden * 128 * 128 * 4);
   w.wtc = carve<void>(cur, (size_t)2 * kStaticMaxHidden * 128 * 128 * 2);
   w.step = carve<int64_t>(cur, 8);
-  w.corr = carve<float>(cur, 8);
   w.status = carve<int>(cur, 4);
   w.cap_n = kStaticMaxPoints;
   w.grid = grid;

@@ -10,6 +10,8 @@
 //   weight staging     : FP32 transposed and 16-bit tensor-core copies
 //   finish             : deterministic loss / gradient reduction (8 slice
 //                        groups per 32 parameters, fixed order) and Adam
+#include <cmath>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -595,20 +597,20 @@ __global__ void k_prep_weights(ProbDev P, const float* __restrict__ params, floa
 // last level.
 __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __restrict__ clp,
                        int nclp, double scale, double* loss, int64_t* step, float* loss_hist,
-                       int64_t hist_base, int* status, float b1, float b2, float* corr,
+                       int64_t hist_base, int* status,
                        double* loss_acc, int acc_in, int last) {
-  __shared__ double red[256];
+  __shared__ double red[8];
   double s = 0.0;
   for (int j = threadIdx.x; j < nlp; j += 256) s += lp[j];
   for (int j = threadIdx.x; j < nclp; j += 256) s += clp[j];
-  red[threadIdx.x] = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    double L = red[0] * scale;
+    double t8 = red[0];
+    for (int w = 1; w < 8; ++w) t8 += red[w];  // fixed order: deterministic
+    double L = t8 * scale;
     if (acc_in) L += *loss_acc;
     if (!last) {
       *loss_acc = L;
@@ -620,8 +622,6 @@ __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __r
       int64_t t = *step + 1;
       *step = t;
       if (loss_hist) loss_hist[t - hist_base - 1] = (float)L;
-      corr[0] = (float)(1.0 - pow((double)b1, (double)t));
-      corr[1] = (float)(1.0 - pow((double)b2, (double)t));
     }
   }
 }
@@ -632,7 +632,7 @@ __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __r
 __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpart,
                               const int* __restrict__ flag, float* grad_out, float* params,
                               float* m, float* v, float lr, float b1, float b2, float eps,
-                              const float* corr, const double* loss, float* wt, void* wtc,
+                              float c1, float c2, const double* loss, float* wt, void* wtc,
                               int prec, const float* gacc_in, float* gacc_out) {
   // Block of 256 threads: 32 consecutive parameters (lane) x 8 groups of the
   // per-CTA partial slices (group cg sums slices cg, cg + 8, ...); the groups
@@ -646,9 +646,13 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
   const int64_t jj = j - s * pn;
   float part = 0.f;
   if (in) {
+    // every slice loaded, a slice of a CTA that stopped early dropped by a
+    // select: the loads do not wait for the flags
 #pragma unroll 4
-    for (int c = cg; c < grid; c += 8)
-      if (flag[2 * c + s]) part += gpart[((int64_t)c * 2 + s) * P.gstride + jj];
+    for (int c = cg; c < grid; c += 8) {
+      const float g = __ldcg(gpart + ((int64_t)c * 2 + s) * P.gstride + jj);
+      part += __ldg(flag + 2 * c + s) ? g : 0.f;
+    }
   }
   red[cg][lane] = part;
   __syncthreads();
@@ -668,7 +672,7 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
   float vj = b2 * v[j] + (1.f - b2) * g * g;
   m[j] = mj;
   v[j] = vj;
-  float mh = mj / corr[0], vh = vj / corr[1];
+  float mh = mj / c1, vh = vj / c2;
   float w = params[j] - lr * mh / (sqrtf(vh) + eps);
   params[j] = w;
   // restage hidden weights for the next step
@@ -698,16 +702,9 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
 // batch reproduces nbm_train_steps bitwise.
 __global__ void k_adam(int64_t n, float* __restrict__ params, float* __restrict__ m,
                        float* __restrict__ v, const float* __restrict__ grad, float lr, float b1,
-                       float b2, float eps, int64_t t, const double* __restrict__ loss) {
+                       float b2, float eps, float c1, float c2,
+                       const double* __restrict__ loss) {
   if (loss && !isfinite(*loss)) return;  // non-finite step: skip the update
-  // bias corrections of step t, by the expression k_loss uses for the fused update
-  __shared__ float corr[2];
-  if (threadIdx.x == 0) {
-    corr[0] = (float)(1.0 - pow((double)b1, (double)t));
-    corr[1] = (float)(1.0 - pow((double)b2, (double)t));
-  }
-  __syncthreads();
-  const float c1 = corr[0], c2 = corr[1];
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     const float g = grad[j];
@@ -723,12 +720,17 @@ __global__ void k_adam(int64_t n, float* __restrict__ params, float* __restrict_
 // ------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------
+float adam_correction(float beta, int64_t t) {
+  return (float)(1.0 - std::pow((double)beta, (double)t));
+}
+
 cudaError_t launch_adam(int64_t n, float* params, float* m, float* v, const float* grad, float lr,
                         float b1, float b2, float eps, int64_t t, const double* loss,
                         cudaStream_t st) {
   const int64_t blocks = (n + 255) / 256;
-  k_adam<<<(int)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(n, params, m, v, grad, lr, b1, b2,
-                                                                eps, t, loss);
+  k_adam<<<(int)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(
+      n, params, m, v, grad, lr, b1, b2, eps, adam_correction(b1, t), adam_correction(b2, t),
+      loss);
   return cudaGetLastError();
 }
 
@@ -790,18 +792,20 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
                           float* params, float* m, float* v, float* grad_out, float lr, float b1,
                           float b2, float eps, float* loss_hist, int64_t hist_base, int prec,
                           Workspace& ws, cudaStream_t st, int level, int n_levels,
-                          double loss_scale) {
+                          double loss_scale, int64_t adam_t) {
   const bool last = level == n_levels - 1;
+  const float c1 = adam ? adam_correction(b1, adam_t) : 1.f;
+  const float c2 = adam ? adam_correction(b2, adam_t) : 1.f;
   int ncb = cut_residual_blocks(n, ws);
   k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb,
                             loss_scale > 0.0 ? loss_scale : 1.0 / (double)n, ws.loss,
-                            adam ? ws.step : nullptr, loss_hist, hist_base, ws.status, b1, b2,
-                            ws.corr, ws.loss_acc, level > 0, last);
+                            adam ? ws.step : nullptr, loss_hist, hist_base, ws.status,
+                            ws.loss_acc, level > 0, last);
   if (adam || want_grad) {
     int64_t tot = 2 * P.p_net;
     k_reduce_adam<<<(int)((tot + 31) / 32), 256, 0, st>>>(
         P, grid, ws.gpart, ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps,
-        ws.corr, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
+        c1, c2, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
         level > 0 ? ws.gacc : nullptr, last ? nullptr : ws.gacc);
   }
   return cudaGetLastError();
