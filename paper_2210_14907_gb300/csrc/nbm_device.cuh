@@ -12,6 +12,19 @@
 namespace nbm {
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of a training step are
+// launched with programmatic stream serialization (launch_pdl), so that a
+// kernel's launch is processed while its predecessor in the stream finishes.
+// Every such kernel begins with pdl_enter(), which waits until the
+// predecessor grid has completed and its writes are visible.  No kernel
+// signals an early launch of its successor (the implicit signal is at grid
+// completion), and data that an earlier kernel of the step writes is read
+// with ordinary loads (no __restrict__ / __ldg read-only path), so that no
+// read of it can be scheduled before the wait.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // Problem constants, passed by value to every kernel.
 // ---------------------------------------------------------------------------
 struct ProbDev {
@@ -602,14 +615,17 @@ __device__ __forceinline__ T uncut_residual_pt(const ProbDev& P, int s, float px
 // group of a warp (all 8 call it for the same point; `mask` covers the
 // calling lanes).  Lane c < 6 takes face c (axis c/2, side c%2), lane 6 the
 // reaction and source term; the balance row and the Dirichlet and face sums
-// are added over the group by shuffles.  Every lane returns r^2 and lane c
-// writes seed c.  The same terms as the one-thread row, added in a different
-// order: for the FP64 rows, whose chain on a single thread is bound by the
-// narrow FP64 pipe, this runs each FP64 instruction on 8 lanes instead of 1.
+// are added over the group by shuffles.  Every lane passes the point's U and
+// the Mt, Dt columns of its face's axis (any value on lanes 6 and 7), returns
+// r^2 and writes seed c.  The same terms as the one-thread row, added in a
+// different order, with the dependency chain of one face per lane: a short
+// chain for the FP32 rows, and for the FP64 rows each instruction of the
+// narrow FP64 pipe carries 8 lanes instead of 1.
 template <typename T>
 __device__ __forceinline__ T uncut_residual_lanes(const ProbDev& P, int s, float px, float py,
-                                                  float pz, T fsrc, const float out[8], T scale,
-                                                  int c, unsigned mask, float& sd_c) {
+                                                  float pz, T fsrc, float U_c, float Mt_c,
+                                                  float Dt_c, T scale, int c, unsigned mask,
+                                                  float& sd_c) {
   const T h = pc_h<T>(P), h2 = h * h, mu = pc_mu<T>(P, s), kk = pc_k<T>(P, s);
   T ih, ih2, iD;
   if constexpr (sizeof(T) == 4) {
@@ -621,15 +637,14 @@ __device__ __forceinline__ T uncut_residual_lanes(const ProbDev& P, int s, float
     ih2 = P.inv_h2;
     iD = P.inv_D[s];
   }
-  const T U = (T)out[0];
+  const T U = (T)U_c;
   const T x[3] = {(T)px, (T)py, (T)pz};
   T term = (T)0, nb = (T)0, cm = (T)0, dv = (T)0;
   if (c < 6) {
-    // (selects, not indexing: the columns and coordinates stay in registers)
+    // (selects, not indexing: the coordinates stay in registers)
     const int i = c >> 1;
     const bool plus = c & 1;
-    const T Mt = (T)(i == 0 ? out[1] : i == 1 ? out[2] : out[3]);
-    const T Dt = (T)(i == 0 ? out[4] : i == 1 ? out[5] : out[6]);
+    const T Mt = (T)Mt_c, Dt = (T)Dt_c;
     const T dq = plus ? h : -h;
     const T q0 = i == 0 ? x[0] + dq : x[0], q1 = i == 1 ? x[1] + dq : x[1],
             q2 = i == 2 ? x[2] + dq : x[2];

@@ -26,6 +26,7 @@ struct Fp32Cfg {
 
 template <int H, int L>
 __global__ void __launch_bounds__(256, 1) k_step_fp32(ProbDev P, StepArgs a) {
+  pdl_enter();
   using C = Fp32Cfg<H, L>;
   constexpr int NJ = C::NJ;
   extern __shared__ __align__(16) float act[];  // [L][kPT][H][8]
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_step_fp32(ProbDev P, StepArgs a) {
         const float4 a1 = *reinterpret_cast<const float4*>(ain + 8 * k + 4);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-          const float wv = __ldg(WT + (int64_t)k * H + lane + 32 * j);
+          const float wv = WT[(int64_t)k * H + lane + 32 * j];
           acc[j][0] = fmaf(wv, a0.x, acc[j][0]);
           acc[j][1] = fmaf(wv, a0.y, acc[j][1]);
           acc[j][2] = fmaf(wv, a0.z, acc[j][2]);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(256, 1) k_step_fp32(ProbDev P, StepArgs a) {
           const float4 g1 = *reinterpret_cast<const float4*>(gzp + 8 * u + 4);
 #pragma unroll
           for (int j = 0; j < NJ; ++j) {
-            const float wv = __ldg(Wg + (int64_t)u * H + lane + 32 * j);
+            const float wv = Wg[(int64_t)u * H + lane + 32 * j];
             G[j][0] = fmaf(wv, g0.x, G[j][0]);
             G[j][1] = fmaf(wv, g0.y, G[j][1]);
             G[j][2] = fmaf(wv, g0.z, G[j][2]);
@@ -430,8 +431,7 @@ static cudaError_t launch_fp32_t(const ProbDev& P, const StepArgs& a, int grid, 
   cudaError_t e = cudaFuncSetAttribute(k_step_fp32<H, L>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_step_fp32<H, L><<<grid, 256, smem, st>>>(P, a);
-  return cudaGetLastError();
+  return launch_pdl(k_step_fp32<H, L>, dim3(grid), dim3(256), smem, st, P, a);
 }
 
 cudaError_t launch_step_fp32(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st) {

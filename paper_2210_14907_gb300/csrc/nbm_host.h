@@ -10,6 +10,26 @@
 
 namespace nbm {
 
+// Launches `kern` on `st` with programmatic stream serialization: the grid may
+// be scheduled while its predecessor in the stream still runs, so the kernel
+// must begin with pdl_enter() (nbm_device.cuh), which waits for that
+// predecessor before any dependent memory access.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct ProbDev;
 
 // Kernel modes of the fused step kernels.

@@ -193,7 +193,8 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
     e = (P.fp64 && prec != NBM_PREC_FP32) ? launch_step_fp32(P, a, grid, st)
                                            : step_launch(MODE_CUT_FWD);
   }
-  if (e == cudaSuccess) e = launch_cut_residual(P, n, (float)(1.0 / (double)n), true, nullptr, w, st);
+  if (e == cudaSuccess)
+    e = launch_cut_residual(P, n, (float)(1.0 / (double)n), true, nullptr, w, st);
   if (e == cudaSuccess) e = step_launch(MODE_TRAIN);
   if (e == cudaSuccess)
     e = launch_finish(P, n, grid, false, true, nullptr, nullptr, nullptr, grad_out, 0.f, 0.9f,

@@ -91,12 +91,13 @@ __device__ inline int count_neg_corners(const ProbDev& P, const float p[3]) {
   return nneg;
 }
 
-__global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float* __restrict__ pts_in,
+__global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float* pts_in,
                                                           uint64_t seed, const int64_t* step_dev,
                                                           int64_t step_host, int64_t n,
                                                           int64_t n_band, float* X, float* Y,
                                                           float* Z, uint8_t* cls, int* blockcnt,
                                                           int nb, int64_t first, int64_t n_total) {
+  pdl_enter();
   int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
   int c = -1;
   if (i < n) {
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float
 // Exclusive scan of the three per-block count arrays (one CTA).  counters[0..2]
 // receive the totals (n-, n+, n_cut).
 __global__ void __launch_bounds__(1024) k_scan_counts(int* blockcnt, int nb, int* counters) {
+  pdl_enter();
   __shared__ int warp_tot[32];
   for (int m = 0; m < 3; ++m) {
     int* a = blockcnt + (int64_t)m * nb;
@@ -172,9 +174,10 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int* blockcnt, int nb, int
 
 // Stable scatter: list order = point order.  Entry >= 0: uncut point index;
 // entry < 0: cut cell -(cut_id + 1).
-__global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* __restrict__ cls, int64_t n,
-                                                  const int* __restrict__ blockoff, int nb,
+__global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
+                                                  const int* blockoff, int nb,
                                                   int* list_m, int* list_p, int* cut_pt) {
+  pdl_enter();
   __shared__ int wsum[3][kBlk / 32];
   int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
   int c = i < n ? (int)cls[i] : -1;
@@ -236,10 +239,10 @@ __device__ inline void cell_pieces(int k, const T F[8], const T C[8][3], T& vneg
 // Cut cell `id` of the list (nc cells) on the 8 lanes of a warp's quarter; the
 // whole warp calls it (full-mask shuffles), lanes past the list compute on
 // cell 0's point and store nothing.
-__device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float* __restrict__ X,
-                                                  const float* __restrict__ Y,
-                                                  const float* __restrict__ Z,
-                                                  const int* __restrict__ cut_pt, CutRec* cut,
+__device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float* X,
+                                                  const float* Y,
+                                                  const float* Z,
+                                                  const int* cut_pt, CutRec* cut,
                                                   int id, int nc) {
   const unsigned full = 0xffffffffu;
   const int k = threadIdx.x & 7, base = (threadIdx.x & 31) & ~7;
@@ -379,12 +382,13 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
 
 // Grid-stride over the cut list in groups of 16 cells (4 per warp), so that
 // the grid need not cover the worst case of every point being cut.
-__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __restrict__ X,
-                                                      const float* __restrict__ Y,
-                                                      const float* __restrict__ Z,
-                                                      const int* __restrict__ cut_pt,
-                                                      const int* __restrict__ counters,
+__global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* X,
+                                                      const float* Y,
+                                                      const float* Z,
+                                                      const int* cut_pt,
+                                                      const int* counters,
                                                       CutRec* cut) {
+  pdl_enter();
   const int nc = counters[2];
   for (int cell0 = blockIdx.x * 16; cell0 < nc; cell0 += gridDim.x * 16) {
     if (cell0 + 4 * (int)(threadIdx.x >> 5) >= nc) break;  // this warp's cells are past the list
@@ -401,50 +405,53 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* __
 // ------------------------------------------------------------------------
 // One warp per block: the cut list (a few thousand cells) spreads over many SMs,
 // each cell's FP64 row on one thread, since GB300's FP64 pipe is narrow.
-__global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* __restrict__ X,
-                                                      const float* __restrict__ Y,
-                                                      const float* __restrict__ Z,
-                                                      const int* __restrict__ counters,
-                                                      const CutRec* __restrict__ cut,
-                                                      const float* __restrict__ out,
+// (Rows in FP32 were tried: the cancellation in B made the seeds, and so the
+// gradient, depend at 1e-5 on how a batch is split into shards.)
+__global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* X,
+                                                      const float* Y,
+                                                      const float* Z,
+                                                      const int* counters,
+                                                      const CutRec* cut,
+                                                      const float* out,
                                                       float* seeds, float scale, float* r2_out,
                                                       double* loss_part) {
+  pdl_enter();
+  using T = double;
   const int nc = counters[2];
   double r2_sum = 0.0;  // this thread's cells (grid-stride), then the block partial
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nc; id += gridDim.x * blockDim.x) {
-    double r2 = 0.0;
-    CutRec c = cut[id];
+    const CutRec c = cut[id];
     const int i = c.point;
-    const double h = P.h, h2 = h * h;
-    const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
+    const T h = pc_h<T>(P), h2 = h * h;
+    const T p[3] = {(T)X[i], (T)Y[i], (T)Z[i]};
     const float* o = out + (int64_t)id * 16;
-    double B = 0.0, D = 0.0;
-    double dU[2], dM[2][3], dD[2][3];
+    T B = 0, D = 0;
+    T dU[2], dM[2][3], dD[2][3];
     bool bnd[6];
-    double g[6];
+    T g[6];
     for (int f = 0; f < 6; ++f) {
       int a = f >> 1;
-      double q[3] = {p[0], p[1], p[2]};
+      T q[3] = {p[0], p[1], p[2]};
       q[a] += (f & 1) ? h : -h;
-      bnd[f] = fabs(q[a]) >= 1.0;
-      g[f] = bnd[f] ? dirichlet_g<double>(P, q[0], q[1], q[2]) : 0.0;
+      bnd[f] = fabs(q[a]) >= (T)1;
+      g[f] = bnd[f] ? dirichlet_g<T>(P, q[0], q[1], q[2]) : (T)0;
     }
     for (int s = 0; s < 2; ++s) {
-      const double V = s ? 1.0 - c.Vm : c.Vm;
-      const double k = P.k[s];
-      const double U = (double)o[8 * s];
-      B += h2 * V * (k * U - c.f[s]);
+      const T V = (T)(s ? 1.0 - c.Vm : c.Vm);
+      const T k = pc_k<T>(P, s);
+      const T U = (T)o[8 * s];
+      B += h2 * V * (k * U - (T)c.f[s]);
       D += h2 * V * k;
       dU[s] = h2 * V * k;
-      for (int a = 0; a < 3; ++a) dM[s][a] = dD[s][a] = 0.0;
+      for (int a = 0; a < 3; ++a) dM[s][a] = dD[s][a] = 0;
       for (int f = 0; f < 6; ++f) {
         const int a = f >> 1;
-        const double sg = (f & 1) ? 1.0 : -1.0;
-        const double A = s ? 1.0 - c.Am[f] : c.Am[f];
+        const T sg = (f & 1) ? (T)1 : (T)-1;
+        const T A = (T)(s ? 1.0 - c.Am[f] : c.Am[f]);
         // mu^s at the face centre (constant for the benchmark pair)
-        double fc[3] = {p[0], p[1], p[2]};
-        fc[a] += 0.5 * sg * h;
-        const double w = A * mu_at<double>(P, s, fc[0], fc[1], fc[2]);
+        T fc[3] = {p[0], p[1], p[2]};
+        fc[a] += (T)0.5 * sg * h;
+        const T w = A * mu_at<T>(P, s, fc[0], fc[1], fc[2]);
         D += w;
         if (bnd[f]) {
           // U^s(p) enters the row directly only through Dirichlet faces: the
@@ -452,19 +459,19 @@ __global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* __r
           B -= w * (g[f] - U);
           dU[s] += w;
         } else {
-          B -= w * (h2 * (double)o[8 * s + 1 + a] + sg * h * (double)o[8 * s + 4 + a]);
+          B -= w * (h2 * (T)o[8 * s + 1 + a] + sg * h * (T)o[8 * s + 4 + a]);
           dM[s][a] -= w * h2;
           dD[s][a] -= w * sg * h;
         }
       }
     }
-    if (c.has_jump) B += h * c.S * c.beta;
-    const double J = c.has_jump ? (double)o[15] - (double)o[7] - c.alpha : 0.0;
-    const double rB = B / D;
-    r2 = rB * rB + P.lambda * J * J;
+    if (c.has_jump) B += h * (T)c.S * (T)c.beta;
+    const T J = c.has_jump ? (T)o[15] - (T)o[7] - (T)c.alpha : (T)0;
+    const T rB = B / D, lam = (T)P.lambda;
+    const T r2 = rB * rB + lam * J * J;
     if (seeds) {
-      const double cB = (double)scale * 2.0 * rB / D;
-      const double cJ = (double)scale * 2.0 * P.lambda * J;
+      const T cB = (T)scale * (T)2 * rB / D;
+      const T cJ = (T)scale * (T)2 * lam * J;
       float* sd = seeds + (int64_t)id * 16;
       for (int s = 0; s < 2; ++s) {
         sd[8 * s] = (float)(cB * dU[s]);
@@ -476,7 +483,7 @@ __global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* __r
       }
     }
     if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
-    r2_sum += r2;
+    r2_sum += (double)r2;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r2_sum += __shfl_xor_sync(0xffffffffu, r2_sum, o);
@@ -491,15 +498,16 @@ __global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* __r
 // arithmetic.  One thread per record; the grid covers the worst case.
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_gather_tiles(const ProbDev P,
-                                                      const int* __restrict__ counters,
-                                                      const int* __restrict__ list_m,
-                                                      const int* __restrict__ list_p,
-                                                      const int* __restrict__ cut_pt,
-                                                      const float* __restrict__ X,
-                                                      const float* __restrict__ Y,
-                                                      const float* __restrict__ Z,
-                                                      const CutRec* __restrict__ cut, PRec* rec,
+                                                      const int* counters,
+                                                      const int* list_m,
+                                                      const int* list_p,
+                                                      const int* cut_pt,
+                                                      const float* X,
+                                                      const float* Y,
+                                                      const float* Z,
+                                                      const CutRec* cut, PRec* rec,
                                                       PRec* rec_cut, int64_t cap) {
+  pdl_enter();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nm = counters[0], np = counters[1], nc = counters[2];
   const int64_t T0 = (nm + 15) / 16, T1 = (np + 15) / 16, Tc = (nc + 15) / 16;
@@ -564,8 +572,9 @@ __global__ void __launch_bounds__(256) k_gather_tiles(const ProbDev P,
 // ------------------------------------------------------------------------
 __host__ __device__ inline uint32_t tc_tile_offset(int u, int c) { return tc::img_off(u, c); }
 
-__global__ void k_prep_weights(ProbDev P, const float* __restrict__ params, float* wt, void* wtc,
+__global__ void k_prep_weights(ProbDev P, const float* params, float* wt, void* wtc,
                                int prec) {
+  pdl_enter();
   const int H = P.H, L = P.L;
   const int64_t per = (int64_t)H * H;
   const int64_t total = 2 * (int64_t)(L - 1) * per;
@@ -595,10 +604,11 @@ __global__ void k_prep_weights(ProbDev P, const float* __restrict__ params, floa
 // levels, the levels' losses are summed in *loss_acc (acc_in: add the levels
 // done so far; last == 0: only accumulate) and the step is finished after the
 // last level.
-__global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __restrict__ clp,
+__global__ void k_loss(const double* lp, int nlp, const double* clp,
                        int nclp, double scale, double* loss, int64_t* step, float* loss_hist,
                        int64_t hist_base, int* status,
                        double* loss_acc, int acc_in, int last) {
+  pdl_enter();
   __shared__ double red[8];
   double s = 0.0;
   for (int j = threadIdx.x; j < nlp; j += 256) s += lp[j];
@@ -629,37 +639,50 @@ __global__ void k_loss(const double* __restrict__ lp, int nlp, const double* __r
 // Gradient of the step (fixed CTA order), then Adam.  With refinement levels
 // the levels' gradients are summed in gacc: gacc_in (levels done so far) is
 // added, and a level that is not the last stores the sum in gacc_out and stops.
-__global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpart,
-                              const int* __restrict__ flag, float* grad_out, float* params,
-                              float* m, float* v, float lr, float b1, float b2, float eps,
-                              float c1, float c2, const double* loss, float* wt, void* wtc,
-                              int prec, const float* gacc_in, float* gacc_out) {
-  // Block of 256 threads: 32 consecutive parameters (lane) x 8 groups of the
-  // per-CTA partial slices (group cg sums slices cg, cg + 8, ...); the groups
-  // are then added in a fixed order, so the sum is deterministic.
-  __shared__ float red[8][33];
-  const int64_t pn = P.p_net;
+// Block of 256 threads on 128 consecutive parameters of one network: warp cg
+// sums the per-CTA partial slices cg, cg + 8, ... (lane l: parameters 4l..4l+3
+// of the block, one float4 per slice, every slice loaded and the slice of a
+// CTA that stopped early dropped by a select, so the loads do not wait for the
+// flags); then thread t < 128 adds the 8 group sums of parameter t in a fixed
+// order, so the sum is deterministic, and applies the update.
+__global__ void __launch_bounds__(256) k_reduce_adam(ProbDev P, int grid, int nb_net,
+                                                     const float* gpart,
+                                                     const int* flag,
+                                                     float* grad_out, float* params, float* m,
+                                                     float* v, float lr, float b1, float b2,
+                                                     float eps, float c1, float c2,
+                                                     const double* loss, float* wt, void* wtc,
+                                                     int prec, const float* gacc_in,
+                                                     float* gacc_out) {
+  pdl_enter();
+  __shared__ float4 red[8][32];
+  const int pn = (int)P.p_net;
+  const int s = blockIdx.x >= nb_net ? 1 : 0;
+  const int blk = blockIdx.x - s * nb_net;
   const int lane = threadIdx.x & 31, cg = threadIdx.x >> 5;
-  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
-  const bool in = j < 2 * pn;
-  const int s = in ? (int)(j / pn) : 0;
-  const int64_t jj = j - s * pn;
-  float part = 0.f;
-  if (in) {
-    // every slice loaded, a slice of a CTA that stopped early dropped by a
-    // select: the loads do not wait for the flags
-#pragma unroll 4
+  const int j4 = (blk * 32 + lane) * 4;  // within the network; < gstride when < pn
+  float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (j4 < pn) {
+    const float* src = gpart + (int64_t)s * P.gstride + j4;
+#pragma unroll 8
     for (int c = cg; c < grid; c += 8) {
-      const float g = __ldcg(gpart + ((int64_t)c * 2 + s) * P.gstride + jj);
-      part += __ldg(flag + 2 * c + s) ? g : 0.f;
+      const float4 g = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)c * 2 * P.gstride));
+      const bool f = flag[2 * c + s] != 0;
+      part.x += f ? g.x : 0.f;
+      part.y += f ? g.y : 0.f;
+      part.z += f ? g.z : 0.f;
+      part.w += f ? g.w : 0.f;
     }
   }
   red[cg][lane] = part;
   __syncthreads();
-  if (cg != 0 || !in) return;
-  float g = red[0][lane];
+  const int t = threadIdx.x;
+  const int jj = blk * 128 + t;
+  if (t >= 128 || jj >= pn) return;
+  float g = reinterpret_cast<const float*>(red[0])[t];
 #pragma unroll
-  for (int q = 1; q < 8; ++q) g += red[q][lane];
+  for (int q = 1; q < 8; ++q) g += reinterpret_cast<const float*>(red[q])[t];
+  const int64_t j = (int64_t)s * pn + jj;
   if (gacc_in) g += gacc_in[j];
   if (gacc_out) {
     gacc_out[j] = g;
@@ -677,17 +700,17 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
   params[j] = w;
   // restage hidden weights for the next step
   const int H = P.H;
-  const int64_t per = (int64_t)H * H;
-  if (jj >= 4 * H && jj < 4 * H + (int64_t)(P.L - 1) * (per + H)) {
-    int64_t q = jj - 4 * H;
-    int l = (int)(q / (per + H)) + 1;
-    int64_t rem = q % (per + H);
+  const int per = H * H;
+  if (jj >= 4 * H && jj < 4 * H + (P.L - 1) * (per + H)) {
+    const int q = jj - 4 * H;
+    const int l = q / (per + H) + 1;
+    const int rem = q - (l - 1) * (per + H);
     if (rem < per) {
-      int u = (int)(rem / H), k = (int)(rem % H);
-      int64_t blk = (int64_t)s * (P.L - 1) + (l - 1);
-      if (wt) wt[blk * per + (int64_t)k * H + u] = w;
+      const int u = rem / H, k = rem - u * H;
+      const int64_t wb = (int64_t)s * (P.L - 1) + (l - 1);
+      if (wt) wt[wb * per + (int64_t)k * H + u] = w;
       if (wtc && H == 128) {
-        char* base = (char*)wtc + blk * per * 2;
+        char* base = (char*)wtc + wb * per * 2;
         if (prec == NBM_PREC_FP16) *(__half*)(base + tc_tile_offset(u, k)) = __float2half_rn(w);
         else *(__nv_bfloat16*)(base + tc_tile_offset(u, k)) = __float2bfloat16_rn(w);
       }
@@ -700,10 +723,11 @@ __global__ void k_reduce_adam(ProbDev P, int grid, const float* __restrict__ gpa
 // locally computed gradient updates are aggregated).  Element for element the
 // arithmetic of the update in k_reduce_adam, so one shard covering the whole
 // batch reproduces nbm_train_steps bitwise.
-__global__ void k_adam(int64_t n, float* __restrict__ params, float* __restrict__ m,
-                       float* __restrict__ v, const float* __restrict__ grad, float lr, float b1,
+__global__ void k_adam(int64_t n, float* params, float* m,
+                       float* v, const float* grad, float lr, float b1,
                        float b2, float eps, float c1, float c2,
-                       const double* __restrict__ loss) {
+                       const double* loss) {
+  pdl_enter();
   if (loss && !isfinite(*loss)) return;  // non-finite step: skip the update
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -728,10 +752,9 @@ cudaError_t launch_adam(int64_t n, float* params, float* m, float* v, const floa
                         float b1, float b2, float eps, int64_t t, const double* loss,
                         cudaStream_t st) {
   const int64_t blocks = (n + 255) / 256;
-  k_adam<<<(int)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(
-      n, params, m, v, grad, lr, b1, b2, eps, adam_correction(b1, t), adam_correction(b2, t),
-      loss);
-  return cudaGetLastError();
+  return launch_pdl(k_adam, dim3((unsigned)(blocks < 1024 ? blocks : 1024)), dim3(256), 0, st, n,
+                    params, m, v, grad, lr, b1, b2, eps, adam_correction(b1, t),
+                    adam_correction(b2, t), loss);
 }
 
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
@@ -739,13 +762,15 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
                                    int64_t n_band, Workspace& ws, cudaStream_t st,
                                    int64_t first, int64_t n_total) {
   int nb = (int)((n + kBlk - 1) / kBlk);
-  k_sample_classify<<<nb, kBlk, 0, st>>>(P, pts_in, seed, step_dev, step_host, n, n_band, ws.x,
-                                         ws.y, ws.z, ws.cls, ws.blockcnt, nb, first,
-                                         n_total > 0 ? n_total : n);
-  k_scan_counts<<<1, 1024, 0, st>>>(ws.blockcnt, nb, ws.counters);
-  k_scatter<<<nb, kBlk, 0, st>>>(ws.cls, n, ws.blockcnt, nb, ws.list_minus, ws.list_plus,
-                                 ws.cut_pt);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_sample_classify, dim3(nb), dim3(kBlk), 0, st, P, pts_in, seed,
+                             step_dev, step_host, n, n_band, ws.x, ws.y, ws.z, ws.cls,
+                             ws.blockcnt, nb, first, n_total > 0 ? n_total : n);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_scan_counts, dim3(1), dim3(1024), 0, st, ws.blockcnt, nb, ws.counters);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_scatter, dim3(nb), dim3(kBlk), 0, st, (const uint8_t*)ws.cls, n,
+                   (const int*)ws.blockcnt, nb, ws.list_minus, ws.list_plus, ws.cut_pt);
+  return e;
 }
 
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
@@ -753,8 +778,9 @@ cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cuda
   // striding over the cut list
   const int64_t worst = (n + 15) / 16, cap = 8 * (int64_t)ws.grid;
   int nb = (int)(worst < cap ? worst : cap);
-  k_cut_geometry<<<nb, 128, 0, st>>>(P, ws.x, ws.y, ws.z, ws.cut_pt, ws.counters, ws.cut);
-  return cudaGetLastError();
+  return launch_pdl(k_cut_geometry, dim3(nb), dim3(128), 0, st, P, (const float*)ws.x,
+                    (const float*)ws.y, (const float*)ws.z, (const int*)ws.cut_pt,
+                    (const int*)ws.counters, ws.cut);
 }
 
 // blocks of the cut-row kernel (grid-stride over the cut cells), i.e. the
@@ -767,25 +793,22 @@ int cut_residual_blocks(int64_t n, const Workspace& ws) {
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
                                 float* r2_out, Workspace& ws, cudaStream_t st) {
   int nb = cut_residual_blocks(n, ws);
-  k_cut_residual<<<nb, 32, 0, st>>>(P, ws.x, ws.y, ws.z, ws.counters, ws.cut, ws.cut_out,
-                                     want_seeds ? ws.cut_seed : nullptr, scale, r2_out,
-                                     ws.cut_loss_part);
-  return cudaGetLastError();
+  return launch_pdl(k_cut_residual, dim3(nb), dim3(32), 0, st, P, ws.x, ws.y, ws.z, ws.counters,
+                    ws.cut, ws.cut_out, want_seeds ? ws.cut_seed : nullptr, scale, r2_out,
+                    ws.cut_loss_part);
 }
 
 cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
   const int64_t worst = 2 * n + 32;  // both lists padded
-  k_gather_tiles<<<(int)((worst + 255) / 256), 256, 0, st>>>(
-      P, ws.counters, ws.list_minus, ws.list_plus, ws.cut_pt, ws.x, ws.y, ws.z, ws.cut, ws.rec,
-      ws.rec_cut, n);
-  return cudaGetLastError();
+  return launch_pdl(k_gather_tiles, dim3((unsigned)((worst + 255) / 256)), dim3(256), 0, st, P,
+                    ws.counters, ws.list_minus, ws.list_plus, ws.cut_pt, ws.x, ws.y, ws.z, ws.cut,
+                    ws.rec, ws.rec_cut, n);
 }
 
 cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,
                                 cudaStream_t st) {
-  k_prep_weights<<<2 * (P.L - 1) * 16, 256, 0, st>>>(P, params, ws.wt,
-                                                     (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
-  return cudaGetLastError();
+  return launch_pdl(k_prep_weights, dim3(2 * (P.L - 1) * 16), dim3(256), 0, st, P, params, ws.wt,
+                    (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
 }
 
 cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool want_grad,
@@ -797,18 +820,19 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
   const float c1 = adam ? adam_correction(b1, adam_t) : 1.f;
   const float c2 = adam ? adam_correction(b2, adam_t) : 1.f;
   int ncb = cut_residual_blocks(n, ws);
-  k_loss<<<1, 256, 0, st>>>(ws.loss_part, grid, ws.cut_loss_part, ncb,
-                            loss_scale > 0.0 ? loss_scale : 1.0 / (double)n, ws.loss,
-                            adam ? ws.step : nullptr, loss_hist, hist_base, ws.status,
-                            ws.loss_acc, level > 0, last);
-  if (adam || want_grad) {
-    int64_t tot = 2 * P.p_net;
-    k_reduce_adam<<<(int)((tot + 31) / 32), 256, 0, st>>>(
-        P, grid, ws.gpart, ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps,
-        c1, c2, ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
-        level > 0 ? ws.gacc : nullptr, last ? nullptr : ws.gacc);
+  cudaError_t e = launch_pdl(k_loss, dim3(1), dim3(256), 0, st, ws.loss_part, grid,
+                             ws.cut_loss_part, ncb,
+                             loss_scale > 0.0 ? loss_scale : 1.0 / (double)n, ws.loss,
+                             adam ? ws.step : nullptr, loss_hist, hist_base, ws.status,
+                             ws.loss_acc, (int)(level > 0), (int)last);
+  if (e == cudaSuccess && (adam || want_grad)) {
+    const int nb_net = (int)((P.p_net + 127) / 128);
+    e = launch_pdl(k_reduce_adam, dim3(2 * nb_net), dim3(256), 0, st, P, grid, nb_net, ws.gpart,
+                   ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps, c1, c2,
+                   ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
+                   level > 0 ? ws.gacc : nullptr, last ? nullptr : ws.gacc);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace nbm

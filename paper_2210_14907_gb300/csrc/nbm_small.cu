@@ -93,6 +93,7 @@ size_t small_smem_bytes(int L) { return (size_t)2 * L * kSPT * kHM * 8 * sizeof(
 
 template <int ACT>
 __global__ void __launch_bounds__(256, 1) k_step_small(ProbDev P, StepArgs a) {
+  pdl_enter();
   extern __shared__ __align__(16) float sbuf[];
   __shared__ double loss_red[8];
   const int H = P.H, L = P.L;
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256, 1) k_step_small(ProbDev P, StepArgs a) {
         for (int k = 0; k < H; ++k) {
           float av[8];
           ld8(A(g - 1, w, k), av);
-          const float wv = __ldg(WT + (int64_t)k * H + u);
+          const float wv = WT[(int64_t)k * H + u];
 #pragma unroll
           for (int c = 0; c < 8; ++c) acc[c] = fmaf(wv, av[c], acc[c]);
         }
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(256, 1) k_step_small(ProbDev P, StepArgs a) {
         for (int u = 0; u < H; ++u) {
           float gv[8];
           ld8(Z(g, w, u), gv);
-          const float wv = __ldg(Wg + (int64_t)u * H + lane);
+          const float wv = Wg[(int64_t)u * H + lane];
 #pragma unroll
           for (int c = 0; c < 8; ++c) G[c] = fmaf(wv, gv[c], G[c]);
         }
@@ -392,8 +393,7 @@ static cudaError_t launch_small_t(const ProbDev& P, const StepArgs& a, int grid,
   cudaError_t e = cudaFuncSetAttribute(k_step_small<ACT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_step_small<ACT><<<grid, 256, smem, st>>>(P, a);
-  return cudaGetLastError();
+  return launch_pdl(k_step_small<ACT>, dim3(grid), dim3(256), smem, st, P, a);
 }
 
 cudaError_t launch_step_small(const ProbDev& P, const StepArgs& a, int grid, cudaStream_t st) {

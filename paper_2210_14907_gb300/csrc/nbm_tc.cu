@@ -192,6 +192,7 @@ int tc_supported(int H, int L) { return H == 128 && L >= 2 && L <= 4; }
 // the scaled convention of the residual rows.
 template <int L, bool BF, bool FAST, bool SCALED>
 __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
+  pdl_enter();
   constexpr int H = 128;
   constexpr int NG = L - 1;  // hidden GEMM layers
   constexpr int kPPT = 4;    // points per thread (8 warps = 4 lane quadrants x 2 column groups)
@@ -427,8 +428,8 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 #pragma unroll 1
     for (int tau = s0 + grp; tau < s1; tau += 2, ++tile_i, ++kk) {
       // layer-1 weights of this thread's unit, loaded while the records arrive
-      const float w1[3] = {__ldg(th + 3 * u), __ldg(th + 3 * u + 1), __ldg(th + 3 * u + 2)};
-      const float b1 = __ldg(th + 3 * H + u);
+      const float w1[3] = {th[3 * u], th[3 * u + 1], th[3 * u + 2]};
+      const float b1 = th[3 * H + u];
       // ---- tile records (prefetched during the previous tile)
       {
         const bool ok = mbar_wait_bounded(smem_u32(bar_p), ph_p);
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 #pragma unroll 1
       for (int g = 1; g <= NG; ++g) {
         // the layer's bias, loaded while the GEMM runs
-        const float bb = __ldg(th + 4 * H + (g - 1) * (H * H + H) + H * H + u);
+        const float bb = th[4 * H + (g - 1) * (H * H + H) + H * H + u];
         if (gtid == 0 && gate(0)) {
           const uint32_t wa = smem_u32(Wimg + (g - 1) * kImg);
           const uint32_t ab = smem_u32(Aimg + (g - 1) * kImgH);
@@ -620,12 +621,16 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       }
       if (train && gtid < 8 * kHP) cp_async_wait_all();
       named_sync(gbar, 256);
-      // ---- output columns and residual rows: thread p of the group's first
-      // warp owns point p and its 8 columns
-      // (the FP64 rows only occur in the accurate, !FAST, instances)
-      if (!FAST && P.fp64 && gtid < 8 * kHP) {
-        // FP64 rows: lane c of the 8 lanes gtid = 8 p + c takes column c of
-        // point p; the row is spread over the 8 lanes (uncut_residual_lanes)
+      // ---- output columns and residual rows: lane c of the 8 lanes
+      // gtid = 8 p + c of the group's first two warps takes column c of point
+      // p, and the point's row is spread over its 8 lanes
+      // (uncut_residual_lanes: one face per lane, sums by shuffles), so the
+      // row's dependency chain runs on 8 lanes instead of 1.  FP64 rows only
+      // occur in the accurate (!FAST) instances.  The fast four-layer
+      // instance keeps one thread per point (uncut_residual_pt): there the
+      // lane rows cost registers elsewhere and made the kernel 4 % slower.
+      constexpr bool kLaneRows = !FAST || L <= 3;
+      if (kLaneRows && gtid < 8 * kHP) {
         const int p = gtid >> 3, c = gtid & 7;
         const unsigned gmask = 0xFFu << (gtid & 24);
         float oc = red[8 * p + c];
@@ -634,31 +639,40 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         if (c == 0 || c == 7) oc += bo;
         const float csc = SCALED ? 1.f : (c >= 1 && c <= 3) ? P.inv_h2f
                                        : (c >= 4 && c <= 6) ? P.inv_hf : 1.f;
-        oc *= csc;  // the scaled convention of the rows
-        float o[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = __shfl_sync(gmask, oc, k, 8);
+        oc *= csc;  // the scaled convention of the rows: U, Mt_i = M_i/h^2, Dt_i = D_i/h
+        // U and the Mt, Dt columns of this lane's face axis (c / 2)
+        const float Uc = __shfl_sync(gmask, oc, 0, 8);
+        const float Mtc = __shfl_sync(gmask, oc, 1 + (c >> 1), 8);
+        const float Dtc = __shfl_sync(gmask, oc, 4 + (c >> 1), 8);
         const PRec pi = pr[p];
         const bool valid = pi.pt >= 0, is_cut = pi.cutj >= 0;
         float* sdp = seeds + 8 * p;
         if (cutfwd) {
           if (valid) a.cut_out[(int64_t)(pi.cutj >> 1) * 16 + net * 8 + c] = oc;
         } else if (valid && !is_cut) {
-          float sdc;
-          const double r2d = uncut_residual_lanes<double>(P, net, pi.x, pi.y, pi.z,
-                                                          (double)pi.gx + (double)pi.gy, o,
-                                                          (double)a.scale, c, gmask, sdc);
-          if (c == 0) {
-            loss_acc_d += r2d;
-            if (a.r2_out) a.r2_out[pi.pt] = (P.level ? a.r2_out[pi.pt] : 0.f) + (float)r2d;
+          float sdc, r2;
+          bool rows64 = false;
+          if constexpr (!FAST) rows64 = P.fp64;
+          if (rows64) {
+            const double r2d = uncut_residual_lanes<double>(P, net, pi.x, pi.y, pi.z,
+                                                            (double)pi.gx + (double)pi.gy, Uc, Mtc,
+                                                            Dtc, (double)a.scale, c, gmask, sdc);
+            if (c == 0) loss_acc_d += r2d;
+            r2 = (float)r2d;
+          } else {
+            r2 = uncut_residual_lanes<float>(P, net, pi.x, pi.y, pi.z, pi.gx, Uc, Mtc, Dtc,
+                                             a.scale, c, gmask, sdc);
+            if (c == 0) loss_acc += r2;
           }
+          if (c == 0 && a.r2_out) a.r2_out[pi.pt] = (P.level ? a.r2_out[pi.pt] : 0.f) + r2;
           sdp[c] = sdc * csc;  // seeds in this kernel's column convention
         } else if (valid && train) {
           sdp[c] *= csc;  // cut point: the seeds copied at the start of the tile, rescaled
         } else {
           sdp[c] = 0.f;
         }
-      } else if ((FAST || !P.fp64) && gtid < kHP) {
+      } else if (!kLaneRows && gtid < kHP) {
+        // one thread per point (FP32 rows)
         const int p = gtid;
         float o[8];
         {
@@ -673,7 +687,6 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
           o[0] = lo.x + bo; o[1] = lo.y; o[2] = lo.z; o[3] = lo.w;
           o[4] = hi.x; o[5] = hi.y; o[6] = hi.z; o[7] = hi.w + bo;
         }
-        // scaled convention of the rows: U, Mt_i = M_i/h^2, Dt_i = D_i/h, U(x_G)
         if (!SCALED) {
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
@@ -691,19 +704,10 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
             co[1] = make_float4(o[4], o[5], o[6], o[7]);
           }
         } else if (valid && !is_cut) {
-          float sd[8], r2;
-          if (P.fp64) {
-            const double r2d = uncut_residual_pt<double>(P, net, pi.x, pi.y, pi.z,
-                                                         (double)pi.gx + (double)pi.gy, o,
-                                                         (double)a.scale, sd);
-            loss_acc_d += r2d;
-            r2 = (float)r2d;
-          } else {
-            r2 = uncut_residual_pt<float>(P, net, pi.x, pi.y, pi.z, pi.gx, o, a.scale, sd);
-            loss_acc += r2;
-          }
+          float sd[8];
+          const float r2 = uncut_residual_pt<float>(P, net, pi.x, pi.y, pi.z, pi.gx, o, a.scale, sd);
+          loss_acc += r2;
           if (a.r2_out) a.r2_out[pi.pt] = (P.level ? a.r2_out[pi.pt] : 0.f) + r2;
-          // seeds in this kernel's column convention
           if (!SCALED) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -974,8 +978,7 @@ static cudaError_t launch_tc_t(const ProbDev& P, const StepArgs& a, int grid, cu
   cudaError_t e = cudaFuncSetAttribute(k_step_tc<L, BF, FAST, SCALED>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_step_tc<L, BF, FAST, SCALED><<<grid, 512, smem, st>>>(P, a);
-  return cudaGetLastError();
+  return launch_pdl(k_step_tc<L, BF, FAST, SCALED>, dim3(grid), dim3(512), smem, st, P, a);
 }
 
 cudaError_t launch_step_tc(const ProbDev& P, const StepArgs& a, int grid, int prec, cudaStream_t st) {
