@@ -31,7 +31,31 @@ __device__ inline T frac_tri(T a, T b, T c) {
   return T(1) - (l / (l - o1)) * (l / (l - o2));
 }
 
-// fraction of the tetrahedron (corner values f) with phi <= 0
+// Element i of a 4-array and row i of a 4 x 3 array by selects, so that the
+// arrays stay in registers: a run-time index into a register array would put
+// it in local memory (the scans below pick vertices by their signs).
+template <typename T>
+__device__ __forceinline__ T sel4(const T a[4], int i) {
+  return i == 0 ? a[0] : i == 1 ? a[1] : i == 2 ? a[2] : a[3];
+}
+template <typename T>
+__device__ __forceinline__ void sel4_row(const T X[4][3], int i, T o[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) o[c] = i == 0 ? X[0][c] : i == 1 ? X[1][c] : i == 2 ? X[2][c] : X[3][c];
+}
+
+// The vertex alone on its side of a tetrahedron with `neg` (1 or 3) corner
+// values <= 0: the last one in vertex order whose sign is the minority's.
+template <typename T>
+__device__ __forceinline__ int lone_vertex(const T f[4], bool want_neg) {
+  int lone = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if ((f[i] <= T(0)) == want_neg) lone = i;
+  return lone;
+}
+
+// fraction of the tetrahedron (corner values f; phi linear) with phi <= 0
 template <typename T>
 __device__ inline T frac_tet(const T f[4]) {
   int neg = 0;
@@ -40,17 +64,17 @@ __device__ inline T frac_tet(const T f[4]) {
   if (neg == 0) return T(0);
   if (neg == 4) return T(1);
   if (neg == 1 || neg == 3) {
-    bool want_neg = neg == 1;
-    int lone = 0;
-    for (int i = 0; i < 4; ++i)
-      if ((f[i] <= T(0)) == want_neg) lone = i;
+    const int lone = lone_vertex<T>(f, neg == 1);
+    const T fl = sel4<T>(f, lone);
     T prod = T(1);
+#pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (i != lone) prod *= f[lone] / (f[lone] - f[i]);
+      if (i != lone) prod *= fl / (fl - f[i]);
     return neg == 1 ? prod : T(1) - prod;
   }
   // two on each side: A, B = -values below, C, D = values above
   T A = T(-1), B = T(-1), C = T(-1), D = T(-1);
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
     if (f[i] <= T(0)) {
       if (A < T(0)) A = -f[i]; else B = -f[i];
@@ -62,12 +86,14 @@ __device__ inline T frac_tet(const T f[4]) {
   return num / ((C + A) * (D + A) * (C + B) * (D + B));
 }
 
+// zero of phi on the edge u -> v
 template <typename T>
 __device__ inline void lerp_zero(const T* xu, T fu, const T* xv, T fv, T* o) {
   T t = fu / (fu - fv);
   for (int i = 0; i < 3; ++i) o[i] = xu[i] + t * (xv[i] - xu[i]);
 }
 
+// area of the triangle a b c; adds area x centroid to wc
 template <typename T>
 __device__ inline T tri_area_acc(const T* a, const T* b, const T* c, T* wc) {
   T e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
@@ -79,37 +105,52 @@ __device__ inline T tri_area_acc(const T* a, const T* b, const T* c, T* wc) {
   return ar;
 }
 
-// interface polygon of one tetrahedron: returns its area, adds area*centroid
+// area of the interface polygon inside the tetrahedron (vertices X, values f);
+// adds area x centroid to wc
 template <typename T>
 __device__ inline T tet_iface(const T X[4][3], const T f[4], T* wc) {
   int neg = 0;
+#pragma unroll
   for (int i = 0; i < 4; ++i) neg += f[i] <= T(0);
   if (neg == 0 || neg == 4) return T(0);
   if (neg == 1 || neg == 3) {
-    bool want_neg = neg == 1;
-    int lone = 0;
-    for (int i = 0; i < 4; ++i)
-      if ((f[i] <= T(0)) == want_neg) lone = i;
+    // a triangle: the zeros on the edges from the lone vertex to the other
+    // three, taken in vertex order, each edge oriented from its <= 0 end
+    const bool want_neg = neg == 1;
+    const int lone = lone_vertex<T>(f, want_neg);
+    const int o[3] = {lone == 0 ? 1 : 0, lone <= 1 ? 2 : 1, lone <= 2 ? 3 : 2};
+    T xl[3];
+    sel4_row<T>(X, lone, xl);
+    const T fl = sel4<T>(f, lone);
     T Pp[3][3];
-    int k = 0;
-    for (int i = 0; i < 4; ++i) {
-      if (i == lone) continue;
-      if (want_neg) lerp_zero<T>(X[lone], f[lone], X[i], f[i], Pp[k]);
-      else lerp_zero<T>(X[i], f[i], X[lone], f[lone], Pp[k]);
-      ++k;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T xi[3];
+      sel4_row<T>(X, o[k], xi);
+      const T fi = sel4<T>(f, o[k]);
+      if (want_neg) lerp_zero<T>(xl, fl, xi, fi, Pp[k]);
+      else lerp_zero<T>(xi, fi, xl, fl, Pp[k]);
     }
     return tri_area_acc<T>(Pp[0], Pp[1], Pp[2], wc);
   }
+  // a quadrilateral: vertices a < b with phi <= 0, c < d above
   int a = -1, b = -1, c = -1, d = -1;
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
     if (f[i] <= T(0)) { if (a < 0) a = i; else b = i; }
     else { if (c < 0) c = i; else d = i; }
   }
+  T xa[3], xb[3], xc[3], xd[3];
+  sel4_row<T>(X, a, xa);
+  sel4_row<T>(X, b, xb);
+  sel4_row<T>(X, c, xc);
+  sel4_row<T>(X, d, xd);
+  const T fa = sel4<T>(f, a), fb = sel4<T>(f, b), fc = sel4<T>(f, c), fd = sel4<T>(f, d);
   T Q[4][3];
-  lerp_zero<T>(X[a], f[a], X[c], f[c], Q[0]);
-  lerp_zero<T>(X[a], f[a], X[d], f[d], Q[1]);
-  lerp_zero<T>(X[b], f[b], X[d], f[d], Q[2]);
-  lerp_zero<T>(X[b], f[b], X[c], f[c], Q[3]);
+  lerp_zero<T>(xa, fa, xc, fc, Q[0]);
+  lerp_zero<T>(xa, fa, xd, fd, Q[1]);
+  lerp_zero<T>(xb, fb, xd, fd, Q[2]);
+  lerp_zero<T>(xb, fb, xc, fc, Q[3]);
   return tri_area_acc<T>(Q[0], Q[1], Q[2], wc) + tri_area_acc<T>(Q[0], Q[2], Q[3], wc);
 }
 
@@ -145,11 +186,13 @@ __device__ inline void cell_geometry_d(const ProbDev& P, const double p[3], doub
   g.cut = 1;
   double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0};
   const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  for (int t = 0; t < 6; ++t) {
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {  // unrolled: every index below is a constant
     int v1 = 1 << perm[t][0];
     int v2 = v1 | (1 << perm[t][1]);
     int idx[4] = {0, v1, v2, 7};
     double Xt[4][3], ft[4];
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
       for (int a = 0; a < 3; ++a) Xt[k][a] = C[idx[k]][a];
       ft[k] = F[idx[k]];

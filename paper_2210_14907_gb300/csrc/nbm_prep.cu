@@ -208,32 +208,40 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
 }
 
 // One cut cell per 8 lanes: corner values, tetrahedra and faces are spread
-// over the lanes and combined with shuffles; beta, alpha, f- and f+ (FP64
-// transcendentals) are evaluated by four different lanes.  FP64 is narrow on
-// this part, so the per-cell dependency chain, not the operation count, sets
-// the time.
-// Lane k's share of a cut cell's closed forms (corner values F, corners C):
-// tetrahedron k of the Kuhn split (k < 6; volume fraction / 6, interface area,
-// area-weighted centroid) and face k (k < 6; fraction of Omega-).
-template <typename T>
-__device__ inline void cell_pieces(int k, const T F[8], const T C[8][3], T& vneg, T& area, T wc[3],
-                                   T& Afk) {
-  if (k >= 6) return;
-  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  const int v1 = 1 << perm[k][0];
-  const int v2 = v1 | (1 << perm[k][1]);
+// over the lanes and combined with shuffles.  FP64 is narrow on this part, so
+// the per-cell dependency chain, not the operation count, sets the time.
+// Lane k's share of a cut cell's closed forms: tetrahedron k of the Kuhn
+// split (k < 6; volume fraction / 6, interface area, area-weighted centroid)
+// and face k (k < 6; fraction of Omega-).  Fk is the lane's own corner value
+// (corner k of the 8 lanes from `base`); the other corners' values come by
+// shuffles, corner(c, a) gives coordinate a of corner c.  Every lane of the
+// warp calls it (full-mask shuffles); lanes 6 and 7 return nothing.  No array
+// is indexed at run time, so nothing goes to local memory.
+template <typename T, typename Corner>
+__device__ inline void cell_pieces(int k, T Fk, int base, Corner corner, T& vneg, T& area,
+                                   T wc[3], T& Afk) {
+  const unsigned full = 0xffffffffu;
+  const int q = k < 6 ? k : 0;
+  // tetrahedron q: corners 0, v1, v2, 7 along the axis order (q/2, second, third)
+  const int second = (q == 0 || q == 5) ? 1 : (q == 1 || q == 3) ? 2 : 0;
+  const int v1 = 1 << (q >> 1), v2 = v1 | (1 << second);
   const int idx[4] = {0, v1, v2, 7};
   T Xt[4][3], ft[4];
+#pragma unroll
   for (int t = 0; t < 4; ++t) {
-    for (int a = 0; a < 3; ++a) Xt[t][a] = C[idx[t]][a];
-    ft[t] = F[idx[t]];
+    ft[t] = __shfl_sync(full, Fk, base + idx[t]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Xt[t][a] = corner(idx[t], a);
   }
+  // face q: axis q/2, side q%2, split along the diagonal c00 - c11
+  const int a = q >> 1, sd = q & 1, j = (a + 1) % 3, kx = (a + 2) % 3;
+  const int c00 = sd << a, c10 = c00 | (1 << j), c01 = c00 | (1 << kx), c11 = c10 | (1 << kx);
+  const T F00 = __shfl_sync(full, Fk, base + c00), F10 = __shfl_sync(full, Fk, base + c10);
+  const T F01 = __shfl_sync(full, Fk, base + c01), F11 = __shfl_sync(full, Fk, base + c11);
+  if (k >= 6) return;
   vneg = frac_tet<T>(ft) / T(6);
   area = tet_iface<T>(Xt, ft, wc);
-  const int a = k >> 1, sd = k & 1, j = (a + 1) % 3, kk = (a + 2) % 3;
-  const int b0 = sd << a;
-  const int c00 = b0, c10 = b0 | (1 << j), c01 = b0 | (1 << kk), c11 = c10 | (1 << kk);
-  Afk = T(0.5) * (frac_tri<T>(F[c00], F[c10], F[c11]) + frac_tri<T>(F[c00], F[c01], F[c11]));
+  Afk = T(0.5) * (frac_tri<T>(F00, F10, F11) + frac_tri<T>(F00, F01, F11));
 }
 
 // Cut cell `id` of the list (nc cells) on the 8 lanes of a warp's quarter; the
@@ -255,19 +263,16 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
   // Vm, S (area / h^2), the centroid cen and face fraction Afk of lane k.
   double vneg_d, S_d, Afk_d, cen[3] = {p[0], p[1], p[2]};
   bool has_area;
+  float f0f = 0.f, f1f = 0.f;  // FP32 rows: f- and f+ at p
   if (P.fp64) {
     // FP64 rows: FP64 corner values and closed forms on absolute coordinates
     double Ck[3];
     for (int a = 0; a < 3; ++a) Ck[a] = p[a] + h * ((double)((k >> a) & 1) - 0.5);
     const double Fk = phi_d(P, Ck[0], Ck[1], Ck[2]);
-    double F[8], C[8][3];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      F[c] = __shfl_sync(full, Fk, base + c);
-      for (int a = 0; a < 3; ++a) C[c][a] = p[a] + h * ((double)((c >> a) & 1) - 0.5);
-    }
     double vneg = 0.0, area = 0.0, wc[3] = {0.0, 0.0, 0.0}, Afk = 0.0;
-    cell_pieces<double>(k, F, C, vneg, area, wc, Afk);
+    cell_pieces<double>(
+        k, Fk, base, [&](int c, int a) { return p[a] + h * ((double)((c >> a) & 1) - 0.5); },
+        vneg, area, wc, Afk);
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
       vneg += __shfl_xor_sync(full, vneg, o);
@@ -287,6 +292,10 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
     // cut; the closed forms in FP32 on cell-local coordinates (corners at
     // exactly +-1/2, lengths in units of h), where nothing cancels
     const float pf[3] = {X[i], Y[i], Z[i]};
+    // f- and f+ at p on every lane (they depend on p only, so their chains
+    // overlap the corner values below)
+    f0f = rhs_f<float>(P, 0, pf[0], pf[1], pf[2]);
+    f1f = rhs_f<float>(P, 1, pf[0], pf[1], pf[2]);
     const float hh = 0.5f * P.hf;
     float Fk = phi_f(P, pf[0] + ((k & 1) ? hh : -hh), pf[1] + ((k & 2) ? hh : -hh),
                      pf[2] + ((k & 4) ? hh : -hh));
@@ -301,14 +310,10 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
       Fk = (float)fd;
       if (Fk == 0.f && fd > 0.0) Fk = __int_as_float(1);  // keep a positive sign
     }
-    float F[8], C[8][3];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      F[c] = __shfl_sync(full, Fk, base + c);
-      for (int a = 0; a < 3; ++a) C[c][a] = (float)((c >> a) & 1) - 0.5f;
-    }
     float vneg = 0.f, area = 0.f, wc[3] = {0.f, 0.f, 0.f}, Afk = 0.f;
-    cell_pieces<float>(k, F, C, vneg, area, wc, Afk);
+    cell_pieces<float>(
+        k, Fk, base, [](int c, int a) { return (float)((c >> a) & 1) - 0.5f; }, vneg, area, wc,
+        Afk);
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
       vneg += __shfl_xor_sync(full, vneg, o);
@@ -348,22 +353,33 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
       for (int a = 0; a < 3; ++a) xg[a] = xf[a];
     }
   }
-  // four point functions on four lanes (FP64 for the FP64 rows, else FP32)
-  double val = 0.0;
+  // beta, alpha (at x_G), f- and f+ (at p)
+  double beta, alpha, f0, f1;
   if (P.fp64) {
+    // FP64: four functions on four lanes
+    double val = 0.0;
     if (k == 0 && has_area) val = beta_d(P, xg);
     else if (k == 1 && has_area) val = alpha_d(P, xg);
     else if (k == 2) val = rhs_f<double>(P, 0, p[0], p[1], p[2]);
     else if (k == 3) val = rhs_f<double>(P, 1, p[0], p[1], p[2]);
+    beta = __shfl_sync(full, val, base + 0);
+    alpha = __shfl_sync(full, val, base + 1);
+    f0 = __shfl_sync(full, val, base + 2);
+    f1 = __shfl_sync(full, val, base + 3);
   } else {
+    // FP32: beta and alpha on every lane, without branches on the lane, so
+    // that their independent chains overlap
     const float xf[3] = {(float)xg[0], (float)xg[1], (float)xg[2]};
-    if (k == 0 && has_area) val = beta_f(P, xf);
-    else if (k == 1 && has_area) val = alpha_f(P, xf);
-    else if (k == 2) val = rhs_f<float>(P, 0, (float)p[0], (float)p[1], (float)p[2]);
-    else if (k == 3) val = rhs_f<float>(P, 1, (float)p[0], (float)p[1], (float)p[2]);
+    float bt = 0.f, al = 0.f;
+    if (has_area) {
+      bt = beta_f(P, xf);
+      al = alpha_f(P, xf);
+    }
+    beta = bt;
+    alpha = al;
+    f0 = f0f;
+    f1 = f1f;
   }
-  const double beta = __shfl_sync(full, val, base + 0), alpha = __shfl_sync(full, val, base + 1);
-  const double f0 = __shfl_sync(full, val, base + 2), f1 = __shfl_sync(full, val, base + 3);
   if (!live) return;
   CutRec* r = cut + id;
   if (k < 6) r->Am[k] = Afk_d;
@@ -403,90 +419,195 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* X,
 //   D = sum_s sum_f A^s_f mu^s + h^2 sum_s V^s k^s,   J = U+(xg) - U-(xg) - alpha,
 //   r^2 = (B/D)^2 + lambda J^2;   seeds = d(scale r^2)/d(outputs).
 // ------------------------------------------------------------------------
-// One warp per block: the cut list (a few thousand cells) spreads over many SMs,
-// each cell's FP64 row on one thread, since GB300's FP64 pipe is narrow.
-// (Rows in FP32 were tried: the cancellation in B made the seeds, and so the
-// gradient, depend at 1e-5 on how a batch is split into shards.)
-__global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* X,
-                                                      const float* Y,
-                                                      const float* Z,
-                                                      const int* counters,
-                                                      const CutRec* cut,
-                                                      const float* out,
+// One warp per block.  The row is FP64 (its balance B cancels), and GB300's
+// FP64 pipe is narrow.  When the cut list fits in one pass of 4 cells per
+// warp (a few thousand cells), each cell takes 8 lanes: lane f < 6 face f of
+// both phases, lane 6 the volume terms, the row's sums added by shuffles,
+// which cuts each cell's dependency chain to about a sixth.  A longer list is
+// bound by the FP64 pipe instead, and takes one cell per thread
+// (cut_row_one), so that every lane of each FP64 instruction is busy.  (Rows in
+// FP32 were tried: the cancellation in B made the seeds, and so the gradient,
+// depend at 1e-5 on how a batch is split into shards.)
+// The same row on one thread (cut cell `id`): with many cut cells per warp
+// the FP64 pipe, not the chain, is the bound, and one cell per lane keeps
+// every lane of each FP64 instruction busy.  Returns r^2.
+__device__ inline double cut_row_one(const ProbDev& P, const float* X, const float* Y,
+                                     const float* Z, const CutRec* c, const float* o,
+                                     float* sd, float scale, float* r2_out) {
+  const int i = c->point;
+  const double h = P.h, h2 = h * h;
+  const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
+  double B = 0.0, D = 0.0, dU[2], dM[2][3], dD[2][3];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double V = s ? 1.0 - c->Vm : c->Vm;
+    const double k = P.k[s];
+    const double U = (double)o[8 * s];
+    B += h2 * V * (k * U - c->f[s]);
+    D += h2 * V * k;
+    dU[s] = h2 * V * k;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dM[s][a] = dD[s][a] = 0.0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int a = f >> 1;
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      double q[3] = {p[0], p[1], p[2]}, fc[3] = {p[0], p[1], p[2]};
+      q[a] += sg * h;
+      fc[a] += 0.5 * sg * h;
+      const double A = s ? 1.0 - c->Am[f] : c->Am[f];
+      const double w = A * mu_at<double>(P, s, fc[0], fc[1], fc[2]);
+      D += w;
+      if (fabs(q[a]) >= 1.0) {
+        B -= w * (dirichlet_g<double>(P, q[0], q[1], q[2]) - U);
+        dU[s] += w;
+      } else {
+        B -= w * (h2 * (double)o[8 * s + 1 + a] + sg * h * (double)o[8 * s + 4 + a]);
+        dM[s][a] -= w * h2;
+        dD[s][a] -= w * sg * h;
+      }
+    }
+  }
+  const bool jump = c->has_jump;
+  if (jump) B += h * c->S * c->beta;
+  const double J = jump ? (double)o[15] - (double)o[7] - c->alpha : 0.0;
+  const double rB = B / D;
+  const double r2 = rB * rB + P.lambda * J * J;
+  if (sd) {
+    const double cB = (double)scale * 2.0 * rB / D;
+    const double cJ = (double)scale * 2.0 * P.lambda * J;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      sd[8 * s] = (float)(cB * dU[s]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sd[8 * s + 1 + a] = (float)(cB * dM[s][a]);
+        sd[8 * s + 4 + a] = (float)(cB * dD[s][a]);
+      }
+      sd[8 * s + 7] = jump ? (float)(s ? cJ : -cJ) : 0.f;
+    }
+  }
+  if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
+  return r2;
+}
+
+__global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* X, const float* Y,
+                                                      const float* Z, const int* counters,
+                                                      const CutRec* cut, const float* out,
                                                       float* seeds, float scale, float* r2_out,
                                                       double* loss_part) {
   pdl_enter();
-  using T = double;
+  const unsigned full = 0xffffffffu;
   const int nc = counters[2];
-  double r2_sum = 0.0;  // this thread's cells (grid-stride), then the block partial
-  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nc; id += gridDim.x * blockDim.x) {
-    const CutRec c = cut[id];
-    const int i = c.point;
-    const T h = pc_h<T>(P), h2 = h * h;
-    const T p[3] = {(T)X[i], (T)Y[i], (T)Z[i]};
-    const float* o = out + (int64_t)id * 16;
-    T B = 0, D = 0;
-    T dU[2], dM[2][3], dD[2][3];
-    bool bnd[6];
-    T g[6];
-    for (int f = 0; f < 6; ++f) {
-      int a = f >> 1;
-      T q[3] = {p[0], p[1], p[2]};
-      q[a] += (f & 1) ? h : -h;
-      bnd[f] = fabs(q[a]) >= (T)1;
-      g[f] = bnd[f] ? dirichlet_g<T>(P, q[0], q[1], q[2]) : (T)0;
-    }
-    for (int s = 0; s < 2; ++s) {
-      const T V = (T)(s ? 1.0 - c.Vm : c.Vm);
-      const T k = pc_k<T>(P, s);
-      const T U = (T)o[8 * s];
-      B += h2 * V * (k * U - (T)c.f[s]);
-      D += h2 * V * k;
-      dU[s] = h2 * V * k;
-      for (int a = 0; a < 3; ++a) dM[s][a] = dD[s][a] = 0;
-      for (int f = 0; f < 6; ++f) {
-        const int a = f >> 1;
-        const T sg = (f & 1) ? (T)1 : (T)-1;
-        const T A = (T)(s ? 1.0 - c.Am[f] : c.Am[f]);
-        // mu^s at the face centre (constant for the benchmark pair)
-        T fc[3] = {p[0], p[1], p[2]};
-        fc[a] += (T)0.5 * sg * h;
-        const T w = A * mu_at<T>(P, s, fc[0], fc[1], fc[2]);
-        D += w;
-        if (bnd[f]) {
-          // U^s(p) enters the row directly only through Dirichlet faces: the
-          // interior faces carry it inside the increments Mt, Dt
-          B -= w * (g[f] - U);
-          dU[s] += w;
+  const int l = threadIdx.x & 7, sub = threadIdx.x >> 3;
+  const double h = P.h, h2 = h * h;
+  double r2_sum = 0.0;  // this lane's cells' r^2, then the block partial
+  if (nc > 4 * (int)gridDim.x) {
+    // more cells than one pass of 4 per warp: one cell per thread
+    for (int id = blockIdx.x * 32 + threadIdx.x; id < nc; id += gridDim.x * 32)
+      r2_sum += cut_row_one(P, X, Y, Z, cut + id, out + (int64_t)id * 16,
+                            seeds ? seeds + (int64_t)id * 16 : nullptr, scale, r2_out);
+  } else {
+    // 4 cells per warp, 8 lanes per cell
+    for (int first = blockIdx.x * 4; first < nc; first += gridDim.x * 4) {  // warp-uniform
+      const int id = first + sub;
+      const bool live = id < nc;
+      const CutRec* c = cut + (live ? id : first);  // fields read where needed (no local copy)
+      const int i = c->point;
+      const double p[3] = {(double)X[i], (double)Y[i], (double)Z[i]};
+      const float* o = out + (int64_t)(live ? id : first) * 16;
+      // this lane's share of B, D, dU^s and (faces) dM^s, dD^s of its axis
+      double B = 0.0, D = 0.0, dU0 = 0.0, dU1 = 0.0, dm0 = 0.0, dm1 = 0.0, dd0 = 0.0, dd1 = 0.0;
+      if (l < 6) {
+        const int ax = l >> 1;
+        const double sg = (l & 1) ? 1.0 : -1.0;
+        // neighbour q and face centre fc (selects: the arrays stay in registers)
+        const double dq = sg * h, df = 0.5 * sg * h;
+        const double q0 = ax == 0 ? p[0] + dq : p[0], q1 = ax == 1 ? p[1] + dq : p[1],
+                     q2 = ax == 2 ? p[2] + dq : p[2];
+        const double f0 = ax == 0 ? p[0] + df : p[0], f1 = ax == 1 ? p[1] + df : p[1],
+                     f2 = ax == 2 ? p[2] + df : p[2];
+        const bool bnd = fabs(ax == 0 ? q0 : ax == 1 ? q1 : q2) >= 1.0;
+        const double g = bnd ? dirichlet_g<double>(P, q0, q1, q2) : 0.0;
+        const double Aml = c->Am[l];
+  #pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const double A = s ? 1.0 - Aml : Aml;
+          // mu^s at the face centre (constant for the benchmark pair)
+          const double w = A * mu_at<double>(P, s, f0, f1, f2);
+          const double U = (double)o[8 * s];
+          D += w;
+          double du = 0.0, dm = 0.0, dd = 0.0;
+          if (bnd) {
+            // U^s(p) enters the row directly only through Dirichlet faces: the
+            // interior faces carry it inside the increments Mt, Dt
+            B -= w * (g - U);
+            du = w;
+          } else {
+            B -= w * (h2 * (double)o[8 * s + 1 + ax] + sg * h * (double)o[8 * s + 4 + ax]);
+            dm = -w * h2;
+            dd = -w * sg * h;
+          }
+          if (s == 0) { dU0 = du; dm0 = dm; dd0 = dd; }
+          else { dU1 = du; dm1 = dm; dd1 = dd; }
+        }
+      } else if (l == 6) {
+  #pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const double V = s ? 1.0 - c->Vm : c->Vm;
+          const double k = P.k[s];
+          const double U = (double)o[8 * s];
+          B += h2 * V * (k * U - c->f[s]);
+          D += h2 * V * k;
+          if (s == 0) dU0 = h2 * V * k;
+          else dU1 = h2 * V * k;
+        }
+        if (c->has_jump) B += h * c->S * c->beta;
+      }
+      // the two faces of an axis: lanes 2a, 2a + 1
+      dm0 += __shfl_xor_sync(full, dm0, 1, 8);
+      dm1 += __shfl_xor_sync(full, dm1, 1, 8);
+      dd0 += __shfl_xor_sync(full, dd0, 1, 8);
+      dd1 += __shfl_xor_sync(full, dd1, 1, 8);
+  #pragma unroll
+      for (int m = 1; m < 8; m <<= 1) {
+        B += __shfl_xor_sync(full, B, m, 8);
+        D += __shfl_xor_sync(full, D, m, 8);
+        dU0 += __shfl_xor_sync(full, dU0, m, 8);
+        dU1 += __shfl_xor_sync(full, dU1, m, 8);
+      }
+      const bool jump = c->has_jump;
+      const double J = jump ? (double)o[15] - (double)o[7] - c->alpha : 0.0;
+      const double rB = B / D;
+      const double r2 = rB * rB + P.lambda * J * J;
+      // seed column l of both networks: 0 dU, 1..3 dM of axis l-1, 4..6 dD of
+      // axis l-4 (held by lane 2 axis), 7 the jump
+      const int src = (l >= 1 && l <= 3) ? 2 * (l - 1) : (l >= 4 && l <= 6) ? 2 * (l - 4) : 0;
+      const double m0 = __shfl_sync(full, dm0, src, 8), m1 = __shfl_sync(full, dm1, src, 8);
+      const double e0 = __shfl_sync(full, dd0, src, 8), e1 = __shfl_sync(full, dd1, src, 8);
+      if (!live) continue;
+      if (seeds) {
+        const double cB = (double)scale * 2.0 * rB / D;
+        const double cJ = (double)scale * 2.0 * P.lambda * J;
+        float* sd = seeds + (int64_t)id * 16;
+        if (l == 7) {
+          sd[7] = jump ? (float)(-cJ) : 0.f;
+          sd[15] = jump ? (float)cJ : 0.f;
         } else {
-          B -= w * (h2 * (T)o[8 * s + 1 + a] + sg * h * (T)o[8 * s + 4 + a]);
-          dM[s][a] -= w * h2;
-          dD[s][a] -= w * sg * h;
+          const double v0 = l == 0 ? dU0 : l <= 3 ? m0 : e0;
+          const double v1 = l == 0 ? dU1 : l <= 3 ? m1 : e1;
+          sd[l] = (float)(cB * v0);
+          sd[8 + l] = (float)(cB * v1);
         }
       }
-    }
-    if (c.has_jump) B += h * (T)c.S * (T)c.beta;
-    const T J = c.has_jump ? (T)o[15] - (T)o[7] - (T)c.alpha : (T)0;
-    const T rB = B / D, lam = (T)P.lambda;
-    const T r2 = rB * rB + lam * J * J;
-    if (seeds) {
-      const T cB = (T)scale * (T)2 * rB / D;
-      const T cJ = (T)scale * (T)2 * lam * J;
-      float* sd = seeds + (int64_t)id * 16;
-      for (int s = 0; s < 2; ++s) {
-        sd[8 * s] = (float)(cB * dU[s]);
-        for (int a = 0; a < 3; ++a) {
-          sd[8 * s + 1 + a] = (float)(cB * dM[s][a]);
-          sd[8 * s + 4 + a] = (float)(cB * dD[s][a]);
-        }
-        sd[8 * s + 7] = c.has_jump ? (float)(s ? cJ : -cJ) : 0.f;
+      if (l == 0) {
+        if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
+        r2_sum += r2;
       }
     }
-    if (r2_out) r2_out[i] = (P.level ? r2_out[i] : 0.f) + (float)r2;
-    r2_sum += (double)r2;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r2_sum += __shfl_xor_sync(0xffffffffu, r2_sum, o);
+  for (int m = 16; m > 0; m >>= 1) r2_sum += __shfl_xor_sync(full, r2_sum, m);
   if (threadIdx.x == 0) loss_part[blockIdx.x] = r2_sum;
 }
 
