@@ -49,13 +49,15 @@ FUSED_TRAFFIC = {"bytes": 8_925_184, "sources_sha16": "6eb59211d6268980"}
 FUSED_SOURCES = ("paper_2210_14907_gb300/csrc/nbm_tc.cu", "paper_2210_14907_gb300/csrc/nbm_tc_ptx.cuh",
                  "paper_2210_14907_gb300/csrc/nbm_device.cuh")
 # libnbm kernel launches per timed step.  One nbm_train_steps call of one C2
-# step: k_prep_weights; k_sample_classify, k_scan_counts, k_scatter;
-# k_cut_geometry, k_gather_tiles; k_step_tc (cut-cell forward),
-# k_cut_residual; k_step_tc (fused train step); k_loss, k_reduce_adam.  The
-# data-parallel step (N > 1) runs the same chain through nbm_loss_grad_shard
-# (k_reduce_adam writes the gradient only) and then k_adam: one more.
-LAUNCHES_PER_STEP = 11
-LAUNCHES_PER_DP_STEP = 12
+# step: k_sample_classify (its extra blocks restage the weights), k_scatter
+# (up to 2048 blocks of points it also does the block-count scan, so no
+# k_scan_counts); k_cut_geometry, k_gather_tiles; k_step_tc (cut-cell
+# forward), k_cut_residual; k_step_tc (fused train step); k_loss,
+# k_reduce_adam.  The data-parallel step (N > 1) runs the same chain through
+# nbm_loss_grad_shard (k_reduce_adam writes the gradient only) and then
+# k_adam: one more.
+LAUNCHES_PER_STEP = 9
+LAUNCHES_PER_DP_STEP = 10
 # FP32 FFMA peak of the plain path's roofline: 152 SMs x 128 FP32 lanes x
 # 2 FLOP per FMA x the SM clock (GB300's 2070 MHz maximum, the clock the
 # timed region ran at).

@@ -261,12 +261,14 @@ static cudaError_t launch_timed(Problem& pb, const ProbDev& P, const StepArgs& a
 static int front_stages(Problem& pb, const ProbDev& P, const float* params, const float* pts,
                         int64_t n, uint64_t seed, const int64_t* step_dev, int64_t step_host,
                         bool want_seeds, float* r2_out, cudaStream_t st, int64_t first = 0,
-                        int64_t n_total = 0) {
+                        int64_t n_total = 0, bool prep_w = false) {
   Workspace& w = pb.ws;
   NvtxRange r("nbm.front (sample, cell geometry, cut rows)");
   const int64_t nt = n_total > 0 ? n_total : n;
+  // prep_w: the same launch restages the hidden weights from params (the
+  // first pass of a call; later steps get them from the Adam kernel)
   NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, nt), w,
-                                  st, first, nt));
+                                  st, first, nt, prep_w ? params : nullptr, pb.desc.precision));
   NBM_CUDA(launch_cut_geometry(P, n, w, st));
   if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(P, n, w, st));
   StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)nt);
@@ -461,15 +463,11 @@ int nbm_residual(nbm_problem* p, const float* params, const float* pts, int64_t 
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
-  ProbDev P0;
-  make_prob_dev(pb.desc, P0, 0);
-  if ((rc = attach_level_set(p, P0))) return rc;
-  NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
   for (int lv = 0; lv < nlev; ++lv) {  // refinement levels: the same points, spacing h/2^lv
     ProbDev P;
     make_prob_dev(pb.desc, P, lv);
     if ((rc = attach_level_set(p, P))) return rc;
-    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, false, r2_out, st);
+    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, false, r2_out, st, 0, 0, lv == 0);
     if (rc) return rc;
     StepArgs a = base_args(pb, params, MODE_RESIDUAL, 1.0f / (float)n);
     a.r2_out = r2_out;
@@ -494,15 +492,11 @@ int nbm_loss_grad(nbm_problem* p, const float* params, const float* pts, int64_t
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
-  ProbDev P0;
-  make_prob_dev(pb.desc, P0, 0);
-  if ((rc = attach_level_set(p, P0))) return rc;
-  NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
   for (int lv = 0; lv < nlev; ++lv) {
     ProbDev P;
     make_prob_dev(pb.desc, P, lv);
     if ((rc = attach_level_set(p, P))) return rc;
-    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st);
+    rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st, 0, 0, lv == 0);
     if (rc) return rc;
     StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)n);
     NBM_CUDA(launch_timed(pb, P, a, st));
@@ -533,16 +527,12 @@ int nbm_loss_grad_shard(nbm_problem* p, const float* params, const float* pts, i
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = pb.desc.precision, nlev = 1 + pb.desc.refine_levels;
   const double inv_total = 1.0 / (double)n_total;
-  ProbDev P0;
-  make_prob_dev(pb.desc, P0, 0);
-  if ((rc = attach_level_set(p, P0))) return rc;
-  NBM_CUDA(launch_prep_weights(P0, params, prec, pb.ws, st));
   for (int lv = 0; lv < nlev; ++lv) {
     ProbDev P;
     make_prob_dev(pb.desc, P, lv);
     if ((rc = attach_level_set(p, P))) return rc;
     rc = front_stages(pb, P, params, pts, n, seed, nullptr, step, true, nullptr, st, first,
-                      n_total);
+                      n_total, lv == 0);
     if (rc) return rc;
     StepArgs a = base_args(pb, params, MODE_TRAIN, (float)inv_total);
     NBM_CUDA(launch_timed(pb, P, a, st));
@@ -604,7 +594,6 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
     if ((rc = attach_level_set(p, PL[lv]))) return rc;
   }
   NBM_CUDA(cudaMemcpyAsync(pb.ws.step, step_io, sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  NBM_CUDA(launch_prep_weights(PL[0], params, prec, pb.ws, st));
   for (int k = 0; k < n_steps; ++k) {
     const float* pk = pts ? pts + (int64_t)k * batch * 3 : nullptr;
     NvtxRange step_range("nbm.train_step");
@@ -612,7 +601,8 @@ int nbm_train_steps(nbm_problem* p, float* params, float* adam_m, float* adam_v,
     // after the last level), spacing h/2^lv; one Adam update per step
     for (int lv = 0; lv < nlev; ++lv) {
       const ProbDev& P = PL[lv];
-      rc = front_stages(pb, P, params, pk, batch, seed, pb.ws.step, 0, true, nullptr, st);
+      rc = front_stages(pb, P, params, pk, batch, seed, pb.ws.step, 0, true, nullptr, st, 0, 0,
+                        k == 0 && lv == 0);
       if (rc) return rc;
       StepArgs a = base_args(pb, params, MODE_TRAIN, 1.0f / (float)batch);
       NBM_CUDA(launch_timed(pb, P, a, st));

@@ -156,7 +156,8 @@ int check_aligned(const void* ptr, size_t align, const char* name);
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st,
-                                   int64_t first = 0, int64_t n_total = 0);
+                                   int64_t first = 0, int64_t n_total = 0,
+                                   const float* prep_params = nullptr, int prec = 0);
 cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,

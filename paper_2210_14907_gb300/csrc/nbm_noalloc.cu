@@ -153,12 +153,13 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = d.precision;
   cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), st);  // must start at zero
-  if (e == cudaSuccess) e = launch_prep_weights(P, params, prec, w, st);
   const int64_t n_band =
       (d.geometry == NBM_GEOM_SPHERE || d.geometry == NBM_GEOM_FLOWER)
           ? (int64_t)floor(d.band_fraction * (double)n + 0.5)
           : 0;
-  if (e == cudaSuccess) e = launch_sample_classify(P, pts, seed, nullptr, step, n, n_band, w, st);
+  // the sampling launch also restages the hidden weights from params
+  if (e == cudaSuccess)
+    e = launch_sample_classify(P, pts, seed, nullptr, step, n, n_band, w, st, 0, 0, params, prec);
   if (e == cudaSuccess) e = launch_cut_geometry(P, n, w, st);
   if (e == cudaSuccess && prec != NBM_PREC_FP32) e = launch_gather_tiles(P, n, w, st);
   StepArgs a;

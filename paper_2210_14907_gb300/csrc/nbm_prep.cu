@@ -91,13 +91,56 @@ __device__ inline int count_neg_corners(const ProbDev& P, const float p[3]) {
   return nneg;
 }
 
+// ------------------------------------------------------------------------
+// Weight staging.  Hidden layer l of net s (W[u][k], u = output unit):
+//   wt  : FP32 transpose, wt[((s*(L-1) + l-1)*H + k)*H + u] = W[u][k]
+//   wtc : 16-bit copy in the tensor-core shared-memory image (H = 128):
+//         8-row x 128-byte atoms with the 128-byte XOR swizzle,
+//         atom (cb, ug) at (cb*16 + ug)*1024 for column block cb = k/64 and
+//         row group ug = u/8.
+// ------------------------------------------------------------------------
+__host__ __device__ inline uint32_t tc_tile_offset(int u, int c) { return tc::img_off(u, c); }
+
+// Hidden weights of both networks restaged from the parameter vector: the
+// FP32 transposed copy wt [net][layer][k][u] and, for the tensor-core path,
+// the 16-bit image in the tcgen05 tile layout.  Element e of block (net,
+// layer) in (u, k) order; blocks b of nblk share the elements.
+__device__ inline void prep_weights_blocks(const ProbDev& P, const float* params, float* wt,
+                                           void* wtc, int prec, int b, int nblk) {
+  const int H = P.H, L = P.L, per = H * H;
+  const int total = 2 * (L - 1) * per;
+  for (int e = b * blockDim.x + threadIdx.x; e < total; e += nblk * blockDim.x) {
+    const int blk = e / per, s = blk / (L - 1), l = blk - s * (L - 1) + 1;
+    const int rem = e - blk * per, u = rem / H, k = rem - u * H;
+    const float w = params[(int64_t)s * P.p_net + 4 * H + (int64_t)(l - 1) * (per + H) + rem];
+    if (wt) wt[(int64_t)blk * per + (int64_t)k * H + u] = w;
+    if (wtc && H == 128) {
+      char* base = (char*)wtc + (int64_t)blk * per * 2;
+      if (prec == NBM_PREC_FP16)
+        *(__half*)(base + tc_tile_offset(u, k)) = __float2half_rn(w);
+      else
+        *(__nv_bfloat16*)(base + tc_tile_offset(u, k)) = __float2bfloat16_rn(w);
+    }
+  }
+}
+
+// blocks of a weight restage
+static int prep_weight_blocks(const ProbDev& P) { return 2 * (P.L - 1) * 16; }
+
 __global__ void __launch_bounds__(kBlk) k_sample_classify(ProbDev P, const float* pts_in,
                                                           uint64_t seed, const int64_t* step_dev,
                                                           int64_t step_host, int64_t n,
                                                           int64_t n_band, float* X, float* Y,
                                                           float* Z, uint8_t* cls, int* blockcnt,
-                                                          int nb, int64_t first, int64_t n_total) {
+                                                          int nb, int64_t first, int64_t n_total,
+                                                          const float* prep_params, float* wt,
+                                                          void* wtc, int prec) {
   pdl_enter();
+  if ((int)blockIdx.x >= nb) {
+    // the blocks past the points restage the hidden weights (first step of a call)
+    prep_weights_blocks(P, prep_params, wt, wtc, prec, blockIdx.x - nb, gridDim.x - nb);
+    return;
+  }
   int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
   int c = -1;
   if (i < n) {
@@ -173,12 +216,37 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int* blockcnt, int nb, int
 }
 
 // Stable scatter: list order = point order.  Entry >= 0: uncut point index;
-// entry < 0: cut cell -(cut_id + 1).
+// entry < 0: cut cell -(cut_id + 1).  scanned: blockcnt holds the exclusive
+// offsets (k_scan_counts ran).  Otherwise (few blocks: the scan's launch
+// costs more than the sums) each block adds up the per-block counts of the
+// blocks before it (integer sums: exact in any order) for its offsets in the
+// three lists, and the last block writes the totals counters[0..2].
 __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
-                                                  const int* blockoff, int nb,
-                                                  int* list_m, int* list_p, int* cut_pt) {
+                                                  const int* blockcnt, int nb, int scanned,
+                                                  int* list_m, int* list_p, int* cut_pt,
+                                                  int* counters) {
   pdl_enter();
+  __shared__ int boff[3][kBlk / 32];
   __shared__ int wsum[3][kBlk / 32];
+  if (!scanned) {
+    int s0 = 0, s1 = 0, s2 = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += kBlk) {
+      s0 += blockcnt[j];
+      s1 += blockcnt[nb + j];
+      s2 += blockcnt[2 * nb + j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      boff[0][threadIdx.x >> 5] = s0;
+      boff[1][threadIdx.x >> 5] = s1;
+      boff[2][threadIdx.x >> 5] = s2;
+    }
+  }
   int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
   int c = i < n ? (int)cls[i] : -1;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -195,7 +263,14 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
   int pos[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    int off = blockoff[(int64_t)m * nb + blockIdx.x];
+    int off = 0;
+    if (scanned) {
+      off = blockcnt[(int64_t)m * nb + blockIdx.x];
+    } else {
+      for (int k = 0; k < kBlk / 32; ++k) off += boff[m][k];
+      if (blockIdx.x == nb - 1 && threadIdx.x == 0)
+        counters[m] = off + blockcnt[(int64_t)m * nb + blockIdx.x];
+    }
     for (int k = 0; k < w; ++k) off += wsum[m][k];
     pos[m] = off + rank[m];
   }
@@ -683,38 +758,12 @@ __global__ void __launch_bounds__(256) k_gather_tiles(const ProbDev P,
   }
 }
 
-// ------------------------------------------------------------------------
-// Weight staging.  Hidden layer l of net s (W[u][k], u = output unit):
-//   wt  : FP32 transpose, wt[((s*(L-1) + l-1)*H + k)*H + u] = W[u][k]
-//   wtc : 16-bit copy in the tensor-core shared-memory image (H = 128):
-//         8-row x 128-byte atoms with the 128-byte XOR swizzle,
-//         atom (cb, ug) at (cb*16 + ug)*1024 for column block cb = k/64 and
-//         row group ug = u/8.
-// ------------------------------------------------------------------------
-__host__ __device__ inline uint32_t tc_tile_offset(int u, int c) { return tc::img_off(u, c); }
-
+// Standalone restage (grid evaluation); the training paths restage inside
+// their sampling launch (k_sample_classify's extra blocks).
 __global__ void k_prep_weights(ProbDev P, const float* params, float* wt, void* wtc,
                                int prec) {
   pdl_enter();
-  const int H = P.H, L = P.L;
-  const int64_t per = (int64_t)H * H;
-  const int64_t total = 2 * (int64_t)(L - 1) * per;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t blk = e / per;
-    int s = (int)(blk / (L - 1)), l = (int)(blk % (L - 1)) + 1;
-    int rem = (int)(e % per);
-    int u = rem / H, k = rem % H;
-    const float w = params[(int64_t)s * P.p_net + 4 * H + (int64_t)(l - 1) * (per + H) + rem];
-    if (wt) wt[blk * per + (int64_t)k * H + u] = w;
-    if (wtc && H == 128) {
-      char* base = (char*)wtc + blk * per * 2;
-      if (prec == NBM_PREC_FP16)
-        *(__half*)(base + tc_tile_offset(u, k)) = __float2half_rn(w);
-      else
-        *(__nv_bfloat16*)(base + tc_tile_offset(u, k)) = __float2bfloat16_rn(w);
-    }
-  }
+  prep_weights_blocks(P, params, wt, wtc, prec, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------------
@@ -881,16 +930,23 @@ cudaError_t launch_adam(int64_t n, float* params, float* m, float* v, const floa
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st,
-                                   int64_t first, int64_t n_total) {
+                                   int64_t first, int64_t n_total, const float* prep_params,
+                                   int prec) {
   int nb = (int)((n + kBlk - 1) / kBlk);
-  cudaError_t e = launch_pdl(k_sample_classify, dim3(nb), dim3(kBlk), 0, st, P, pts_in, seed,
-                             step_dev, step_host, n, n_band, ws.x, ws.y, ws.z, ws.cls,
-                             ws.blockcnt, nb, first, n_total > 0 ? n_total : n);
-  if (e == cudaSuccess)
+  const int npb = prep_params ? prep_weight_blocks(P) : 0;
+  cudaError_t e = launch_pdl(k_sample_classify, dim3(nb + npb), dim3(kBlk), 0, st, P, pts_in,
+                             seed, step_dev, step_host, n, n_band, ws.x, ws.y, ws.z, ws.cls,
+                             ws.blockcnt, nb, first, n_total > 0 ? n_total : n, prep_params,
+                             ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
+  // up to 2048 blocks the scatter blocks sum the earlier blocks' counts
+  // themselves (at most 6 K integers each); beyond, one scan kernel
+  const int scanned = nb > 2048;
+  if (e == cudaSuccess && scanned)
     e = launch_pdl(k_scan_counts, dim3(1), dim3(1024), 0, st, ws.blockcnt, nb, ws.counters);
   if (e == cudaSuccess)
     e = launch_pdl(k_scatter, dim3(nb), dim3(kBlk), 0, st, (const uint8_t*)ws.cls, n,
-                   (const int*)ws.blockcnt, nb, ws.list_minus, ws.list_plus, ws.cut_pt);
+                   (const int*)ws.blockcnt, nb, scanned, ws.list_minus, ws.list_plus,
+                   ws.cut_pt, ws.counters);
   return e;
 }
 
@@ -928,7 +984,7 @@ cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cuda
 
 cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,
                                 cudaStream_t st) {
-  return launch_pdl(k_prep_weights, dim3(2 * (P.L - 1) * 16), dim3(256), 0, st, P, params, ws.wt,
+  return launch_pdl(k_prep_weights, dim3(prep_weight_blocks(P)), dim3(256), 0, st, P, params, ws.wt,
                     (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
 }
 
