@@ -58,6 +58,10 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P, int level) {
   P.amp = d.amp;
   P.lt = d.lobes_theta;
   P.lp = d.lobes_psi;
+  // integer lobe counts: the level set's angular factors by Chebyshev recurrences
+  auto as_int = [](double v) { return (v >= 0.0 && v <= 64.0 && v == floor(v)) ? (int)v : -1; };
+  P.lt_i = as_int(d.lobes_theta);
+  P.lp_i = as_int(d.lobes_psi);
   P.mu[0] = d.mu_minus;
   P.mu[1] = d.mu_plus;
   P.k[0] = d.k_minus;

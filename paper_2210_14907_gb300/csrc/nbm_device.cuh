@@ -45,6 +45,7 @@ struct ProbDev {
   float muf[2], kf[2];
   double inv_h, inv_h2, inv_D[2];  // 1/h, 1/h^2, 1/(6 mu_s + h^2 k_s) of the uncut rows
   float inv_Df[2];
+  int lt_i, lp_i;  // flower lobe counts when integers (else -1): Chebyshev evaluation
   int64_t p_net;  // parameters per network
   int64_t gstride;  // per-CTA partial-gradient slice stride (p_net rounded up to 4)
 };
@@ -121,49 +122,103 @@ __device__ inline T grid_phi(const ProbDev& P, T x, T y, T z, T* g) {
   return c0 * ((T)1 - f[2]) + c1 * f[2];
 }
 
+// Chebyshev recurrences: cos(n a) = T_n(c), sin(n a) = sin(a) U_{n-1}(c) for
+// c = cos(a).  Returns T_n(c) and U_{n-1}(c) (n >= 0; U_{-1} = 0).
+template <typename T>
+__device__ inline void chebyshev_tu(int n, T c, T& Tn, T& Un1) {
+  T t0 = T(1), t1 = c, u0 = T(0), u1 = T(1);
+  for (int k = 1; k < n; ++k) {
+    const T t2 = T(2) * c * t1 - t0, u2 = T(2) * c * u1 - u0;
+    t0 = t1;
+    t1 = t2;
+    u0 = u1;
+    u1 = u2;
+  }
+  Tn = n == 0 ? T(1) : t1;
+  Un1 = n == 0 ? T(0) : u1;
+}
+
+// The flower's angular factors from cos/sin of the polar angle theta and the
+// azimuth psi: sin(lt theta), cos(lt theta), cos(lp psi), sin(lp psi).  Integer
+// lobe counts (the configurations here) take the Chebyshev recurrences and no
+// transcendental function; other counts go through the angles.
+template <typename T>
+__device__ inline void flower_factors(const ProbDev& P, T cth, T sth, T cps, T sps, T& st, T& ct,
+                                      T& cp, T& sp) {
+  if (P.lt_i >= 0) {
+    T Tn, Un;
+    chebyshev_tu<T>(P.lt_i, cth, Tn, Un);
+    ct = Tn;
+    st = sth * Un;
+  } else {
+    const T a = (sizeof(T) == 4 ? (T)P.ltf : (T)P.lt) * atan2(sth, cth);
+    st = sin(a);
+    ct = cos(a);
+  }
+  if (P.lp_i >= 0) {
+    T Tn, Un;
+    chebyshev_tu<T>(P.lp_i, cps, Tn, Un);
+    cp = Tn;
+    sp = sps * Un;
+  } else {
+    const T a = (sizeof(T) == 4 ? (T)P.lpf : (T)P.lp) * atan2(sps, cps);
+    sp = sin(a);
+    cp = cos(a);
+  }
+}
+
+// phi = r - r0 - amp sin(lt theta) cos(lp psi) (flower), r - r0 (sphere)
+template <typename T>
+__device__ inline T phi_t(const ProbDev& P, T x, T y, T z) {
+  if (P.geometry == NBM_GEOM_GRID) return grid_phi<T>(P, x, y, z, nullptr);
+  if (P.geometry == NBM_GEOM_ALL_PLUS) return T(1);
+  if (P.geometry == NBM_GEOM_ALL_MINUS) return T(-1);
+  const T r0 = sizeof(T) == 4 ? (T)P.r0f : (T)P.r0, amp = sizeof(T) == 4 ? (T)P.ampf : (T)P.amp;
+  const T rho2 = x * x + y * y;
+  const T r = sqrt(rho2 + z * z);
+  if (P.geometry == NBM_GEOM_SPHERE) return r - r0;
+  if (r == T(0)) return -r0;
+  const T rho = sqrt(rho2);
+  const T cps = rho > T(0) ? x / rho : T(1), sps = rho > T(0) ? y / rho : T(0);
+  T st, ct, cp, sp;
+  flower_factors<T>(P, z / r, rho / r, cps, sps, st, ct, cp, sp);
+  return r - r0 - amp * st * cp;
+}
 __device__ inline float phi_f(const ProbDev& P, float x, float y, float z) {
-  if (P.geometry == NBM_GEOM_GRID) return grid_phi<float>(P, x, y, z, nullptr);
-  if (P.geometry == NBM_GEOM_ALL_PLUS) return 1.f;
-  if (P.geometry == NBM_GEOM_ALL_MINUS) return -1.f;
-  float rho2 = x * x + y * y;
-  float r = sqrtf(rho2 + z * z);
-  if (P.geometry == NBM_GEOM_SPHERE) return r - P.r0f;
-  if (r == 0.f) return -P.r0f;
-  float th = atan2f(sqrtf(rho2), z), ps = atan2f(y, x);
-  return r - P.r0f - P.ampf * sinf(P.ltf * th) * cosf(P.lpf * ps);
+  return phi_t<float>(P, x, y, z);
 }
-
 __device__ inline double phi_d(const ProbDev& P, double x, double y, double z) {
-  if (P.geometry == NBM_GEOM_GRID) return grid_phi<double>(P, x, y, z, nullptr);
-  if (P.geometry == NBM_GEOM_ALL_PLUS) return 1.0;
-  if (P.geometry == NBM_GEOM_ALL_MINUS) return -1.0;
-  double rho2 = x * x + y * y;
-  double r = sqrt(rho2 + z * z);
-  if (P.geometry == NBM_GEOM_SPHERE) return r - P.r0;
-  if (r == 0.0) return -P.r0;
-  double th = atan2(sqrt(rho2), z), ps = atan2(y, x);
-  return r - P.r0 - P.amp * sin(P.lt * th) * cos(P.lp * ps);
+  return phi_t<double>(P, x, y, z);
 }
 
-__device__ inline void grad_phi_d(const ProbDev& P, const double x[3], double g[3]) {
+// grad phi: x / r, plus for the flower the derivatives of the angular factor
+// through theta and psi
+template <typename T>
+__device__ inline void grad_phi_t(const ProbDev& P, const T x[3], T g[3]) {
   if (P.geometry == NBM_GEOM_GRID) {
-    grid_phi<double>(P, x[0], x[1], x[2], g);
+    grid_phi<T>(P, x[0], x[1], x[2], g);
     return;
   }
-  g[0] = g[1] = g[2] = 0.0;
+  g[0] = g[1] = g[2] = T(0);
   if (P.geometry == NBM_GEOM_ALL_PLUS || P.geometry == NBM_GEOM_ALL_MINUS) return;
-  double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
-  double r = sqrt(rho * rho + x[2] * x[2]);
-  if (r == 0.0) return;
+  const T rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+  const T r = sqrt(rho * rho + x[2] * x[2]);
+  if (r == T(0)) return;
   for (int i = 0; i < 3; ++i) g[i] = x[i] / r;
-  if (P.geometry != NBM_GEOM_FLOWER || rho == 0.0) return;
-  double th = atan2(rho, x[2]), ps = atan2(x[1], x[0]);
-  double r2 = r * r;
-  double dth[3] = {x[2] * x[0] / (r2 * rho), x[2] * x[1] / (r2 * rho), -rho / r2};
-  double dps[3] = {-x[1] / (rho * rho), x[0] / (rho * rho), 0.0};
-  double a = -P.amp * P.lt * cos(P.lt * th) * cos(P.lp * ps);
-  double b = P.amp * P.lp * sin(P.lt * th) * sin(P.lp * ps);
-  for (int i = 0; i < 3; ++i) g[i] += a * dth[i] + b * dps[i];
+  if (P.geometry != NBM_GEOM_FLOWER || rho == T(0)) return;
+  const T amp = sizeof(T) == 4 ? (T)P.ampf : (T)P.amp;
+  const T lt = sizeof(T) == 4 ? (T)P.ltf : (T)P.lt, lp = sizeof(T) == 4 ? (T)P.lpf : (T)P.lp;
+  T st, ct, cp, sp;
+  flower_factors<T>(P, x[2] / r, rho / r, x[0] / rho, x[1] / rho, st, ct, cp, sp);
+  const T r2 = r * r;
+  const T dth[3] = {x[2] * x[0] / (r2 * rho), x[2] * x[1] / (r2 * rho), -rho / r2};
+  const T dps[3] = {-x[1] / (rho * rho), x[0] / (rho * rho), T(0)};
+  const T ga = -amp * lt * ct * cp;
+  const T gb = amp * lp * st * sp;
+  for (int i = 0; i < 3; ++i) g[i] += ga * dth[i] + gb * dps[i];
+}
+__device__ inline void grad_phi_d(const ProbDev& P, const double x[3], double g[3]) {
+  grad_phi_t<double>(P, x, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -266,24 +321,7 @@ __device__ inline double alpha_d(const ProbDev& P, const double x[3]) {
 
 // FP32 versions of the level-set gradient, [u] and [mu d_n u] (the FP32 rows)
 __device__ inline void grad_phi_f(const ProbDev& P, const float x[3], float g[3]) {
-  if (P.geometry == NBM_GEOM_GRID) {
-    grid_phi<float>(P, x[0], x[1], x[2], g);
-    return;
-  }
-  g[0] = g[1] = g[2] = 0.f;
-  if (P.geometry == NBM_GEOM_ALL_PLUS || P.geometry == NBM_GEOM_ALL_MINUS) return;
-  const float rho = sqrtf(x[0] * x[0] + x[1] * x[1]);
-  const float r = sqrtf(rho * rho + x[2] * x[2]);
-  if (r == 0.f) return;
-  for (int i = 0; i < 3; ++i) g[i] = x[i] / r;
-  if (P.geometry != NBM_GEOM_FLOWER || rho == 0.f) return;
-  const float th = atan2f(rho, x[2]), ps = atan2f(x[1], x[0]);
-  const float r2 = r * r;
-  const float dth[3] = {x[2] * x[0] / (r2 * rho), x[2] * x[1] / (r2 * rho), -rho / r2};
-  const float dps[3] = {-x[1] / (rho * rho), x[0] / (rho * rho), 0.f};
-  const float a = -P.ampf * P.ltf * cosf(P.ltf * th) * cosf(P.lpf * ps);
-  const float b = P.ampf * P.lpf * sinf(P.ltf * th) * sinf(P.lpf * ps);
-  for (int i = 0; i < 3; ++i) g[i] += a * dth[i] + b * dps[i];
+  grad_phi_t<float>(P, x, g);
 }
 
 __device__ inline float alpha_f(const ProbDev& P, const float x[3]) {

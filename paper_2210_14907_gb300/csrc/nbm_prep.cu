@@ -53,40 +53,43 @@ __device__ inline void draw_point(const ProbDev& P, uint64_t seed, int64_t step,
   double u2 = ((double)(r[2] >> 8) + 0.5) / 16777216.0;
   double cth = 1.0 - 2.0 * u0;
   double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
-  double psi = 2.0 * 3.14159265358979323846 * u1;
+  // azimuth psi = 2 pi u1: its cosine and sine by sincospi (no argument
+  // reduction of 2 pi u1)
+  double sps, cps;
+  sincospi(2.0 * u1, &sps, &cps);
   double t = (2.0 * u2 - 1.0) * 4.0 * P.h_band;
   double R = P.r0;
-  if (P.geometry == NBM_GEOM_FLOWER) R += P.amp * sin(P.lt * acos(cth)) * cos(P.lp * psi);
-  p[0] = (float)quantize_coord((R + t) * sth * cos(psi));
-  p[1] = (float)quantize_coord((R + t) * sth * sin(psi));
+  if (P.geometry == NBM_GEOM_FLOWER) {
+    // theta = acos(cth), sin(theta) = sth >= 0
+    double st, ct, cp, sp;
+    flower_factors<double>(P, cth, sth, cps, sps, st, ct, cp, sp);
+    R += P.amp * st * cp;
+  }
+  p[0] = (float)quantize_coord((R + t) * sth * cps);
+  p[1] = (float)quantize_coord((R + t) * sth * sps);
   p[2] = (float)quantize_coord((R + t) * cth);
 }
 
 // Number of corners of the cell p + [-h/2, h/2]^3 with phi <= 0.  FP32 first;
-// corners whose FP32 value is within the FP32 error band of 0 are redone in
-// FP64 so that the decision is the FP64 one.
+// a corner whose FP32 value is within the FP32 error band of 0 is redone in
+// FP64, so that every decision is the FP64 one.
 __device__ inline int count_neg_corners(const ProbDev& P, const float p[3]) {
   const float hh = 0.5f * P.hf;
-  float f[8];
-  float mn = 1e30f;
+  int nneg = 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    float cx = p[0] + ((c & 1) ? hh : -hh), cy = p[1] + ((c & 2) ? hh : -hh),
-          cz = p[2] + ((c & 4) ? hh : -hh);
-    f[c] = phi_f(P, cx, cy, cz);
-    mn = fminf(mn, fabsf(f[c]));
-  }
-  int nneg = 0;
-  if (mn < 2e-5f) {
-    const double hd = 0.5 * P.h;
-    for (int c = 0; c < 8; ++c) {
-      double cx = (double)p[0] + ((c & 1) ? hd : -hd), cy = (double)p[1] + ((c & 2) ? hd : -hd),
-             cz = (double)p[2] + ((c & 4) ? hd : -hd);
-      nneg += phi_d(P, cx, cy, cz) <= 0.0;
+    const float cx = p[0] + ((c & 1) ? hh : -hh), cy = p[1] + ((c & 2) ? hh : -hh),
+                cz = p[2] + ((c & 4) ? hh : -hh);
+    const float f = phi_f(P, cx, cy, cz);
+    bool neg = f <= 0.f;
+    if (fabsf(f) < 2e-5f) {
+      // within the FP32 error band of 0: the FP64 sign (a corner outside the
+      // band has the same sign in both precisions)
+      const double hd = 0.5 * P.h;
+      neg = phi_d(P, (double)p[0] + ((c & 1) ? hd : -hd), (double)p[1] + ((c & 2) ? hd : -hd),
+                  (double)p[2] + ((c & 4) ? hd : -hd)) <= 0.0;
     }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) nneg += f[c] <= 0.f;
+    nneg += neg;
   }
   return nneg;
 }
@@ -362,10 +365,10 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
       for (int a = 0; a < 3; ++a) cen[a] = wc[a] / area;
   } else {
     // FP32 rows: corner values with the classifier's rule (FP32 at the same
-    // FP32 coordinates; every corner of the cell in FP64 when one is within
-    // the FP32 error band of 0), so the signs are those that made the cell
-    // cut; the closed forms in FP32 on cell-local coordinates (corners at
-    // exactly +-1/2, lengths in units of h), where nothing cancels
+    // FP32 coordinates; a corner within the FP32 error band of 0 in FP64), so
+    // the signs are those that made the cell cut; the closed forms in FP32 on
+    // cell-local coordinates (corners at exactly +-1/2, lengths in units of
+    // h), where nothing cancels
     const float pf[3] = {X[i], Y[i], Z[i]};
     // f- and f+ at p on every lane (they depend on p only, so their chains
     // overlap the corner values below)
@@ -374,10 +377,7 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
     const float hh = 0.5f * P.hf;
     float Fk = phi_f(P, pf[0] + ((k & 1) ? hh : -hh), pf[1] + ((k & 2) ? hh : -hh),
                      pf[2] + ((k & 4) ? hh : -hh));
-    float mn = fabsf(Fk);
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) mn = fminf(mn, __shfl_xor_sync(full, mn, o));
-    if (mn < 2e-5f) {
+    if (fabsf(Fk) < 2e-5f) {  // this corner within the FP32 error band of 0
       const double hd = 0.5 * P.h;
       const double fd = phi_d(P, (double)pf[0] + ((k & 1) ? hd : -hd),
                               (double)pf[1] + ((k & 2) ? hd : -hd),
