@@ -325,6 +325,7 @@ __device__ inline void cell_pieces(int k, T Fk, int base, Corner corner, T& vneg
 // Cut cell `id` of the list (nc cells) on the 8 lanes of a warp's quarter; the
 // whole warp calls it (full-mask shuffles), lanes past the list compute on
 // cell 0's point and store nothing.
+template <bool FP64>
 __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float* X,
                                                   const float* Y,
                                                   const float* Z,
@@ -342,7 +343,7 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
   double vneg_d, S_d, Afk_d, cen[3] = {p[0], p[1], p[2]};
   bool has_area;
   float f0f = 0.f, f1f = 0.f;  // FP32 rows: f- and f+ at p
-  if (P.fp64) {
+  if constexpr (FP64) {
     // FP64 rows: FP64 corner values and closed forms on absolute coordinates
     double Ck[3];
     for (int a = 0; a < 3; ++a) Ck[a] = p[a] + h * ((double)((k >> a) & 1) - 0.5);
@@ -404,7 +405,7 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
   }
   double xg[3] = {cen[0], cen[1], cen[2]};
   if (has_area) {
-    if (P.fp64) {
+    if constexpr (FP64) {
       for (int it = 0; it < 3; ++it) {  // Newton projection onto phi = 0
         double g[3];
         const double ph = phi_d(P, xg[0], xg[1], xg[2]);
@@ -430,7 +431,7 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
   }
   // beta, alpha (at x_G), f- and f+ (at p)
   double beta, alpha, f0, f1;
-  if (P.fp64) {
+  if constexpr (FP64) {
     // FP64: four functions on four lanes
     double val = 0.0;
     if (k == 0 && has_area) val = beta_d(P, xg);
@@ -473,6 +474,9 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
 
 // Grid-stride over the cut list in groups of 16 cells (4 per warp), so that
 // the grid need not cover the worst case of every point being cut.
+// FP64: the FP64-row mode (its own instance: the FP32 one needs fewer
+// registers, so more of its warps are resident).
+template <bool FP64>
 __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* X,
                                                       const float* Y,
                                                       const float* Z,
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* X,
   const int nc = counters[2];
   for (int cell0 = blockIdx.x * 16; cell0 < nc; cell0 += gridDim.x * 16) {
     if (cell0 + 4 * (int)(threadIdx.x >> 5) >= nc) break;  // this warp's cells are past the list
-    cut_cell_geometry(P, X, Y, Z, cut_pt, cut, cell0 + (int)(threadIdx.x >> 3), nc);
+    cut_cell_geometry<FP64>(P, X, Y, Z, cut_pt, cut, cell0 + (int)(threadIdx.x >> 3), nc);
   }
 }
 
@@ -955,9 +959,9 @@ cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cuda
   // striding over the cut list
   const int64_t worst = (n + 15) / 16, cap = 8 * (int64_t)ws.grid;
   int nb = (int)(worst < cap ? worst : cap);
-  return launch_pdl(k_cut_geometry, dim3(nb), dim3(128), 0, st, P, (const float*)ws.x,
-                    (const float*)ws.y, (const float*)ws.z, (const int*)ws.cut_pt,
-                    (const int*)ws.counters, ws.cut);
+  return launch_pdl(P.fp64 ? k_cut_geometry<true> : k_cut_geometry<false>, dim3(nb), dim3(128), 0,
+                    st, P, (const float*)ws.x, (const float*)ws.y, (const float*)ws.z,
+                    (const int*)ws.cut_pt, (const int*)ws.counters, ws.cut);
 }
 
 // blocks of the cut-row kernel (grid-stride over the cut cells), i.e. the
