@@ -63,9 +63,10 @@ __device__ inline void jump_corr(double jmp, int sx, double c[2]) {
 // Rows of every interior node.  Jn (interior-node array) holds the node jump
 // J = u+ - u- carried to each node; NULL takes the manufactured pair's own
 // u+(x) - u-(x) (the exact jump).
-__global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, const double* __restrict__ Jn,
+__global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, const double* Jn,
                                                   double* diag, double* wx, double* wy, double* wz,
                                                   double* rhs) {
+  pdl_enter();
   const int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (r >= G.m) return;
   int idx[3];
@@ -122,8 +123,9 @@ __global__ void __launch_bounds__(kB) k_grid_rows(ProbDev P, Grid G, const doubl
 // diag A): unit diagonal, face weights w / sqrt(d_p d_q), in place.  CG on it
 // is Jacobi-preconditioned CG on A in exact arithmetic, and it reads neither
 // the diagonal nor its inverse in the SpMV or the direction update.
-__global__ void __launch_bounds__(kB) k_scale_rows(Grid G, const double* __restrict__ diag,
+__global__ void __launch_bounds__(kB) k_scale_rows(Grid G, const double* diag,
                                                    double* wx, double* wy, double* wz, double* b) {
+  pdl_enter();
   const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
   for (int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x; r < G.m; r += (int64_t)gridDim.x * kB) {
     const int i = (int)(r % G.m1), j = (int)((r / G.m1) % G.m1), k = (int)(r / s2);
@@ -229,8 +231,9 @@ __device__ void fold_partials(const double* part, int nparts, int nvec, double* 
 // The same sum as fold_partials as a separate one-block launch.  A fold costs
 // every block a device-scope fence before it retires; on large grids that
 // costs more than the extra launch, so they use this kernel instead.
-__global__ void __launch_bounds__(kB) k_reduce_parts(const double* __restrict__ part, int nparts,
+__global__ void __launch_bounds__(kB) k_reduce_parts(const double* part, int nparts,
                                                      int nvec, double* sc, int slot, int post) {
+  pdl_enter();
   sum_partials(part, nparts, nvec, sc, slot, post, false);
 }
 
@@ -244,12 +247,13 @@ __global__ void __launch_bounds__(kB) k_reduce_parts(const double* __restrict__ 
 // (FP32: 8 blocks, i.e. 2048 threads, per SM; at most 32 registers)
 template <typename T, bool UNIT>
 __global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 8 : 6) k_spmv_dot(Grid G, int kz,
-                                                 const T* __restrict__ diag,
-                                                 const T* __restrict__ wx,
-                                                 const T* __restrict__ wy,
-                                                 const T* __restrict__ wz,
-                                                 const T* __restrict__ v, T* y,
+                                                 const T* diag,
+                                                 const T* wx,
+                                                 const T* wy,
+                                                 const T* wz,
+                                                 const T* v, T* y,
                                                  double* part, double* sc, int post, int* ticket) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * kz, k1 = min(k0 + kz, G.m1);
   const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
@@ -287,10 +291,11 @@ __global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 8 : 6) k_spmv_dot(Grid G,
 // r.z = sum r^2 / d and ||r||^2 = r.r.  The scalars stay FP64 and each thread
 // strides over the nodes, reducing once.
 template <typename T, bool UNIT>
-__global__ void __launch_bounds__(kB) k_update(Grid G, double* sc, const T* __restrict__ dv,
-                                               const T* __restrict__ p,
-                                               const T* __restrict__ Ap, T* x, T* r,
+__global__ void __launch_bounds__(kB) k_update(Grid G, double* sc, const T* dv,
+                                               const T* p,
+                                               const T* Ap, T* x, T* r,
                                                double* part, int* ticket) {
+  pdl_enter();
   T acc[2] = {T(0), T(0)};
   const T a = (T)sc[2];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
@@ -308,9 +313,10 @@ __global__ void __launch_bounds__(kB) k_update(Grid G, double* sc, const T* __re
 // p = z + beta p with z = r (UNIT) or r / D (`inv_diag`; Jacobi PCG)
 // (beta = 0: p = z for the first direction)
 template <typename T, bool UNIT>
-__global__ void __launch_bounds__(kB) k_pupdate(Grid G, const double* __restrict__ sc, int first,
-                                                const T* __restrict__ inv_diag,
-                                                const T* __restrict__ r, T* p) {
+__global__ void __launch_bounds__(kB) k_pupdate(Grid G, const double* sc, int first,
+                                                const T* inv_diag,
+                                                const T* r, T* p) {
+  pdl_enter();
   const T beta = first ? T(0) : (T)sc[5];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
     const T z = UNIT ? r[i] : r[i] * inv_diag[i];
@@ -322,12 +328,13 @@ __global__ void __launch_bounds__(kB) k_pupdate(Grid G, const double* __restrict
 
 // FP32 copies of the unscaled operator for the inner Jacobi PCG of the
 // refined solve: D, 1/D and the face weights w = w^ sqrt(d_p d_q)
-__global__ void __launch_bounds__(kB) k_to_f32(Grid G, const double* __restrict__ diag,
-                                               const double* __restrict__ wx,
-                                               const double* __restrict__ wy,
-                                               const double* __restrict__ wz, float* d32,
+__global__ void __launch_bounds__(kB) k_to_f32(Grid G, const double* diag,
+                                               const double* wx,
+                                               const double* wy,
+                                               const double* wz, float* d32,
                                                float* idg32, float* wx32, float* wy32,
                                                float* wz32) {
+  pdl_enter();
   const int64_t s1 = G.m1, s2 = (int64_t)G.m1 * G.m1;
   for (int64_t r = (int64_t)blockIdx.x * kB + threadIdx.x; r < G.m; r += (int64_t)gridDim.x * kB) {
     const int i = (int)(r % G.m1), j = (int)((r / G.m1) % G.m1), k = (int)(r / s2);
@@ -342,9 +349,10 @@ __global__ void __launch_bounds__(kB) k_to_f32(Grid G, const double* __restrict_
 
 // r^ = b^ - r^ (r^ holds A^ x^ on entry); partials of sum d r^2 (= ||r||^2)
 // and sum d b^2 (= ||b||^2), summed into sc[8], sc[9] (POST_NORM)
-__global__ void __launch_bounds__(kB) k_defect(Grid G, const double* __restrict__ d,
-                                               const double* __restrict__ b, double* r,
+__global__ void __launch_bounds__(kB) k_defect(Grid G, const double* d,
+                                               const double* b, double* r,
                                                double* part, double* sc, int* ticket) {
+  pdl_enter();
   double acc[2] = {0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
     const double bi = b[i], ri = bi - r[i], di = d[i];
@@ -360,11 +368,12 @@ __global__ void __launch_bounds__(kB) k_defect(Grid G, const double* __restrict_
 // A e = r / ||r|| with r = D^1/2 r^: e = 0, r32 = r / ||r|| (norm 1),
 // p32 = r32 / D; partials of r32.p32 and r32.r32
 __global__ void __launch_bounds__(kB) k_inner_init(Grid G, double* sc,
-                                                   const double* __restrict__ r64,
-                                                   const float* __restrict__ d32,
-                                                   const float* __restrict__ idg32, float* r32,
+                                                   const double* r64,
+                                                   const float* d32,
+                                                   const float* idg32, float* r32,
                                                    float* e32, float* p32, double* part,
                                                    int* ticket) {
+  pdl_enter();
   float acc[2] = {0.f, 0.f};
   const double inv = sc[7];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB) {
@@ -493,9 +502,10 @@ __device__ double node_jump(const ProbDev& P, const Grid& G, const double p[3], 
 // the scaled system (node values x^ / sqrt(d)).  Block partials of
 // max |J_new - J| and max |J_new| go to part[] and part[gridDim.x + ...].
 __global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
-                                                  const double* __restrict__ x,
-                                                  const double* __restrict__ diag, double* J,
+                                                  const double* x,
+                                                  const double* diag, double* J,
                                                   double* part) {
+  pdl_enter();
   __shared__ double red[2][kB / 32];
   double mx[2] = {0.0, 0.0};
   auto val = [&](const int*, int64_t rq) { return x[rq] / sqrt(diag[rq]); };
@@ -527,7 +537,8 @@ __global__ void __launch_bounds__(kB) k_node_jump(ProbDev P, Grid G, int lag,
 // alpha(x) = u+(x) - u-(x) of the manufactured pair, or node_jump (first
 // order: lag 0; lagged: lag 1).
 __global__ void __launch_bounds__(kB) k_node_jump_all(ProbDev P, Grid G, int mode,
-                                                      const double* __restrict__ u, double* J) {
+                                                      const double* u, double* J) {
+  pdl_enter();
   const int64_t n1 = G.n + 1, nodes = n1 * n1 * n1;
   auto val = [&](const int* q, int64_t) { return u[q[0] + n1 * (q[1] + n1 * (int64_t)q[2])]; };
   for (int64_t e = (int64_t)blockIdx.x * kB + threadIdx.x; e < nodes;
@@ -540,7 +551,8 @@ __global__ void __launch_bounds__(kB) k_node_jump_all(ProbDev P, Grid G, int mod
 }
 
 // sc[slot], sc[slot + 1] = maxima of the two partial vectors
-__global__ void k_reduce_max2(const double* __restrict__ part, int nparts, double* sc, int slot) {
+__global__ void k_reduce_max2(const double* part, int nparts, double* sc, int slot) {
+  pdl_enter();
   __shared__ double red[2][256];
   double m0 = 0.0, m1 = 0.0;
   for (int b = threadIdx.x; b < nparts; b += 256) {
@@ -564,17 +576,19 @@ __global__ void k_reduce_max2(const double* __restrict__ part, int nparts, doubl
 }
 
 // x^ += ||r|| D^1/2 e   (FP64; e is the inner solve's unscaled correction)
-__global__ void __launch_bounds__(kB) k_correct(Grid G, const double* __restrict__ sc,
-                                                const float* __restrict__ d32,
-                                                const float* __restrict__ e32, double* x) {
+__global__ void __launch_bounds__(kB) k_correct(Grid G, const double* sc,
+                                                const float* d32,
+                                                const float* e32, double* x) {
+  pdl_enter();
   const double s = sc[6];
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < G.m; i += (int64_t)gridDim.x * kB)
     x[i] += s * (double)(e32[i] * sqrtf(d32[i]));
 }
 
 // the (n+1)^3 node array: x = x^ / sqrt(d) inside, Dirichlet data on the boundary
-__global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const double* __restrict__ x,
-                                                    const double* __restrict__ diag, double* u) {
+__global__ void __launch_bounds__(kB) k_write_nodes(ProbDev P, Grid G, const double* x,
+                                                    const double* diag, double* u) {
+  pdl_enter();
   const int64_t N1 = G.n + 1;
   const int64_t id = (int64_t)blockIdx.x * kB + threadIdx.x;
   if (id >= N1 * N1 * N1) return;
@@ -741,7 +755,8 @@ struct GridSolve {
   int* tk() const { return S.fold ? ticket : nullptr; }
   // the separate reduction of a launch's partials when they are not folded
   void reduce(int nparts, int nvec, int slot, int post) {
-    if (!S.fold) k_reduce_parts<<<1, kB, 0, st>>>(part, nparts, nvec, sc, slot, post);
+    if (!S.fold) launch_pdl(k_reduce_parts, dim3(1),
+                            dim3(kB), 0, st, part, nparts, nvec, sc, slot, post);
   }
 
   cudaError_t read_sc() {
@@ -755,9 +770,10 @@ struct GridSolve {
   void defect() {
     const Grid& G = S.G;
     cudaMemsetAsync(sc, 0, sizeof(double) * 16, st);
-    k_spmv_dot<double, true><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, nullptr, wx, wy, wz, x, r,
-                                                            part, sc, POST_SKIP, nullptr);
-    k_defect<<<S.nu, kB, 0, st>>>(G, diag, b, r, part, sc, tk());
+    launch_pdl(k_spmv_dot<double, true>, dim3(S.sgrid),
+               dim3(S.sblock), 0, st, G, S.kz, nullptr, wx, wy, wz, x, r, part, sc, POST_SKIP,
+               nullptr);
+    launch_pdl(k_defect, dim3(S.nu), dim3(kB), 0, st, G, diag, b, r, part, sc, tk());
     reduce(S.nu, 2, 8, POST_NORM);
   }
 
@@ -770,21 +786,23 @@ struct GridSolve {
     cudaMemsetAsync(pv, 0, sizeof(double) * G.m, st);
     cudaMemsetAsync(Ap, 0, sizeof(double) * G.m, st);
     // rz = r^.r^, rr = ||r||^2 (an update with alpha = sc[2] = 0), p = r^
-    k_update<double, true><<<S.nu, kB, 0, st>>>(G, sc, diag, pv, Ap, x, r, part, tk());
+    launch_pdl(k_update<double, true>, dim3(S.nu), dim3(kB), 0, st, G, sc, diag, pv, Ap, x, r, part,
+               tk());
     reduce(S.nu, 2, 3, POST_BETA);
-    k_pupdate<double, true><<<S.nu, kB, 0, st>>>(G, sc, 1, nullptr, r, pv);
+    launch_pdl(k_pupdate<double, true>, dim3(S.nu), dim3(kB), 0, st, G, sc, 1, nullptr, r, pv);
     if ((e = read_sc()) != cudaSuccess) return -1;
     bnorm = sqrt(host_sc[9]);
     rnorm = sqrt(host_sc[4]);
     int it = 0;
     bool converged = rnorm <= rtol * bnorm;
     while (!converged && it < max_iter && rnorm == rnorm) {
-      k_spmv_dot<double, true><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, nullptr, wx, wy, wz, pv, Ap,
-                                                              part, sc, POST_ALPHA, tk());
+      launch_pdl(k_spmv_dot<double, true>, dim3(S.sgrid), dim3(S.sblock), 0, st, G, S.kz, nullptr,
+                 wx, wy, wz, pv, Ap, part, sc, POST_ALPHA, tk());
       reduce(S.nsp, 1, 1, POST_ALPHA);
-      k_update<double, true><<<S.nu, kB, 0, st>>>(G, sc, diag, pv, Ap, x, r, part, tk());
+      launch_pdl(k_update<double, true>, dim3(S.nu), dim3(kB), 0, st, G, sc, diag, pv, Ap, x, r,
+                 part, tk());
       reduce(S.nu, 2, 3, POST_BETA);
-      k_pupdate<double, true><<<S.nu, kB, 0, st>>>(G, sc, 0, nullptr, r, pv);
+      launch_pdl(k_pupdate<double, true>, dim3(S.nu), dim3(kB), 0, st, G, sc, 0, nullptr, r, pv);
       ++it;
       if (it % kCheckEvery == 0 || it == max_iter) {
         if ((e = read_sc()) != cudaSuccess) return -1;
@@ -812,16 +830,17 @@ struct GridSolve {
       // 1), stopped at kInnerTol or where the outer target needs no more
       double tau = 0.5 * rtol * bnorm / rnorm;
       tau = tau < kInnerTol ? kInnerTol : tau > 0.5 ? 0.5 : tau;
-      k_inner_init<<<S.nu, kB, 0, st>>>(G, sc, r, d32, idg32, r32, e32, p32, part, tk());
+      launch_pdl(k_inner_init, dim3(S.nu), dim3(kB), 0, st, G, sc, r, d32, idg32, r32, e32, p32,
+                 part, tk());
       reduce(S.nu, 2, 3, POST_BETA);
       for (int inner = 1; it < max_iter; ++inner) {
-        k_spmv_dot<float, false><<<S.sgrid, S.sblock, 0, st>>>(G, S.kz, d32, wx32, wy32, wz32,
-                                                                p32, Ap32, part, sc, POST_ALPHA,
-                                                                tk());
+        launch_pdl(k_spmv_dot<float, false>, dim3(S.sgrid), dim3(S.sblock), 0, st, G, S.kz, d32,
+                   wx32, wy32, wz32, p32, Ap32, part, sc, POST_ALPHA, tk());
         reduce(S.nsp, 1, 1, POST_ALPHA);
-        k_update<float, false><<<S.nu, kB, 0, st>>>(G, sc, idg32, p32, Ap32, e32, r32, part, tk());
+        launch_pdl(k_update<float, false>, dim3(S.nu), dim3(kB), 0, st, G, sc, idg32, p32, Ap32,
+                   e32, r32, part, tk());
         reduce(S.nu, 2, 3, POST_BETA);
-        k_pupdate<float, false><<<S.nu, kB, 0, st>>>(G, sc, 0, idg32, r32, p32);
+        launch_pdl(k_pupdate<float, false>, dim3(S.nu), dim3(kB), 0, st, G, sc, 0, idg32, r32, p32);
         ++it;
         if (inner % kCheckEvery == 0 || it == max_iter) {
           if ((e = read_sc()) != cudaSuccess) return -1;
@@ -830,7 +849,7 @@ struct GridSolve {
         }
       }
       // x^ += ||r|| D^1/2 e in FP64, then the FP64 residual r^ = b^ - A^ x^
-      k_correct<<<S.nu, kB, 0, st>>>(G, sc, d32, e32, x);
+      launch_pdl(k_correct, dim3(S.nu), dim3(kB), 0, st, G, sc, d32, e32, x);
       defect();
       if ((e = read_sc()) != cudaSuccess) return -1;
       const double rnew = sqrt(host_sc[8]);
@@ -849,15 +868,15 @@ struct GridSolve {
 
   // the rows of the current jumps, then the scaled system
   void rows() {
-    k_grid_rows<<<S.nb, kB, 0, st>>>(S.P, S.G, J, diag, wx, wy, wz, b);
-    k_scale_rows<<<S.nu, kB, 0, st>>>(S.G, diag, wx, wy, wz, b);
+    launch_pdl(k_grid_rows, dim3(S.nb), dim3(kB), 0, st, S.P, S.G, J, diag, wx, wy, wz, b);
+    launch_pdl(k_scale_rows, dim3(S.nu), dim3(kB), 0, st, S.G, diag, wx, wy, wz, b);
   }
 
   // J from the current x (lag 1) or first order (lag 0); sc[12] = max |dJ|,
   // sc[13] = max |J|
   void jumps(int lag) {
-    k_node_jump<<<S.nu, kB, 0, st>>>(S.P, S.G, lag, x, diag, J, part);
-    k_reduce_max2<<<1, 256, 0, st>>>(part, S.nu, sc, 12);
+    launch_pdl(k_node_jump, dim3(S.nu), dim3(kB), 0, st, S.P, S.G, lag, x, diag, J, part);
+    launch_pdl(k_reduce_max2, dim3(1), dim3(256), 0, st, part, S.nu, sc, 12);
   }
 };
 
@@ -908,8 +927,9 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
   }
   W.rows();
   if (refined)  // the operator is the same for every pass: round it once
-    k_to_f32<<<W.S.nu, kB, 0, st>>>(G, W.diag, W.wx, W.wy, W.wz, W.d32, W.idg32, W.wx32, W.wy32,
-                                     W.wz32);
+    launch_pdl(k_to_f32, dim3(W.S.nu),
+               dim3(kB), 0, st, G, W.diag, W.wx, W.wy, W.wz, W.d32, W.idg32, W.wx32, W.wy32,
+               W.wz32);
   cudaError_t e = cudaSuccess;
   int status = W.solve(rtol, max_iter, e);
   JumpInfo info;
@@ -938,7 +958,8 @@ int grid_solve(nbm_problem* p, int n, double rtol, int max_iter, double* u_out, 
     }
   }
   if (status < 0) return cg_cuda_fail(W.who, e);
-  k_write_nodes<<<(int)((W.S.nodes + kB - 1) / kB), kB, 0, st>>>(W.S.P, G, W.x, W.diag, u_out);
+  launch_pdl(k_write_nodes, dim3((int)((W.S.nodes + kB - 1) / kB)),
+             dim3(kB), 0, st, W.S.P, G, W.x, W.diag, u_out);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cg_cuda_fail(W.who, e);
@@ -982,8 +1003,8 @@ extern "C" int nbm_grid_node_jump(nbm_problem* p, int n, int mode, const double*
   CgSetup S;
   if (int rc = cg_setup(p, n, 1.0, 0, jump_out, "node jump", S)) return rc;
   const int64_t blocks = (S.nodes + kB - 1) / kB, cap = 8 * (int64_t)problem_num_sms(p);
-  k_node_jump_all<<<(int)(blocks < cap ? blocks : cap), kB, 0, (cudaStream_t)stream>>>(
-      S.P, S.G, mode, u, jump_out);
+  launch_pdl(k_node_jump_all, dim3((int)(blocks < cap ? blocks : cap)), dim3(kB), 0,
+             (cudaStream_t)stream, S.P, S.G, mode, u, jump_out);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? NBM_OK : cg_cuda_fail("node jump", e);
 }
