@@ -63,6 +63,9 @@ __device__ inline void draw_point(const ProbDev& P, uint64_t seed, int64_t step,
     // theta = acos(cth), sin(theta) = sth >= 0
     double st, ct, cp, sp;
     flower_factors<double>(P, cth, sth, cps, sps, st, ct, cp, sp);
+    // a lobe count that is not an integer: the factor of the draw's own
+    // azimuth 2 pi u1 in (0, 2 pi) (not periodic in 2 pi)
+    if (P.lp_i < 0) cp = cos(P.lp * (2.0 * 3.14159265358979323846 * u1));
     R += P.amp * st * cp;
   }
   p[0] = (float)quantize_coord((R + t) * sth * cps);

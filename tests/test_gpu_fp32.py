@@ -189,3 +189,50 @@ def test_invalid_arguments_fail_cleanly():
     # the problem object stays usable after a rejected call
     loss, _ = prob.loss_grad(torch.from_numpy(inputs.glorot_params(64, 2, 1)).cuda(), n=256)
     assert np.isfinite(loss)
+
+
+@pytest.mark.parametrize("lobes", [(5.0, 3.0), (4.5, 2.5)], ids=["integer", "fractional"])
+def test_flower_lobes_match_oracle(lobes):
+    """The flower's angular factor sin(lt theta) cos(lp psi) is evaluated by
+    Chebyshev recurrences for integer lobe counts and through the angles
+    otherwise; both against the oracle, which always takes the angles."""
+    nbm = _nbm()
+    lt, lp = lobes
+    h = 2 / 64
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_FLOWER, n_hidden=3, width=64, h=h, mu_minus=1.0,
+                        mu_plus=100.0, lobes_theta=lt, lobes_psi=lp)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_FLOWER, n_hidden=3, width=64, h=h, mu_minus=1.0,
+                       mu_plus=100.0, lobes_theta=lt, lobes_psi=lp)
+    pts = inputs.mixed_points(1500, 1500, seed=11)
+    th = inputs.glorot_params(64, 3, seed=7, bias_scale=0.1)
+    L_ref, r2_ref = O.loss(o, th.astype(np.float64), pts, want_r2=True)
+    _, g_ref = O.loss_grad(o, th.astype(np.float64), pts)
+    tp = torch.from_numpy(th).cuda()
+    tx = torch.from_numpy(pts.astype(np.float32)).cuda()
+    loss, r2 = prob.residual(tp, tx)
+    loss2, g = prob.loss_grad(tp, tx)
+    r2 = r2.cpu().numpy().astype(np.float64)
+    assert _rel(np.sqrt(r2), np.sqrt(r2_ref)) <= RES_TOL
+    parity.check_points(o, th, pts, r2, r2_ref, RES_TOL, RES_TOL, label=f"flower lobes {lobes}")
+    assert abs(loss - L_ref) / L_ref <= LOSS_TOL
+    assert abs(loss2 - L_ref) / L_ref <= LOSS_TOL
+    assert _rel(g.cpu().numpy(), g_ref) <= GRAD_TOL
+
+
+def test_sampler_matches_oracle_fractional_lobes():
+    """Band points of a flower whose lobe counts are not integers (the draw's
+    angular factor through the angles, on the draw's own azimuth)."""
+    nbm = _nbm()
+    h = 2 / 256
+    d = nbm.ProblemDesc(geometry=nbm.GEOM_FLOWER, n_hidden=2, width=64, h=h, band_fraction=0.3,
+                        lobes_theta=4.5, lobes_psi=2.5)
+    prob = nbm.Problem(d)
+    o = O.make_problem(geometry=O.GEOM_FLOWER, h=h, lobes_theta=4.5, lobes_psi=2.5)
+    n = 20000
+    nb = int(np.floor(0.3 * n + 0.5))
+    got = prob.sample_points(n, seed=2, step=5).cpu().numpy().astype(np.float64)
+    ref = O.sample_points(o, 2, 5, n, nb)
+    assert np.array_equal(got[: n - nb], ref[: n - nb])
+    q = np.abs(got[n - nb:] - ref[n - nb:]) / 2.0 ** -22
+    assert q.max() <= 1.0 and np.mean(q == 0) > 0.999
