@@ -77,3 +77,36 @@ def test_static_scratch_rejects_oversized_batch():
             ctypes.c_void_p(g.data_ptr()), None, None)
     assert rc == 1
     assert b"static-scratch limit" in prob.lib.nbm_last_error()
+
+
+def test_static_entry_allocates_no_device_memory():
+    """Repeated calls on a problem whose workspace was never allocated leave
+    the device's free memory unchanged; the allocating entry point on another
+    fresh problem does change it (the check sees a workspace allocation)."""
+    import paper_2210_14907_gb300 as nbm
+    d = nbm.config("C2")
+    prob = nbm.Problem(d)  # fresh: nothing of its own allocated yet
+    fn = _static_entry(prob.lib)
+    n = 8192
+    pts = torch.from_numpy(inputs.mixed_points(n - 2000, 2000, seed=5).astype(np.float32)).cuda()
+    th = torch.from_numpy(inputs.glorot_params(128, 3, seed=5, bias_scale=0.1)).cuda()
+    g = torch.empty(prob.P, device="cuda")
+    stream = torch.cuda.current_stream()
+    args = (prob.handle, ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(pts.data_ptr()), n, 1, 1,
+            ctypes.c_void_p(g.data_ptr()), None, ctypes.c_void_p(stream.cuda_stream))
+    assert fn(*args) == 0, prob.lib.nbm_last_error()  # warm: the library is loaded
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert fn(*args) == 0, prob.lib.nbm_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    # control: the allocating entry point reserves its workspace on first use
+    other = nbm.Problem(d)
+    lg = other.lib.nbm_loss_grad  # argument types as the package declares them
+    assert lg(other.handle, th.data_ptr(), pts.data_ptr(), n, 1, 1, g.data_ptr(), None,
+              stream.cuda_stream) == 0, other.lib.nbm_last_error()
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 < free1
