@@ -407,12 +407,29 @@ __device__ __forceinline__ float rcp(float x) {
 constexpr float kSmallMu = 0.05f;
 constexpr float kSmallMuAccurate = 0.00390625f;
 
+// small_de (accurate path only; every lane of the warp has |del| <= 2^-4): the
+// antisymmetric part's tanh and reciprocal from their series,
+//   tanh d = d (1 - d^2/3 + 2 d^4/15) + R,        |R| <= 17 |d|^7 / 315,
+//   1 / (1 - x) = 1 + x + x^2 + x^3 + x^4/(1-x),  x = tw^2 Td^2 <= 2^-8,
+// relative errors below 4e-9 and 2.4e-10 (FP32 rounding is 6e-8), in place of
+// tanhf and an IEEE division.  The SFU path keeps tanh.approx and rcp.approx,
+// which cost less than the series there.
+constexpr float kSmallDelAccurate = 0.0625f;
+__device__ __forceinline__ float tanh_small(float d) {
+  const float d2 = d * d;
+  return d * fmaf(d2, fmaf(d2, 2.0f / 15.0f, -1.0f / 3.0f), 1.0f);
+}
+__device__ __forceinline__ float rcp_one_minus_small(float x) {  // 1 / (1 - x), 0 <= x <= 2^-8
+  return fmaf(x, fmaf(x, x + 1.0f, 1.0f), 1.0f);
+}
+
 template <bool FAST>
 __device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, float h, float h2,
                                                  float inv_h, float inv_h2, float& mo, float& dout,
-                                                 bool small_mu = false) {
+                                                 bool small_mu = false, bool small_de = false) {
   float mu = mt * h2, de = dt * h;
-  float Td = act_tanh<FAST>(de);
+  const bool sde = !FAST && small_de;
+  float Td = sde ? tanh_small(de) : act_tanh<FAST>(de);
   float tw, dm;
   if (small_mu) {
     const float poly = fmaf(fmaf(t, t, -1.0f / 3.0f), mu * mu, fmaf(-t, mu, 1.0f));
@@ -426,7 +443,8 @@ __device__ __forceinline__ void tanh_stencil_fwd(float t, float mt, float dt, fl
   }
   float sw = fmaf(-tw, tw, 1.0f);
   float Td2 = Td * Td;
-  float r2 = rcp<FAST>(fmaf(sw - 1.0f, Td2, 1.0f));  // 1 / (1 - tw^2 Td^2)
+  float r2 = sde ? rcp_one_minus_small(tw * tw * Td2)
+                 : rcp<FAST>(fmaf(sw - 1.0f, Td2, 1.0f));  // 1 / (1 - tw^2 Td^2)
   float k = sw * r2;
   float m = fmaf(-tw * Td2, k, dm);
   float d = k * Td;

@@ -149,19 +149,32 @@ __device__ __forceinline__ void warp_transpose_reduce32(const float (&x)[32], fl
 // series path, operation for operation.
 template <bool FAST>
 __device__ __forceinline__ void tanh_stencil_fwd_pair(F2 T, F2 NT, F2 S0, F2 MU, F2 DE, F2& M,
-                                                      F2& D) {
-  float dA, dB;
-  f2get(DE, dA, dB);
-  const F2 TD = f2(act_tanh<FAST>(dA), act_tanh<FAST>(dB));
+                                                      F2& D, bool small_de = false) {
+  const bool sde = !FAST && small_de;  // the series of tanh d and 1/(1-x) (accurate path)
+  F2 TD;
+  if (sde) {
+    const F2 d2 = mul2(DE, DE);
+    TD = mul2(DE, fma2(d2, fma2(d2, f2s(2.0f / 15.0f), f2s(-1.0f / 3.0f)), f2s(1.0f)));
+  } else {
+    float dA, dB;
+    f2get(DE, dA, dB);
+    TD = f2(act_tanh<FAST>(dA), act_tanh<FAST>(dB));
+  }
   const F2 poly = fma2(fma2(T, T, f2s(-1.0f / 3.0f)), mul2(MU, MU), fma2(NT, MU, f2s(1.0f)));
   const F2 dm = mul2(mul2(S0, MU), poly);
   const F2 tw = add2(T, dm);
   const F2 ntw = mul2(tw, f2s(-1.0f));
   const F2 sw = fma2(ntw, tw, f2s(1.0f));
   const F2 td2 = mul2(TD, TD);
-  float eA, eB;
-  f2get(fma2(add2(sw, f2s(-1.0f)), td2, f2s(1.0f)), eA, eB);
-  const F2 r2 = f2(rcp<FAST>(eA), rcp<FAST>(eB));
+  F2 r2;
+  if (sde) {
+    const F2 x = mul2(mul2(tw, tw), td2);  // 1/(1-x) = 1 + x (1 + x (1 + x))
+    r2 = fma2(x, fma2(x, add2(x, f2s(1.0f)), f2s(1.0f)), f2s(1.0f));
+  } else {
+    float eA, eB;
+    f2get(fma2(add2(sw, f2s(-1.0f)), td2, f2s(1.0f)), eA, eB);
+    r2 = f2(rcp<FAST>(eA), rcp<FAST>(eB));
+  }
   const F2 k = mul2(sw, r2);
   M = fma2(mul2(ntw, td2), k, dm);
   D = mul2(k, TD);
@@ -462,8 +475,13 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
           // two points per packed FP32 instruction; tanh(h W1[u][i]) depends on the
           // unit only
           float Td[3];
+          // accurate path with small increments h W1[u][i] in every lane: the series
+          bool sd1 = false;
+          if constexpr (!FAST)
+            sd1 = __all_sync(0xffffffffu, fmaxf(fabsf(dl1[0]), fmaxf(fabsf(dl1[1]), fabsf(dl1[2]))) <=
+                                              kSmallDelAccurate);
 #pragma unroll
-          for (int i = 0; i < 3; ++i) Td[i] = act_tanh<FAST>(dl1[i]);
+          for (int i = 0; i < 3; ++i) Td[i] = sd1 ? tanh_small(dl1[i]) : act_tanh<FAST>(dl1[i]);
 #pragma unroll
           for (int pp = 0; pp < kPPT; pp += 2) {
             const PRec pa = pr[4 * cgl + pp], pb = pr[4 * cgl + pp + 1];
@@ -481,9 +499,15 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
               const F2 TD = f2s(Td[i]), TD2 = mul2(TD, TD);
-              float eA, eB;
-              f2get(fma2(NTT, TD2, f2s(1.0f)), eA, eB);
-              const F2 R2 = f2(rcp<FAST>(eA), rcp<FAST>(eB));
+              F2 R2;
+              if (sd1) {  // 1 / (1 - t^2 Td^2) by its series
+                const F2 x = mul2(mul2(T, T), TD2);
+                R2 = fma2(x, fma2(x, add2(x, f2s(1.0f)), f2s(1.0f)), f2s(1.0f));
+              } else {
+                float eA, eB;
+                f2get(fma2(NTT, TD2, f2s(1.0f)), eA, eB);
+                R2 = f2(rcp<FAST>(eA), rcp<FAST>(eB));
+              }
               f2get(mul2(mul2(NTS, TD2), R2), oA[1 + i], oB[1 + i]);
               f2get(mul2(mul2(SW, TD), R2), oA[4 + i], oB[4 + i]);
             }
@@ -548,6 +572,14 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
                 0xffffffffu, fmaxf(fabsf(cA[1]), fmaxf(fabsf(cA[2]), fabsf(cA[3]))) <= kSmall);
             const bool smB = __all_sync(
                 0xffffffffu, fmaxf(fabsf(cB[1]), fmaxf(fabsf(cB[2]), fabsf(cB[3]))) <= kSmall);
+            // accurate path: antisymmetric increments small in every lane (their series)
+            bool sdA = false, sdB = false;
+            if constexpr (!FAST) {
+              sdA = __all_sync(0xffffffffu, fmaxf(fabsf(cA[4]), fmaxf(fabsf(cA[5]), fabsf(cA[6]))) <=
+                                                kSmallDelAccurate);
+              sdB = __all_sync(0xffffffffu, fmaxf(fabsf(cB[4]), fmaxf(fabsf(cB[5]), fabsf(cB[6]))) <=
+                                                kSmallDelAccurate);
+            }
             if (smA && smB) {
               const F2 T = f2(tA, tB), NT = mul2(T, f2s(-1.0f));
               const F2 S0 = fma2(NT, T, f2s(1.0f));
@@ -555,7 +587,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
               for (int i = 0; i < 3; ++i) {
                 F2 M, D;
                 tanh_stencil_fwd_pair<FAST>(T, NT, S0, f2(cA[1 + i], cB[1 + i]),
-                                            f2(cA[4 + i], cB[4 + i]), M, D);
+                                            f2(cA[4 + i], cB[4 + i]), M, D, sdA && sdB);
                 f2get(M, oA[1 + i], oB[1 + i]);
                 f2get(D, oA[4 + i], oB[4 + i]);
               }
@@ -563,9 +595,9 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
 #pragma unroll
               for (int i = 0; i < 3; ++i) {
                 tanh_stencil_fwd<FAST>(tA, cA[1 + i], cA[4 + i], 1.f, 1.f, 1.f, 1.f, oA[1 + i],
-                                       oA[4 + i], smA);
+                                       oA[4 + i], smA, sdA);
                 tanh_stencil_fwd<FAST>(tB, cB[1 + i], cB[4 + i], 1.f, 1.f, 1.f, 1.f, oB[1 + i],
-                                       oB[4 + i], smB);
+                                       oB[4 + i], smB, sdB);
               }
             }
             oA[7] = act_tanh<FAST>(cA[7] + bb);
