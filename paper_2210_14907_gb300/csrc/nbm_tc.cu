@@ -600,8 +600,19 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
                                        oB[4 + i], smB, sdB);
               }
             }
-            oA[7] = act_tanh<FAST>(cA[7] + bb);
-            oB[7] = act_tanh<FAST>(cB[7] + bb);
+            // column 7 (the interface point) only matters for cut cells with a jump
+            // row; elsewhere its seeds are 0.  The accurate path skips its tanh there
+            // (0, as layer 1 leaves it); in the SFU path the test cost more than it
+            // saved (C2 6 % slower), so that path keeps computing it.
+            if constexpr (FAST) {
+              oA[7] = act_tanh<FAST>(cA[7] + bb);
+              oB[7] = act_tanh<FAST>(cB[7] + bb);
+            } else {
+              const PRec& qa = pr[4 * cgl + jp];
+              const PRec& qb = pr[4 * cgl + jp + 1];
+              oA[7] = (qa.cutj >= 0 && (qa.cutj & 1)) ? act_tanh<FAST>(cA[7] + bb) : 0.f;
+              oB[7] = (qb.cutj >= 0 && (qb.cutj & 1)) ? act_tanh<FAST>(cB[7] + bb) : 0.f;
+            }
             if (g < NG) {
               store8o<BF>(Aimg + g * kImgH, poff(jp), oA);
               store8o<BF>(Aimg + g * kImgH, poff(jp + 1), oB);
