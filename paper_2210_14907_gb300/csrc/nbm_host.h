@@ -153,6 +153,9 @@ int check_aligned(const void* ptr, size_t align, const char* name);
 // point i is point first + i of a batch of n_total points (0: n_total = n), so
 // a shard of a batch gets the counters and band decisions the whole batch
 // would give it; n_band counts the band points of that whole batch.
+// Sampling and classification of a step's points, then the phase lists.
+// prep_params non-NULL: extra blocks of the same launch restage the hidden
+// weights from those parameters (prec: the tensor-core image's 16-bit type).
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st,
