@@ -1016,33 +1016,66 @@ def main():
     clocks = clk.summary()
 
     # end to end through the public API: per step, the step's collocation points
-    # are copied from pinned host memory and the step's loss is read back
+    # are copied from pinned host memory and the step's loss is read back.  The
+    # copies run on their own stream into two device buffers, so that step k+1's
+    # points cross while step k computes (each copy waits until the step that
+    # last read its buffer has finished; each step waits for its own copy), and
+    # the host reads step k's loss once step k+1 is enqueued, so the device does
+    # not idle while the host checks it.
     k_e2e = max(10, args.steps // 20)
     rng = np.random.default_rng(rank)
     host = torch.from_numpy(
         (-1.0 + rng.integers(1, 2**23, size=(k_e2e, BATCH, 3)) * 2.0**-22).astype(np.float32)
     ).pin_memory()
-    dpts = torch.empty(BATCH, 3, device=dev)
+    dbuf = [torch.empty(BATCH, 3, device=dev) for _ in range(2)]
     ldt = torch.float32 if ws == 1 else torch.float64  # loss_hist (fused) / all-reduced loss
     hist = torch.zeros(1, device=dev, dtype=ldt)
-    hloss = torch.zeros(1, dtype=ldt).pin_memory()
-    for k in range(2):  # untimed: first touch of the pinned buffers and the copy path
-        dpts.copy_(host[k], non_blocking=True)
-        one(pts=dpts, loss_hist=hist)
-        hloss.copy_(hist, non_blocking=True)
+    hl = [torch.zeros(1, dtype=ldt).pin_memory() for _ in range(2)]
+    cur = torch.cuda.current_stream()
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]
+    read = [torch.cuda.Event() for _ in range(2)]
+
+    def stage(k):
+        b = k % 2
+        copy_stream.wait_event(used[b])  # (an event never recorded: no wait)
+        with torch.cuda.stream(copy_stream):
+            dbuf[b].copy_(host[k], non_blocking=True)
+        copied[b].record(copy_stream)
+
+    def check(k):
+        read[k % 2].synchronize()
+        assert np.isfinite(hl[k % 2].item())
+
+    def e2e_steps(n):
+        stage(0)
+        for k in range(n):
+            if k + 1 < n:
+                stage(k + 1)  # the next step's points cross while this step runs
+            b = k % 2
+            cur.wait_event(copied[b])
+            one(pts=dbuf[b], loss_hist=hist)
+            used[b].record(cur)
+            hl[b].copy_(hist, non_blocking=True)  # this step's loss to the host
+            read[b].record(cur)
+            if k > 0:
+                check(k - 1)  # the previous step's loss, while this step runs
+        check(n - 1)
+
+    e2e_steps(2)  # untimed: first touch of the pinned buffers and the copy path
     torch.cuda.synchronize()
     _barrier(ws)
     t0 = time.perf_counter()
-    for k in range(k_e2e):
-        dpts.copy_(host[k], non_blocking=True)
-        one(pts=dpts, loss_hist=hist)
-        hloss.copy_(hist, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        assert np.isfinite(hloss.item())
+    e2e_steps(k_e2e)
     e2e_s = _max_over_ranks(ws, time.perf_counter() - t0)
     e2e = {"value": ws * k_e2e * BATCH / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": BATCH * 3 * 4, "d2h_bytes_per_step": hloss.element_size(),
-           "steps": k_e2e}
+           "h2d_bytes_per_step": BATCH * 3 * 4, "d2h_bytes_per_step": hl[0].element_size(),
+           "steps": k_e2e,
+           "pipelining": "inputs copied on a second stream while the previous step computes; "
+                         "each step's loss read on the host while the next step computes",
+           "l2": "not flushed: back-to-back steps, as a training loop runs (the device-timed "
+                 "value flushes L2 before every step)"}
 
     # roofline of the fused tcgen05 kernel: algorithmic FLOPs = 7 stencil
     # evaluations x (forward + input-gradient + weight-gradient) x 2 H^2 per
