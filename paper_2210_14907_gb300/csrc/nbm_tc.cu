@@ -203,6 +203,27 @@ int tc_supported(int H, int L) { return H == 128 && L >= 2 && L <= 4; }
 // whose exponent range is that of FP32): they hold mu and del themselves,
 // which saves the rescaling in every epilogue; the output stage converts to
 // the scaled convention of the residual rows.
+// Forward weights of one network from their shared-memory images into TMEM,
+// the forward GEMMs' A operand: layer g (1..ng) in the 64 columns from tw +
+// 64 (g-1), row u of W in the calling lane (tw carries the warp's lane
+// quadrant), W[u][2c] and W[u][2c+1] in column c.  Out of line: it runs twice
+// per launch and keeps its registers out of the hot loop's allocation.
+__device__ __noinline__ void stage_weights_tmem(const unsigned char* Wimg, uint32_t tw, int u,
+                                                int ng) {
+  for (int g = 1; g <= ng; ++g) {
+    const unsigned char* img = Wimg + (g - 1) * kImg;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      uint32_t v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        v[c] = *reinterpret_cast<const uint32_t*>(img + img_off(u, 2 * (16 * j + c)));
+      tmem_st16(tw + 64u * (uint32_t)(g - 1) + 16u * (uint32_t)j, v);
+    }
+  }
+  tmem_wait_st();
+}
+
 template <int L, bool BF, bool FAST, bool SCALED>
 __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
   pdl_enter();
@@ -210,6 +231,10 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
   constexpr int NG = L - 1;  // hidden GEMM layers
   constexpr int kPPT = 4;    // points per thread (8 warps = 4 lane quadrants x 2 column groups)
   constexpr uint32_t NCOLS = (NG + 1) * 128 <= 256 ? 256 : 512;
+  // Two hidden GEMMs use 384 of the 512 columns: the forward GEMMs then take
+  // their weights (the A operand) from the last 128, which spares each of them
+  // the 32 KB weight read from shared memory.
+  constexpr bool kWTmem = NG == 2;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -436,6 +461,15 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         break;
       }
     }
+    if constexpr (kWTmem) {
+      // this network's forward weights into TMEM: layer g in columns 384 +
+      // 64 (g-1) .., unit u (row of W) in lane u, W[u][2c] and W[u][2c+1] in
+      // column c; the previous segment's GEMMs have all completed
+      if (w < 4) stage_weights_tmem(Wimg, tmem + ((uint32_t)(32 * w) << 16) + 384u, u, NG);
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+    }
 
     int tile_i = 0;  // index of the half-tile among this group's tiles of the segment
 #pragma unroll 1
@@ -547,11 +581,18 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
         // the layer's bias, loaded while the GEMM runs
         const float bb = th[4 * H + (g - 1) * (H * H + H) + H * H + u];
         if (gtid == 0 && gate(0)) {
-          const uint32_t wa = smem_u32(Wimg + (g - 1) * kImg);
           const uint32_t ab = smem_u32(Aimg + (g - 1) * kImgH);
+          if constexpr (kWTmem) {
+            const uint32_t wt = tmem + 384u + 64u * (uint32_t)(g - 1);
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            mma_f16(d_tm, desc_kmajor(wa, k), desc_mnmajor(ab, k), id_fwd, k > 0);
+            for (int k = 0; k < 8; ++k)
+              mma_f16_ta(d_tm, wt + 8u * (uint32_t)k, desc_mnmajor(ab, k), id_fwd, k > 0);
+          } else {
+            const uint32_t wa = smem_u32(Wimg + (g - 1) * kImg);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              mma_f16(d_tm, desc_kmajor(wa, k), desc_mnmajor(ab, k), id_fwd, k > 0);
+          }
           mma_commit(smem_u32(bar_mma));
         }
         const bool ok_w = wait_mma();
