@@ -147,14 +147,27 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
   const float hg = 2.0f / (float)n;
   bool aborted = false;
 
-  // the layer-g GEMM of tile X: weights g (K-major) x image X (MN-major)
+  // The tiles' D use 384 of the 512 TMEM columns; the first kWT hidden layers'
+  // weights sit in the last 128 (the GEMMs' A operand), which spares those
+  // GEMMs the 32 KB weight read from shared memory.
+  constexpr int kWT = NG < 2 ? NG : 2;
+  // the layer-g GEMM of tile X: weights g (K-major; TMEM for g < kWT) x image X
+  // (MN-major)
   auto issue = [&](int X, int g) {
     if (gtid == 0) {
       fence_after_sync();
-      const uint32_t wa = smem_u32(Wimg + g * kImgE), ab = smem_u32(Aimg + X * kImgG);
+      const uint32_t ab = smem_u32(Aimg + X * kImgG);
+      if (g < kWT) {
+        const uint32_t wt = tmem + 384u + 64u * (uint32_t)g;
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        mma_f16(d_tm + kTP * X, desc_kmajor(wa, k), desc_mnmajor(ab, k), idf, k > 0);
+        for (int k = 0; k < 8; ++k)
+          mma_f16_ta(d_tm + kTP * X, wt + 8u * (uint32_t)k, desc_mnmajor(ab, k), idf, k > 0);
+      } else {
+        const uint32_t wa = smem_u32(Wimg + g * kImgE);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          mma_f16(d_tm + kTP * X, desc_kmajor(wa, k), desc_mnmajor(ab, k), idf, k > 0);
+      }
       mma_commit(smem_u32(bar_mma + X));
     }
     pending_bits |= 1u << X;
@@ -204,6 +217,12 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
         break;
       }
     }
+    // this network's first kWT weight layers into TMEM (the previous pass's
+    // GEMMs have all completed)
+    if (w < 4) stage_weights_tmem(Wimg, kImgE, tmem + ((uint32_t)(32 * w) << 16) + 384u, u, kWT);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
     int set = 0;
 #pragma unroll 1
     for (int64_t t = tb + grp; t < te; t += 2 * kX, ++set) {

@@ -203,27 +203,6 @@ int tc_supported(int H, int L) { return H == 128 && L >= 2 && L <= 4; }
 // whose exponent range is that of FP32): they hold mu and del themselves,
 // which saves the rescaling in every epilogue; the output stage converts to
 // the scaled convention of the residual rows.
-// Forward weights of one network from their shared-memory images into TMEM,
-// the forward GEMMs' A operand: layer g (1..ng) in the 64 columns from tw +
-// 64 (g-1), row u of W in the calling lane (tw carries the warp's lane
-// quadrant), W[u][2c] and W[u][2c+1] in column c.  Out of line: it runs twice
-// per launch and keeps its registers out of the hot loop's allocation.
-__device__ __noinline__ void stage_weights_tmem(const unsigned char* Wimg, uint32_t tw, int u,
-                                                int ng) {
-  for (int g = 1; g <= ng; ++g) {
-    const unsigned char* img = Wimg + (g - 1) * kImg;
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      uint32_t v[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c)
-        v[c] = *reinterpret_cast<const uint32_t*>(img + img_off(u, 2 * (16 * j + c)));
-      tmem_st16(tw + 64u * (uint32_t)(g - 1) + 16u * (uint32_t)j, v);
-    }
-  }
-  tmem_wait_st();
-}
-
 template <int L, bool BF, bool FAST, bool SCALED>
 __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
   pdl_enter();
@@ -465,7 +444,7 @@ __global__ void __launch_bounds__(512, 1) k_step_tc(ProbDev P, StepArgs a) {
       // this network's forward weights into TMEM: layer g in columns 384 +
       // 64 (g-1) .., unit u (row of W) in lane u, W[u][2c] and W[u][2c+1] in
       // column c; the previous segment's GEMMs have all completed
-      if (w < 4) stage_weights_tmem(Wimg, tmem + ((uint32_t)(32 * w) << 16) + 384u, u, NG);
+      if (w < 4) stage_weights_tmem(Wimg, kImg, tmem + ((uint32_t)(32 * w) << 16) + 384u, u, NG);
       fence_before_sync();
       __syncthreads();
       fence_after_sync();

@@ -142,6 +142,26 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+// Weights of hidden layers 1..nl from their shared-memory images (img_bytes
+// apart) into TMEM as the A operand of GEMMs: layer l in the 64 columns from
+// tw + 64 (l-1), row u of W in the calling lane (tw carries the warp's lane
+// quadrant), W[u][2c] and W[u][2c+1] in column c.  Out of line: it runs once
+// per network and keeps its registers out of the callers' hot loops.
+static __device__ __noinline__ void stage_weights_tmem(const unsigned char* img0, int img_bytes,
+                                                       uint32_t tw, int u, int nl) {
+  for (int l = 0; l < nl; ++l) {
+    const unsigned char* img = img0 + l * img_bytes;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      uint32_t v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        v[c] = *reinterpret_cast<const uint32_t*>(img + img_off(u, 2 * (16 * j + c)));
+      tmem_st16(tw + 64u * (uint32_t)l + 16u * (uint32_t)j, v);
+    }
+  }
+  tmem_wait_st();
+}
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
