@@ -17,9 +17,8 @@
 // on request).  In the BF16 training path the epilogues' FP32 arithmetic runs
 // on packed pairs (add/mul/fma .f32x2: two points per instruction, each
 // rounded as its scalar form).  The backward reuses the stored images: per
-// hidden layer one
-// input-gradient MMA (W^T gz, into the group's D columns) and one
-// weight-gradient MMA (gz A^T, K = 64) accumulated across all half-tiles of
+// hidden layer one input-gradient MMA (W^T gz, into the group's D columns)
+// and one weight-gradient MMA (gz A^T, K = 64) accumulated across all half-tiles of
 // the CTA in shared TMEM columns, in a fixed order of the half-tiles, so the
 // weight gradient never leaves the SM until the CTA's partial is written once
 // per network and is bitwise reproducible.
