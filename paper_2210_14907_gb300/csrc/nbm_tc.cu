@@ -16,17 +16,15 @@
 // transpose-reduction), the residual rows and the seeds stay FP32 (FP64 rows
 // on request).  In the BF16 training path the epilogues' FP32 arithmetic runs
 // on packed pairs (add/mul/fma .f32x2: two points per instruction, each
-// rounded as its scalar form).  The backward reuses the stored images: per
-// hidden layer one input-gradient MMA (W^T gz, into the group's D columns)
-// and one weight-gradient MMA (gz A^T, K = 64) accumulated across all half-tiles of
+// rounded as its scalar form).  The backward reuses the stored images: per hidden layer one
+// input-gradient MMA (W^T gz, into the group's D columns) and one
+// weight-gradient MMA (gz A^T, K = 64) accumulated across all half-tiles of
 // the CTA in shared TMEM columns, in a fixed order of the half-tiles, so the
 // weight gradient never leaves the SM until the CTA's partial is written once
 // per network and is bitwise reproducible.
 //
 // Shared memory: (L-1) weight images of 32 KB + 2 x L operand images of 16 KB.
-// TMEM: 2 x 64 columns for D + 128 per hidden layer for the weight gradient;
-// with two hidden layers the last 128 of the 512 hold the forward weights
-// (64 columns per 128 x 128 16-bit matrix), the forward GEMMs' A operand.
+// TMEM: 2 x 64 columns for D + 128 per hidden layer for the weight gradient.
 // Every wait is bounded.  The group barrier that ends each phase agrees on an
 // abort; an aborted CTA gives its MMAs and copies in flight a short bounded
 // wait before it frees TMEM.
