@@ -29,7 +29,7 @@ constexpr int kImgE = 32768;
 // 64-point tiles in flight per warp group of the tensor-core evaluation, and the
 // TMEM columns they take (2 groups x kEvalTiles x 64, rounded up to a power of 2)
 constexpr int kEvalTiles = 3;
-constexpr int kEvalTmemCols = 2 * kEvalTiles * 64 <= 256 ? 256 : 512;
+constexpr int kEvalTmemCols = 512;  // the tiles' D, then weights (see kWT)
 
 // side of a grid node, decided as the FP64 level set would (FP32 first)
 __device__ inline int node_phase(const ProbDev& P, float x, float y, float z) {
@@ -147,10 +147,12 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
   const float hg = 2.0f / (float)n;
   bool aborted = false;
 
-  // The tiles' D use 384 of the 512 TMEM columns; the first kWT hidden layers'
-  // weights sit in the last 128 (the GEMMs' A operand), which spares those
-  // GEMMs the 32 KB weight read from shared memory.
-  constexpr int kWT = NG < 2 ? NG : 2;
+  // The weights of the first kWT hidden layers sit in the TMEM columns past
+  // the tiles' D (64 columns per layer; the GEMMs' A operand), which spares
+  // those GEMMs the 32 KB weight read from shared memory.
+  constexpr uint32_t kWCol = 2 * kX * kTP;  // first column past the tiles' D
+  constexpr int kFreeLayers = (kEvalTmemCols - (int)kWCol) / 64;
+  constexpr int kWT = NG < kFreeLayers ? NG : kFreeLayers;
   // the layer-g GEMM of tile X: weights g (K-major; TMEM for g < kWT) x image X
   // (MN-major)
   auto issue = [&](int X, int g) {
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
       fence_after_sync();
       const uint32_t ab = smem_u32(Aimg + X * kImgG);
       if (g < kWT) {
-        const uint32_t wt = tmem + 384u + 64u * (uint32_t)g;
+        const uint32_t wt = tmem + kWCol + 64u * (uint32_t)g;
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           mma_f16_ta(d_tm + kTP * X, wt + 8u * (uint32_t)k, desc_mnmajor(ab, k), idf, k > 0);
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(512, 1) k_eval_tc(ProbDev P, const float* __re
     }
     // this network's first kWT weight layers into TMEM (the previous pass's
     // GEMMs have all completed)
-    if (w < 4) stage_weights_tmem(Wimg, kImgE, tmem + ((uint32_t)(32 * w) << 16) + 384u, u, kWT);
+    if (w < 4) stage_weights_tmem(Wimg, kImgE, tmem + ((uint32_t)(32 * w) << 16) + kWCol, u, kWT);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
