@@ -51,13 +51,15 @@ FUSED_SOURCES = ("paper_2210_14907_gb300/csrc/nbm_tc.cu", "paper_2210_14907_gb30
 # libnbm kernel launches per timed step.  One nbm_train_steps call of one C2
 # step: k_sample_classify (its extra blocks restage the weights), k_scatter
 # (up to 2048 blocks of points it also does the block-count scan, so no
-# k_scan_counts); k_cut_geometry, k_gather_tiles; k_step_tc (cut-cell
-# forward), k_cut_residual; k_step_tc (fused train step); k_loss,
-# k_reduce_adam.  The data-parallel step (N > 1) runs the same chain through
-# nbm_loss_grad_shard (k_reduce_adam writes the gradient only) and then
-# k_adam: one more.
-LAUNCHES_PER_STEP = 9
-LAUNCHES_PER_DP_STEP = 10
+# k_scan_counts; it writes the uncut points' tile records); k_cut_geometry
+# (the cut cells' records); k_step_tc (cut-cell forward), k_cut_residual;
+# k_step_tc (fused train step); k_reduce_adam (loss, gradient, update).  The
+# data-parallel step (N > 1) runs the same chain through nbm_loss_grad_shard
+# (k_reduce_adam writes the loss and gradient only) and then k_adam: one more.
+# (Batches above 2048 blocks of 256 points, such as the 1M-point secondary
+# workload, add k_scan_counts and k_gather_tiles, which writes the records.)
+LAUNCHES_PER_STEP = 7
+LAUNCHES_PER_DP_STEP = 8
 # FP32 FFMA peak of the plain path's roofline: 152 SMs x 128 FP32 lanes x
 # 2 FLOP per FMA x the SM clock (GB300's 2070 MHz maximum, the clock the
 # timed region ran at).

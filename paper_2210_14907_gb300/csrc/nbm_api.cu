@@ -93,7 +93,7 @@ void make_prob_dev(const nbm_problem_desc& d, ProbDev& P, int level) {
 
 static void ws_free(Workspace& w) {
   void* ptrs[] = {w.x, w.y, w.z, w.cls, w.blockcnt, w.list_minus, w.list_plus, w.cut_pt, w.rec,
-                  w.rec_cut,
+                  w.rec_cut, w.cut_rpos,
                   w.counters, w.cut, w.cut_out, w.cut_seed, w.loss_part, w.cut_loss_part, w.loss,
                   w.gpart, w.gpart_flag, w.wt, w.wtc, w.grad, w.step, w.status, w.loss_acc,
                   w.gacc};
@@ -142,6 +142,8 @@ static int ws_reserve(Problem& pb, int64_t n) {
   NBM_CUDA(dalloc(w.grad, 2 * (size_t)pb.p_net));
   NBM_CUDA(dalloc(w.step, 1));
   NBM_CUDA(dalloc(w.status, 1));
+  // last, so that the buffers above keep the placement they had without it
+  NBM_CUDA(dalloc(w.cut_rpos, cap));
   NBM_CUDA(cudaMemset(w.status, 0, sizeof(int)));
   NBM_CUDA(cudaMemset(w.step, 0, sizeof(int64_t)));
   w.cap_n = cap;
@@ -270,11 +272,15 @@ static int front_stages(Problem& pb, const ProbDev& P, const float* params, cons
   NvtxRange r("nbm.front (sample, cell geometry, cut rows)");
   const int64_t nt = n_total > 0 ? n_total : n;
   // prep_w: the same launch restages the hidden weights from params (the
-  // first pass of a call; later steps get them from the Adam kernel)
+  // first pass of a call; later steps get them from the Adam kernel).  The
+  // tensor-core paths' tile records come from the scatter (uncut points) and
+  // the cut geometry (cut cells), or for large batches from a gather after both.
+  const bool tiles = pb.desc.precision != NBM_PREC_FP32;
   NBM_CUDA(launch_sample_classify(P, pts, seed, step_dev, step_host, n, band_count(pb.desc, nt), w,
-                                  st, first, nt, prep_w ? params : nullptr, pb.desc.precision));
-  NBM_CUDA(launch_cut_geometry(P, n, w, st));
-  if (pb.desc.precision != NBM_PREC_FP32) NBM_CUDA(launch_gather_tiles(P, n, w, st));
+                                  st, first, nt, prep_w ? params : nullptr, pb.desc.precision,
+                                  tiles));
+  NBM_CUDA(launch_cut_geometry(P, n, w, st, tiles));
+  if (tiles && !tiles_in_scatter(n)) NBM_CUDA(launch_gather_tiles(P, n, w, st));
   StepArgs a = base_args(pb, params, MODE_CUT_FWD, 1.0f / (float)nt);
   // The fine-h mode (FP64 rows) evaluates the cut cells' networks on the FP32
   // path: their jump rows U+(x_G) - U-(x_G) - alpha difference two O(1) network

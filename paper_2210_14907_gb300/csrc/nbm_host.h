@@ -101,6 +101,7 @@ struct Workspace {
   CutRec* cut = nullptr;
   PRec* rec = nullptr;      // [2 cap + 64]
   PRec* rec_cut = nullptr;  // [cap + 32]
+  int2* cut_rpos = nullptr; // [cap] a cut cell's record slots in rec (minus, plus)
   float* cut_out = nullptr;
   float* cut_seed = nullptr;
   double* loss_part = nullptr;      // [grid]
@@ -156,12 +157,21 @@ int check_aligned(const void* ptr, size_t align, const char* name);
 // Sampling and classification of a step's points, then the phase lists.
 // prep_params non-NULL: extra blocks of the same launch restage the hidden
 // weights from those parameters (prec: the tensor-core image's 16-bit type).
+// tiles: the scatter also writes the tensor-core kernel's tile records of the
+// uncut points and their padding, and each cut cell's record slots.
 cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64_t seed,
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st,
                                    int64_t first = 0, int64_t n_total = 0,
-                                   const float* prep_params = nullptr, int prec = 0);
-cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
+                                   const float* prep_params = nullptr, int prec = 0,
+                                   bool tiles = false);
+// tiles: also the cut cells' tile records (slots from the scatter's tiles pass)
+cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st,
+                                bool tiles = false);
+// Whether a batch of n points gets its tile records from the scatter and the
+// cut geometry (true: up to 2048 point blocks) or from launch_gather_tiles,
+// which runs after the cut geometry (larger batches).
+bool tiles_in_scatter(int64_t n);
 cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st);
 cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool want_seeds,
                                 float* r2_out, Workspace& ws, cudaStream_t st);

@@ -34,6 +34,7 @@ constexpr size_t kScratchBytes =
     + align256(kStaticMaxPoints * sizeof(CutRec))          // cut cells
     + align256((2 * kStaticMaxPoints + 64) * sizeof(PRec))  // tile records, phase lists
     + align256((kStaticMaxPoints + 32) * sizeof(PRec))      // tile records, cut list
+    + align256(kStaticMaxPoints * 8)                       // cut cells' record slots
     + 2 * align256(kStaticMaxPoints * 16 * 4)              // cut outputs and seeds
     + align256(kStaticMaxGrid * 8)                         // loss partials
     + align256(((kStaticMaxPoints + 127) / 128) * 8)       // cut loss partials
@@ -134,6 +135,7 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
   w.cut = carve<CutRec>(cur, kStaticMaxPoints * sizeof(CutRec));
   w.rec = carve<PRec>(cur, (2 * kStaticMaxPoints + 64) * sizeof(PRec));
   w.rec_cut = carve<PRec>(cur, (kStaticMaxPoints + 32) * sizeof(PRec));
+  w.cut_rpos = carve<int2>(cur, kStaticMaxPoints * 8);
   w.cut_out = carve<float>(cur, kStaticMaxPoints * 16 * 4);
   w.cut_seed = carve<float>(cur, kStaticMaxPoints * 16 * 4);
   w.loss_part = carve<double>(cur, kStaticMaxGrid * 8);
@@ -157,11 +159,14 @@ extern "C" int nbm_loss_grad_static(nbm_problem* p, const float* params, const f
       (d.geometry == NBM_GEOM_SPHERE || d.geometry == NBM_GEOM_FLOWER)
           ? (int64_t)floor(d.band_fraction * (double)n + 0.5)
           : 0;
-  // the sampling launch also restages the hidden weights from params
+  // the sampling launch also restages the hidden weights from params; the
+  // scatter and the cut geometry write the tensor-core tile records
+  const bool tiles = prec != NBM_PREC_FP32;
   if (e == cudaSuccess)
-    e = launch_sample_classify(P, pts, seed, nullptr, step, n, n_band, w, st, 0, 0, params, prec);
-  if (e == cudaSuccess) e = launch_cut_geometry(P, n, w, st);
-  if (e == cudaSuccess && prec != NBM_PREC_FP32) e = launch_gather_tiles(P, n, w, st);
+    e = launch_sample_classify(P, pts, seed, nullptr, step, n, n_band, w, st, 0, 0, params, prec,
+                               tiles);
+  if (e == cudaSuccess) e = launch_cut_geometry(P, n, w, st, tiles);
+  if (e == cudaSuccess && tiles && !tiles_in_scatter(n)) e = launch_gather_tiles(P, n, w, st);
   StepArgs a;
   memset(&a, 0, sizeof(a));
   a.x = w.x;

@@ -22,6 +22,9 @@
 namespace nbm {
 
 constexpr int kBlk = 256;
+// Batches of up to this many point blocks: the scatter sums the block counts
+// itself and writes the tile records (else k_scan_counts and k_gather_tiles).
+constexpr int kScatterPrefixBlocks = 2048;
 
 // ------------------------------------------------------------------------
 // Collocation points.  Uniform: lattice -1 + k 2^-22, k = 1 + floor(r (2^23-1)
@@ -221,36 +224,89 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int* blockcnt, int nb, int
   }
 }
 
+// Record of an uncut point of phase s (tile layout of the tensor-core kernel):
+// the point and the source term f^s(p) of its balance row (Sec. 3), so that
+// the fused kernel's residual stage does no transcendental arithmetic.
+__device__ inline PRec uncut_record(const ProbDev& P, int s, int pt, float x, float y, float z) {
+  PRec o;
+  o.x = x;
+  o.y = y;
+  o.z = z;
+  o.pt = pt;
+  o.cutj = -1;
+  o.gz = 0.f;
+  if (P.fp64) {  // FP64 rows: f^s(p) as a two-float sum gx + gy
+    const double f = rhs_f<double>(P, s, (double)x, (double)y, (double)z);
+    o.gx = (float)f;
+    o.gy = (float)(f - (double)o.gx);
+  } else {
+    o.gx = rhs_f<float>(P, s, x, y, z);
+    o.gy = 0.f;
+  }
+  return o;
+}
+
+// A record is 32 bytes at a 32-byte aligned address: two 16-byte stores.
+__device__ inline void store_record(PRec* dst, const PRec& o) {
+  float4* d = reinterpret_cast<float4*>(dst);
+  d[0] = make_float4(o.x, o.y, o.z, o.gx);
+  d[1] = make_float4(o.gy, o.gz, __int_as_float(o.pt), __int_as_float(o.cutj));
+}
+
+__device__ inline PRec pad_record() {
+  PRec o;
+  o.x = o.y = o.z = o.gx = o.gy = o.gz = 0.f;
+  o.pt = -1;
+  o.cutj = -1;
+  return o;
+}
+
 // Stable scatter: list order = point order.  Entry >= 0: uncut point index;
 // entry < 0: cut cell -(cut_id + 1).  scanned: blockcnt holds the exclusive
 // offsets (k_scan_counts ran).  Otherwise (few blocks: the scan's launch
 // costs more than the sums) each block adds up the per-block counts of the
 // blocks before it (integer sums: exact in any order) for its offsets in the
 // three lists, and the last block writes the totals counters[0..2].
-__global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
+// rec != nullptr (tensor-core paths): the tile records too.  rec holds the
+// minus list, then the plus list, each padded to a multiple of 16 records
+// (the plus list starts at 16 ceil(n-/16)); rec_cut the cut list, padded the
+// same way.  An uncut point writes its own record; a cut point writes its two
+// record slots to cut_rpos, and k_cut_geometry writes the cut cell's three
+// records once its interface point is known; the last block writes the
+// padding.  Every slot up to the padded ends is written each step.
+__global__ void __launch_bounds__(kBlk) k_scatter(const ProbDev P, const uint8_t* cls, int64_t n,
                                                   const int* blockcnt, int nb, int scanned,
                                                   int* list_m, int* list_p, int* cut_pt,
-                                                  int* counters) {
+                                                  int* counters, const float* X, const float* Y,
+                                                  const float* Z, PRec* rec, PRec* rec_cut,
+                                                  int2* cut_rpos) {
   pdl_enter();
-  __shared__ int boff[3][kBlk / 32];
+  __shared__ int boff[4][kBlk / 32];
   __shared__ int wsum[3][kBlk / 32];
   if (!scanned) {
-    int s0 = 0, s1 = 0, s2 = 0;
-    for (int j = threadIdx.x; j < (int)blockIdx.x; j += kBlk) {
-      s0 += blockcnt[j];
-      s1 += blockcnt[nb + j];
-      s2 += blockcnt[2 * nb + j];
+    // s*: counts of the blocks before this one; t0: all blocks' minus count
+    int s0 = 0, s1 = 0, s2 = 0, t0 = 0;
+    for (int j = threadIdx.x; j < nb; j += kBlk) {
+      const int c0 = blockcnt[j];
+      t0 += c0;
+      if (j < (int)blockIdx.x) {
+        s0 += c0;
+        s1 += blockcnt[nb + j];
+        s2 += blockcnt[2 * nb + j];
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       s0 += __shfl_xor_sync(0xffffffffu, s0, o);
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      t0 += __shfl_xor_sync(0xffffffffu, t0, o);
     }
     if ((threadIdx.x & 31) == 0) {
       boff[0][threadIdx.x >> 5] = s0;
       boff[1][threadIdx.x >> 5] = s1;
       boff[2][threadIdx.x >> 5] = s2;
+      boff[3][threadIdx.x >> 5] = t0;
     }
   }
   int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
@@ -266,19 +322,34 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
     if (lane == 0) wsum[m][w] = __popc(b);
   }
   __syncthreads();
-  int pos[3];
+  int pos[3], tot[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    int off = 0;
+    int off = 0, own = 0;
     if (scanned) {
       off = blockcnt[(int64_t)m * nb + blockIdx.x];
     } else {
       for (int k = 0; k < kBlk / 32; ++k) off += boff[m][k];
-      if (blockIdx.x == nb - 1 && threadIdx.x == 0)
-        counters[m] = off + blockcnt[(int64_t)m * nb + blockIdx.x];
     }
+    for (int k = 0; k < kBlk / 32; ++k) own += wsum[m][k];
+    tot[m] = off + own;  // the list's length when this is the last block
+    if (!scanned && blockIdx.x == nb - 1 && threadIdx.x == 0) counters[m] = tot[m];
     for (int k = 0; k < w; ++k) off += wsum[m][k];
     pos[m] = off + rank[m];
+  }
+  int nm = 0;  // minus-list length: the plus list's records start at 16 ceil(nm/16)
+  if (scanned) {
+    nm = counters[0];
+  } else {
+    for (int k = 0; k < kBlk / 32; ++k) nm += boff[3][k];
+  }
+  const int base_p = 16 * ((nm + 15) / 16);
+  if (rec && blockIdx.x == nb - 1 && threadIdx.x < 48) {
+    const int m = threadIdx.x >> 4, k = threadIdx.x & 15;
+    const int len = tot[m], slot = len + k;
+    if (slot < 16 * ((len + 15) / 16)) {
+      store_record(m == 2 ? rec_cut + slot : rec + (m == 1 ? base_p : 0) + slot, pad_record());
+    }
   }
   if (c < 0) return;
   int cut_id = pos[2];
@@ -286,6 +357,13 @@ __global__ void __launch_bounds__(kBlk) k_scatter(const uint8_t* cls, int64_t n,
   int e = c == 2 ? -(cut_id + 1) : (int)i;
   if (f[0]) list_m[pos[0]] = e;
   if (f[1]) list_p[pos[1]] = e;
+  if (!rec) return;
+  if (c == 2) {
+    cut_rpos[cut_id] = make_int2(pos[0], base_p + pos[1]);
+  } else {
+    store_record(rec + (c == 0 ? pos[0] : base_p + pos[1]),
+                 uncut_record(P, c, (int)i, X[i], Y[i], Z[i]));
+  }
 }
 
 // One cut cell per 8 lanes: corner values, tetrahedra and faces are spread
@@ -327,13 +405,15 @@ __device__ inline void cell_pieces(int k, T Fk, int base, Corner corner, T& vneg
 
 // Cut cell `id` of the list (nc cells) on the 8 lanes of a warp's quarter; the
 // whole warp calls it (full-mask shuffles), lanes past the list compute on
-// cell 0's point and store nothing.
+// cell 0's point and store nothing.  rec != nullptr: lanes 0..2 also write the
+// cell's three tile records (cut list, minus and plus list slots from rpos).
 template <bool FP64>
 __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float* X,
                                                   const float* Y,
                                                   const float* Z,
                                                   const int* cut_pt, CutRec* cut,
-                                                  int id, int nc) {
+                                                  int id, int nc, PRec* rec, PRec* rec_cut,
+                                                  const int2* rpos) {
   const unsigned full = 0xffffffffu;
   const int k = threadIdx.x & 7, base = (threadIdx.x & 31) & ~7;
   const bool live = id < nc;
@@ -460,6 +540,19 @@ __device__ __forceinline__ void cut_cell_geometry(const ProbDev& P, const float*
     f1 = f1f;
   }
   if (!live) return;
+  if (rec && k < 3) {
+    // the interface point rounded as the fused kernel reads it
+    PRec o;
+    o.x = X[i];
+    o.y = Y[i];
+    o.z = Z[i];
+    o.gx = (float)xg[0];
+    o.gy = (float)xg[1];
+    o.gz = (float)xg[2];
+    o.pt = i;
+    o.cutj = 2 * id + (has_area ? 1 : 0);
+    store_record(k == 0 ? rec_cut + id : rec + (k == 1 ? rpos[id].x : rpos[id].y), o);
+  }
   CutRec* r = cut + id;
   if (k < 6) r->Am[k] = Afk_d;
   if (k == 0) {
@@ -485,12 +578,15 @@ __global__ void __launch_bounds__(128) k_cut_geometry(ProbDev P, const float* X,
                                                       const float* Z,
                                                       const int* cut_pt,
                                                       const int* counters,
-                                                      CutRec* cut) {
+                                                      CutRec* cut, PRec* rec,
+                                                      PRec* rec_cut,
+                                                      const int2* rpos) {
   pdl_enter();
   const int nc = counters[2];
   for (int cell0 = blockIdx.x * 16; cell0 < nc; cell0 += gridDim.x * 16) {
     if (cell0 + 4 * (int)(threadIdx.x >> 5) >= nc) break;  // this warp's cells are past the list
-    cut_cell_geometry<FP64>(P, X, Y, Z, cut_pt, cut, cell0 + (int)(threadIdx.x >> 3), nc);
+    cut_cell_geometry<FP64>(P, X, Y, Z, cut_pt, cut, cell0 + (int)(threadIdx.x >> 3), nc, rec,
+                            rec_cut, rpos);
   }
 }
 
@@ -694,75 +790,50 @@ __global__ void __launch_bounds__(32) k_cut_residual(ProbDev P, const float* X, 
 }
 
 // ------------------------------------------------------------------------
-// Tile records of the tensor-core kernel: the minus list, then the plus list
-// (each padded to a multiple of 16 records), and the cut list on its own.  An
-// uncut point's record also carries the source term f^s(p) of its balance row
-// (Sec. 3), so that the fused kernel's residual stage does no transcendental
-// arithmetic.  One thread per record; the grid covers the worst case.
+// Tile records in list order, one thread per record, for batches of more
+// than 2048 point blocks (the scan path).  There the records and the cut
+// cells' geometry together outgrow L2, and records written in list order
+// right before the cut-cell forward and the fused kernel read them cost less
+// than records written by the scatter and the cut geometry as they go.  The
+// same records as those two write: rec = minus list, then plus list (each
+// padded to a multiple of 16), rec_cut = cut list (padded).
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gather_tiles(const ProbDev P,
-                                                      const int* counters,
-                                                      const int* list_m,
-                                                      const int* list_p,
-                                                      const int* cut_pt,
-                                                      const float* X,
-                                                      const float* Y,
-                                                      const float* Z,
+__global__ void __launch_bounds__(256) k_gather_tiles(const ProbDev P, const int* counters,
+                                                      const int* list_m, const int* list_p,
+                                                      const int* cut_pt, const float* X,
+                                                      const float* Y, const float* Z,
                                                       const CutRec* cut, PRec* rec,
-                                                      PRec* rec_cut, int64_t cap) {
+                                                      PRec* rec_cut) {
   pdl_enter();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nm = counters[0], np = counters[1], nc = counters[2];
-  const int64_t T0 = (nm + 15) / 16, T1 = (np + 15) / 16, Tc = (nc + 15) / 16;
-  // s: phase of the list (0 minus, 1 plus); uncut points carry f^s(p)
-  auto fill = [&](int e, int s, PRec& o) {
-    int pt, cid = -1;
-    if (e >= 0) {
-      pt = e;
-    } else {
-      cid = -e - 1;
-      pt = cut_pt[cid];
-    }
+  const int64_t base_p = 16 * (int64_t)((nm + 15) / 16);
+  const int64_t end_p = base_p + 16 * (int64_t)((np + 15) / 16);
+  // the record of list entry e (>= 0 uncut point of phase s, < 0 cut cell)
+  auto entry = [&](int e, int s) {
+    if (e >= 0) return uncut_record(P, s, e, X[e], Y[e], Z[e]);
+    const int id = -e - 1, pt = cut_pt[id];
+    const CutRec& c = cut[id];
+    PRec o;
     o.x = X[pt];
     o.y = Y[pt];
     o.z = Z[pt];
+    o.gx = (float)c.xg[0];
+    o.gy = (float)c.xg[1];
+    o.gz = (float)c.xg[2];
     o.pt = pt;
-    if (cid >= 0) {
-      const CutRec& c = cut[cid];
-      o.gx = (float)c.xg[0];
-      o.gy = (float)c.xg[1];
-      o.gz = (float)c.xg[2];
-      o.cutj = 2 * cid + (c.has_jump ? 1 : 0);
-    } else if (P.fp64) {
-      const double f = rhs_f<double>(P, s, (double)o.x, (double)o.y, (double)o.z);
-      o.gx = (float)f;
-      o.gy = (float)(f - (double)o.gx);
-      o.gz = 0.f;
-      o.cutj = -1;
-    } else {
-      o.gx = rhs_f<float>(P, s, o.x, o.y, o.z);
-      o.gy = o.gz = 0.f;
-      o.cutj = -1;
-    }
+    o.cutj = 2 * id + (c.has_jump ? 1 : 0);
+    return o;
   };
-  PRec o;
-  o.x = o.y = o.z = o.gx = o.gy = o.gz = 0.f;
-  o.pt = -1;
-  o.cutj = -1;
-  if (r < 16 * (T0 + T1)) {
-    const int64_t t = r / 16, k = r % 16;
-    const int64_t slot = (t < T0 ? t : t - T0) * 16 + k;
-    if (t < T0 ? slot < nm : slot < np) fill((t < T0 ? list_m : list_p)[slot], t < T0 ? 0 : 1, o);
-    rec[r] = o;
+  if (r < end_p) {
+    const bool minus = r < base_p;
+    const int64_t slot = minus ? r : r - base_p;
+    const bool live = slot < (minus ? nm : np);
+    store_record(rec + r, live ? entry((minus ? list_m : list_p)[slot], minus ? 0 : 1)
+                                : pad_record());
   }
-  if (r < 16 * Tc) {
-    PRec c;
-    c.x = c.y = c.z = c.gx = c.gy = c.gz = 0.f;
-    c.pt = -1;
-    c.cutj = -1;
-    if (r < nc) fill(-(int)r - 1, 0, c);
-    rec_cut[r] = c;
-  }
+  if (r < 16 * (int64_t)((nc + 15) / 16))
+    store_record(rec_cut + r, r < nc ? entry(-(int)r - 1, 0) : pad_record());
 }
 
 // Standalone restage (grid evaluation); the training paths restage inside
@@ -777,45 +848,81 @@ __global__ void k_prep_weights(ProbDev P, const float* params, float* wt, void* 
 // Finish: loss (fixed-order sums), then gradient reduction over CTA partials
 // (fixed order) and, when training, Adam (Kingma & Ba, bias-corrected).
 // ------------------------------------------------------------------------
-// Loss of the step: the sum of the partials times 1/N.  With refinement
-// levels, the levels' losses are summed in *loss_acc (acc_in: add the levels
-// done so far; last == 0: only accumulate) and the step is finished after the
-// last level.
-__global__ void k_loss(const double* lp, int nlp, const double* clp,
-                       int nclp, double scale, double* loss, int64_t* step, float* loss_hist,
-                       int64_t hist_base, int* status,
-                       double* loss_acc, int acc_in, int last) {
-  pdl_enter();
-  __shared__ double red[8];
+// Where the loss of the step goes.  With refinement levels, the levels' losses
+// are summed in *loss_acc (acc_in: add the levels done so far; last == 0: only
+// accumulate) and the step is finished after the last level.
+struct LossOut {
+  const double* lp;  // [nlp] loss partials of the fused kernel's CTAs
+  int nlp;
+  const double* clp;  // [nclp] loss partials of the cut-row blocks
+  int nclp;
+  double scale;       // 1/N
+  double* loss;
+  int64_t* step;      // non-NULL: advance the device step counter
+  float* loss_hist;
+  int64_t hist_base;
+  int* status;
+  double* loss_acc;
+  int acc_in, last;
+};
+
+// Sum of the step's loss partials on a block of 256 threads, in three parts
+// so that a caller can overlap the loads with other work: thread-strided
+// partial sums (loss_thread_sum), warp shuffles into red8 (loss_warp_sum), a
+// __syncthreads by the caller, then the 8 warp sums in a fixed order
+// (finish_loss).  Every block that does this gets the same value.
+__device__ inline double loss_thread_sum(const LossOut& o) {
   double s = 0.0;
-  for (int j = threadIdx.x; j < nlp; j += 256) s += lp[j];
-  for (int j = threadIdx.x; j < nclp; j += 256) s += clp[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t8 = red[0];
-    for (int w = 1; w < 8; ++w) t8 += red[w];  // fixed order: deterministic
-    double L = t8 * scale;
-    if (acc_in) L += *loss_acc;
-    if (!last) {
-      *loss_acc = L;
-      return;
-    }
-    *loss = L;
-    if (!isfinite(L)) atomicOr(status, 1);
-    if (step) {
-      int64_t t = *step + 1;
-      *step = t;
-      if (loss_hist) loss_hist[t - hist_base - 1] = (float)L;
-    }
-  }
+  for (int j = threadIdx.x; j < o.nlp; j += 256) s += o.lp[j];
+  for (int j = threadIdx.x; j < o.nclp; j += 256) s += o.clp[j];
+  return s;
 }
 
-// Gradient of the step (fixed CTA order), then Adam.  With refinement levels
-// the levels' gradients are summed in gacc: gacc_in (levels done so far) is
-// added, and a level that is not the last stores the sum in gacc_out and stops.
+__device__ inline void loss_warp_sum(double s, double* red8) {
+#pragma unroll
+  for (int q = 16; q > 0; q >>= 1) s += __shfl_xor_sync(0xffffffffu, s, q);
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = s;
+}
+
+// L = scale * (sum of the partials) (+ the earlier levels' sum) from the warp
+// sums in red8; with `store`, thread 0 stores it (and finishes the step when
+// `last`).
+__device__ inline double finish_loss(const LossOut& o, const double* red8, bool store) {
+  double t8 = red8[0];
+  for (int w = 1; w < 8; ++w) t8 += red8[w];
+  double L = t8 * o.scale;
+  if (o.acc_in) L += *o.loss_acc;
+  if (!store || threadIdx.x != 0) return L;
+  if (!o.last) {
+    *o.loss_acc = L;
+    return L;
+  }
+  *o.loss = L;
+  if (!isfinite(L)) atomicOr(o.status, 1);
+  if (o.step) {
+    const int64_t t = *o.step + 1;
+    *o.step = t;
+    if (o.loss_hist) o.loss_hist[t - o.hist_base - 1] = (float)L;
+  }
+  return L;
+}
+
+// Loss only (a step with neither gradient nor update).
+__global__ void k_loss(LossOut o) {
+  pdl_enter();
+  __shared__ double red[8];
+  loss_warp_sum(loss_thread_sum(o), red);
+  __syncthreads();
+  finish_loss(o, red, true);
+}
+
+// Loss and gradient of the step (fixed CTA order), then Adam.  Block 0 stores
+// the loss (finish_loss); every block of an Adam step that is the last level
+// sums the same partials in the same order itself, to skip the update of a
+// non-finite step without waiting for block 0.  With refinement levels the
+// levels' gradients are summed in gacc: gacc_in (levels done so far) is
+// added, and a level that is not the last stores the sum in gacc_out and stops
+// (only block 0 then touches the loss: it alone reads and writes *loss_acc).
 // Block of 256 threads on 128 consecutive parameters of one network: warp cg
 // sums the per-CTA partial slices cg, cg + 8, ... (lane l: parameters 4l..4l+3
 // of the block, one float4 per slice, every slice loaded and the slice of a
@@ -828,11 +935,15 @@ __global__ void __launch_bounds__(256) k_reduce_adam(ProbDev P, int grid, int nb
                                                      float* grad_out, float* params, float* m,
                                                      float* v, float lr, float b1, float b2,
                                                      float eps, float c1, float c2,
-                                                     const double* loss, float* wt, void* wtc,
+                                                     LossOut lo, float* wt, void* wtc,
                                                      int prec, const float* gacc_in,
                                                      float* gacc_out) {
   pdl_enter();
   __shared__ float4 red[8][32];
+  __shared__ double red8[8];
+  // the loss partials' loads overlap the gradient slices' loads
+  const bool want_loss = blockIdx.x == 0 || (params && lo.last);  // block-uniform
+  const double ls = want_loss ? loss_thread_sum(lo) : 0.0;
   const int pn = (int)P.p_net;
   const int s = blockIdx.x >= nb_net ? 1 : 0;
   const int blk = blockIdx.x - s * nb_net;
@@ -852,7 +963,9 @@ __global__ void __launch_bounds__(256) k_reduce_adam(ProbDev P, int grid, int nb
     }
   }
   red[cg][lane] = part;
+  if (want_loss) loss_warp_sum(ls, red8);
   __syncthreads();
+  const double L = want_loss ? finish_loss(lo, red8, blockIdx.x == 0) : 0.0;
   const int t = threadIdx.x;
   const int jj = blk * 128 + t;
   if (t >= 128 || jj >= pn) return;
@@ -867,7 +980,7 @@ __global__ void __launch_bounds__(256) k_reduce_adam(ProbDev P, int grid, int nb
   }
   if (grad_out) grad_out[j] = g;
   if (!params) return;
-  if (!isfinite(*loss)) return;  // non-finite step: skip the update
+  if (!isfinite(L)) return;  // non-finite step: skip the update
   float mj = b1 * m[j] + (1.f - b1) * g;
   float vj = b2 * v[j] + (1.f - b2) * g * g;
   m[j] = mj;
@@ -938,7 +1051,7 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
                                    const int64_t* step_dev, int64_t step_host, int64_t n,
                                    int64_t n_band, Workspace& ws, cudaStream_t st,
                                    int64_t first, int64_t n_total, const float* prep_params,
-                                   int prec) {
+                                   int prec, bool tiles) {
   int nb = (int)((n + kBlk - 1) / kBlk);
   const int npb = prep_params ? prep_weight_blocks(P) : 0;
   cudaError_t e = launch_pdl(k_sample_classify, dim3(nb + npb), dim3(kBlk), 0, st, P, pts_in,
@@ -946,25 +1059,42 @@ cudaError_t launch_sample_classify(const ProbDev& P, const float* pts_in, uint64
                              ws.blockcnt, nb, first, n_total > 0 ? n_total : n, prep_params,
                              ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec);
   // up to 2048 blocks the scatter blocks sum the earlier blocks' counts
-  // themselves (at most 6 K integers each); beyond, one scan kernel
-  const int scanned = nb > 2048;
+  // themselves (at most 6 K integers each) and write the tile records;
+  // beyond, one scan kernel, and the records come from k_gather_tiles
+  const int scanned = tiles_in_scatter(n) ? 0 : 1;
+  if (scanned) tiles = false;
   if (e == cudaSuccess && scanned)
     e = launch_pdl(k_scan_counts, dim3(1), dim3(1024), 0, st, ws.blockcnt, nb, ws.counters);
   if (e == cudaSuccess)
-    e = launch_pdl(k_scatter, dim3(nb), dim3(kBlk), 0, st, (const uint8_t*)ws.cls, n,
+    e = launch_pdl(k_scatter, dim3(nb), dim3(kBlk), 0, st, P, (const uint8_t*)ws.cls, n,
                    (const int*)ws.blockcnt, nb, scanned, ws.list_minus, ws.list_plus,
-                   ws.cut_pt, ws.counters);
+                   ws.cut_pt, ws.counters, (const float*)ws.x, (const float*)ws.y,
+                   (const float*)ws.z, tiles ? ws.rec : nullptr, ws.rec_cut, ws.cut_rpos);
   return e;
 }
 
-cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
+bool tiles_in_scatter(int64_t n) { return (n + kBlk - 1) / kBlk <= kScatterPrefixBlocks; }
+
+cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
+  const int64_t worst = 2 * n + 32;  // both lists, padded
+  return launch_pdl(k_gather_tiles, dim3((unsigned)((worst + 255) / 256)), dim3(256), 0, st, P,
+                    (const int*)ws.counters, (const int*)ws.list_minus,
+                    (const int*)ws.list_plus, (const int*)ws.cut_pt, (const float*)ws.x,
+                    (const float*)ws.y, (const float*)ws.z, (const CutRec*)ws.cut, ws.rec,
+                    ws.rec_cut);
+}
+
+cudaError_t launch_cut_geometry(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st,
+                                bool tiles) {
+  if (!tiles_in_scatter(n)) tiles = false;
   // 8 lanes per cut cell, 16 cells per block; at most 8 blocks per SM, each
   // striding over the cut list
   const int64_t worst = (n + 15) / 16, cap = 8 * (int64_t)ws.grid;
   int nb = (int)(worst < cap ? worst : cap);
   return launch_pdl(P.fp64 ? k_cut_geometry<true> : k_cut_geometry<false>, dim3(nb), dim3(128), 0,
                     st, P, (const float*)ws.x, (const float*)ws.y, (const float*)ws.z,
-                    (const int*)ws.cut_pt, (const int*)ws.counters, ws.cut);
+                    (const int*)ws.cut_pt, (const int*)ws.counters, ws.cut,
+                    tiles ? ws.rec : nullptr, ws.rec_cut, (const int2*)ws.cut_rpos);
 }
 
 // blocks of the cut-row kernel (grid-stride over the cut cells), i.e. the
@@ -982,13 +1112,6 @@ cudaError_t launch_cut_residual(const ProbDev& P, int64_t n, float scale, bool w
                     ws.cut_loss_part);
 }
 
-cudaError_t launch_gather_tiles(const ProbDev& P, int64_t n, Workspace& ws, cudaStream_t st) {
-  const int64_t worst = 2 * n + 32;  // both lists padded
-  return launch_pdl(k_gather_tiles, dim3((unsigned)((worst + 255) / 256)), dim3(256), 0, st, P,
-                    ws.counters, ws.list_minus, ws.list_plus, ws.cut_pt, ws.x, ws.y, ws.z, ws.cut,
-                    ws.rec, ws.rec_cut, n);
-}
-
 cudaError_t launch_prep_weights(const ProbDev& P, const float* params, int prec, Workspace& ws,
                                 cudaStream_t st) {
   return launch_pdl(k_prep_weights, dim3(prep_weight_blocks(P)), dim3(256), 0, st, P, params, ws.wt,
@@ -1003,19 +1126,28 @@ cudaError_t launch_finish(const ProbDev& P, int64_t n, int grid, bool adam, bool
   const bool last = level == n_levels - 1;
   const float c1 = adam ? adam_correction(b1, adam_t) : 1.f;
   const float c2 = adam ? adam_correction(b2, adam_t) : 1.f;
-  int ncb = cut_residual_blocks(n, ws);
-  cudaError_t e = launch_pdl(k_loss, dim3(1), dim3(256), 0, st, ws.loss_part, grid,
-                             ws.cut_loss_part, ncb,
-                             loss_scale > 0.0 ? loss_scale : 1.0 / (double)n, ws.loss,
-                             adam ? ws.step : nullptr, loss_hist, hist_base, ws.status,
-                             ws.loss_acc, (int)(level > 0), (int)last);
-  if (e == cudaSuccess && (adam || want_grad)) {
-    const int nb_net = (int)((P.p_net + 127) / 128);
-    e = launch_pdl(k_reduce_adam, dim3(2 * nb_net), dim3(256), 0, st, P, grid, nb_net, ws.gpart,
-                   ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2, eps, c1, c2,
-                   ws.loss, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
-                   level > 0 ? ws.gacc : nullptr, last ? nullptr : ws.gacc);
-  }
+  LossOut lo;
+  lo.lp = ws.loss_part;
+  lo.nlp = grid;
+  lo.clp = ws.cut_loss_part;
+  lo.nclp = cut_residual_blocks(n, ws);
+  lo.scale = loss_scale > 0.0 ? loss_scale : 1.0 / (double)n;
+  lo.loss = ws.loss;
+  lo.step = adam ? ws.step : nullptr;
+  lo.loss_hist = loss_hist;
+  lo.hist_base = hist_base;
+  lo.status = ws.status;
+  lo.loss_acc = ws.loss_acc;
+  lo.acc_in = (int)(level > 0);
+  lo.last = (int)last;
+  if (!(adam || want_grad)) return launch_pdl(k_loss, dim3(1), dim3(256), 0, st, lo);
+  // the reduction kernel finishes the loss too
+  const int nb_net = (int)((P.p_net + 127) / 128);
+  cudaError_t e =
+      launch_pdl(k_reduce_adam, dim3(2 * nb_net), dim3(256), 0, st, P, grid, nb_net, ws.gpart,
+                 (const int*)ws.gpart_flag, grad_out, adam ? params : nullptr, m, v, lr, b1, b2,
+                 eps, c1, c2, lo, ws.wt, (prec == NBM_PREC_FP32) ? nullptr : ws.wtc, prec,
+                 (const float*)(level > 0 ? ws.gacc : nullptr), last ? nullptr : ws.gacc);
   return e;
 }
 
