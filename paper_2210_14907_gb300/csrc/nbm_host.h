@@ -52,7 +52,7 @@ struct CutRec {
   int has_jump;    // S > 0
 };
 
-// One collocation point of a tensor-core tile, gathered in list order (each list
+// One collocation point of a tensor-core tile, stored in list order (each list
 // padded to a multiple of 16) so that a half-tile's 8 records are one
 // contiguous 256-byte block.
 struct PRec {

@@ -2,14 +2,18 @@
 //   sample + classify  : Philox collocation points, cut/uncut decision of the
 //                        implicit cell from the level set at its 8 corners
 //   scan + scatter     : stable phase partition (two networks -> two lists;
-//                        cut cells go into both and into the cut list)
+//                        cut cells go into both and into the cut list) and
+//                        the tensor-core tile records of the uncut points
 //   cut geometry       : Kuhn-split volume / face / interface fractions and
 //                        the interface point of every cut cell (FP32 on
-//                        cell-local coordinates, FP64 in the FP64-row mode)
+//                        cell-local coordinates, FP64 in the FP64-row mode),
+//                        and the cut cells' tile records
+//   gather             : the tile records in list order (large batches)
 //   cut residual       : balance + jump rows of cut cells (both networks)
 //   weight staging     : FP32 transposed and 16-bit tensor-core copies
 //   finish             : deterministic loss / gradient reduction (8 slice
-//                        groups per 32 parameters, fixed order) and Adam
+//                        groups per 32 parameters, fixed order) and Adam,
+//                        one launch
 #include <cmath>
 
 #include <cuda_bf16.h>
